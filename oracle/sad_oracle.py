@@ -1,0 +1,587 @@
+"""CPU oracle for Soft Anisotropic Diagrams (SAD).
+
+TEST INFRASTRUCTURE.  This is a plain, slow, obviously correct restatement of
+what the SAD hot path computes, written from the paper (arXiv 2604.21984).
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import it.  It shares no code,
+header, table or constant with the CUDA path and never imports it; the only
+module both sides use is the seeded input generator
+``paper_2604_21984_gb300.inputs``, which holds none of the method's arithmetic.
+
+Site parameters: ``float[11, N]`` planes (x, y, log_tau, r, cr, cg, cb, ux, uy,
+a, b), positions and radii in pixels, pixel (col, row) centred at
+(col + 0.5, row + 0.5).  Index maps: ``uint32[P, K]`` with sentinel 0xffffffff.
+
+Part 1 (fp64, the definitions):
+  metric            Sec. 4.1, metric G_i (+ log isotropic scale b; b = 0 is the paper)
+  logits            Sec. 4.1 score d_mix and Sec. 4.2 logit l_i = -tau_i d_mix
+  render            Sec. 4.2 softmax weights w_i and colour c(x)
+  exact_topk        Sec. 4.3: the set the propagation approximates (brute force)
+  render_backward   App. A.4 "Per-pixel gradients": adjoint of the blend
+  removal_delta     Sec. 4.5 removal delta
+  adam_step         Sec. 6.1 (Adam, clamps, re-normalised u)
+Part 2 (fp32, the top-K propagation as the kernel's precision decides it):
+  exp32             Cody-Waite reduced Taylor exponential (see its docstring)
+  prepare_fp32      per-site derived table ("pack", App. A.2)
+  score_fp32        l_i(x) in a fixed fp32 operation order
+  jump_step         Sec. 4.3 jump schedule s_t;  step_code: App. A.3 "Step encoding"
+  splitmix64 / inject_ids   App. A.3 seeded stochastic injection (counter-based)
+  topk_seed_fp32    App. A.3 "JFA prepass" seed pass
+  topk_pass_fp32    Sec. 4.3 update C_t = topK(C_{t-1} U P_t U G_t)
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+N_PARAMS = 11
+PX, PY, PLOGTAU, PR, PCR, PCG, PCB, PUX, PUY, PA, PB = range(N_PARAMS)
+INVALID = 0xFFFFFFFF
+
+
+# =============================================================================
+# Part 1: fp64 definitions
+# =============================================================================
+
+def scale_s(H: int, W: int) -> float:
+    """s = 1 / max(H, W) (Sec. 4.1, resolution-invariant score)."""
+    return 1.0 / max(H, W)
+
+
+def unit_direction(ux, uy):
+    """u = (ux, uy) / |(ux, uy)|; a zero vector reads as u = (1, 0)."""
+    ux = np.asarray(ux, dtype=np.float64)
+    uy = np.asarray(uy, dtype=np.float64)
+    nrm = np.hypot(ux, uy)
+    ok = nrm > 0
+    safe = np.where(ok, nrm, 1.0)
+    return np.where(ok, ux / safe, 1.0), np.where(ok, uy / safe, 0.0)
+
+
+def metric(params):
+    """Per-site SPD metric G = e^b (e^a u u^T + e^-a v v^T), v = u rotated by +90 deg.
+
+    Sec. 4.1 (metric G_i): eigenvalue e^a along u and e^-a along v, det = 1.
+    The factor e^b is the log isotropic scale read from the configs' "metric
+    scale" (b = 0 reproduces the paper exactly).  Returns (G00, G01, G11).
+    """
+    p = np.asarray(params, dtype=np.float64)
+    ux, uy = unit_direction(p[PUX], p[PUY])
+    vx, vy = -uy, ux
+    ea = np.exp(p[PB] + p[PA])
+    eb = np.exp(p[PB] - p[PA])
+    G00 = ea * ux * ux + eb * vx * vx
+    G01 = ea * ux * uy + eb * vx * vy
+    G11 = ea * uy * uy + eb * vy * vy
+    return G00, G01, G11
+
+
+def active_mask(params):
+    """Inactive sentinel: x < 0 (App. A.2 "Site buffer")."""
+    return np.asarray(params, dtype=np.float64)[PX] >= 0
+
+
+def pixel_centres(H: int, W: int):
+    """Centres (col + 0.5, row + 0.5) of all pixels in row-major order."""
+    row, col = np.divmod(np.arange(H * W), W)
+    return col + 0.5, row + 0.5
+
+
+def logits(params, H, W, ids, px, py):
+    """l_i(x) = -tau_i * d_mix(x, i) for every (query point, listed id).
+
+    Sec. 4.1: d_mix = |x - p_i|_{G_i} s - r_i s with |v|_G = sqrt(v^T G v);
+    Sec. 4.2: l_i(x) = -tau_i d_mix(x, i), tau_i = exp(log_tau_i).
+    ``ids`` is int64[Q, M] of valid site ids, px/py are float[Q].
+    """
+    p = np.asarray(params, dtype=np.float64)
+    G00, G01, G11 = metric(p)
+    s = scale_s(H, W)
+    dx = np.asarray(px, np.float64)[:, None] - p[PX][ids]
+    dy = np.asarray(py, np.float64)[:, None] - p[PY][ids]
+    quad = G00[ids] * dx * dx + 2.0 * G01[ids] * dx * dy + G11[ids] * dy * dy
+    norm = np.sqrt(np.maximum(quad, 0.0))
+    d_mix = norm * s - p[PR][ids] * s
+    return -np.exp(p[PLOGTAU][ids]) * d_mix
+
+
+def _valid_entries(params, ids):
+    """Mask of list entries that name an existing, active site."""
+    ids = np.asarray(ids)
+    n = np.asarray(params).shape[1]
+    valid = (ids != INVALID) & (ids.astype(np.int64) < n)
+    safe = np.where(valid, ids, 0).astype(np.int64)
+    valid &= active_mask(params)[safe]
+    return valid, safe
+
+
+def weights(params, H, W, ids, px=None, py=None):
+    """Softmax weights w_i(x) over the listed set C(x) (Sec. 4.2).
+
+    Invalid or inactive entries get weight 0; a pixel with no valid entry gets
+    all-zero weights.  Returns (w[Q,K], logits[Q,K] with -inf at invalid,
+    valid mask, safe ids).
+    """
+    if px is None:
+        px, py = pixel_centres(H, W)
+    valid, safe = _valid_entries(params, ids)
+    ell = np.where(valid, logits(params, H, W, safe, px, py), -np.inf)
+    any_valid = valid.any(axis=1)
+    m = np.where(any_valid, np.max(np.where(valid, ell, -np.inf), axis=1), 0.0)
+    e = np.where(valid, np.exp(ell - m[:, None]), 0.0)
+    z = e.sum(axis=1)
+    w = e / np.where(z > 0, z, 1.0)[:, None]
+    return w, ell, valid, safe
+
+
+def render(params, H, W, ids, px=None, py=None):
+    """c(x) = sum_{i in C(x)} w_i(x) c_i (Sec. 4.2).  Returns float64[Q, 3]."""
+    p = np.asarray(params, dtype=np.float64)
+    w, _, _, safe = weights(p, H, W, ids, px, py)
+    col = np.stack([p[PCR], p[PCG], p[PCB]], axis=1)   # [N, 3]
+    return np.einsum("qk,qkc->qc", w, col[safe])
+
+
+def exact_topk(params, H, W, K, pixels=None, chunk=4096):
+    """Exact top-K ids under l_i(x) over ALL active sites (brute force).
+
+    This is the set the propagation of Sec. 4.3 approximates.  Order: l
+    descending, ties to the smaller id; fewer than K active sites leaves
+    trailing sentinels.  Returns (uint32[Q, K], float64 logits[Q, K]).
+    """
+    p = np.asarray(params, dtype=np.float64)
+    act = np.nonzero(active_mask(p))[0]
+    if pixels is None:
+        pixels = np.arange(H * W)
+    pixels = np.asarray(pixels)
+    out = np.full((len(pixels), K), INVALID, dtype=np.uint32)
+    out_l = np.full((len(pixels), K), -np.inf)
+    kk = min(K, len(act))
+    if kk == 0:
+        return out, out_l
+    for c0 in range(0, len(pixels), chunk):
+        pix = pixels[c0:c0 + chunk]
+        row, col = np.divmod(pix, W)
+        ids = np.broadcast_to(act, (len(pix), len(act)))
+        ell = logits(p, H, W, ids, col + 0.5, row + 0.5)
+        sel = select_topk(ids, ell, np.ones(ell.shape, bool), kk)
+        out[c0:c0 + len(pix), :kk] = sel
+        pos = np.searchsorted(act, sel.astype(np.int64))
+        out_l[c0:c0 + len(pix), :kk] = np.take_along_axis(ell, pos, axis=1)
+    return out, out_l
+
+
+def select_topk(pool_ids, ell, valid, K):
+    """Per row: drop invalid entries, collapse duplicate ids, keep the K best
+    by (l descending, id ascending), pad with the sentinel.
+
+    A duplicate id in one row carries the same logit, so after sorting rows by
+    (row, -l, id) duplicates are adjacent.  Returns uint32[Q, K].
+    """
+    pool_ids = np.asarray(pool_ids)
+    Q, M = pool_ids.shape
+    rows = np.repeat(np.arange(Q), M)[valid.ravel()]
+    ids = pool_ids.ravel()[valid.ravel()].astype(np.int64)
+    neg = -np.asarray(ell).ravel()[valid.ravel()]
+    order = np.lexsort((ids, neg, rows))
+    rows, ids = rows[order], ids[order]
+    keep = np.ones(len(rows), dtype=bool)
+    keep[1:] = ~((rows[1:] == rows[:-1]) & (ids[1:] == ids[:-1]))
+    rows, ids = rows[keep], ids[keep]
+    rank = np.arange(len(rows)) - np.searchsorted(rows, rows, side="left")
+    take = rank < K
+    out = np.full((Q, K), INVALID, dtype=np.uint32)
+    out[rows[take], rank[take]] = ids[take]
+    return out
+
+
+def render_backward(params, H, W, ids, grad_rgb, px=None, py=None):
+    """Adjoint of the blend into every site parameter (App. A.4), fp64.
+
+    Given g(x) = dL/dc(x) (``grad_rgb`` [Q, 3]) and a frozen index set C(x),
+    returns dL/dparams as float64[11, N] in plane order.  Per pixel, with the
+    max-subtracted softmax w and blended colour cbar:
+      dL/dc_k      = w_k g
+      dL/dl_k      = delta_k = w_k g . (c_k - cbar)
+      dl/dlog_tau  = l_k                 dl/dr = tau s
+      Delta = x - p, alpha = u.Delta, beta = v.Delta,
+      q = e^b (e^a alpha^2 + e^-a beta^2), n = sqrt(q), dl/dn = -tau s
+      dn/dp = -G Delta / n
+      dn/da = e^b (e^a alpha^2 - e^-a beta^2) / (2n),   dn/db = n / 2
+      dn/dtheta = e^b alpha beta (e^a - e^-a) / n,  theta = atan2(uy, ux),
+      dtheta/d(ux, uy) = (-uy, ux) / (ux^2 + uy^2).
+    At n = 0 (query exactly on a site) the geometric terms (p, a, b, u) are
+    taken as 0; invalid/inactive entries contribute nothing.
+    """
+    p = np.asarray(params, dtype=np.float64)
+    N = p.shape[1]
+    if px is None:
+        px, py = pixel_centres(H, W)
+    px = np.asarray(px, np.float64)
+    py = np.asarray(py, np.float64)
+    g = np.asarray(grad_rgb, dtype=np.float64).reshape(-1, 3)
+    w, ell, valid, sid = weights(p, H, W, ids, px, py)
+    col = np.stack([p[PCR], p[PCG], p[PCB]], axis=1)
+    ck = col[sid]                                        # [Q, K, 3]
+    cbar = np.einsum("qk,qkc->qc", w, ck)
+    delta = w * np.einsum("qc,qkc->qk", g, ck - cbar[:, None, :])
+
+    s = scale_s(H, W)
+    tau = np.exp(p[PLOGTAU])[sid]
+    a, b = p[PA][sid], p[PB][sid]
+    ux, uy = unit_direction(p[PUX], p[PUY])
+    ux, uy = ux[sid], uy[sid]
+    vx, vy = -uy, ux
+    dx = px[:, None] - p[PX][sid]
+    dy = py[:, None] - p[PY][sid]
+    alpha = ux * dx + uy * dy
+    beta = vx * dx + vy * dy
+    ea, em, eb = np.exp(a), np.exp(-a), np.exp(b)
+    q = eb * (ea * alpha ** 2 + em * beta ** 2)
+    n = np.sqrt(q)
+    has_n = valid & (n > 0)
+    inv_n = np.where(has_n, 1.0 / np.where(has_n, n, 1.0), 0.0)
+    dl_dn = -tau * s
+    G00, G01, G11 = metric(p)
+    GDx = G00[sid] * dx + G01[sid] * dy
+    GDy = G01[sid] * dx + G11[sid] * dy
+    dn_dpx = -GDx * inv_n
+    dn_dpy = -GDy * inv_n
+    dn_da = eb * (ea * alpha ** 2 - em * beta ** 2) * 0.5 * inv_n
+    dn_db = 0.5 * n * has_n
+    dn_dth = eb * alpha * beta * (ea - em) * inv_n
+    rawx, rawy = p[PUX][sid], p[PUY][sid]
+    r2 = rawx ** 2 + rawy ** 2
+    r2 = np.where(r2 > 0, r2, 1.0)
+    dth_dux, dth_duy = -rawy / r2, rawx / r2
+
+    dv = np.where(valid, delta, 0.0)
+    contrib = np.zeros((N_PARAMS,) + sid.shape)
+    contrib[PX] = dv * dl_dn * dn_dpx
+    contrib[PY] = dv * dl_dn * dn_dpy
+    contrib[PLOGTAU] = dv * np.where(valid, ell, 0.0)
+    contrib[PR] = dv * tau * s
+    for c, plane in enumerate((PCR, PCG, PCB)):
+        contrib[plane] = np.where(valid, w * g[:, c:c + 1], 0.0)
+    contrib[PUX] = dv * dl_dn * dn_dth * dth_dux
+    contrib[PUY] = dv * dl_dn * dn_dth * dth_duy
+    contrib[PA] = dv * dl_dn * dn_da
+    contrib[PB] = dv * dl_dn * dn_db
+
+    grads = np.zeros((N_PARAMS, N))
+    flat_ids = np.where(valid, sid, 0).ravel()
+    for j in range(N_PARAMS):
+        np.add.at(grads[j], flat_ids, np.where(valid, contrib[j], 0.0).ravel())
+    return grads
+
+
+def mse_loss_and_grad_rgb(rgb, target):
+    """L = E_x |c(x) - I(x)|^2 (Sec. 6.1) and g = dL/dc = 2 (c - I) / P."""
+    c = np.asarray(rgb, np.float64).reshape(-1, 3)
+    t = np.asarray(target, np.float64).reshape(-1, 3)
+    P = c.shape[0]
+    diff = c - t
+    return float((diff ** 2).sum() / P), 2.0 * diff / P
+
+
+def removal_delta(params, H, W, ids, target):
+    """Per-site removal delta summed over pixels (Sec. 4.5, removal delta).
+
+    For each listed site k at pixel x with weight w_k: c' = (c - w_k c_k) /
+    (1 - w_k) and dL(x) = |c' - I|^2 - |c - I|^2, summed per site.  A site
+    that is the only valid entry of a pixel (w_k = 1) adds |I|^2 there, the
+    loss of rendering nothing.  Returns float64[N].
+    """
+    p = np.asarray(params, dtype=np.float64)
+    w, _, valid, sid = weights(p, H, W, ids)
+    col = np.stack([p[PCR], p[PCG], p[PCB]], axis=1)
+    ck = col[sid]
+    c = np.einsum("qk,qkc->qc", w, ck)
+    I = np.asarray(target, np.float64).reshape(-1, 3)
+    base = ((c - I) ** 2).sum(1)
+    out = np.zeros(p.shape[1])
+    for k in range(ids.shape[1]):
+        wk = w[:, k]
+        alone = wk >= 1.0
+        denom = np.where(alone, 1.0, 1.0 - wk)
+        cprime = (c - wk[:, None] * ck[:, k]) / denom[:, None]
+        dl = np.where(alone, (I ** 2).sum(1), ((cprime - I) ** 2).sum(1)) - base
+        np.add.at(out, sid[valid[:, k], k], dl[valid[:, k]])
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Adam (Sec. 6.1): per-parameter learning rates, fixed betas / eps, clamps,
+# re-normalised direction.  Positions and radii step in normalised units p*s.
+# ---------------------------------------------------------------------------
+
+DEFAULT_LR = {
+    "x": 1e-3, "y": 1e-3, "log_tau": 1e-2, "r": 1e-3, "cr": 5e-3, "cg": 5e-3,
+    "cb": 5e-3, "ux": 1e-2, "uy": 1e-2, "a": 1e-2, "b": 0.0,
+}
+PLANE_NAMES = ("x", "y", "log_tau", "r", "cr", "cg", "cb", "ux", "uy", "a", "b")
+
+
+def adam_step(params, grads, m, v, t, H, W, lr=None, beta1=0.9, beta2=0.999,
+              eps=1e-8, log_tau_range=(2.0, 20.0), r_range=(1.0, 512.0),
+              a_range=(-2.0, 2.0), b_range=(-8.0, 8.0)):
+    """One bias-corrected Adam step (Kingma & Ba 2015) with the paper's clamps.
+
+    Sec. 6.1: positions clamped to the image, log_tau in [2, 20], r in [1, 512],
+    a in [-2, 2], colours in [0, 1], u re-normalised after the step.  x, y and
+    r are optimised in normalised units (value * s), so their gradient is
+    divided by s and their step multiplied by 1/s.  Inactive sites (x < 0) are
+    left untouched.  ``t`` is the 1-based step count.  Returns new
+    (params, m, v) as float64.
+    """
+    lr = dict(DEFAULT_LR if lr is None else lr)
+    p = np.array(params, dtype=np.float64)
+    g = np.asarray(grads, dtype=np.float64)
+    m = np.array(m, dtype=np.float64)
+    v = np.array(v, dtype=np.float64)
+    s = scale_s(H, W)
+    act = p[PX] >= 0
+    for j, name in enumerate(PLANE_NAMES):
+        unit = s if j in (PX, PY, PR) else 1.0
+        gj = g[j] / unit
+        mj = beta1 * m[j] + (1 - beta1) * gj
+        vj = beta2 * v[j] + (1 - beta2) * gj * gj
+        mhat = mj / (1 - beta1 ** t)
+        vhat = vj / (1 - beta2 ** t)
+        step = lr[name] * mhat / (np.sqrt(vhat) + eps) / unit
+        p[j] = np.where(act, p[j] - step, p[j])
+        m[j] = np.where(act, mj, m[j])
+        v[j] = np.where(act, vj, v[j])
+    clip = lambda j, lo, hi: np.where(act, np.clip(p[j], lo, hi), p[j])
+    p[PX] = clip(PX, 0.0, float(W))
+    p[PY] = clip(PY, 0.0, float(H))
+    p[PLOGTAU] = clip(PLOGTAU, *log_tau_range)
+    p[PR] = clip(PR, *r_range)
+    p[PA] = clip(PA, *a_range)
+    p[PB] = clip(PB, *b_range)
+    for j in (PCR, PCG, PCB):
+        p[j] = clip(j, 0.0, 1.0)
+    ux, uy = unit_direction(p[PUX], p[PUY])
+    p[PUX] = np.where(act, ux, p[PUX])
+    p[PUY] = np.where(act, uy, p[PUY])
+    return p, m, v
+
+
+# =============================================================================
+# Part 2: the fp32 top-K propagation, decided in the kernel's precision
+# =============================================================================
+
+F32 = np.float32
+# 1/k! for k = 2..7, each the float32 nearest to the exact rational (hex).
+_INV_FACT = [F32(float.fromhex(h)) for h in (
+    "0x1.000000p-1",   # 1/2
+    "0x1.555556p-3",   # 1/6
+    "0x1.555556p-5",   # 1/24
+    "0x1.111112p-7",   # 1/120
+    "0x1.6c16c2p-10",  # 1/720
+    "0x1.a01a02p-13",  # 1/5040
+)]
+_LOG2E = F32(float.fromhex("0x1.715476p+0"))     # 1/ln 2, nearest float32
+_LN2_HI = F32(45426.0 / 65536.0)                  # ln 2 cut to 16 bits: k*LN2_HI exact
+_LN2_LO = F32(math.log(2.0) - 45426.0 / 65536.0)  # remainder of ln 2
+
+
+def exp32(x):
+    """Reproducible float32 e^x (every step a rounded fp32 + or *).
+
+    Published method: Cody & Waite (1980) argument reduction with ln 2 split
+    into a 16-bit head and a tail, x = k ln2 + r, |r| <= ln2/2, then the
+    degree-7 Taylor polynomial of e^r (coefficients 1/k!) by Horner's rule,
+    then scaling by 2^k.  Inputs are clamped to [-80, 80] so 2^k and the
+    result stay normal.  Accuracy: a few ulp (pinned in the tests).  The same
+    definition is implemented independently on the GPU so that the derived
+    site table, and hence the top-K decisions, agree bit for bit.
+    """
+    x = np.clip(np.asarray(x, dtype=F32), F32(-80.0), F32(80.0)).astype(F32)
+    k = np.rint((x * _LOG2E).astype(F32)).astype(F32)
+    r = (x - (k * _LN2_HI).astype(F32)).astype(F32)
+    r = (r - (k * _LN2_LO).astype(F32)).astype(F32)
+    p = _INV_FACT[5]
+    for c in (_INV_FACT[4], _INV_FACT[3], _INV_FACT[2], _INV_FACT[1], _INV_FACT[0], F32(1.0), F32(1.0)):
+        p = ((p * r).astype(F32) + c).astype(F32)
+    scale = np.ldexp(np.ones_like(k, dtype=F32), k.astype(np.int32)).astype(F32)
+    return (p * scale).astype(F32)
+
+
+def prepare_fp32(params, H, W):
+    """Per-site derived table for scoring (App. A.2 packed candidate sites).
+
+    In float32, operation by operation:
+      s = 1 / max(H, W);  nrm = sqrt(ux*ux + uy*uy);  u = (ux, uy)/nrm (or (1,0))
+      e+ = exp32(b + a);  e- = exp32(b - a)
+      G00 = e+ (ux ux) + e- (uy uy);  G01 = (e+ - e-)(ux uy);  G11 = e+ (uy uy) + e- (ux ux)
+      tau_s = exp32(log_tau) * s;   active = x >= 0
+    Returns dict of float32 arrays x, y, ts, r, G00, G01, G11, active(bool),
+    cr, cg, cb.
+    """
+    p = np.asarray(params, dtype=F32)
+    s = F32(F32(1.0) / F32(max(H, W)))
+    ux, uy = p[PUX], p[PUY]
+    nrm = np.sqrt(((ux * ux).astype(F32) + (uy * uy).astype(F32)).astype(F32)).astype(F32)
+    ok = nrm > F32(0)
+    safe = np.where(ok, nrm, F32(1)).astype(F32)
+    uxn = np.where(ok, (ux / safe).astype(F32), F32(1)).astype(F32)
+    uyn = np.where(ok, (uy / safe).astype(F32), F32(0)).astype(F32)
+    ep = exp32((p[PB] + p[PA]).astype(F32))
+    em = exp32((p[PB] - p[PA]).astype(F32))
+    xx = (uxn * uxn).astype(F32)
+    yy = (uyn * uyn).astype(F32)
+    xy = (uxn * uyn).astype(F32)
+    G00 = ((ep * xx).astype(F32) + (em * yy).astype(F32)).astype(F32)
+    G01 = ((ep - em).astype(F32) * xy).astype(F32)
+    G11 = ((ep * yy).astype(F32) + (em * xx).astype(F32)).astype(F32)
+    ts = (exp32(p[PLOGTAU]) * s).astype(F32)
+    return {
+        "x": p[PX].copy(), "y": p[PY].copy(), "ts": ts, "r": p[PR].copy(),
+        "G00": G00, "G01": G01, "G11": G11, "active": p[PX] >= F32(0),
+        "cr": p[PCR].copy(), "cg": p[PCG].copy(), "cb": p[PCB].copy(),
+    }
+
+
+def score_fp32(prep, ids, px, py):
+    """l_i(x) in float32, fixed order, no fused multiply-add:
+
+    dx = px - x; dy = py - y; t0 = (G00 dx) dx; t1 = (G01 dx) dy; t1 = t1 + t1;
+    t2 = (G11 dy) dy; q = (t0 + t1) + t2; n = sqrt(max(q, 0)); l = ts (r - n).
+    (l = -tau d_mix = tau s (r - |x - p|_G), Sec. 4.1-4.2.)  ``ids`` int64
+    array of valid ids; px, py broadcastable float32.
+    """
+    px = np.asarray(px, F32)
+    py = np.asarray(py, F32)
+    dx = (px - prep["x"][ids]).astype(F32)
+    dy = (py - prep["y"][ids]).astype(F32)
+    t0 = ((prep["G00"][ids] * dx).astype(F32) * dx).astype(F32)
+    t1 = ((prep["G01"][ids] * dx).astype(F32) * dy).astype(F32)
+    t1 = (t1 + t1).astype(F32)
+    t2 = ((prep["G11"][ids] * dy).astype(F32) * dy).astype(F32)
+    q = ((t0 + t1).astype(F32) + t2).astype(F32)
+    n = np.sqrt(np.fmax(q, F32(0))).astype(F32)
+    return (prep["ts"][ids] * (prep["r"][ids] - n).astype(F32)).astype(F32)
+
+
+def jump_step(t: int, H: int, W: int) -> int:
+    """s_t = max(1, B / 2^(min(t, log2 B - 1) + 1)), B = 2^ceil(log2 max(H, W)) (Sec. 4.3)."""
+    L = max(H, W)
+    log2B = max(0, math.ceil(math.log2(L))) if L > 1 else 0
+    B = 1 << log2B
+    return max(1, B >> (min(t, log2B - 1) + 1)) if log2B > 0 else 1
+
+
+def step_code(t: int, H: int, W: int) -> int:
+    """32-bit step parameter: low 16 bits step index, high 16 bits jump (App. A.3)."""
+    return ((jump_step(t, H, W) & 0xFFFF) << 16) | (t & 0xFFFF)
+
+
+_M64 = (1 << 64) - 1
+
+
+def splitmix64(seed: int, counter):
+    """Output number counter+1 of SplitMix64 started at ``seed``.
+
+    Steele, Lea & Flood (2014): state_n = seed + n * 0x9E3779B97F4A7C15, and
+    the output function z ^= z >> 30; z *= 0xBF58476D1CE4E5B9; z ^= z >> 27;
+    z *= 0x94D049BB133111EB; z ^= z >> 31.  Vectorised over ``counter``.
+    """
+    c = np.asarray(counter, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & _M64) + (c + np.uint64(1)) * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def inject_ids(seed: int, code: int, pixels, J: int, capacity: int):
+    """The J injected candidate ids of each pixel for one pass (App. A.3).
+
+    Counter = (step_code << 32) | (pixel * J + j), draw = SplitMix64 output,
+    id = (draw_hi32 * capacity) >> 32 (Lemire's multiply-shift range map).
+    Returns int64[len(pixels), J].
+    """
+    pix = np.asarray(pixels, dtype=np.uint64)
+    j = np.arange(J, dtype=np.uint64)
+    ctr = (np.uint64(code) << np.uint64(32)) | (pix[:, None] * np.uint64(J) + j[None, :])
+    h = splitmix64(seed, ctr)
+    hi = h >> np.uint64(32)
+    with np.errstate(over="ignore"):
+        ids = (hi * np.uint64(capacity)) >> np.uint64(32)
+    return ids.astype(np.int64)
+
+
+def topk_seed_fp32(prep, H, W, K):
+    """Seed pass of the JFA prepass (App. A.3): every active site writes its id
+    into slot 0 of the pixel that contains it; on a collision the smaller id
+    wins.  All other entries are the sentinel.  Returns uint32[P, K]."""
+    out = np.full((H * W, K), INVALID, dtype=np.uint32)
+    for i in np.nonzero(prep["active"])[0]:
+        col = min(max(int(math.floor(float(prep["x"][i]))), 0), W - 1)
+        row = min(max(int(math.floor(float(prep["y"][i]))), 0), H - 1)
+        pix = row * W + col
+        out[pix, 0] = min(int(out[pix, 0]), int(i))
+    return out
+
+
+def topk_pass_fp32(prep, ids_in, H, W, K, code, J, seed, pixels=None):
+    """One propagation pass (Sec. 4.3, update of C_t), for all or some pixels.
+
+    Pool = C_{t-1}(x) (the pixel's own list) U P_t(x) (the lists of the four
+    neighbours at (+-s, 0), (0, +-s), s = jump distance in ``code``; neighbours
+    outside the image are skipped) U G_t(x) (J injected ids).  Entries that are
+    the sentinel, out of range, inactive or score NaN are dropped; duplicates
+    collapse; the K best by (l descending, id ascending) are kept, the rest of
+    the list is the sentinel.  Reads ``ids_in`` only (Jacobi update).
+    Returns uint32[len(pixels), K].
+    """
+    cap = len(prep["x"])
+    if pixels is None:
+        pixels = np.arange(H * W)
+    pixels = np.asarray(pixels, dtype=np.int64)
+    s = (code >> 16) & 0xFFFF
+    row, col = np.divmod(pixels, W)
+    pools = [ids_in[pixels].astype(np.int64)]
+    for ddx, ddy in ((-s, 0), (s, 0), (0, -s), (0, s)):
+        nc, nr = col + ddx, row + ddy
+        inside = (nc >= 0) & (nc < W) & (nr >= 0) & (nr < H)
+        nb = np.where(inside, nr * W + nc, 0)
+        lst = ids_in[nb].astype(np.int64)
+        pools.append(np.where(inside[:, None], lst, INVALID))
+    if J > 0:
+        pools.append(inject_ids(seed, code, pixels, J, cap))
+    pool = np.concatenate(pools, axis=1)                  # [Q, M]
+    valid = (pool != INVALID) & (pool >= 0) & (pool < cap)
+    safe = np.where(valid, pool, 0)
+    valid &= prep["active"][safe]
+    px = (col.astype(F32) + F32(0.5)).astype(F32)[:, None]
+    py = (row.astype(F32) + F32(0.5)).astype(F32)[:, None]
+    ell = score_fp32(prep, safe, px, py)
+    valid &= ~np.isnan(ell)
+    return select_topk(pool, ell, valid, K)
+
+
+def propagate_fp32(params, H, W, K, passes, J, seed, ids_in=None, t0=0):
+    """Seed (unless ``ids_in`` is given) then ``passes`` propagation passes
+    with the jump schedule starting at step index t0.  Returns uint32[P, K]."""
+    prep = prepare_fp32(params, H, W)
+    ids = topk_seed_fp32(prep, H, W, K) if ids_in is None else np.asarray(ids_in, np.uint32)
+    for t in range(t0, t0 + passes):
+        ids = topk_pass_fp32(prep, ids, H, W, K, step_code(t, H, W), J, seed)
+    return ids
+
+
+def topk_match_stats(approx, exact):
+    """Recall (fraction of exact top-K ids present) and exact-match fraction
+    (pixels whose K-sets agree), as used for Table "Top-K propagation
+    convergence" (Sec. 6.6)."""
+    rec, match = [], []
+    for a, e in zip(approx, exact):
+        ea = set(int(v) for v in e if v != INVALID)
+        aa = set(int(v) for v in a if v != INVALID)
+        rec.append(len(ea & aa) / max(len(ea), 1))
+        match.append(ea == aa)
+    return float(np.mean(rec)), float(np.mean(match))

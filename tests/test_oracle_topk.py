@@ -1,0 +1,196 @@
+"""Pins of the oracle's fp32 top-K propagation (Sec. 4.3, App. A.3).  CPU."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2604_21984_gb300 import inputs as gen
+
+INV = 0xFFFFFFFF
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_exp32_accuracy(oracle):
+    xs = np.linspace(-30, 30, 200001).astype(np.float32)
+    e = oracle.exp32(xs).astype(np.float64)
+    ref = np.exp(xs.astype(np.float64))
+    ulp = np.spacing(ref.astype(np.float32)).astype(np.float64)
+    assert np.max(np.abs(e - ref) / ulp) <= 2.0
+    assert oracle.exp32(np.float32(0.0)) == np.float32(1.0)
+    assert np.all(np.diff(e) >= 0)                     # monotone across reduction cuts
+    prod = e * oracle.exp32(-xs).astype(np.float64)    # e^x e^-x = 1
+    assert np.max(np.abs(prod - 1.0)) < 5e-7
+
+
+def test_splitmix64_published_vector(oracle):
+    vals = [int(l, 16) for l in open(os.path.join(GOLDEN, "splitmix64_seed0.txt"))
+            if l.strip() and not l.startswith("#")]
+    got = oracle.splitmix64(0, np.arange(3))
+    assert [int(v) for v in got] == vals
+
+
+def test_injected_ids_in_range_and_uniform(oracle):
+    cap = 37
+    ids = oracle.inject_ids(seed=123, code=oracle.step_code(3, 64, 64),
+                            pixels=np.arange(20000), J=4, capacity=cap)
+    assert ids.min() >= 0 and ids.max() < cap
+    counts = np.bincount(ids.ravel(), minlength=cap)
+    expect = ids.size / cap
+    chi2 = ((counts - expect) ** 2 / expect).sum()
+    assert chi2 < 80                                   # dof 36, p ~ 1e-5
+    # different step codes / seeds give different draws
+    other = oracle.inject_ids(seed=123, code=oracle.step_code(4, 64, 64),
+                              pixels=np.arange(20000), J=4, capacity=cap)
+    assert (other != ids).mean() > 0.9
+
+
+def test_jump_schedule(oracle):
+    assert [oracle.jump_step(t, 64, 64) for t in range(8)] == [32, 16, 8, 4, 2, 1, 1, 1]
+    assert [oracle.jump_step(t, 512, 768) for t in range(11)] == [512, 256, 128, 64, 32, 16, 8, 4, 2, 1, 1]
+    assert [oracle.jump_step(t, 100, 3) for t in range(8)] == [64, 32, 16, 8, 4, 2, 1, 1]
+    assert oracle.jump_step(0, 1, 1) == 1
+    c = oracle.step_code(2, 64, 64)
+    assert c & 0xFFFF == 2 and c >> 16 == 8
+
+
+def test_prepare_fp32_close_to_fp64_metric(oracle):
+    p = gen.sites_random_spd(64, 64, 500, seed=7)
+    prep = oracle.prepare_fp32(p, 64, 64)
+    G00, G01, G11 = oracle.metric(p)
+    for a, b in ((prep["G00"], G00), (prep["G01"], G01), (prep["G11"], G11)):
+        np.testing.assert_allclose(a, b, rtol=2e-6, atol=2e-6 * np.abs(b).max())
+    np.testing.assert_allclose(prep["ts"], np.exp(p[2].astype(np.float64)) / 64, rtol=1e-6)
+
+
+def test_seed_pass(oracle):
+    p = gen.sites_isotropic(gen.image_sinusoid_polygons(16, 16, 1), 40, seed=2, capacity=44)
+    p[0, 5], p[1, 5] = p[0, 3], p[1, 3]               # collision: smaller id wins
+    p[0, 7], p[1, 7] = 16.0, 16.0                     # on the far border: clamps into the image
+    prep = oracle.prepare_fp32(p, 16, 16)
+    m = oracle.topk_seed_fp32(prep, 16, 16, 4)
+    assert np.all(m[:, 1:] == INV)
+    cols = np.clip(np.floor(p[0, :40]).astype(int), 0, 15)
+    rows = np.clip(np.floor(p[1, :40]).astype(int), 0, 15)
+    for i in range(40):
+        assert m[rows[i] * 16 + cols[i], 0] <= i
+    assert m[rows[3] * 16 + cols[3], 0] == 3
+    assert m[15 * 16 + 15, 0] <= 7
+    assert len(set(m[:, 0][m[:, 0] != INV].tolist())) == (m[:, 0] != INV).sum()
+
+
+def _brute_force_pass(oracle, p, ids_in, H, W, K, t, J, seed, pixels):
+    """Per-pixel loops: gather the pool by explicit offsets, score in fp64."""
+    s = oracle.jump_step(t, H, W)
+    code = oracle.step_code(t, H, W)
+    cap = p.shape[1]
+    out = []
+    for pix in pixels:
+        row, col = divmod(int(pix), W)
+        pool = list(ids_in[pix])
+        for dc, dr in ((-s, 0), (s, 0), (0, -s), (0, s)):
+            c2, r2 = col + dc, row + dr
+            if 0 <= c2 < W and 0 <= r2 < H:
+                pool += list(ids_in[r2 * W + c2])
+        pool += list(oracle.inject_ids(seed, code, [pix], J, cap)[0])
+        cand = {int(i) for i in pool if int(i) != INV and int(i) < cap and p[0, int(i)] >= 0}
+        ids = np.array(sorted(cand), dtype=np.int64)
+        ell = oracle.logits(p, H, W, ids[None, :], [col + 0.5], [row + 0.5])[0] if len(ids) else np.array([])
+        order = sorted(range(len(ids)), key=lambda k: (-ell[k], ids[k]))[:K]
+        out.append(([int(ids[k]) for k in order], [float(ell[k]) for k in order],
+                    sorted(((float(l), int(i)) for l, i in zip(ell, ids)), reverse=True)))
+    return out
+
+
+@pytest.mark.parametrize("t", [0, 2, 5])
+def test_pass_matches_brute_force(oracle, t):
+    H, W, K, J = 24, 20, 6, 3
+    p = gen.sites_random_spd(H, W, 70, seed=60, capacity=80)
+    p = gen.deactivate_random(p, 0.1, seed=61)
+    ids_in = gen.knn_map(p, H, W, K, seed=62, truncate_frac=0.3, shuffle=True,
+                         include_inactive_frac=0.1)
+    ids_in[::7, 0] = 79                                # inactive / out-of-list entries
+    prep = oracle.prepare_fp32(p, H, W)
+    pixels = np.arange(H * W)
+    got = oracle.topk_pass_fp32(prep, ids_in, H, W, K, oracle.step_code(t, H, W), J, 99, pixels)
+    ref = _brute_force_pass(oracle, p.astype(np.float64), ids_in, H, W, K, t, J, 99, pixels)
+    mismatches = 0
+    for q, (ref_ids, ref_l, allpool) in enumerate(ref):
+        g = [int(v) for v in got[q] if v != INV]
+        if g == ref_ids:
+            continue
+        # only near-ties (fp32 vs fp64 ranking) may differ: rank by rank, the
+        # fp64 logits of both lists must agree to rounding
+        mismatches += 1
+        assert len(g) == len(ref_ids)
+        l64 = dict((j, l) for l, j in allpool)
+        for a, b in zip(g, ref_ids):
+            assert abs(l64[a] - l64[b]) <= 1e-6 * max(1.0, abs(l64[b]))
+    assert mismatches <= 2
+
+
+def test_pass_invariants(oracle):
+    H, W, K, J = 32, 32, 8, 2
+    img = gen.image_sinusoid_polygons(H, W, seed=70)
+    p = gen.sites_isotropic(img, 100, seed=71)
+    prep = oracle.prepare_fp32(p, H, W)
+    ids = oracle.topk_seed_fp32(prep, H, W, K)
+    for t in range(5):
+        code = oracle.step_code(t, H, W)
+        new = oracle.topk_pass_fp32(prep, ids, H, W, K, code, J, 5)
+        for q in range(0, H * W, 37):
+            lst = [int(v) for v in new[q] if v != INV]
+            assert len(lst) == len(set(lst))                       # distinct
+            assert all(v == INV for v in new[q][len(lst):])        # sentinel tail
+            row, col = divmod(q, W)
+            l = oracle.score_fp32(prep, np.array(lst, dtype=np.int64),
+                                  np.float32(col + 0.5), np.float32(row + 0.5))
+            keys = [(-float(a), b) for a, b in zip(l, lst)]
+            assert keys == sorted(keys)                            # (l desc, id asc)
+            # every kept entry beats every dropped pool entry
+            old = [int(v) for v in ids[q] if v != INV]
+            dropped = [i for i in old if i not in lst]
+            if dropped and len(lst) == K:
+                ld = oracle.score_fp32(prep, np.array(dropped, dtype=np.int64),
+                                       np.float32(col + 0.5), np.float32(row + 0.5))
+                assert max((-float(a), b) for a, b in zip(ld, dropped)) > keys[-1]
+        ids = new
+
+
+def test_few_sites_reach_exact_topk(oracle):
+    """With N <= K every pixel's exact top-K is the full active set; the seed
+    plus propagation plus injection must reach it."""
+    H, W, K, J = 32, 32, 8, 2
+    p = gen.sites_random_spd(H, W, 6, seed=80, capacity=8)
+    got = oracle.propagate_fp32(p, H, W, K, passes=12, J=J, seed=3)
+    assert all(sorted(int(v) for v in row if v != INV) == list(range(6)) for row in got)
+
+
+def test_convergence_like_paper_table(oracle):
+    """Scaled-down rerun of Sec. 6.6's experiment: sites in unique pixel cells
+    with sub-pixel offsets, K=8, J=4; exact-match rises with passes and is high
+    at low density (paper: 0.96-0.99 at 16k sites on 1024^2 / 2048^2)."""
+    table = [l.split() for l in open(os.path.join(GOLDEN, "topk_convergence_table.txt"))
+             if l.strip() and not l.startswith("#")]
+    low_density = [float(r[4]) for r in table if int(r[1]) == 16384]
+    H = W = 128
+    n = 256                                            # 1/64 px density, as 16k on 1024^2
+    g = np.random.default_rng(90)
+    cells = g.choice(H * W, n, replace=False)
+    p = np.zeros((11, n), np.float32)
+    p[1], p[0] = np.divmod(cells, W)
+    p[0] += g.uniform(0.05, 0.95, n)
+    p[1] += g.uniform(0.05, 0.95, n)
+    p[2] = 0.0
+    p[7] = 1.0
+    sample = g.choice(H * W, 256, replace=False)
+    ex, _ = oracle.exact_topk(p, H, W, 8, sample)
+    prep = oracle.prepare_fp32(p, H, W)
+    ids = oracle.topk_seed_fp32(prep, H, W, 8)
+    em = {}
+    for t in range(16):
+        ids = oracle.topk_pass_fp32(prep, ids, H, W, 8, oracle.step_code(t, H, W), 4, 7)
+        if t + 1 in (8, 16):
+            em[t + 1] = oracle.topk_match_stats(ids[sample], ex)[1]
+    assert em[16] >= em[8] - 0.02
+    assert em[16] >= min(low_density) - 0.08
