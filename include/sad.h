@@ -1,0 +1,200 @@
+/*
+ * sad.h -- C-ABI of libsad.so, the GB300 (sm_103a) hot path of Soft
+ * Anisotropic Diagrams (SAD, arXiv 2604.21984).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ *  - All array arguments are DEVICE pointers unless stated otherwise; the
+ *    caller allocates and owns them (including workspaces).  The library never
+ *    allocates device memory, never frees caller memory and does not keep any
+ *    pointer after the call returns.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls are asynchronous on that stream unless stated otherwise.
+ *  - Return value: a sad_status code (int).  Argument errors are detected on
+ *    the host before any launch and return SAD_EINVAL; a failed launch returns
+ *    SAD_ECUDA.  sad_last_error() gives a thread-local message for the last
+ *    failure on the calling thread.
+ *  - Site parameters are float32[11][capacity] planes in the order
+ *      0 x  1 y  2 log_tau  3 r  4 cr  5 cg  6 cb  7 ux  8 uy  9 a  10 b
+ *    (Sec. 4.1 "Site Representation": position, temperature, additive radius,
+ *    colour, anisotropy direction u (stored unnormalised), log-anisotropy a;
+ *    b is a per-site log isotropic metric scale, b = 0 being the paper's
+ *    unit-determinant metric).  Positions and radii are in pixels; pixel
+ *    (col,row) has its centre at (col+0.5, row+0.5).  A site with x < 0 is
+ *    inactive (App. A.2 "Site buffer") and is skipped by every kernel.
+ *  - The top-K map is K/4 planes of uint32x4 (App. A.2 "Top-K candidate
+ *    list"): plane j holds, for every pixel in row-major order, the ids of
+ *    list positions 4j..4j+3, i.e. uint32[K/4][H*W][4].  Sentinel 0xffffffff.
+ *    K must be 4, 8 or 16.  Lists are ordered by logit descending, ties by
+ *    smaller id (for maps produced by sad_update_topk).
+ *  - The prepared site table (the "pack" of App. A.2) is float32[3][capacity][4]:
+ *      plane 0 {x, y, tau*s, r}, plane 1 {G00, G01, G11, active},
+ *      plane 2 {cr, cg, cb, 0},  with s = 1/max(H,W) (Sec. 4.1).
+ *    Every device pointer must be 16-byte aligned.
+ */
+#ifndef SAD_H
+#define SAD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  SAD_OK = 0,
+  SAD_EINVAL = 1,     /* bad argument (size, alignment, null pointer, K) */
+  SAD_ECUDA = 2,      /* a CUDA launch or copy failed */
+  SAD_EWORKSPACE = 3, /* workspace too small (detected on the host) */
+  SAD_ETIMEOUT = 4,   /* reserved: a bounded device wait gave up */
+  SAD_EINTERNAL = 5
+};
+
+#define SAD_NPARAMS 11
+#define SAD_INVALID_ID 0xffffffffu
+
+/* Static string for a status code; never freed. */
+const char* sad_status_string(int status);
+/* Thread-local detail message of the last failing call on this thread. */
+const char* sad_last_error(void);
+/* ABI version of this header (bumped on any signature change). */
+int sad_abi_version(void);
+
+/*
+ * sad_prepare_sites -- per-site derived table ("pack", App. A.2; metric G of
+ * Sec. 4.1).  For every site i < capacity, in float32 with each operation
+ * separately rounded (no fused multiply-add):
+ *   s = 1/max(H,W); u = (ux,uy)/|(ux,uy)| (or (1,0) if zero);
+ *   e+ = exp(b+a), e- = exp(b-a) with a reproducible exponential (Cody-Waite
+ *   reduction + degree-7 Taylor polynomial); G00 = e+ ux^2 + e- uy^2,
+ *   G01 = (e+ - e-) ux uy, G11 = e+ uy^2 + e- ux^2; tau*s = exp(log_tau) s;
+ *   active = (x >= 0).
+ * params: float32[11][capacity] (read).  prep: float32[3][capacity][4] (written).
+ */
+int sad_prepare_sites(const float* params, int32_t capacity, int32_t H, int32_t W,
+                      float* prep, void* stream);
+
+/*
+ * sad_topk_seed -- seed pass of the JFA prepass (App. A.3 "JFA prepass").
+ * Fills the whole map with the sentinel, then every active site writes its id
+ * into list position 0 of the pixel that contains it (floor of its position,
+ * clamped to the image); on collisions the smallest id wins (deterministic).
+ * map: uint32[K/4][H*W][4] (written).
+ */
+int sad_topk_seed(const float* prep, int32_t capacity, int32_t H, int32_t W, int32_t K,
+                  uint32_t* map, void* stream);
+
+/*
+ * sad_update_topk -- one propagation pass of the per-pixel top-K field
+ * (Sec. 4.3, update C_t = topK over C_{t-1} U P_t U G_t).  Pool of pixel x:
+ * its own list in map_in, the lists of the 4 neighbours at (+-s,0), (0,+-s)
+ * (s = step_code >> 16; neighbours outside the image are skipped), and
+ * n_inject ids drawn from SplitMix64 (Steele et al. 2014) at counter
+ * ((step_code << 32) | (pixel*n_inject + j)) with `seed`, mapped to
+ * [0,capacity) by (hi32 * capacity) >> 32.  Invalid, inactive and NaN-scored
+ * candidates are dropped, duplicates collapse, and the K best by
+ * (logit descending, id ascending) are written to map_out (sentinel tail).
+ * Logits are computed in float32 without contraction:
+ *   dx = px-x, dy = py-y, q = ((G00 dx)dx + 2((G01 dx)dy)) + (G11 dy)dy,
+ *   n = sqrt(max(q,0)), l = (tau s)(r - n).
+ * step_code: low 16 bits = pass index, high 16 bits = jump (App. A.3 "Step
+ * encoding").  map_in and map_out must not overlap (Jacobi update).
+ * Requires H*W*n_inject < 2^32 and 0 <= n_inject <= 16.
+ */
+int sad_update_topk(const float* prep, int32_t capacity, int32_t H, int32_t W, int32_t K,
+                    const uint32_t* map_in, uint32_t* map_out, uint32_t step_code,
+                    int32_t n_inject, uint64_t seed, void* stream);
+
+/*
+ * sad_render -- soft anisotropic additively weighted render (Sec. 4.2):
+ * c(x) = sum_i w_i(x) c_i, w = softmax over the listed sites of
+ * l_i(x) = -tau_i d_mix(x,i) (max-subtracted).  Pixels whose list holds no
+ * valid active site render black.  rgb: float32[H][W][3] (written).
+ */
+int sad_render(const float* prep, int32_t capacity, int32_t H, int32_t W, int32_t K,
+               const uint32_t* map, float* rgb, void* stream);
+
+/*
+ * sad_decode_points -- random-access decode at float coordinates (the
+ * render-only path with cached top-K lists, Sec. 6.7).  Query (x,y) uses the
+ * list of pixel (clamp(floor x), clamp(floor y)) and evaluates the blend of
+ * Sec. 4.2 at (x,y) itself.  xy: float32[n][2]; rgb: float32[n][3].
+ */
+int sad_decode_points(const float* prep, int32_t capacity, int32_t H, int32_t W, int32_t K,
+                      const uint32_t* map, const float* xy, int64_t n, float* rgb,
+                      void* stream);
+
+/*
+ * Workspace of sad_render_backward / sad_train_grads, in bytes, for a problem
+ * of H x W pixels, list size K and `capacity` sites, able to hold
+ * `max_records` per-tile partial records (0 = default H*W*K/4, at least
+ * 64 per 16x16 tile).  The caller allocates it (any content; 256-B aligned).
+ */
+size_t sad_backward_workspace_bytes(int32_t H, int32_t W, int32_t K, int32_t capacity,
+                                    int64_t max_records);
+
+/*
+ * sad_render_backward -- adjoint of sad_render into every site parameter
+ * (App. A.4 "Per-pixel gradients"), with the top-K map a frozen index set.
+ * Per pixel the softmax is recomputed (nothing from the forward is stored);
+ * per 16x16 tile the contributions are reduced per site in a fixed order
+ * (atomic-free per-tile partials, replacing the tile hash + global atomics of
+ * Sec. 4.8), then a deterministic segmented reduction sums each site's
+ * partials in tile order.  Bitwise reproducible run to run.
+ * grad_rgb: float32[H][W][3] = dL/dc.  grads: float32[11][capacity], fully
+ * written (zero for sites no pixel lists).  params/prep must describe the
+ * same sites.  If more partial records are produced than the workspace holds,
+ * the gradients are incomplete and sad_workspace_status reports it.
+ */
+int sad_render_backward(const float* params, const float* prep, int32_t capacity, int32_t H,
+                        int32_t W, int32_t K, const uint32_t* map, const float* grad_rgb,
+                        float* grads, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * sad_train_grads -- fused training gradient (Sec. 6.1): renders, forms the
+ * MSE loss L = (1/P) sum_x |c(x) - I(x)|^2 against target float32[H][W][3],
+ * and back-propagates g = 2(c - I)/P exactly as sad_render_backward does.
+ * loss: device float32[1] (written, deterministic); rgb_out may be NULL or
+ * float32[H][W][3] to also receive the render.
+ */
+int sad_train_grads(const float* params, const float* prep, int32_t capacity, int32_t H,
+                    int32_t W, int32_t K, const uint32_t* map, const float* target,
+                    float* grads, float* loss, float* rgb_out, void* workspace,
+                    size_t workspace_bytes, void* stream);
+
+/*
+ * Reads the workspace status word of the last backward call on `stream`
+ * (synchronises the stream).  *records_used receives the number of partial
+ * records written; returns SAD_EWORKSPACE if they overflowed the workspace.
+ */
+int sad_workspace_status(const void* workspace, int64_t* records_used, void* stream);
+
+/* Adam hyper-parameters (Sec. 6.1; betas/eps after Kingma & Ba 2015). */
+typedef struct sad_adam_hparams {
+  float lr[SAD_NPARAMS]; /* per plane; x, y, r step in units of 1/s */
+  float beta1, beta2, eps;
+  float log_tau_min, log_tau_max; /* clamp (paper: [2, 20]) */
+  float r_min, r_max;             /* clamp (paper: [1, 512]) */
+  float a_min, a_max;             /* clamp (paper: [-2, 2]) */
+  float b_min, b_max;             /* clamp of the log isotropic scale */
+} sad_adam_hparams;
+
+/*
+ * sad_adam_step -- one bias-corrected Adam step on every active site
+ * (Sec. 6.1): m = b1 m + (1-b1) g', v = b2 v + (1-b2) g'^2,
+ * p -= lr mhat/(sqrt(vhat)+eps), where g' = g/s and the step is divided by s
+ * for x, y and r (normalised units); then positions clamp to [0,W]x[0,H],
+ * log_tau/r/a/b to their ranges, colours to [0,1], and (ux,uy) is
+ * re-normalised.  Inactive sites are untouched.  t is the 1-based step.
+ * params, m, v: float32[11][capacity] (updated in place); grads read.
+ * hp: HOST pointer.
+ */
+int sad_adam_step(float* params, const float* grads, float* m, float* v, int32_t capacity,
+                  int32_t H, int32_t W, int32_t t, const sad_adam_hparams* hp, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SAD_H */

@@ -1,0 +1,274 @@
+"""Thin Python binding of libsad.so (the C-ABI declared in include/sad.h).
+
+Argument marshalling only: every function checks tensor dtypes, devices,
+shapes and contiguity, passes raw device pointers and the current CUDA
+stream, and raises ``SadError`` on a non-zero status.  All arithmetic runs in
+the library's CUDA kernels; there is no CPU fallback.  If the library is
+missing or cannot be loaded, ``lib()`` raises and nothing else works.
+
+Layouts (see include/sad.h): params float32[11, cap]; prep float32[3, cap, 4];
+map uint32 planes stored as int32[K/4, H*W, 4] (torch has no uint32 kernels
+on all versions, the bits are the same); rgb float32[H, W, 3].
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libsad.so")
+_lib = None
+
+N_PARAMS = 11
+INVALID = 0xFFFFFFFF
+
+
+class SadError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+class AdamHparams(ctypes.Structure):
+    _fields_ = [
+        ("lr", ctypes.c_float * N_PARAMS),
+        ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+        ("log_tau_min", ctypes.c_float), ("log_tau_max", ctypes.c_float),
+        ("r_min", ctypes.c_float), ("r_max", ctypes.c_float),
+        ("a_min", ctypes.c_float), ("a_max", ctypes.c_float),
+        ("b_min", ctypes.c_float), ("b_max", ctypes.c_float),
+    ]
+
+
+_SIGS = {
+    "sad_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "sad_last_error": (ctypes.c_char_p, []),
+    "sad_abi_version": (ctypes.c_int, []),
+    "sad_prepare_sites": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "sad_topk_seed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                     ctypes.c_void_p]),
+    "sad_update_topk": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int32,
+                                       ctypes.c_uint64, ctypes.c_void_p]),
+    "sad_render": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                  ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_void_p]),
+    "sad_decode_points": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                         ctypes.c_void_p]),
+    "sad_backward_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32,
+                                                       ctypes.c_int32, ctypes.c_int32,
+                                                       ctypes.c_int64]),
+    "sad_render_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "sad_train_grads": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_size_t, ctypes.c_void_p]),
+    "sad_workspace_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                            ctypes.c_void_p]),
+    "sad_adam_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.POINTER(AdamHparams), ctypes.c_void_p]),
+}
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Loads libsad.so once (raises if it is missing: no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"libsad.so not built at {_LIB_PATH}; run "
+                              "paper_2604_21984_gb300.build.build() first")
+        L = ctypes.CDLL(_LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(status, what):
+    if status != 0:
+        msg = lib().sad_last_error().decode(errors="replace")
+        raise SadError(status, f"{what}: {msg}")
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t, dtype, name, numel=None):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ----------------------------------------------------------------------------
+# allocation helpers (torch owns all device memory)
+# ----------------------------------------------------------------------------
+
+def empty_prep(cap, device="cuda"):
+    return torch.empty((3, max(cap, 1), 4), dtype=torch.float32, device=device)
+
+
+def empty_map(H, W, K, device="cuda"):
+    return torch.empty((K // 4, H * W, 4), dtype=torch.int32, device=device)
+
+
+def map_from_ids(ids, device="cuda"):
+    """uint32[P, K] (numpy or torch) -> device planes int32[K/4, P, 4]."""
+    if isinstance(ids, np.ndarray):
+        ids = torch.from_numpy(ids.astype(np.uint32).view(np.int32))
+    P, K = ids.shape
+    return ids.reshape(P, K // 4, 4).permute(1, 0, 2).contiguous().to(device)
+
+
+def ids_from_map(m):
+    """device planes int32[K/4, P, 4] -> numpy uint32[P, K]."""
+    Kq, P, _ = m.shape
+    return m.permute(1, 0, 2).reshape(P, Kq * 4).cpu().numpy().view(np.uint32)
+
+
+def backward_workspace(H, W, K, cap, max_records=0, device="cuda"):
+    n = lib().sad_backward_workspace_bytes(H, W, K, cap, max_records)
+    if n == 0:
+        raise ValueError("invalid problem for sad_backward_workspace_bytes")
+    return torch.empty(n, dtype=torch.uint8, device=device)
+
+
+# ----------------------------------------------------------------------------
+# entry points (same names as the C-ABI)
+# ----------------------------------------------------------------------------
+
+def sad_prepare_sites(params, H, W, prep, stream=None):
+    cap = params.shape[1]
+    _check(lib().sad_prepare_sites(_ptr(params, torch.float32, "params", N_PARAMS * cap), cap, H, W,
+                                   _ptr(prep, torch.float32, "prep"), _stream(stream)),
+           "sad_prepare_sites")
+    return prep
+
+
+def sad_topk_seed(prep, cap, H, W, K, map_out, stream=None):
+    _check(lib().sad_topk_seed(_ptr(prep, torch.float32, "prep"), cap, H, W, K,
+                               _ptr(map_out, torch.int32, "map", H * W * K), _stream(stream)),
+           "sad_topk_seed")
+    return map_out
+
+
+def sad_update_topk(prep, cap, H, W, K, map_in, map_out, step_code, n_inject, seed, stream=None):
+    _check(lib().sad_update_topk(_ptr(prep, torch.float32, "prep"), cap, H, W, K,
+                                 _ptr(map_in, torch.int32, "map_in", H * W * K),
+                                 _ptr(map_out, torch.int32, "map_out", H * W * K),
+                                 step_code & 0xFFFFFFFF, n_inject, seed & ((1 << 64) - 1),
+                                 _stream(stream)), "sad_update_topk")
+    return map_out
+
+
+def sad_render(prep, cap, H, W, K, map_in, rgb, stream=None):
+    _check(lib().sad_render(_ptr(prep, torch.float32, "prep"), cap, H, W, K,
+                            _ptr(map_in, torch.int32, "map", H * W * K),
+                            _ptr(rgb, torch.float32, "rgb", H * W * 3), _stream(stream)),
+           "sad_render")
+    return rgb
+
+
+def sad_decode_points(prep, cap, H, W, K, map_in, xy, rgb, stream=None):
+    n = xy.shape[0]
+    _check(lib().sad_decode_points(_ptr(prep, torch.float32, "prep"), cap, H, W, K,
+                                   _ptr(map_in, torch.int32, "map", H * W * K),
+                                   _ptr(xy, torch.float32, "xy", 2 * n), n,
+                                   _ptr(rgb, torch.float32, "rgb", 3 * n), _stream(stream)),
+           "sad_decode_points")
+    return rgb
+
+
+def sad_render_backward(params, prep, H, W, K, map_in, grad_rgb, grads, ws, stream=None):
+    cap = params.shape[1]
+    _check(lib().sad_render_backward(_ptr(params, torch.float32, "params", N_PARAMS * cap),
+                                     _ptr(prep, torch.float32, "prep"), cap, H, W, K,
+                                     _ptr(map_in, torch.int32, "map", H * W * K),
+                                     _ptr(grad_rgb, torch.float32, "grad_rgb", H * W * 3),
+                                     _ptr(grads, torch.float32, "grads", N_PARAMS * cap),
+                                     _ptr(ws, torch.uint8, "workspace"), ws.numel(),
+                                     _stream(stream)), "sad_render_backward")
+    return grads
+
+
+def sad_train_grads(params, prep, H, W, K, map_in, target, grads, loss, ws, rgb_out=None,
+                    stream=None):
+    cap = params.shape[1]
+    _check(lib().sad_train_grads(_ptr(params, torch.float32, "params", N_PARAMS * cap),
+                                 _ptr(prep, torch.float32, "prep"), cap, H, W, K,
+                                 _ptr(map_in, torch.int32, "map", H * W * K),
+                                 _ptr(target, torch.float32, "target", H * W * 3),
+                                 _ptr(grads, torch.float32, "grads", N_PARAMS * cap),
+                                 _ptr(loss, torch.float32, "loss", 1),
+                                 _ptr(rgb_out, torch.float32, "rgb_out", H * W * 3),
+                                 _ptr(ws, torch.uint8, "workspace"), ws.numel(),
+                                 _stream(stream)), "sad_train_grads")
+    return grads
+
+
+def sad_workspace_status(ws, stream=None):
+    used = ctypes.c_int64(0)
+    st = lib().sad_workspace_status(_ptr(ws, torch.uint8, "workspace"), ctypes.byref(used),
+                                    _stream(stream))
+    return st, int(used.value)
+
+
+def adam_hparams(lr=None, beta1=0.9, beta2=0.999, eps=1e-8, log_tau_range=(2.0, 20.0),
+                 r_range=(1.0, 512.0), a_range=(-2.0, 2.0), b_range=(-8.0, 8.0)):
+    """Defaults: Sec. 6.1 clamps; per-plane learning rates (x, y, log_tau, r,
+    cr, cg, cb, ux, uy, a, b)."""
+    if lr is None:
+        lr = (1e-3, 1e-3, 1e-2, 1e-3, 5e-3, 5e-3, 5e-3, 1e-2, 1e-2, 1e-2, 0.0)
+    hp = AdamHparams()
+    for i, v in enumerate(lr):
+        hp.lr[i] = v
+    hp.beta1, hp.beta2, hp.eps = beta1, beta2, eps
+    hp.log_tau_min, hp.log_tau_max = log_tau_range
+    hp.r_min, hp.r_max = r_range
+    hp.a_min, hp.a_max = a_range
+    hp.b_min, hp.b_max = b_range
+    return hp
+
+
+def sad_adam_step(params, grads, m, v, H, W, t, hp, stream=None):
+    cap = params.shape[1]
+    n = N_PARAMS * cap
+    _check(lib().sad_adam_step(_ptr(params, torch.float32, "params", n),
+                               _ptr(grads, torch.float32, "grads", n),
+                               _ptr(m, torch.float32, "m", n), _ptr(v, torch.float32, "v", n),
+                               cap, H, W, t, ctypes.byref(hp), _stream(stream)),
+           "sad_adam_step")
+    return params

@@ -1,0 +1,647 @@
+// Adjoint of the blend (App. A.4 "Per-pixel gradients") with an atomic-free,
+// deterministic gradient reduction that replaces the per-tile hash table plus
+// global float atomics of Sec. 4.8 / Alg. "Threadgroup hash reduction".
+//
+// Per 16x16 pixel tile (one CTA, one pixel per thread):
+//  1. forward: every pixel recomputes its max-subtracted softmax over its K
+//     listed sites (nothing from the forward pass is stored), forms its
+//     upstream gradient g (given, or 2(c - I)/P for the fused MSE loss) and
+//     parks {m, 1/Z, cbar, g} in shared memory;
+//  2. the tile's distinct sites get slots in a shared hash table (the paper's
+//     multiplicative hash, linear probing); each warp records, per slot, the
+//     bitmask of its 32 pixels that list the site (__match_any_sync, no
+//     atomics: a warp owns its mask word);
+//  3. the masks give each slot a stable, pixel-ordered pair list; the lists
+//     are cut into chunks of kChunk pairs, each chunk summed by one thread in
+//     list order, and each slot's chunks summed in chunk order, giving ten
+//     sufficient statistics per (site, tile):
+//       sum w g (3),  sum d,  sum d n,  sum d dx/n,  sum d dy/n,
+//       sum d dx^2/n, sum d dx dy/n, sum d dy^2/n,   d = dL/dl = w g.(c_k - cbar)
+//     written as one partial record per (site, tile).  If the table fills,
+//     the remaining sites are handled in further rounds.
+// Then a segmented reduction gathers each site's records, orders them by tile
+// index and sums them in that order; the eleven parameter gradients follow
+// from the statistics by the chain rule through G(a, b, u) of Sec. 4.1.
+#include "sad_device.cuh"
+#include "sad_host.h"
+
+namespace sad {
+
+constexpr int kTileSide = 16;
+constexpr int kTileThreads = kTileSide * kTileSide;
+constexpr int kChunk = 16;
+constexpr int kSlots = 128;  // shared hash table size per round (power of 2)
+constexpr int kLog2Slots = 7;
+constexpr uint32_t kNone = 0xffffffffu;
+
+struct alignas(16) Record {
+  uint32_t site;
+  uint32_t tile;
+  float acc[10];
+};
+static_assert(sizeof(Record) == 48, "record layout");
+
+struct WsHeader {
+  uint32_t cursor;
+  uint32_t overflow;
+  uint32_t pad[62];
+};
+static_assert(sizeof(WsHeader) == 256, "header layout");
+
+// ---------------------------------------------------------------------------
+// workspace layout
+// ---------------------------------------------------------------------------
+struct WsLayout {
+  size_t hdr, tile_loss, records, counts, fill, offs, blocksums, refs, total;
+  uint32_t max_records, n_tiles, n_blocks;
+};
+
+static inline size_t align256(size_t v) { return (v + 255) & ~static_cast<size_t>(255); }
+
+static WsLayout ws_layout(int H, int W, int K, int cap, int64_t max_records) {
+  WsLayout L{};
+  const uint64_t tiles_x = (W + kTileSide - 1) / kTileSide;
+  const uint64_t tiles_y = (H + kTileSide - 1) / kTileSide;
+  L.n_tiles = static_cast<uint32_t>(tiles_x * tiles_y);
+  uint64_t mr = max_records > 0 ? static_cast<uint64_t>(max_records)
+                                : static_cast<uint64_t>(H) * W * K / 4;
+  if (max_records <= 0 && mr < 64ull * L.n_tiles) mr = 64ull * L.n_tiles;
+  if (mr > 0xfffffff0ull) mr = 0xfffffff0ull;
+  L.max_records = static_cast<uint32_t>(mr);
+  L.n_blocks = static_cast<uint32_t>((cap + 1023) / 1024);
+  size_t o = 0;
+  L.hdr = o;        o = align256(o + sizeof(WsHeader));
+  L.tile_loss = o;  o = align256(o + sizeof(float) * L.n_tiles);
+  L.records = o;    o = align256(o + sizeof(Record) * L.max_records);
+  L.counts = o;     o = align256(o + sizeof(uint32_t) * cap);
+  L.fill = o;       o = align256(o + sizeof(uint32_t) * cap);
+  L.offs = o;       o = align256(o + sizeof(uint32_t) * cap);
+  L.blocksums = o;  o = align256(o + sizeof(uint32_t) * (L.n_blocks + 1));
+  L.refs = o;       o = align256(o + sizeof(uint64_t) * L.max_records);
+  L.total = o;
+  return L;
+}
+
+// ---------------------------------------------------------------------------
+// block-wide exclusive scan of a 64-bit value over 256 threads (fixed order)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t block_excl_scan256(uint64_t v, uint64_t* warp_tot,
+                                                       uint64_t& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[warp] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t run = 0;
+    for (int w = 0; w < kTileThreads / 32; ++w) {
+      run += warp_tot[w];
+      warp_tot[w] = run;
+    }
+  }
+  __syncthreads();
+  const uint64_t pre = warp ? warp_tot[warp - 1] : 0ull;
+  total = warp_tot[kTileThreads / 32 - 1];
+  __syncthreads();
+  return pre + x - v;
+}
+
+__device__ __forceinline__ uint32_t probe_slot(uint32_t id, uint32_t* keys) {
+  const uint32_t h = (id * 2654435761u) >> (32 - kLog2Slots);
+  volatile uint32_t* vk = keys;
+  for (int i = 0; i < kSlots; ++i) {
+    const uint32_t s = (h + i) & (kSlots - 1);
+    const uint32_t k = vk[s];
+    if (k == id) return s;
+    if (k == kInvalid) {
+      const uint32_t old = atomicCAS(&keys[s], kInvalid, id);
+      if (old == kInvalid || old == id) return s;
+    }
+  }
+  return kNone;
+}
+
+// ---------------------------------------------------------------------------
+// per-tile kernel
+// ---------------------------------------------------------------------------
+template <int K>
+__global__ void __launch_bounds__(kTileThreads) k_bwd_tile(
+    const float4* __restrict__ geo, const float4* __restrict__ met,
+    const float4* __restrict__ col, int cap, int H, int W, const uint4* __restrict__ map,
+    const float* __restrict__ grad_rgb, const float* __restrict__ target, float two_over_P,
+    float* __restrict__ rgb_out, float* __restrict__ tile_loss, Record* __restrict__ records,
+    uint32_t max_records, WsHeader* __restrict__ hdr) {
+  constexpr int kMaxChunks = kTileThreads * K / kChunk + kSlots;
+  __shared__ uint32_t s_keys[kSlots];
+  __shared__ uint32_t s_mask[kSlots][8];
+  __shared__ uint16_t s_wpre[kSlots][8];
+  __shared__ uint32_t s_cnt[kSlots];
+  __shared__ uint32_t s_off[kSlots];
+  __shared__ uint32_t s_choff[kSlots + 1];
+  __shared__ uint32_t s_rix[kSlots];
+  __shared__ uint8_t s_chslot[kMaxChunks];
+  __shared__ uint8_t s_list[kTileThreads * K];
+  __shared__ float4 s_pa[kTileThreads];
+  __shared__ float4 s_pb[kTileThreads];
+  __shared__ float s_part[kMaxChunks][10];
+  __shared__ uint64_t s_scan[kTileThreads / 32];
+  __shared__ float s_red[kTileThreads / 32];
+  __shared__ uint32_t s_base;
+
+  const int t = threadIdx.x;
+  const int lane = t & 31, warp = t >> 5;
+  const uint32_t tiles_x = (W + kTileSide - 1) / kTileSide;
+  const uint32_t tile = blockIdx.x;
+  const int x0 = (tile % tiles_x) * kTileSide;
+  const int y0 = (tile / tiles_x) * kTileSide;
+  const int x = x0 + (t & (kTileSide - 1));
+  const int y = y0 + (t >> 4);
+  const bool inimg = x < W && y < H;
+  const size_t P = static_cast<size_t>(H) * W;
+  const size_t q = inimg ? static_cast<size_t>(y) * W + x : 0;
+  const uint32_t ucap = static_cast<uint32_t>(cap);
+  const float px = x + 0.5f, py = y + 0.5f;
+
+  // ---- 1. per-pixel forward --------------------------------------------
+  uint32_t ids[K];
+#pragma unroll
+  for (int j = 0; j < K / 4; ++j) {
+    uint4 v = make_uint4(kInvalid, kInvalid, kInvalid, kInvalid);
+    if (inimg) v = ldg(&map[j * P + q]);
+    ids[4 * j] = v.x;
+    ids[4 * j + 1] = v.y;
+    ids[4 * j + 2] = v.z;
+    ids[4 * j + 3] = v.w;
+  }
+  float l[K];
+  float m = -INFINITY;
+  uint32_t vm = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    l[k] = -INFINITY;
+    if (ids[k] < ucap) {
+      const float4 mt = ldg(&met[ids[k]]);
+      if (mt.w != 0.f) {
+        l[k] = score_fast(px, py, ldg(&geo[ids[k]]), mt).l;
+        vm |= 1u << k;
+        m = fmaxf(m, l[k]);
+      }
+    }
+  }
+  float z = 0.f;
+  float3 cb = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (vm >> k & 1u) {
+      const float e = __expf(l[k] - m);
+      const float4 ck = ldg(&col[ids[k]]);
+      z += e;
+      cb.x += e * ck.x;
+      cb.y += e * ck.y;
+      cb.z += e * ck.z;
+    }
+  }
+  const float iz = vm ? 1.f / z : 0.f;
+  cb.x *= iz;
+  cb.y *= iz;
+  cb.z *= iz;
+  float3 g = make_float3(0.f, 0.f, 0.f);
+  float lpx = 0.f;
+  if (inimg) {
+    if (grad_rgb) {
+      g = make_float3(grad_rgb[3 * q], grad_rgb[3 * q + 1], grad_rgb[3 * q + 2]);
+    } else {
+      const float rx = cb.x - target[3 * q], ry = cb.y - target[3 * q + 1],
+                  rz = cb.z - target[3 * q + 2];
+      lpx = rx * rx + ry * ry + rz * rz;
+      g = make_float3(two_over_P * rx, two_over_P * ry, two_over_P * rz);
+    }
+    if (rgb_out) {
+      rgb_out[3 * q] = cb.x;
+      rgb_out[3 * q + 1] = cb.y;
+      rgb_out[3 * q + 2] = cb.z;
+    }
+  }
+  s_pa[t] = make_float4(m, iz, cb.x, cb.y);
+  s_pb[t] = make_float4(cb.z, g.x, g.y, g.z);
+  if (tile_loss) {  // deterministic tile sum of the per-pixel squared error
+    float v = lpx;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) s_red[warp] = v;
+    __syncthreads();
+    if (t == 0) {
+      float s = 0.f;
+      for (int w = 0; w < kTileThreads / 32; ++w) s += s_red[w];
+      tile_loss[tile] = s;
+    }
+  }
+
+  // ---- 2..3. rounds of slot assignment and ordered reduction ------------
+  uint32_t pending = vm;
+  uint32_t slot[K];
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  for (;;) {
+    for (int i = t; i < kSlots; i += kTileThreads) {
+      s_keys[i] = kInvalid;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) s_mask[i][w] = 0u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      uint32_t sl = kNone;
+      if (pending >> k & 1u) {
+        sl = probe_slot(ids[k], s_keys);
+        if (sl != kNone) pending &= ~(1u << k);
+      }
+      slot[k] = sl;
+      const uint32_t peers = __match_any_sync(0xffffffffu, sl);
+      if (sl != kNone && lane == __ffs(peers) - 1) s_mask[sl][warp] |= peers;
+    }
+    __syncthreads();
+    uint64_t packed = 0;
+    if (t < kSlots && s_keys[t] != kInvalid) {
+      uint32_t c = 0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        s_wpre[t][w] = static_cast<uint16_t>(c);
+        c += __popc(s_mask[t][w]);
+      }
+      const uint32_t nch = (c + kChunk - 1) / kChunk;
+      packed = static_cast<uint64_t>(c) | (static_cast<uint64_t>(nch) << 20) | (1ull << 40);
+    }
+    uint64_t total;
+    const uint64_t ex = block_excl_scan256(packed, s_scan, total);
+    if (t < kSlots) {
+      s_cnt[t] = static_cast<uint32_t>(packed & 0xfffffu);
+      s_off[t] = static_cast<uint32_t>(ex & 0xfffffu);
+      s_choff[t] = static_cast<uint32_t>((ex >> 20) & 0xfffffu);
+      s_rix[t] = static_cast<uint32_t>(ex >> 40);
+    }
+    const uint32_t n_chunks = static_cast<uint32_t>((total >> 20) & 0xfffffu);
+    const uint32_t n_used = static_cast<uint32_t>(total >> 40);
+    if (t == 0) {
+      s_choff[kSlots] = n_chunks;
+      s_base = atomicAdd(&hdr->cursor, n_used);
+    }
+    __syncthreads();
+    if (t < kSlots && s_cnt[t] > 0) {
+      const uint32_t c0 = s_choff[t], nch = (s_cnt[t] + kChunk - 1) / kChunk;
+      for (uint32_t c = 0; c < nch; ++c) s_chslot[c0 + c] = static_cast<uint8_t>(t);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const uint32_t sl = slot[k];
+      if (sl != kNone) {
+        const uint32_t pos = s_off[sl] + s_wpre[sl][warp] + __popc(s_mask[sl][warp] & lt_mask);
+        s_list[pos] = static_cast<uint8_t>(t);
+      }
+    }
+    __syncthreads();
+    for (uint32_t c = t; c < n_chunks; c += kTileThreads) {
+      const uint32_t sl = s_chslot[c];
+      const uint32_t id = s_keys[sl];
+      const uint32_t first = (c - s_choff[sl]) * kChunk;
+      const uint32_t len = min(static_cast<uint32_t>(kChunk), s_cnt[sl] - first);
+      const uint32_t start = s_off[sl] + first;
+      const float4 gs = ldg(&geo[id]), ms = ldg(&met[id]), cs = ldg(&col[id]);
+      float acc[10];
+#pragma unroll
+      for (int j = 0; j < 10; ++j) acc[j] = 0.f;
+      for (uint32_t i = 0; i < len; ++i) {
+        const uint32_t p = s_list[start + i];
+        const float4 A = s_pa[p], B = s_pb[p];
+        const float qx = x0 + static_cast<int>(p & (kTileSide - 1)) + 0.5f;
+        const float qy = y0 + static_cast<int>(p >> 4) + 0.5f;
+        const ScoreParts sp = score_fast(qx, qy, gs, ms);
+        const float w = __expf(sp.l - A.x) * A.y;
+        const float d = w * (B.y * (cs.x - A.z) + B.z * (cs.y - A.w) + B.w * (cs.z - B.x));
+        acc[0] += w * B.y;
+        acc[1] += w * B.z;
+        acc[2] += w * B.w;
+        acc[3] += d;
+        acc[4] += d * sp.n;
+        if (sp.n > 0.f) {
+          const float a = d / sp.n;
+          acc[5] += a * sp.dx;
+          acc[6] += a * sp.dy;
+          acc[7] += a * sp.dx * sp.dx;
+          acc[8] += a * sp.dx * sp.dy;
+          acc[9] += a * sp.dy * sp.dy;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 10; ++j) s_part[c][j] = acc[j];
+    }
+    __syncthreads();
+    if (t < kSlots && s_cnt[t] > 0) {
+      float acc[10];
+#pragma unroll
+      for (int j = 0; j < 10; ++j) acc[j] = 0.f;
+      const uint32_t c0 = s_choff[t], nch = (s_cnt[t] + kChunk - 1) / kChunk;
+      for (uint32_t c = c0; c < c0 + nch; ++c) {
+#pragma unroll
+        for (int j = 0; j < 10; ++j) acc[j] += s_part[c][j];
+      }
+      const uint32_t ridx = s_base + s_rix[t];
+      if (ridx < max_records) {
+        float4* dst = reinterpret_cast<float4*>(&records[ridx]);
+        dst[0] = make_float4(__uint_as_float(s_keys[t]), __uint_as_float(tile), acc[0], acc[1]);
+        dst[1] = make_float4(acc[2], acc[3], acc[4], acc[5]);
+        dst[2] = make_float4(acc[6], acc[7], acc[8], acc[9]);
+      } else {
+        hdr->overflow = 1u;
+      }
+    }
+    if (!__syncthreads_or(pending != 0u)) break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// segmented reduction of the per-tile records
+// ---------------------------------------------------------------------------
+__global__ void k_seg_count(const Record* __restrict__ rec, const WsHeader* __restrict__ hdr,
+                            uint32_t max_records, uint32_t* __restrict__ counts) {
+  const uint32_t n = min(hdr->cursor, max_records);
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
+    atomicAdd(&counts[rec[r].site], 1u);
+}
+
+// exclusive scan of counts[cap] -> offs[cap], blocks of 1024
+__global__ void k_scan_blocks(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int n,
+                              uint32_t* __restrict__ block_sums) {
+  __shared__ uint32_t s_w[32];
+  const int i = blockIdx.x * 1024 + threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t v = i < n ? in[i] : 0u;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_w[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = s_w[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    s_w[lane] = w;
+  }
+  __syncthreads();
+  const uint32_t pre = warp ? s_w[warp - 1] : 0u;
+  if (i < n) out[i] = pre + x - v;
+  if (threadIdx.x == 1023) block_sums[blockIdx.x] = pre + x;
+}
+
+__global__ void k_scan_sums(uint32_t* __restrict__ block_sums, int nb) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    uint32_t run = 0;
+    for (int b = 0; b < nb; ++b) {
+      const uint32_t v = block_sums[b];
+      block_sums[b] = run;
+      run += v;
+    }
+  }
+}
+
+__global__ void k_scan_add(uint32_t* __restrict__ out, int n, const uint32_t* __restrict__ block_sums) {
+  const int i = blockIdx.x * 1024 + threadIdx.x;
+  if (i < n) out[i] += block_sums[blockIdx.x];
+}
+
+__global__ void k_seg_scatter(const Record* __restrict__ rec, const WsHeader* __restrict__ hdr,
+                              uint32_t max_records, const uint32_t* __restrict__ offs,
+                              uint32_t* __restrict__ fill, uint64_t* __restrict__ refs) {
+  const uint32_t n = min(hdr->cursor, max_records);
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const uint32_t s = rec[r].site;
+    const uint32_t pos = offs[s] + atomicAdd(&fill[s], 1u);
+    refs[pos] = (static_cast<uint64_t>(rec[r].tile) << 32) | r;
+  }
+}
+
+// Per site: sum its records in tile order, then the chain rule to 11 grads.
+__global__ void k_site_grads(const float* __restrict__ params, const float4* __restrict__ geo,
+                             const float4* __restrict__ met, int cap,
+                             const Record* __restrict__ rec, const uint32_t* __restrict__ counts,
+                             const uint32_t* __restrict__ offs, const uint64_t* __restrict__ refs,
+                             float* __restrict__ grads) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cap) return;
+  const size_t c = static_cast<size_t>(cap);
+  const uint32_t cnt = counts[i];
+  float out[kNParams];
+#pragma unroll
+  for (int j = 0; j < kNParams; ++j) out[j] = 0.f;
+  if (cnt > 0) {
+    const uint64_t* seg = refs + offs[i];
+    float acc[10];
+#pragma unroll
+    for (int j = 0; j < 10; ++j) acc[j] = 0.f;
+    uint64_t last = 0;
+    for (uint32_t it = 0; it < cnt; ++it) {
+      uint64_t best = ~0ull;
+      for (uint32_t j = 0; j < cnt; ++j) {
+        const uint64_t v = seg[j];
+        if ((it == 0 || v > last) && v < best) best = v;
+      }
+      last = best;
+      const float4* src = reinterpret_cast<const float4*>(&rec[static_cast<uint32_t>(best)]);
+      const float4 r0 = src[0], r1 = src[1], r2 = src[2];
+      acc[0] += r0.z; acc[1] += r0.w;
+      acc[2] += r1.x; acc[3] += r1.y; acc[4] += r1.z; acc[5] += r1.w;
+      acc[6] += r2.x; acc[7] += r2.y; acc[8] += r2.z; acc[9] += r2.w;
+    }
+    const float4 gs = geo[i], ms = met[i];
+    const float ts = gs.z, r = gs.w;
+    const float G00 = ms.x, G01 = ms.y, G11 = ms.z;
+    const float rawx = params[PUX * c + i], rawy = params[PUY * c + i];
+    const float a = params[PA * c + i], b = params[PB * c + i];
+    float nrm2 = rawx * rawx + rawy * rawy;
+    float ux = 1.f, uy = 0.f;
+    if (nrm2 > 0.f) {
+      const float inv = rsqrtf(nrm2);
+      ux = rawx * inv;
+      uy = rawy * inv;
+    }
+    const float ep = expf(b + a), em = expf(b - a);
+    const float gG00 = -0.5f * ts * acc[7];
+    const float gG01 = -ts * acc[8];
+    const float gG11 = -0.5f * ts * acc[9];
+    out[PX] = ts * (G00 * acc[5] + G01 * acc[6]);
+    out[PY] = ts * (G01 * acc[5] + G11 * acc[6]);
+    out[PLOGTAU] = ts * (r * acc[3] - acc[4]);
+    out[PR] = ts * acc[3];
+    out[PCR] = acc[0];
+    out[PCG] = acc[1];
+    out[PCB] = acc[2];
+    const float xx = ux * ux, yy = uy * uy, xy = ux * uy;
+    out[PA] = gG00 * (ep * xx - em * yy) + gG01 * (ep + em) * xy + gG11 * (ep * yy - em * xx);
+    out[PB] = gG00 * G00 + gG01 * G01 + gG11 * G11;
+    const float gth = (ep - em) * (-2.f * xy * gG00 + (xx - yy) * gG01 + 2.f * xy * gG11);
+    if (nrm2 > 0.f) {
+      out[PUX] = -gth * rawy / nrm2;
+      out[PUY] = gth * rawx / nrm2;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kNParams; ++j) grads[j * c + i] = out[j];
+}
+
+__global__ void k_loss_final(const float* __restrict__ tile_loss, uint32_t n_tiles, float inv_P,
+                             float* __restrict__ loss) {
+  __shared__ float s_w[8];
+  float v = 0.f;
+  for (uint32_t i = threadIdx.x; i < n_tiles; i += 256) v += tile_loss[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.f;
+    for (int w = 0; w < 8; ++w) s += s_w[w];
+    loss[0] = s * inv_P;
+  }
+}
+
+// ---------------------------------------------------------------------------
+static int run_backward(const float* params, const float* prep, int cap, int H, int W, int K,
+                        const uint32_t* map, const float* grad_rgb, const float* target,
+                        float* grads, float* loss, float* rgb_out, void* ws, size_t ws_bytes,
+                        cudaStream_t st, const char* name) {
+  if (int e = check_problem(cap, H, W, K, true)) return e;
+  if (!map || !grads || !ws || (!prep && cap > 0) || (!params && cap > 0))
+    return einval("%s: null pointer", name);
+  if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return einval("%s: workspace must be 256-byte aligned", name);
+  if (!aligned16(map) || !aligned16(prep)) return einval("%s: pointers must be 16-byte aligned", name);
+  const WsLayout L = ws_layout(H, W, K, cap, 0);
+  if (ws_bytes < L.total) {
+    set_error("%s: workspace has %zu bytes, needs %zu", name, ws_bytes, L.total);
+    return SAD_EWORKSPACE;
+  }
+  // a caller-provided larger workspace holds proportionally more records
+  WsLayout LL = L;
+  if (ws_bytes > L.total) {
+    const uint64_t per = sizeof(Record) + sizeof(uint64_t);
+    uint64_t mr = L.max_records + (ws_bytes - L.total) / per;
+    if (mr > 0xfffffff0ull) mr = 0xfffffff0ull;
+    for (int it = 0; it < 64 && mr > L.max_records; ++it, --mr) {
+      const WsLayout T = ws_layout(H, W, K, cap, static_cast<int64_t>(mr));
+      if (T.total <= ws_bytes) {
+        LL = T;
+        break;
+      }
+    }
+  }
+  char* base = static_cast<char*>(ws);
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(base + LL.hdr);
+  float* tile_loss = reinterpret_cast<float*>(base + LL.tile_loss);
+  Record* rec = reinterpret_cast<Record*>(base + LL.records);
+  uint32_t* counts = reinterpret_cast<uint32_t*>(base + LL.counts);
+  uint32_t* fill = reinterpret_cast<uint32_t*>(base + LL.fill);
+  uint32_t* offs = reinterpret_cast<uint32_t*>(base + LL.offs);
+  uint32_t* bsums = reinterpret_cast<uint32_t*>(base + LL.blocksums);
+  uint64_t* refs = reinterpret_cast<uint64_t*>(base + LL.refs);
+
+  cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st);
+  if (e == cudaSuccess && cap > 0) e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * cap, st);
+  if (e == cudaSuccess && cap > 0) e = cudaMemsetAsync(fill, 0, sizeof(uint32_t) * cap, st);
+  if (e != cudaSuccess) {
+    set_error("%s memset: %s", name, cudaGetErrorString(e));
+    return SAD_ECUDA;
+  }
+  const float4* p4 = reinterpret_cast<const float4*>(prep);
+  const float4 *geo = p4, *met = p4 + cap, *col = p4 + 2 * static_cast<size_t>(cap);
+  const uint4* m4 = reinterpret_cast<const uint4*>(map);
+  const float two_over_P = 2.0f / static_cast<float>(static_cast<double>(H) * W);
+  float* tl = target ? tile_loss : nullptr;
+  switch (K) {
+    case 4:
+      k_bwd_tile<4><<<LL.n_tiles, kTileThreads, 0, st>>>(geo, met, col, cap, H, W, m4, grad_rgb, target,
+                                                         two_over_P, rgb_out, tl, rec, LL.max_records, hdr);
+      break;
+    case 8:
+      k_bwd_tile<8><<<LL.n_tiles, kTileThreads, 0, st>>>(geo, met, col, cap, H, W, m4, grad_rgb, target,
+                                                         two_over_P, rgb_out, tl, rec, LL.max_records, hdr);
+      break;
+    default:
+      k_bwd_tile<16><<<LL.n_tiles, kTileThreads, 0, st>>>(geo, met, col, cap, H, W, m4, grad_rgb, target,
+                                                          two_over_P, rgb_out, tl, rec, LL.max_records, hdr);
+      break;
+  }
+  if (int r = check_launch("k_bwd_tile")) return r;
+  if (target) {
+    k_loss_final<<<1, 256, 0, st>>>(tile_loss, LL.n_tiles, 1.0f / static_cast<float>(static_cast<double>(H) * W), loss);
+    if (int r = check_launch("k_loss_final")) return r;
+  }
+  if (cap == 0) return SAD_OK;
+  const int sgrid = 152 * 8;
+  k_seg_count<<<sgrid, 256, 0, st>>>(rec, hdr, LL.max_records, counts);
+  if (int r = check_launch("k_seg_count")) return r;
+  k_scan_blocks<<<LL.n_blocks, 1024, 0, st>>>(counts, offs, cap, bsums);
+  k_scan_sums<<<1, 32, 0, st>>>(bsums, static_cast<int>(LL.n_blocks));
+  k_scan_add<<<LL.n_blocks, 1024, 0, st>>>(offs, cap, bsums);
+  if (int r = check_launch("k_scan")) return r;
+  k_seg_scatter<<<sgrid, 256, 0, st>>>(rec, hdr, LL.max_records, offs, fill, refs);
+  if (int r = check_launch("k_seg_scatter")) return r;
+  k_site_grads<<<(cap + 255) / 256, 256, 0, st>>>(params, geo, met, cap, rec, counts, offs, refs, grads);
+  return check_launch("k_site_grads");
+}
+
+}  // namespace sad
+
+using namespace sad;
+
+extern "C" {
+
+size_t sad_backward_workspace_bytes(int32_t H, int32_t W, int32_t K, int32_t capacity,
+                                    int64_t max_records) {
+  if (H <= 0 || W <= 0 || capacity < 0 || (K != 4 && K != 8 && K != 16)) return 0;
+  return ws_layout(H, W, K, capacity, max_records).total;
+}
+
+int sad_render_backward(const float* params, const float* prep, int32_t capacity, int32_t H,
+                        int32_t W, int32_t K, const uint32_t* map, const float* grad_rgb,
+                        float* grads, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!grad_rgb) return einval("sad_render_backward: null grad_rgb");
+  return run_backward(params, prep, capacity, H, W, K, map, grad_rgb, nullptr, grads, nullptr,
+                      nullptr, workspace, workspace_bytes, as_stream(stream), "sad_render_backward");
+}
+
+int sad_train_grads(const float* params, const float* prep, int32_t capacity, int32_t H,
+                    int32_t W, int32_t K, const uint32_t* map, const float* target,
+                    float* grads, float* loss, float* rgb_out, void* workspace,
+                    size_t workspace_bytes, void* stream) {
+  if (!target || !loss) return einval("sad_train_grads: null target or loss");
+  return run_backward(params, prep, capacity, H, W, K, map, nullptr, target, grads, loss, rgb_out,
+                      workspace, workspace_bytes, as_stream(stream), "sad_train_grads");
+}
+
+int sad_workspace_status(const void* workspace, int64_t* records_used, void* stream) {
+  if (!workspace) return einval("sad_workspace_status: null workspace");
+  WsHeader h;
+  cudaStream_t st = as_stream(stream);
+  cudaError_t e = cudaMemcpyAsync(&h, workspace, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    set_error("sad_workspace_status: %s", cudaGetErrorString(e));
+    return SAD_ECUDA;
+  }
+  if (records_used) *records_used = h.cursor;
+  if (h.overflow) {
+    set_error("partial records overflowed the workspace (%u produced)", h.cursor);
+    return SAD_EWORKSPACE;
+  }
+  return SAD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,133 @@
+"""GPU top-K field vs the oracle's fp32 propagation: bit-exact (Sec. 4.3,
+App. A.3).  Calls go through the C-ABI binding."""
+import numpy as np
+import pytest
+
+from paper_2604_21984_gb300 import inputs as gen
+from tests.gpu_util import dev, prep_to_oracle_dict, prepare, require_gpu
+
+pytestmark = pytest.mark.gpu
+INV = 0xFFFFFFFF
+
+
+@pytest.fixture(scope="module")
+def capi():
+    return require_gpu()
+
+
+@pytest.mark.parametrize("kind", ["isotropic", "spd", "inactive"])
+def test_prepare_bit_exact(capi, oracle, kind):
+    H, W = 70, 45
+    if kind == "isotropic":
+        p = gen.sites_isotropic(gen.image_sinusoid_polygons(H, W, 1), 300, seed=2, capacity=333)
+    else:
+        p = gen.sites_random_spd(H, W, 1000, seed=3)
+        p[7] *= 2.5                                    # unnormalised directions
+        p[7, ::17] = 0.0
+        p[8, ::17] = 0.0                               # zero direction -> (1, 0)
+        if kind == "inactive":
+            p = gen.deactivate_random(p, 0.3, seed=4)
+    _, prep = prepare(capi, p, H, W)
+    got = prep_to_oracle_dict(prep, p.shape[1])
+    ref = oracle.prepare_fp32(p, H, W)
+    for k in ("x", "y", "ts", "r", "G00", "G01", "G11", "active", "cr", "cg", "cb"):
+        assert np.array_equal(got[k].view(np.uint32) if got[k].dtype == np.float32 else got[k],
+                              ref[k].view(np.uint32) if ref[k].dtype == np.float32 else ref[k]), k
+
+
+@pytest.mark.parametrize("K", [4, 8, 16])
+def test_seed_bit_exact(capi, oracle, K):
+    H, W = 37, 53
+    p = gen.sites_random_spd(H, W, 400, seed=5, capacity=420)
+    p[0, 7], p[1, 7] = p[0, 3], p[1, 3]
+    p[0, 9], p[1, 9] = float(W), float(H)
+    _, prep = prepare(capi, p, H, W)
+    m = capi.empty_map(H, W, K)
+    capi.sad_topk_seed(prep, p.shape[1], H, W, K, m)
+    ref = oracle.topk_seed_fp32(oracle.prepare_fp32(p, H, W), H, W, K)
+    assert np.array_equal(capi.ids_from_map(m), ref)
+
+
+def _gpu_propagate(capi, oracle, p, H, W, K, passes, J, seed):
+    cap = p.shape[1]
+    _, prep = prepare(capi, p, H, W)
+    a, b = capi.empty_map(H, W, K), capi.empty_map(H, W, K)
+    capi.sad_topk_seed(prep, cap, H, W, K, a)
+    for t in range(passes):
+        capi.sad_update_topk(prep, cap, H, W, K, a, b, oracle.step_code(t, H, W), J, seed)
+        a, b = b, a
+    return capi.ids_from_map(a)
+
+
+@pytest.mark.parametrize("K,J", [(8, 2), (16, 2), (4, 4), (16, 0)])
+def test_config1_pipeline_bit_exact(capi, oracle, K, J):
+    """64x64, 256 isotropic sites (scale 4 px, tau 1, r 0), seed + 6 passes
+    (steps 32..1) with J injections: GPU map == oracle fp32 map."""
+    H = W = 64
+    img = gen.image_sinusoid_polygons(H, W, seed=1000)
+    p = gen.sites_isotropic(img, 256, seed=1001)
+    got = _gpu_propagate(capi, oracle, p, H, W, K, 6, J, seed=77)
+    ref = oracle.propagate_fp32(p, H, W, K, passes=6, J=J, seed=77)
+    assert np.array_equal(got, ref)
+    ex, _ = oracle.exact_topk(p, H, W, K, np.arange(0, H * W, 7))
+    rec, em = oracle.topk_match_stats(got[::7], ex)
+    print(f"K={K} J={J}: recall {rec:.4f}, exact-match {em:.4f} vs exact top-K")
+    assert rec > 0.9
+
+
+@pytest.mark.parametrize("t", [0, 3, 9])
+def test_single_pass_from_perturbed_map(capi, oracle, t):
+    """Ragged image, inactive sites, truncated/shuffled lists, out-of-range ids."""
+    H, W, K, J = 45, 77, 16, 5
+    p = gen.sites_random_spd(H, W, 500, seed=11, capacity=530)
+    p = gen.deactivate_random(p, 0.15, seed=12)
+    ids = gen.knn_map(p, H, W, K, seed=13, truncate_frac=0.25, shuffle=True,
+                      include_inactive_frac=0.2)
+    ids[::13, 2] = 100000                              # beyond capacity
+    ids[::11, 5] = ids[::11, 4]                        # duplicate within a list
+    _, prep = prepare(capi, p, H, W)
+    mi = capi.map_from_ids(ids)
+    mo = capi.empty_map(H, W, K)
+    code = oracle.step_code(t, H, W)
+    capi.sad_update_topk(prep, p.shape[1], H, W, K, mi, mo, code, J, 2024)
+    ref = oracle.topk_pass_fp32(oracle.prepare_fp32(p, H, W), ids, H, W, K, code, J, 2024)
+    assert np.array_equal(capi.ids_from_map(mo), ref)
+
+
+def test_degenerate_cases(capi, oracle):
+    # 1x1 image; no active site; capacity 0
+    for H, W, n, cap in ((1, 1, 3, 3), (5, 9, 0, 4), (6, 6, 0, 0)):
+        p = gen.sites_random_spd(H, W, n, seed=20, capacity=cap) if cap else np.zeros((11, 0), np.float32)
+        got = _gpu_propagate(capi, oracle, p, H, W, 8, 3, 2, 5) if cap else None
+        if cap:
+            ref = oracle.propagate_fp32(p, H, W, 8, 3, 2, 5)
+            assert np.array_equal(got, ref)
+        else:
+            m = capi.empty_map(H, W, 8)
+            capi.sad_topk_seed(capi.empty_prep(0), 0, H, W, 8, m)
+            m2 = capi.empty_map(H, W, 8)
+            capi.sad_update_topk(capi.empty_prep(0), 0, H, W, 8, m, m2, 0x10000, 2, 1)
+            assert np.all(capi.ids_from_map(m2) == INV)
+
+
+def test_full_size_sampled_pixels(capi, oracle):
+    """2048x2048, 262144 random anisotropic sites, K=16, J=2: one pass from a
+    coherent map; 2048 sampled pixels checked bit-exact against the oracle."""
+    H = W = 2048
+    K, J = 16, 2
+    p = gen.sites_random_spd(H, W, 262144, seed=3000)
+    ids = gen.knn_map(p, H, W, K, seed=3001)
+    _, prep = prepare(capi, p, H, W)
+    mi = capi.map_from_ids(ids)
+    mo = capi.empty_map(H, W, K)
+    code = oracle.step_code(11, H, W)                  # jump 1 (training refresh)
+    capi.sad_update_topk(prep, p.shape[1], H, W, K, mi, mo, code, J, 99)
+    got = capi.ids_from_map(mo)
+    sample = np.random.default_rng(5).choice(H * W, 2048, replace=False)
+    ref = oracle.topk_pass_fp32(oracle.prepare_fp32(p, H, W), ids, H, W, K, code, J, 99, sample)
+    assert np.array_equal(got[sample], ref)
+    # a long jump too
+    code = oracle.step_code(2, H, W)
+    capi.sad_update_topk(prep, p.shape[1], H, W, K, mi, mo, code, J, 99)
+    ref = oracle.topk_pass_fp32(oracle.prepare_fp32(p, H, W), ids, H, W, K, code, J, 99, sample)
+    assert np.array_equal(capi.ids_from_map(mo)[sample], ref)
