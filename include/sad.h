@@ -21,13 +21,13 @@
  *    b is a per-site log isotropic metric scale, b = 0 being the paper's
  *    unit-determinant metric).  Positions and radii are in pixels; pixel
  *    (col,row) has its centre at (col+0.5, row+0.5).  A site with x < 0 is
- *    inactive (App. A.2 "Site buffer") and is skipped by every kernel.
- *  - The top-K map is K/4 planes of uint32x4 (App. A.2 "Top-K candidate
- *    list"): plane j holds, for every pixel in row-major order, the ids of
+ *    inactive (App. "Data Layout and Packing", Site buffer) and is skipped by every kernel.
+ *  - The top-K map is K/4 planes of uint32x4 (App. "Data Layout and Packing", Top-K candidate
+ *    list): plane j holds, for every pixel in row-major order, the ids of
  *    list positions 4j..4j+3, i.e. uint32[K/4][H*W][4].  Sentinel 0xffffffff.
  *    K must be 4, 8 or 16.  Lists are ordered by logit descending, ties by
  *    smaller id (for maps produced by sad_update_topk).
- *  - The prepared site table (the "pack" of App. A.2) is float32[3][capacity][4]:
+ *  - The prepared site table (the "pack" of App. "Data Layout and Packing") is float32[3][capacity][4]:
  *      plane 0 {x, y, tau*s, r}, plane 1 {G00, G01, G11, active},
  *      plane 2 {cr, cg, cb, 0},  with s = 1/max(H,W) (Sec. 4.1).
  *    Every device pointer must be 16-byte aligned.
@@ -62,7 +62,7 @@ const char* sad_last_error(void);
 int sad_abi_version(void);
 
 /*
- * sad_prepare_sites -- per-site derived table ("pack", App. A.2; metric G of
+ * sad_prepare_sites -- per-site derived table ("pack", App. "Data Layout and Packing"; metric G of
  * Sec. 4.1).  For every site i < capacity, in float32 with each operation
  * separately rounded (no fused multiply-add):
  *   s = 1/max(H,W); u = (ux,uy)/|(ux,uy)| (or (1,0) if zero);
@@ -76,7 +76,7 @@ int sad_prepare_sites(const float* params, int32_t capacity, int32_t H, int32_t 
                       float* prep, void* stream);
 
 /*
- * sad_topk_seed -- seed pass of the JFA prepass (App. A.3 "JFA prepass").
+ * sad_topk_seed -- seed pass of the JFA prepass (App. "Candidate Field and Jump Schedule", JFA prepass).
  * Fills the whole map with the sentinel, then every active site writes its id
  * into list position 0 of the pixel that contains it (floor of its position,
  * clamped to the image); on collisions the smallest id wins (deterministic).
@@ -98,8 +98,8 @@ int sad_topk_seed(const float* prep, int32_t capacity, int32_t H, int32_t W, int
  * Logits are computed in float32 without contraction:
  *   dx = px-x, dy = py-y, q = ((G00 dx)dx + 2((G01 dx)dy)) + (G11 dy)dy,
  *   n = sqrt(max(q,0)), l = (tau s)(r - n).
- * step_code: low 16 bits = pass index, high 16 bits = jump (App. A.3 "Step
- * encoding").  map_in and map_out must not overlap (Jacobi update).
+ * step_code: low 16 bits = pass index, high 16 bits = jump (App. "Candidate Field and Jump Schedule", Step
+ * encoding).  map_in and map_out must not overlap (Jacobi update).
  * Requires H*W*n_inject < 2^32 and 0 <= n_inject <= 16.
  */
 int sad_update_topk(const float* prep, int32_t capacity, int32_t H, int32_t W, int32_t K,
@@ -117,7 +117,7 @@ int sad_render(const float* prep, int32_t capacity, int32_t H, int32_t W, int32_
 
 /*
  * sad_decode_points -- random-access decode at float coordinates (the
- * render-only path with cached top-K lists, Sec. 6.7).  Query (x,y) uses the
+ * render-only path with cached top-K lists, Sec. 6.6).  Query (x,y) uses the
  * list of pixel (clamp(floor x), clamp(floor y)) and evaluates the blend of
  * Sec. 4.2 at (x,y) itself.  xy: float32[n][2]; rgb: float32[n][3].
  */
@@ -136,7 +136,7 @@ size_t sad_backward_workspace_bytes(int32_t H, int32_t W, int32_t K, int32_t cap
 
 /*
  * sad_render_backward -- adjoint of sad_render into every site parameter
- * (App. A.4 "Per-pixel gradients"), with the top-K map a frozen index set.
+ * (App. "Gradient Computation and Reduction", Per-pixel gradients), with the top-K map a frozen index set.
  * Per pixel the softmax is recomputed (nothing from the forward is stored);
  * per 16x16 tile the contributions are reduced per site in a fixed order
  * (atomic-free per-tile partials, replacing the tile hash + global atomics of

@@ -17,16 +17,16 @@ Part 1 (fp64, the definitions):
   logits            Sec. 4.1 score d_mix and Sec. 4.2 logit l_i = -tau_i d_mix
   render            Sec. 4.2 softmax weights w_i and colour c(x)
   exact_topk        Sec. 4.3: the set the propagation approximates (brute force)
-  render_backward   App. A.4 "Per-pixel gradients": adjoint of the blend
+  render_backward   App. "Gradient Computation and Reduction", Per-pixel gradients: adjoint of the blend
   removal_delta     Sec. 4.5 removal delta
   adam_step         Sec. 6.1 (Adam, clamps, re-normalised u)
 Part 2 (fp32, the top-K propagation as the kernel's precision decides it):
   exp32             Cody-Waite reduced Taylor exponential (see its docstring)
-  prepare_fp32      per-site derived table ("pack", App. A.2)
+  prepare_fp32      per-site derived table ("pack", App. "Data Layout and Packing")
   score_fp32        l_i(x) in a fixed fp32 operation order
-  jump_step         Sec. 4.3 jump schedule s_t;  step_code: App. A.3 "Step encoding"
-  splitmix64 / inject_ids   App. A.3 seeded stochastic injection (counter-based)
-  topk_seed_fp32    App. A.3 "JFA prepass" seed pass
+  jump_step         Sec. 4.3 jump schedule s_t;  step_code: App. "Candidate Field and Jump Schedule", Step encoding
+  splitmix64 / inject_ids   App. "Candidate Field and Jump Schedule" seeded stochastic injection (counter-based)
+  topk_seed_fp32    App. "Candidate Field and Jump Schedule", JFA prepass seed pass
   topk_pass_fp32    Sec. 4.3 update C_t = topK(C_{t-1} U P_t U G_t)
 """
 from __future__ import annotations
@@ -78,7 +78,7 @@ def metric(params):
 
 
 def active_mask(params):
-    """Inactive sentinel: x < 0 (App. A.2 "Site buffer")."""
+    """Inactive sentinel: x < 0 (App. "Data Layout and Packing", Site buffer)."""
     return np.asarray(params, dtype=np.float64)[PX] >= 0
 
 
@@ -197,7 +197,7 @@ def select_topk(pool_ids, ell, valid, K):
 
 
 def render_backward(params, H, W, ids, grad_rgb, px=None, py=None):
-    """Adjoint of the blend into every site parameter (App. A.4), fp64.
+    """Adjoint of the blend into every site parameter (App. "Gradient Computation and Reduction"), fp64.
 
     Given g(x) = dL/dc(x) (``grad_rgb`` [Q, 3]) and a frozen index set C(x),
     returns dL/dparams as float64[11, N] in plane order.  Per pixel, with the
@@ -410,7 +410,7 @@ def exp32(x):
 
 
 def prepare_fp32(params, H, W):
-    """Per-site derived table for scoring (App. A.2 packed candidate sites).
+    """Per-site derived table for scoring (App. "Data Layout and Packing", packed candidate sites).
 
     In float32, operation by operation:
       s = 1 / max(H, W);  nrm = sqrt(ux*ux + uy*uy);  u = (ux, uy)/nrm (or (1,0))
@@ -474,7 +474,7 @@ def jump_step(t: int, H: int, W: int) -> int:
 
 
 def step_code(t: int, H: int, W: int) -> int:
-    """32-bit step parameter: low 16 bits step index, high 16 bits jump (App. A.3)."""
+    """32-bit step parameter: low 16 bits step index, high 16 bits jump (App. "Candidate Field and Jump Schedule")."""
     return ((jump_step(t, H, W) & 0xFFFF) << 16) | (t & 0xFFFF)
 
 
@@ -498,7 +498,7 @@ def splitmix64(seed: int, counter):
 
 
 def inject_ids(seed: int, code: int, pixels, J: int, capacity: int):
-    """The J injected candidate ids of each pixel for one pass (App. A.3).
+    """The J injected candidate ids of each pixel for one pass (App. "Candidate Field and Jump Schedule").
 
     Counter = (step_code << 32) | (pixel * J + j), draw = SplitMix64 output,
     id = (draw_hi32 * capacity) >> 32 (Lemire's multiply-shift range map).
@@ -515,7 +515,7 @@ def inject_ids(seed: int, code: int, pixels, J: int, capacity: int):
 
 
 def topk_seed_fp32(prep, H, W, K):
-    """Seed pass of the JFA prepass (App. A.3): every active site writes its id
+    """Seed pass of the JFA prepass (App. "Candidate Field and Jump Schedule"): every active site writes its id
     into slot 0 of the pixel that contains it; on a collision the smaller id
     wins.  All other entries are the sentinel.  Returns uint32[P, K]."""
     out = np.full((H * W, K), INVALID, dtype=np.uint32)
@@ -577,7 +577,7 @@ def propagate_fp32(params, H, W, K, passes, J, seed, ids_in=None, t0=0):
 def topk_match_stats(approx, exact):
     """Recall (fraction of exact top-K ids present) and exact-match fraction
     (pixels whose K-sets agree), as used for Table "Top-K propagation
-    convergence" (Sec. 6.6)."""
+    convergence" (Sec. 6.5)."""
     rec, match = [], []
     for a, e in zip(approx, exact):
         ea = set(int(v) for v in e if v != INVALID)

@@ -1,6 +1,6 @@
-// Adjoint of the blend (App. A.4 "Per-pixel gradients") with an atomic-free,
+// Adjoint of the blend (App. "Gradient Computation and Reduction", Per-pixel gradients) with an atomic-free,
 // deterministic gradient reduction that replaces the per-tile hash table plus
-// global float atomics of Sec. 4.8 / Alg. "Threadgroup hash reduction".
+// global float atomics of Sec. 4.8, Alg. 1 (threadgroup hash reduction).
 //
 // Per 16x16 pixel tile (one CTA, one pixel per thread):
 //  1. forward: every pixel recomputes its max-subtracted softmax over its K
@@ -523,18 +523,19 @@ static int run_backward(const float* params, const float* prep, int cap, int H, 
     return einval("%s: null pointer", name);
   if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return einval("%s: workspace must be 256-byte aligned", name);
   if (!aligned16(map) || !aligned16(prep)) return einval("%s: pointers must be 16-byte aligned", name);
-  const WsLayout L = ws_layout(H, W, K, cap, 0);
-  if (ws_bytes < L.total) {
-    set_error("%s: workspace has %zu bytes, needs %zu", name, ws_bytes, L.total);
+  // Minimum: room for one record; any larger workspace holds as many
+  // records as fit (the default size holds H*W*K/4).
+  const WsLayout L1 = ws_layout(H, W, K, cap, 1);
+  if (ws_bytes < L1.total) {
+    set_error("%s: workspace has %zu bytes, needs at least %zu", name, ws_bytes, L1.total);
     return SAD_EWORKSPACE;
   }
-  // a caller-provided larger workspace holds proportionally more records
-  WsLayout LL = L;
-  if (ws_bytes > L.total) {
+  WsLayout LL = L1;
+  {
     const uint64_t per = sizeof(Record) + sizeof(uint64_t);
-    uint64_t mr = L.max_records + (ws_bytes - L.total) / per;
+    uint64_t mr = 1 + (ws_bytes - L1.total) / per;
     if (mr > 0xfffffff0ull) mr = 0xfffffff0ull;
-    for (int it = 0; it < 64 && mr > L.max_records; ++it, --mr) {
+    for (int it = 0; it < 64 && mr > 1; ++it, --mr) {
       const WsLayout T = ws_layout(H, W, K, cap, static_cast<int64_t>(mr));
       if (T.total <= ws_bytes) {
         LL = T;

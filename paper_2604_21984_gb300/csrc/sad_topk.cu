@@ -1,5 +1,5 @@
 // Site preparation ("pack") and the per-pixel top-K field: seed pass and one
-// propagation pass (Sec. 4.3; App. A.2-A.3).
+// propagation pass (Sec. 4.3; App. "Data Layout and Packing", "Candidate Field and Jump Schedule").
 #include "sad_device.cuh"
 #include "sad_host.h"
 

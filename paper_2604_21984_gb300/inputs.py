@@ -13,10 +13,10 @@ Site parameters use the 11-plane structure-of-arrays layout of the C-ABI
 Positions and radii are in pixels; pixel (col, row) has its centre at
 (col + 0.5, row + 0.5).  ``b`` is a log isotropic metric scale (b = 0 gives the
 unit-determinant metric of the paper's site representation, Sec. 4.1).
-An inactive site has x < 0 (the paper stores (-1, -1), App. A.2 "Site buffer").
+An inactive site has x < 0 (the paper stores (-1, -1), App. "Data Layout and Packing", Site buffer).
 
 Index maps are ``uint32[P, K]`` (pixel-major, P = H*W, row-major pixels) with
-the invalid sentinel 0xffffffff (App. A.2 "Top-K candidate list").
+the invalid sentinel 0xffffffff (App. "Data Layout and Packing", Top-K candidate list).
 """
 from __future__ import annotations
 

@@ -62,6 +62,7 @@ def test_bad_arguments_rejected_on_host(L):
     assert L.sad_render(ctypes.c_void_p(260), 10, 8, 8, 8, p, p, None) == 1   # misaligned prep
     assert L.sad_decode_points(p, 10, 8, 8, 8, p, p, -1, p, None) == 1
     assert L.sad_render_backward(p, p, 10, 8, 8, 8, p, p, p, p, 16, None) == 3  # workspace too small
+    assert b"at least" in L.sad_last_error()
     assert L.sad_adam_step(p, p, p, p, 10, 8, 8, 0, None, None) == 1
 
 

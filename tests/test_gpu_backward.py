@@ -1,4 +1,4 @@
-"""GPU adjoint (App. A.4) vs the oracle's fp64 adjoint: gradients within 1e-4
+"""GPU adjoint (App. "Gradient Computation and Reduction") vs the oracle's fp64 adjoint: gradients within 1e-4
 norm-relative per parameter plane (floor 1e-4 max|grad|); bitwise determinism;
 the fused MSE training gradient and loss."""
 import numpy as np

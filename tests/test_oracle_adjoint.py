@@ -1,4 +1,4 @@
-"""Pins of the oracle adjoint (App. A.4 "Per-pixel gradients") and removal
+"""Pins of the oracle adjoint (App. "Gradient Computation and Reduction", Per-pixel gradients) and removal
 delta (Sec. 4.5) against central finite differences and brute force.  CPU."""
 import math
 

@@ -1,4 +1,4 @@
-"""Pins of the oracle's fp32 top-K propagation (Sec. 4.3, App. A.3).  CPU."""
+"""Pins of the oracle's fp32 top-K propagation (Sec. 4.3, App. "Candidate Field and Jump Schedule").  CPU."""
 import math
 import os
 
@@ -167,7 +167,7 @@ def test_few_sites_reach_exact_topk(oracle):
 
 
 def test_convergence_like_paper_table(oracle):
-    """Scaled-down rerun of Sec. 6.6's experiment: sites in unique pixel cells
+    """Scaled-down rerun of Sec. 6.5's experiment: sites in unique pixel cells
     with sub-pixel offsets, K=8, J=4; exact-match rises with passes and is high
     at low density (paper: 0.96-0.99 at 16k sites on 1024^2 / 2048^2)."""
     table = [l.split() for l in open(os.path.join(GOLDEN, "topk_convergence_table.txt"))
