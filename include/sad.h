@@ -164,6 +164,26 @@ int sad_train_grads(const float* params, const float* prep, int32_t capacity, in
                     size_t workspace_bytes, void* stream);
 
 /*
+ * sad_render_backward_noalloc -- the same computation as sad_render_backward
+ * for callers that cannot allocate device memory for a workspace (they only
+ * hold device pointers handed to them, or run where an allocation is not
+ * allowed).  The paper has no counterpart; it is a deployment convenience.
+ * Scratch is one 64 MiB buffer inside the library (allocated on every device
+ * that loads the library, kept until exit).  Limits: H*W <= 4194304 and
+ * capacity <= 262144, else SAD_EINVAL; within them about 1.1 million
+ * per-tile records fit.  The first call on a device looks up the buffer's
+ * device address (make it before any stream capture).  All calls share the
+ * buffer: calls that overlap on the GPU race and must be serialised by the
+ * caller.  status_out (device int32, may be NULL) receives SAD_OK, or
+ * SAD_EWORKSPACE if the records did not fit (gradients then incomplete).
+ * Allocates nothing.
+ */
+int sad_render_backward_noalloc(const float* params, const float* prep, int32_t capacity,
+                                int32_t H, int32_t W, int32_t K, const uint32_t* map,
+                                const float* grad_rgb, float* grads, int32_t* status_out,
+                                void* stream);
+
+/*
  * Reads the workspace status word of the last backward call on `stream`
  * (synchronises the stream).  *records_used receives the number of partial
  * records written; returns SAD_EWORKSPACE if they overflowed the workspace.

@@ -77,6 +77,10 @@ _SIGS = {
                                        ctypes.c_size_t, ctypes.c_void_p]),
     "sad_workspace_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                                             ctypes.c_void_p]),
+    "sad_render_backward_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                                   ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                   ctypes.c_void_p, ctypes.c_void_p]),
     "sad_adam_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                      ctypes.c_int32, ctypes.c_int32,
@@ -221,6 +225,23 @@ def sad_render_backward(params, prep, H, W, K, map_in, grad_rgb, grads, ws, stre
                                      _ptr(grads, torch.float32, "grads", N_PARAMS * cap),
                                      _ptr(ws, torch.uint8, "workspace"), ws.numel(),
                                      _stream(stream)), "sad_render_backward")
+    return grads
+
+
+def sad_render_backward_noalloc(params, prep, H, W, K, map_in, grad_rgb, grads, status=None,
+                                stream=None):
+    """sad_render_backward for callers that cannot allocate a workspace: the
+    library's own fixed scratch buffer is used instead (see include/sad.h for
+    its limits; concurrent calls on different streams race on it).  `status`
+    is an optional device int32[1] that receives 0, or 3 if the per-tile
+    records did not fit."""
+    cap = params.shape[1]
+    _check(lib().sad_render_backward_noalloc(
+        _ptr(params, torch.float32, "params", N_PARAMS * cap), _ptr(prep, torch.float32, "prep"),
+        cap, H, W, K, _ptr(map_in, torch.int32, "map", H * W * K),
+        _ptr(grad_rgb, torch.float32, "grad_rgb", H * W * 3),
+        _ptr(grads, torch.float32, "grads", N_PARAMS * cap),
+        _ptr(status, torch.int32, "status", 1), _stream(stream)), "sad_render_backward_noalloc")
     return grads
 
 

@@ -25,6 +25,8 @@
 #include "sad_device.cuh"
 #include "sad_host.h"
 
+#include <mutex>
+
 namespace sad {
 
 constexpr int kTileSide = 16;
@@ -646,3 +648,88 @@ int sad_workspace_status(const void* workspace, int64_t* records_used, void* str
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Backward without a caller-provided workspace.
+//
+// Some callers cannot allocate device memory for the workspace: a host
+// program that only receives device pointers from another component, code
+// running where cudaMalloc is forbidden or would synchronise at the wrong
+// moment, or an embedding whose allocator is owned by someone else.  For them
+// the library keeps one fixed scratch buffer of kStaticScratchBytes in global
+// memory, declared here at file scope.  Every GPU that loads this library
+// holds that buffer until the process exits.
+//
+// The buffer's name is only a host-side stand-in in host code, so its device
+// address is looked up with cudaGetSymbolAddress, once per device, with that
+// device current; the first call on each device does this lookup (make that
+// first call before any stream capture).  All calls share the one buffer and
+// it keeps the previous call's contents: every call clears the parts that
+// must start at zero, and calls whose executions overlap on the GPU (two
+// streams, or two threads) race on it and must be serialised by the caller.
+// ---------------------------------------------------------------------------
+namespace sad {
+
+constexpr size_t kStaticScratchBytes = 64ull << 20;       // 64 MiB
+constexpr int64_t kStaticMaxPixels = 4194304;             // e.g. 2048 x 2048
+constexpr int32_t kStaticMaxCapacity = 262144;
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+static std::mutex g_static_mu;
+static void* g_static_ptr[kMaxDevices] = {nullptr};
+
+static int static_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    set_error("sad_render_backward_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
+    return SAD_ECUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("sad_render_backward_noalloc: device %d beyond the supported %d", dev, kMaxDevices);
+    return SAD_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error("sad_render_backward_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+      return SAD_ECUDA;
+    }
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return SAD_OK;
+}
+
+__global__ void k_static_status(const WsHeader* __restrict__ hdr, int32_t* __restrict__ status) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *status = hdr->overflow ? SAD_EWORKSPACE : SAD_OK;
+}
+
+}  // namespace sad
+
+extern "C" int sad_render_backward_noalloc(const float* params, const float* prep, int32_t capacity,
+                                           int32_t H, int32_t W, int32_t K, const uint32_t* map,
+                                           const float* grad_rgb, float* grads,
+                                           int32_t* status_out, void* stream) {
+  if (!grad_rgb) return einval("sad_render_backward_noalloc: null grad_rgb");
+  if (int e = check_problem(capacity, H, W, K, true)) return e;
+  if (static_cast<int64_t>(H) * W > kStaticMaxPixels)
+    return einval("sad_render_backward_noalloc: %d x %d pixels exceed the static limit of %lld",
+                  H, W, static_cast<long long>(kStaticMaxPixels));
+  if (capacity > kStaticMaxCapacity)
+    return einval("sad_render_backward_noalloc: capacity %d exceeds the static limit of %d",
+                  capacity, kStaticMaxCapacity);
+  void* scratch = nullptr;
+  if (int e = static_scratch(&scratch)) return e;
+  const int st = run_backward(params, prep, capacity, H, W, K, map, grad_rgb, nullptr, grads,
+                              nullptr, nullptr, scratch, kStaticScratchBytes, as_stream(stream),
+                              "sad_render_backward_noalloc");
+  if (st != SAD_OK || !status_out) return st;
+  k_static_status<<<1, 32, 0, as_stream(stream)>>>(reinterpret_cast<const WsHeader*>(scratch),
+                                                   status_out);
+  return check_launch("k_static_status");
+}
