@@ -54,78 +54,97 @@ __global__ void k_seed(const float4* __restrict__ geo, const float4* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// one propagation pass.  One thread per pixel keeps the K best (logit, id)
-// pairs sorted in registers; candidates already in the list are skipped
-// before scoring (a duplicate has an identical key).
+// one propagation pass.
+//
+// Candidate keys: (logit, id) packed into one 64-bit integer whose unsigned
+// order is the list order (logit descending, then id ascending):
+//   key = orderable(logit) << 32 | ~id,
+// with orderable() the usual sign-flip map of IEEE floats (-0 is first turned
+// into +0 so that the two zeros tie, as they do in float comparison).  The
+// empty entry is key 0, below every real candidate.
+//
+// Per pixel (one thread):
+//  A. score the pixel's own list (independent gathers) and sort it with a
+//     bitonic network; drop duplicate ids (only possible in a damaged input);
+//  B. filter the 4 neighbour lists and the J injected ids against the list
+//     and queue the novel ids in shared memory (per-thread column);
+//  C. each thread scores its own queue and inserts winners.
+// Phase C runs per lane, so the insertion network is paid for the queued
+// candidates only, not for every candidate of every lane in the warp.
 // ---------------------------------------------------------------------------
-template <int K>
-struct TopK {
-  float l[K];
-  uint32_t id[K];
+constexpr int kUpdThreads = 256;
+constexpr int kQueue = 24;
 
-  __device__ __forceinline__ void init() {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      l[k] = -INFINITY;
-      id[k] = kInvalid;
-    }
-  }
-  __device__ __forceinline__ bool contains(uint32_t c) const {
-    bool hit = false;
-#pragma unroll
-    for (int k = 0; k < K; ++k) hit |= (id[k] == c);
-    return hit;
-  }
-  // Insert (cl, cid) known to precede the last entry and not to be present.
-  __device__ __forceinline__ void insert(float cl, uint32_t cid) {
-#pragma unroll
-    for (int k = K - 1; k > 0; --k) {
-      const bool shift = key_before(cl, cid, l[k - 1], id[k - 1]);
-      const bool here = !shift && key_before(cl, cid, l[k], id[k]);
-      const float nl = shift ? l[k - 1] : (here ? cl : l[k]);
-      const uint32_t ni = shift ? id[k - 1] : (here ? cid : id[k]);
-      l[k] = nl;
-      id[k] = ni;
-    }
-    if (key_before(cl, cid, l[0], id[0])) {
-      l[0] = cl;
-      id[0] = cid;
-    }
-  }
-};
+__device__ __forceinline__ uint64_t make_key(float l, uint32_t id) {
+  uint32_t u = __float_as_uint(__fadd_rn(l, 0.0f));
+  u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+  return (static_cast<uint64_t>(u) << 32) | static_cast<uint64_t>(~id);
+}
+
+__device__ __forceinline__ uint32_t key_id(uint64_t k) { return ~static_cast<uint32_t>(k); }
 
 template <int K>
-__device__ __forceinline__ void consider(TopK<K>& tk, uint32_t cid, uint32_t ucap, float px,
-                                         float py, const float4* __restrict__ geo,
-                                         const float4* __restrict__ met) {
-  if (cid >= ucap) return;  // also rejects the sentinel
-  if (tk.contains(cid)) return;
-  const float4 m = ldg(&met[cid]);
-  if (m.w == 0.f) return;
-  const float4 g = ldg(&geo[cid]);
-  const float l = score_exact(px, py, g, m);
-  if (l != l) return;  // NaN
-  if (!key_before(l, cid, tk.l[K - 1], tk.id[K - 1])) return;
-  tk.insert(l, cid);
+__device__ __forceinline__ void bitonic_sort_desc(uint64_t (&v)[K]) {
+#pragma unroll
+  for (int k = 2; k <= K; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        const int l = i ^ j;
+        if (l > i) {
+          const bool desc = (i & k) == 0;
+          const uint64_t a = v[i], b = v[l];
+          const bool sw = desc ? (a < b) : (a > b);
+          v[i] = sw ? b : a;
+          v[l] = sw ? a : b;
+        }
+      }
+    }
+  }
 }
 
 template <int K>
-__device__ __forceinline__ void consider4(TopK<K>& tk, uint4 v, uint32_t ucap, float px, float py,
-                                          const float4* __restrict__ geo,
-                                          const float4* __restrict__ met) {
-  consider<K>(tk, v.x, ucap, px, py, geo, met);
-  consider<K>(tk, v.y, ucap, px, py, geo, met);
-  consider<K>(tk, v.z, ucap, px, py, geo, met);
-  consider<K>(tk, v.w, ucap, px, py, geo, met);
+__device__ __forceinline__ bool list_has(const uint64_t (&v)[K], uint32_t id) {
+  const uint32_t nid = ~id;
+  bool hit = false;
+#pragma unroll
+  for (int k = 0; k < K; ++k) hit |= (static_cast<uint32_t>(v[k]) == nid);
+  return hit;
+}
+
+// Insert key c (greater than v[K-1], id not present) keeping v sorted.
+template <int K>
+__device__ __forceinline__ void list_insert(uint64_t (&v)[K], uint64_t c) {
+  bool gt[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) gt[k] = c > v[k];
+#pragma unroll
+  for (int k = K - 1; k > 0; --k) v[k] = gt[k - 1] ? v[k - 1] : (gt[k] ? c : v[k]);
+  v[0] = gt[0] ? c : v[0];
+}
+
+// Logit key of candidate id at (px, py), or 0 if the id cannot enter.
+__device__ __forceinline__ uint64_t cand_key(uint32_t id, uint32_t ucap, float px, float py,
+                                             const float4* __restrict__ geo,
+                                             const float4* __restrict__ met) {
+  if (id >= ucap) return 0ull;
+  const float4 m = ldg(&met[id]);
+  if (m.w == 0.f) return 0ull;
+  const float l = score_exact(px, py, ldg(&geo[id]), m);
+  if (l != l) return 0ull;
+  return make_key(l, id);
 }
 
 template <int K>
-__global__ void __launch_bounds__(256) k_topk_update(const float4* __restrict__ geo,
-                                                     const float4* __restrict__ met, int cap,
-                                                     int H, int W,
-                                                     const uint4* __restrict__ map_in,
-                                                     uint4* __restrict__ map_out, uint32_t code,
-                                                     int J, uint64_t seed) {
+__global__ void __launch_bounds__(kUpdThreads) k_topk_update(const float4* __restrict__ geo,
+                                                             const float4* __restrict__ met, int cap,
+                                                             int H, int W,
+                                                             const uint4* __restrict__ map_in,
+                                                             uint4* __restrict__ map_out,
+                                                             uint32_t code, int J, uint64_t seed) {
+  __shared__ uint32_t s_q[kQueue][kUpdThreads];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int col = blockIdx.x * blockDim.x + threadIdx.x;
   const int row = blockIdx.y * blockDim.y + threadIdx.y;
   if (col >= W || row >= H) return;
@@ -134,11 +153,50 @@ __global__ void __launch_bounds__(256) k_topk_update(const float4* __restrict__ 
   const uint32_t ucap = static_cast<uint32_t>(cap);
   const float px = __fadd_rn(static_cast<float>(col), 0.5f);
   const float py = __fadd_rn(static_cast<float>(row), 0.5f);
-  TopK<K> tk;
-  tk.init();
   constexpr int NP = K / 4;
+
+  // A. own list
+  uint64_t v[K];
 #pragma unroll
-  for (int j = 0; j < NP; ++j) consider4<K>(tk, ldg(&map_in[j * P + q]), ucap, px, py, geo, met);
+  for (int j = 0; j < NP; ++j) {
+    const uint4 w = ldg(&map_in[j * P + q]);
+    v[4 * j] = cand_key(w.x, ucap, px, py, geo, met);
+    v[4 * j + 1] = cand_key(w.y, ucap, px, py, geo, met);
+    v[4 * j + 2] = cand_key(w.z, ucap, px, py, geo, met);
+    v[4 * j + 3] = cand_key(w.w, ucap, px, py, geo, met);
+  }
+  bitonic_sort_desc<K>(v);
+  bool dup = false;
+#pragma unroll
+  for (int k = 1; k < K; ++k) {
+    const bool d = v[k] != 0ull && v[k] == v[k - 1];
+    dup |= d;
+  }
+  if (dup) {  // damaged input list: zero repeated keys, re-sort
+#pragma unroll
+    for (int k = K - 1; k > 0; --k)
+      if (v[k] != 0ull && v[k] == v[k - 1]) v[k] = 0ull;
+    bitonic_sort_desc<K>(v);
+  }
+
+  // B + C. queue novel candidates; drain the queue when full and at the end
+  int qn = 0;
+  auto drain = [&]() {
+    for (int i = 0; i < qn; ++i) {
+      const uint32_t id = s_q[i][tid];
+      if (list_has<K>(v, id)) continue;
+      const uint64_t c = cand_key(id, ucap, px, py, geo, met);
+      if (c > v[K - 1]) list_insert<K>(v, c);
+    }
+    qn = 0;
+  };
+  auto offer = [&](uint32_t id) {
+    if (id >= ucap || list_has<K>(v, id)) return;
+    for (int i = 0; i < qn; ++i)
+      if (s_q[i][tid] == id) return;
+    if (qn == kQueue) drain();
+    s_q[qn++][tid] = id;
+  };
   const int s = static_cast<int>(code >> 16);
   const int nc[4] = {col - s, col + s, col, col};
   const int nr[4] = {row, row, row - s, row + s};
@@ -147,18 +205,25 @@ __global__ void __launch_bounds__(256) k_topk_update(const float4* __restrict__ 
     if (nc[d] < 0 || nc[d] >= W || nr[d] < 0 || nr[d] >= H) continue;
     const size_t nq = static_cast<size_t>(nr[d]) * W + nc[d];
 #pragma unroll
-    for (int j = 0; j < NP; ++j) consider4<K>(tk, ldg(&map_in[j * P + nq]), ucap, px, py, geo, met);
+    for (int j = 0; j < NP; ++j) {
+      const uint4 w = ldg(&map_in[j * P + nq]);
+      offer(w.x);
+      offer(w.y);
+      offer(w.z);
+      offer(w.w);
+    }
   }
   const uint64_t base = (static_cast<uint64_t>(code) << 32);
   for (int j = 0; j < J; ++j) {
     const uint64_t ctr = base | static_cast<uint32_t>(q * static_cast<uint32_t>(J) + j);
     const uint64_t h = splitmix64_at(seed, ctr);
-    const uint32_t cid = static_cast<uint32_t>(((h >> 32) * static_cast<uint64_t>(ucap)) >> 32);
-    consider<K>(tk, cid, ucap, px, py, geo, met);
+    offer(static_cast<uint32_t>(((h >> 32) * static_cast<uint64_t>(ucap)) >> 32));
   }
+  drain();
 #pragma unroll
   for (int j = 0; j < NP; ++j)
-    map_out[j * P + q] = make_uint4(tk.id[4 * j], tk.id[4 * j + 1], tk.id[4 * j + 2], tk.id[4 * j + 3]);
+    map_out[j * P + q] = make_uint4(key_id(v[4 * j]), key_id(v[4 * j + 1]), key_id(v[4 * j + 2]),
+                                    key_id(v[4 * j + 3]));
 }
 
 }  // namespace sad
