@@ -11,10 +11,10 @@
 //     multiplicative hash, linear probing); each warp records, per slot, the
 //     bitmask of its 32 pixels that list the site (__match_any_sync, no
 //     atomics: a warp owns its mask word);
-//  3. the masks give each slot a stable, pixel-ordered pair list; the lists
-//     are cut into chunks of kChunk pairs, each chunk summed by one thread in
-//     list order, and each slot's chunks summed in chunk order, giving ten
-//     sufficient statistics per (site, tile):
+//  3. the masks give each slot a stable, pixel-ordered pair list; one warp
+//     walks a slot's list 32 pairs at a time with the site's parameters in
+//     registers (lane i takes pairs i, i+32, ...) and a fixed butterfly sums
+//     the lane partials, giving ten sufficient statistics per (site, tile):
 //       sum w g (3),  sum d,  sum d n,  sum d dx/n,  sum d dy/n,
 //       sum d dx^2/n, sum d dx dy/n, sum d dy^2/n,   d = dL/dl = w g.(c_k - cbar)
 //     written as one partial record per (site, tile).  If the table fills,
@@ -31,7 +31,6 @@ namespace sad {
 
 constexpr int kTileSide = 16;
 constexpr int kTileThreads = kTileSide * kTileSide;
-constexpr int kChunk = 16;
 constexpr int kSlots = 128;  // shared hash table size per round (power of 2)
 constexpr int kLog2Slots = 7;
 constexpr uint32_t kNone = 0xffffffffu;
@@ -131,27 +130,24 @@ __device__ __forceinline__ uint32_t probe_slot(uint32_t id, uint32_t* keys) {
 // per-tile kernel
 // ---------------------------------------------------------------------------
 template <int K>
-__global__ void __launch_bounds__(kTileThreads) k_bwd_tile(
+__global__ void __launch_bounds__(kTileThreads, 4) k_bwd_tile(
     const float4* __restrict__ geo, const float4* __restrict__ met,
     const float4* __restrict__ col, int cap, int H, int W, const uint4* __restrict__ map,
     const float* __restrict__ grad_rgb, const float* __restrict__ target, float two_over_P,
     float* __restrict__ rgb_out, float* __restrict__ tile_loss, Record* __restrict__ records,
     uint32_t max_records, WsHeader* __restrict__ hdr) {
-  constexpr int kMaxChunks = kTileThreads * K / kChunk + kSlots;
+  constexpr int kWarps = kTileThreads / 32;
   __shared__ uint32_t s_keys[kSlots];
-  __shared__ uint32_t s_mask[kSlots][8];
-  __shared__ uint16_t s_wpre[kSlots][8];
+  __shared__ uint32_t s_mask[kWarps][kSlots];   // [warp word][slot]: conflict-free per-slot reads
+  __shared__ uint16_t s_wpre[kWarps][kSlots];
   __shared__ uint32_t s_cnt[kSlots];
   __shared__ uint32_t s_off[kSlots];
-  __shared__ uint32_t s_choff[kSlots + 1];
   __shared__ uint32_t s_rix[kSlots];
-  __shared__ uint8_t s_chslot[kMaxChunks];
   __shared__ uint8_t s_list[kTileThreads * K];
-  __shared__ float4 s_pa[kTileThreads];
-  __shared__ float4 s_pb[kTileThreads];
-  __shared__ float s_part[kMaxChunks][10];
-  __shared__ uint64_t s_scan[kTileThreads / 32];
-  __shared__ float s_red[kTileThreads / 32];
+  __shared__ float4 s_pa[kTileThreads];   // {m, 1/Z, g.cbar, gx}
+  __shared__ float2 s_pb[kTileThreads];   // {gy, gz}
+  __shared__ uint64_t s_scan[kWarps];
+  __shared__ float s_red[kWarps];
   __shared__ uint32_t s_base;
 
   const int t = threadIdx.x;
@@ -228,8 +224,8 @@ __global__ void __launch_bounds__(kTileThreads) k_bwd_tile(
       rgb_out[3 * q + 2] = cb.z;
     }
   }
-  s_pa[t] = make_float4(m, iz, cb.x, cb.y);
-  s_pb[t] = make_float4(cb.z, g.x, g.y, g.z);
+  s_pa[t] = make_float4(m, iz, g.x * cb.x + g.y * cb.y + g.z * cb.z, g.x);
+  s_pb[t] = make_float2(g.y, g.z);
   if (tile_loss) {  // deterministic tile sum of the per-pixel squared error
     float v = lpx;
 #pragma unroll
@@ -237,13 +233,13 @@ __global__ void __launch_bounds__(kTileThreads) k_bwd_tile(
     if (lane == 0) s_red[warp] = v;
     __syncthreads();
     if (t == 0) {
-      float s = 0.f;
-      for (int w = 0; w < kTileThreads / 32; ++w) s += s_red[w];
-      tile_loss[tile] = s;
+      float sum = 0.f;
+      for (int w = 0; w < kWarps; ++w) sum += s_red[w];
+      tile_loss[tile] = sum;
     }
   }
 
-  // ---- 2..3. rounds of slot assignment and ordered reduction ------------
+  // ---- 2..3. rounds: slot assignment, stable pair lists, warp per slot ---
   uint32_t pending = vm;
   uint32_t slot[K];
   const uint32_t lt_mask = (1u << lane) - 1u;
@@ -251,7 +247,7 @@ __global__ void __launch_bounds__(kTileThreads) k_bwd_tile(
     for (int i = t; i < kSlots; i += kTileThreads) {
       s_keys[i] = kInvalid;
 #pragma unroll
-      for (int w = 0; w < 8; ++w) s_mask[i][w] = 0u;
+      for (int w = 0; w < kWarps; ++w) s_mask[w][i] = 0u;
     }
     __syncthreads();
 #pragma unroll
@@ -263,101 +259,87 @@ __global__ void __launch_bounds__(kTileThreads) k_bwd_tile(
       }
       slot[k] = sl;
       const uint32_t peers = __match_any_sync(0xffffffffu, sl);
-      if (sl != kNone && lane == __ffs(peers) - 1) s_mask[sl][warp] |= peers;
+      if (sl != kNone && lane == __ffs(peers) - 1) s_mask[warp][sl] |= peers;
     }
     __syncthreads();
     uint64_t packed = 0;
     if (t < kSlots && s_keys[t] != kInvalid) {
       uint32_t c = 0;
 #pragma unroll
-      for (int w = 0; w < 8; ++w) {
-        s_wpre[t][w] = static_cast<uint16_t>(c);
-        c += __popc(s_mask[t][w]);
+      for (int w = 0; w < kWarps; ++w) {
+        s_wpre[w][t] = static_cast<uint16_t>(c);
+        c += __popc(s_mask[w][t]);
       }
-      const uint32_t nch = (c + kChunk - 1) / kChunk;
-      packed = static_cast<uint64_t>(c) | (static_cast<uint64_t>(nch) << 20) | (1ull << 40);
+      packed = static_cast<uint64_t>(c) | (1ull << 32);
     }
     uint64_t total;
     const uint64_t ex = block_excl_scan256(packed, s_scan, total);
     if (t < kSlots) {
-      s_cnt[t] = static_cast<uint32_t>(packed & 0xfffffu);
-      s_off[t] = static_cast<uint32_t>(ex & 0xfffffu);
-      s_choff[t] = static_cast<uint32_t>((ex >> 20) & 0xfffffu);
-      s_rix[t] = static_cast<uint32_t>(ex >> 40);
+      s_cnt[t] = static_cast<uint32_t>(packed & 0xffffffffu);
+      s_off[t] = static_cast<uint32_t>(ex & 0xffffffffu);
+      s_rix[t] = static_cast<uint32_t>(ex >> 32);
     }
-    const uint32_t n_chunks = static_cast<uint32_t>((total >> 20) & 0xfffffu);
-    const uint32_t n_used = static_cast<uint32_t>(total >> 40);
-    if (t == 0) {
-      s_choff[kSlots] = n_chunks;
-      s_base = atomicAdd(&hdr->cursor, n_used);
-    }
+    if (t == 0) s_base = atomicAdd(&hdr->cursor, static_cast<uint32_t>(total >> 32));
     __syncthreads();
-    if (t < kSlots && s_cnt[t] > 0) {
-      const uint32_t c0 = s_choff[t], nch = (s_cnt[t] + kChunk - 1) / kChunk;
-      for (uint32_t c = 0; c < nch; ++c) s_chslot[c0 + c] = static_cast<uint8_t>(t);
-    }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const uint32_t sl = slot[k];
       if (sl != kNone) {
-        const uint32_t pos = s_off[sl] + s_wpre[sl][warp] + __popc(s_mask[sl][warp] & lt_mask);
+        const uint32_t pos = s_off[sl] + s_wpre[warp][sl] + __popc(s_mask[warp][sl] & lt_mask);
         s_list[pos] = static_cast<uint8_t>(t);
       }
     }
     __syncthreads();
-    for (uint32_t c = t; c < n_chunks; c += kTileThreads) {
-      const uint32_t sl = s_chslot[c];
+    // one warp per slot: lanes walk the slot's pixel-ordered pairs, then a
+    // fixed butterfly sums the 32 lane partials (deterministic order)
+    for (int sl = warp; sl < kSlots; sl += kWarps) {
+      const uint32_t cnt = s_cnt[sl];
+      if (cnt == 0) continue;
       const uint32_t id = s_keys[sl];
-      const uint32_t first = (c - s_choff[sl]) * kChunk;
-      const uint32_t len = min(static_cast<uint32_t>(kChunk), s_cnt[sl] - first);
-      const uint32_t start = s_off[sl] + first;
+      const uint32_t off = s_off[sl];
       const float4 gs = ldg(&geo[id]), ms = ldg(&met[id]), cs = ldg(&col[id]);
       float acc[10];
 #pragma unroll
       for (int j = 0; j < 10; ++j) acc[j] = 0.f;
-      for (uint32_t i = 0; i < len; ++i) {
-        const uint32_t p = s_list[start + i];
-        const float4 A = s_pa[p], B = s_pb[p];
-        const float qx = x0 + static_cast<int>(p & (kTileSide - 1)) + 0.5f;
-        const float qy = y0 + static_cast<int>(p >> 4) + 0.5f;
-        const ScoreParts sp = score_fast(qx, qy, gs, ms);
-        const float w = __expf(sp.l - A.x) * A.y;
-        const float d = w * (B.y * (cs.x - A.z) + B.z * (cs.y - A.w) + B.w * (cs.z - B.x));
-        acc[0] += w * B.y;
-        acc[1] += w * B.z;
-        acc[2] += w * B.w;
+      for (uint32_t i = lane; i < cnt; i += 32) {
+        const uint32_t p = s_list[off + i];
+        const float4 A = s_pa[p];
+        const float2 B = s_pb[p];
+        const float dx = (x0 + static_cast<int>(p & (kTileSide - 1)) + 0.5f) - gs.x;
+        const float dy = (y0 + static_cast<int>(p >> 4) + 0.5f) - gs.y;
+        const float qq = ms.x * dx * dx + 2.f * ms.y * dx * dy + ms.z * dy * dy;
+        const float n = sqrtf(fmaxf(qq, 0.f));
+        const float w = __expf(gs.z * (gs.w - n) - A.x) * A.y;
+        const float d = w * (A.w * cs.x + B.x * cs.y + B.y * cs.z - A.z);
+        acc[0] += w * A.w;
+        acc[1] += w * B.x;
+        acc[2] += w * B.y;
         acc[3] += d;
-        acc[4] += d * sp.n;
-        if (sp.n > 0.f) {
-          const float a = d / sp.n;
-          acc[5] += a * sp.dx;
-          acc[6] += a * sp.dy;
-          acc[7] += a * sp.dx * sp.dx;
-          acc[8] += a * sp.dx * sp.dy;
-          acc[9] += a * sp.dy * sp.dy;
+        acc[4] += d * n;
+        if (n > 0.f) {
+          const float a = d / n;
+          acc[5] += a * dx;
+          acc[6] += a * dy;
+          acc[7] += a * dx * dx;
+          acc[8] += a * dx * dy;
+          acc[9] += a * dy * dy;
         }
       }
 #pragma unroll
-      for (int j = 0; j < 10; ++j) s_part[c][j] = acc[j];
-    }
-    __syncthreads();
-    if (t < kSlots && s_cnt[t] > 0) {
-      float acc[10];
+      for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-      for (int j = 0; j < 10; ++j) acc[j] = 0.f;
-      const uint32_t c0 = s_choff[t], nch = (s_cnt[t] + kChunk - 1) / kChunk;
-      for (uint32_t c = c0; c < c0 + nch; ++c) {
-#pragma unroll
-        for (int j = 0; j < 10; ++j) acc[j] += s_part[c][j];
+        for (int j = 0; j < 10; ++j) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
       }
-      const uint32_t ridx = s_base + s_rix[t];
-      if (ridx < max_records) {
-        float4* dst = reinterpret_cast<float4*>(&records[ridx]);
-        dst[0] = make_float4(__uint_as_float(s_keys[t]), __uint_as_float(tile), acc[0], acc[1]);
-        dst[1] = make_float4(acc[2], acc[3], acc[4], acc[5]);
-        dst[2] = make_float4(acc[6], acc[7], acc[8], acc[9]);
-      } else {
-        hdr->overflow = 1u;
+      if (lane == 0) {
+        const uint32_t ridx = s_base + s_rix[sl];
+        if (ridx < max_records) {
+          float4* dst = reinterpret_cast<float4*>(&records[ridx]);
+          dst[0] = make_float4(__uint_as_float(id), __uint_as_float(tile), acc[0], acc[1]);
+          dst[1] = make_float4(acc[2], acc[3], acc[4], acc[5]);
+          dst[2] = make_float4(acc[6], acc[7], acc[8], acc[9]);
+        } else {
+          hdr->overflow = 1u;
+        }
       }
     }
     if (!__syncthreads_or(pending != 0u)) break;
