@@ -585,3 +585,134 @@ def topk_match_stats(approx, exact):
         rec.append(len(ea & aa) / max(len(ea), 1))
         match.append(ea == aa)
     return float(np.mean(rec)), float(np.mean(match))
+
+
+# =============================================================================
+# Part 3: gradient-weighted initialisation (Sec. 4.4), decided in fp32
+# =============================================================================
+
+_LN2_HI_L = F32(45426.0 / 65536.0)
+_LN2_LO_L = F32(math.log(2.0) - 45426.0 / 65536.0)
+_SQRT2 = F32(float.fromhex("0x1.6a09e6p+0"))      # sqrt(2) rounded to float32
+_INV_ODD = [F32(float.fromhex(h)) for h in ("0x1.555556p-2",   # 1/3
+                                              "0x1.99999ap-3",   # 1/5
+                                              "0x1.24924ap-3",   # 1/7
+                                              "0x1.c71c72p-4")]  # 1/9
+
+
+def log32(x):
+    """Reproducible float32 natural log of positive normal x, every step a
+    rounded fp32 op.  Published method (Cody & Waite 1980): x = 2^e m with
+    m in [sqrt(1/2), sqrt(2)), s = (m-1)/(m+1), log m = 2 atanh(s) =
+    2s + 2s (s^2/3 + s^4/5 + s^6/7 + s^8/9) by Horner in s^2, and
+    log x = e ln2_hi + (e ln2_lo + log m) with ln 2 split at 2^-16."""
+    x = np.asarray(x, dtype=F32)
+    bits = x.view(np.uint32).astype(np.int64)
+    e = ((bits >> 23) & 0xFF) - 127
+    m = ((bits & 0x7FFFFF) | (127 << 23)).astype(np.uint32).view(F32)
+    big = m > _SQRT2
+    m = np.where(big, (m * F32(0.5)).astype(F32), m).astype(F32)
+    e = np.where(big, e + 1, e)
+    ef = e.astype(F32)
+    s = ((m - F32(1)).astype(F32) / (m + F32(1)).astype(F32)).astype(F32)
+    s2 = (s * s).astype(F32)
+    p = _INV_ODD[3]
+    for c in (_INV_ODD[2], _INV_ODD[1], _INV_ODD[0]):
+        p = ((p * s2).astype(F32) + c).astype(F32)
+    p = (p * s2).astype(F32)
+    s2x = (s + s).astype(F32)
+    lm = (s2x + (s2x * p).astype(F32)).astype(F32)
+    return ((ef * _LN2_HI_L).astype(F32) + ((ef * _LN2_LO_L).astype(F32) + lm).astype(F32)).astype(F32)
+
+
+def grad_magnitude_fp32(img):
+    """|grad I|_2 over the three channels with central differences (one-sided
+    at the borders, zero across a single-pixel axis), float32:
+    per channel dx = (I[x+1] - I[x-1]) * inv_dist, dy likewise, then
+    g^2 = sum over channels in order of (dx^2 + dy^2), g = sqrt(g^2)."""
+    I = np.asarray(img, dtype=F32)
+    H, W, _ = I.shape
+    cols = np.arange(W)
+    rows = np.arange(H)
+    cR, cL = np.minimum(cols + 1, W - 1), np.maximum(cols - 1, 0)
+    rD, rU = np.minimum(rows + 1, H - 1), np.maximum(rows - 1, 0)
+    invx = np.where(cR - cL == 2, F32(0.5), np.where(cR - cL == 1, F32(1.0), F32(0.0))).astype(F32)
+    invy = np.where(rD - rU == 2, F32(0.5), np.where(rD - rU == 1, F32(1.0), F32(0.0))).astype(F32)
+    g2 = np.zeros((H, W), dtype=F32)
+    for c in range(3):
+        dx = ((I[:, cR, c] - I[:, cL, c]).astype(F32) * invx[None, :]).astype(F32)
+        dy = ((I[rD, :, c] - I[rU, :, c]).astype(F32) * invy[:, None]).astype(F32)
+        g2 = (g2 + (dx * dx).astype(F32)).astype(F32)
+        g2 = (g2 + (dy * dy).astype(F32)).astype(F32)
+    return np.sqrt(g2).astype(F32)
+
+
+def init_weights_fp32(img, lam):
+    """P_init(x) = (1 - lam) |grad I(x)| / sum |grad I| + lam / (H W)
+    (Sec. 4.4, Eq. P_init).  The normaliser is summed exactly: each |grad I|
+    rounded to a 2^-32 fixed-point integer, summed in int64, converted back
+    (so the result does not depend on summation order)."""
+    g = grad_magnitude_fp32(img).ravel()
+    P = g.size
+    fx = np.rint((g.astype(F32) * F32(2.0 ** 32)).astype(F32)).astype(np.int64)
+    S = F32(float(int(fx.sum())) * 2.0 ** -32)
+    a = F32(F32(1.0) - F32(lam))
+    b = F32(F32(lam) / F32(P))
+    if S > 0:
+        t = (g / S).astype(F32)
+    else:
+        t = np.zeros_like(g)
+    return ((a * t).astype(F32) + b).astype(F32)
+
+
+def _u24(seed, counters):
+    """24-bit uniform draws u = hi24(SplitMix64) * 2^-24 in [0, 1)."""
+    h = splitmix64(seed, counters)
+    return ((h >> np.uint64(40)).astype(np.float64) * 2.0 ** -24).astype(F32)
+
+
+def init_keys_fp32(w, seed):
+    """Efraimidis-Spirakis (2006) weighted sampling without replacement: key =
+    E / w with E = -log(U) ~ Exp(1), U in (0, 1] the 24-bit draw at counter =
+    pixel index (+2^-24); the n smallest keys form the sample.  w = 0 gives
+    +inf.  float32 throughout."""
+    P = len(w)
+    u = (_u24(seed, np.arange(P, dtype=np.uint64)) + F32(2.0 ** -24)).astype(F32)
+    E = (-log32(u)).astype(F32)
+    E = np.where(u == F32(1.0), F32(0.0), E).astype(F32)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        k = (E / w).astype(F32)
+    return np.where(w > F32(0), k, F32(np.inf)).astype(F32)
+
+
+def init_select(keys, n):
+    """Indices of the n smallest keys, ties by smaller index, returned in
+    ascending index order."""
+    order = np.lexsort((np.arange(len(keys)), keys))
+    return np.sort(order[:n])
+
+
+def init_sites(img, n, capacity, lam, seed, log_tau0):
+    """Site set of Sec. 4.4: positions sampled at pixel centres by P_init
+    (without replacement) plus a U[-0.25, 0.25) jitter per axis (24-bit draws
+    at counters 2^40 + 2 pixel + {0, 1}), colour = target at the pixel, and
+    the fixed defaults log_tau = log_tau0, r = 0, u = (1, 0), a = b = 0.
+    Sites n..capacity-1 are inactive.  Returns float32[11, capacity]."""
+    I = np.asarray(img, dtype=F32)
+    H, W, _ = I.shape
+    n = min(n, H * W)
+    w = init_weights_fp32(I, lam)
+    pix = init_select(init_keys_fp32(w, seed), n)
+    row, col = np.divmod(pix, W)
+    cnt = np.uint64(1 << 40) + np.uint64(2) * pix.astype(np.uint64)
+    jx = ((_u24(seed, cnt) - F32(0.5)).astype(F32) * F32(0.5)).astype(F32)
+    jy = ((_u24(seed, cnt + np.uint64(1)) - F32(0.5)).astype(F32) * F32(0.5)).astype(F32)
+    p = np.zeros((N_PARAMS, capacity), dtype=F32)
+    p[PX, :n] = ((col.astype(F32) + F32(0.5)).astype(F32) + jx).astype(F32)
+    p[PY, :n] = ((row.astype(F32) + F32(0.5)).astype(F32) + jy).astype(F32)
+    p[PLOGTAU, :n] = F32(log_tau0)
+    p[PCR:PCB + 1, :n] = I[row, col].T
+    p[PUX, :] = 1.0
+    p[PX, n:] = -1.0
+    p[PY, n:] = -1.0
+    return p
