@@ -190,6 +190,27 @@ int sad_render_backward_noalloc(const float* params, const float* prep, int32_t 
  */
 int sad_workspace_status(const void* workspace, int64_t* records_used, void* stream);
 
+/*
+ * sad_init_sites -- gradient-weighted initialisation (Sec. 4.4, Eq. P_init).
+ * P_init(x) = (1-lambda) |grad I(x)| / sum |grad I| + lambda/(H W), with
+ * |grad I| the 2-norm over RGB of central differences (one-sided at the
+ * borders); the normaliser is summed exactly in 2^-32 fixed point.  n pixels
+ * are drawn without replacement by Efraimidis-Spirakis keys E/P_init,
+ * E = -log U with U the 24-bit SplitMix64 draw of `seed` at counter = pixel
+ * index (the n smallest keys, ties to the smaller index); site i (in pixel
+ * order) sits at the pixel centre plus a U[-0.25,0.25) jitter per axis
+ * (draws at counters 2^40 + 2 pixel + {0,1}), takes the image colour there,
+ * log_tau = log_tau0, r = 0, u = (1,0), a = b = 0.  Sites n..capacity-1 are
+ * set inactive.  Deterministic; fp32 steps are explicitly rounded.
+ * img: float32[H][W][3]; params: float32[11][capacity] (written).
+ * workspace: sad_init_workspace_bytes(H, W) bytes, 256-B aligned.
+ * Requires 0 <= n <= min(capacity, H*W), 0 <= lambda_init <= 1.
+ */
+size_t sad_init_workspace_bytes(int32_t H, int32_t W);
+int sad_init_sites(const float* img, int32_t H, int32_t W, int32_t n, int32_t capacity,
+                   float lambda_init, uint64_t seed, float log_tau0, float* params,
+                   void* workspace, size_t workspace_bytes, void* stream);
+
 /* Adam hyper-parameters (Sec. 6.1; betas/eps after Kingma & Ba 2015). */
 typedef struct sad_adam_hparams {
   float lr[SAD_NPARAMS]; /* per plane; x, y, r step in units of 1/s */

@@ -81,6 +81,11 @@ _SIGS = {
                                                    ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                    ctypes.c_void_p, ctypes.c_void_p]),
+    "sad_init_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32]),
+    "sad_init_sites": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.c_float, ctypes.c_uint64, ctypes.c_float,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                      ctypes.c_void_p]),
     "sad_adam_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                      ctypes.c_int32, ctypes.c_int32,
@@ -265,6 +270,22 @@ def sad_workspace_status(ws, stream=None):
     st = lib().sad_workspace_status(_ptr(ws, torch.uint8, "workspace"), ctypes.byref(used),
                                     _stream(stream))
     return st, int(used.value)
+
+
+def sad_init_sites(img, n, capacity, lambda_init, seed, log_tau0, params=None, ws=None,
+                   stream=None):
+    """Gradient-weighted initial site set (see include/sad.h); returns params."""
+    H, W, _ = img.shape
+    if params is None:
+        params = torch.empty((N_PARAMS, capacity), dtype=torch.float32, device=img.device)
+    if ws is None:
+        ws = torch.empty(lib().sad_init_workspace_bytes(H, W), dtype=torch.uint8, device=img.device)
+    _check(lib().sad_init_sites(_ptr(img, torch.float32, "img", H * W * 3), H, W, n, capacity,
+                                lambda_init, seed & ((1 << 64) - 1), log_tau0,
+                                _ptr(params, torch.float32, "params", N_PARAMS * capacity),
+                                _ptr(ws, torch.uint8, "workspace"), ws.numel(), _stream(stream)),
+           "sad_init_sites")
+    return params
 
 
 def adam_hparams(lr=None, beta1=0.9, beta2=0.999, eps=1e-8, log_tau_range=(2.0, 20.0),
