@@ -716,3 +716,152 @@ def init_sites(img, n, capacity, lam, seed, log_tau0):
     p[PX, n:] = -1.0
     p[PY, n:] = -1.0
     return p
+
+
+# =============================================================================
+# Part 4: adaptive budget -- statistics, densify (split) and prune (Sec. 4.5;
+# App. "Densification and Pruning")
+# =============================================================================
+
+STAT_NAMES = ("mass", "energy", "mx", "my", "mxx", "mxy", "myy", "removal")
+
+
+def site_stats(params, H, W, ids, target):
+    """Per-site statistics of one render, fp64, float64[8, N]:
+      mass    m_i = sum_x w_i(x)                            (Sec. 4.5)
+      energy  E_i = sum_x w_i(x) |c(x) - I(x)|^2            (Sec. 4.5)
+      mx..myy residual-weighted moments of D = x - p_i with omega = w_i e(x):
+              sum omega Dx, sum omega Dy, sum omega Dx^2, sum omega Dx Dy,
+              sum omega Dy^2 (the 'weighted second moments' of the
+              statistics pass; the zeroth moment is the energy)
+      removal sum_x of the removal delta (Sec. 4.5, as removal_delta())."""
+    p = np.asarray(params, dtype=np.float64)
+    N = p.shape[1]
+    px, py = pixel_centres(H, W)
+    w, _, valid, sid = weights(p, H, W, ids, px, py)
+    col = np.stack([p[PCR], p[PCG], p[PCB]], axis=1)
+    c = np.einsum("qk,qkc->qc", w, col[sid])
+    I = np.asarray(target, np.float64).reshape(-1, 3)
+    e = ((c - I) ** 2).sum(1)
+    om = w * e[:, None]
+    dx = px[:, None] - p[PX][sid]
+    dy = py[:, None] - p[PY][sid]
+    out = np.zeros((8, N))
+    vals = [w, om, om * dx, om * dy, om * dx * dx, om * dx * dy, om * dy * dy]
+    flat = np.where(valid, sid, 0).ravel()
+    for j, v in enumerate(vals):
+        np.add.at(out[j], flat, np.where(valid, v, 0.0).ravel())
+    out[7] = removal_delta(p, H, W, ids, target)
+    return out
+
+
+def sobel_direction(target, x, y):
+    """Unit direction of the 3x3 Sobel gradient of the RGB-summed target at
+    the pixel containing (x, y) (borders clamp); (1, 0) if it vanishes."""
+    I = np.asarray(target, np.float64).sum(axis=2)
+    H, W = I.shape
+    c = min(max(int(math.floor(x)), 0), W - 1)
+    r = min(max(int(math.floor(y)), 0), H - 1)
+    at = lambda rr, cc: I[min(max(rr, 0), H - 1), min(max(cc, 0), W - 1)]
+    gx = (at(r - 1, c + 1) + 2 * at(r, c + 1) + at(r + 1, c + 1)
+          - at(r - 1, c - 1) - 2 * at(r, c - 1) - at(r + 1, c - 1))
+    gy = (at(r + 1, c - 1) + 2 * at(r + 1, c) + at(r + 1, c + 1)
+          - at(r - 1, c - 1) - 2 * at(r - 1, c) - at(r - 1, c + 1))
+    n = math.hypot(gx, gy)
+    return (1.0, 0.0) if n == 0 else (gx / n, gy / n)
+
+
+def densify_prune_select(params, stats, densify_pct, prune_pct, alpha=0.7, eps=1e-8):
+    """Which sites split and which are pruned (Sec. 4.5).
+
+    Densify: among active sites with mass > 1, the top floor(pct N_active) by
+    s_i = E_i / max(m_i, eps)^alpha (ties to the smaller id).  Prune: among the
+    other active sites, the bottom floor(pct N_active) by removal delta (ties
+    to the smaller id).  Returns (densify ids ascending, prune ids ascending).
+    """
+    p = np.asarray(params)
+    act = np.nonzero(p[PX] >= 0)[0]
+    n_act = len(act)
+    m, E, R = stats[0], stats[1], stats[7]
+    cand = act[m[act] > 1.0]
+    score = E[cand] / np.maximum(m[cand], eps) ** alpha
+    nd = min(int(math.floor(densify_pct * n_act)), len(cand))
+    dens = np.sort(cand[np.lexsort((cand, -score))[:nd]]) if nd > 0 else np.zeros(0, np.int64)
+    rest = np.setdiff1d(act, dens)
+    npr = min(int(math.floor(prune_pct * n_act)), len(rest))
+    prune = np.sort(rest[np.lexsort((rest, R[rest]))[:npr]]) if npr > 0 else np.zeros(0, np.int64)
+    return dens, prune
+
+
+def split_site(params, stats, target, i, H, W):
+    """The two children of site i (Sec. 4.5; App. "Densification and Pruning"):
+    residual-weighted centroid mu and covariance C from the moments; axis =
+    major eigenvector of C and a = -log(l1/l2)/2 clamped to [-2, 2] (u = axis);
+    if the energy is below 1e-6 or l1/l2 < 1.01 the axis is the Sobel
+    gradient direction of the target, the centre the parent position and
+    a = 0.8 a_parent (u kept).  Children at centre +- d axis,
+    d = clamp(0.5 sqrt(m_i), 1.5, 48) px, clamped to the image; both inherit
+    the parent, log_tau -= 0.25, r *= 0.85, colour = target at the child.
+    Returns two float64[11] parameter vectors (plus, minus)."""
+    p = np.asarray(params, dtype=np.float64)[:, i].copy()
+    st = stats[:, i]
+    S0 = st[1]
+    use_cov = False
+    if S0 >= 1e-6:
+        mux, muy = st[2] / S0, st[3] / S0
+        C = np.array([[st[4] / S0 - mux * mux, st[5] / S0 - mux * muy],
+                      [st[5] / S0 - mux * muy, st[6] / S0 - muy * muy]])
+        lam, vec = np.linalg.eigh(C)
+        l1, l2 = lam[1], lam[0]
+        if l1 > 0 and l1 / max(l2, 1e-12) >= 1.01:
+            use_cov = True
+            axis = vec[:, 1]
+            centre = (p[PX] + mux, p[PY] + muy)
+            a_new = float(np.clip(-0.5 * math.log(l1 / max(l2, 1e-12)), -2.0, 2.0))
+    if not use_cov:
+        axis = np.array(sobel_direction(target, p[PX], p[PY]))
+        centre = (p[PX], p[PY])
+        a_new = 0.8 * p[PA]
+    d = min(max(0.5 * math.sqrt(max(st[0], 0.0)), 1.5), 48.0)
+    I = np.asarray(target, np.float64)
+    kids = []
+    for sgn in (1.0, -1.0):
+        q = p.copy()
+        q[PX] = min(max(centre[0] + sgn * d * axis[0], 0.0), float(W))
+        q[PY] = min(max(centre[1] + sgn * d * axis[1], 0.0), float(H))
+        q[PLOGTAU] -= 0.25
+        q[PR] *= 0.85
+        q[PA] = a_new
+        if use_cov:
+            q[PUX], q[PUY] = axis[0], axis[1]
+        cc = min(max(int(math.floor(q[PX])), 0), W - 1)
+        rr = min(max(int(math.floor(q[PY])), 0), H - 1)
+        q[PCR:PCB + 1] = I[rr, cc]
+        kids.append(q)
+    return kids[0], kids[1]
+
+
+def densify_prune(params, m, v, stats, target, H, W, densify_pct, prune_pct, alpha=0.7):
+    """Apply one densify-then-prune event.  Parent i becomes the '+' child;
+    the k-th split parent (ascending id) takes the k-th inactive slot
+    (ascending) for its '-' child, and parents beyond the free slots are not
+    split.  Adam state of parents and children is zeroed; pruned sites are set
+    to (-1, -1).  Returns (params, m, v, n_active) as float64."""
+    p = np.array(params, dtype=np.float64)
+    m = np.array(m, dtype=np.float64)
+    v = np.array(v, dtype=np.float64)
+    dens, prune = densify_prune_select(p, stats, densify_pct, prune_pct, alpha)
+    free = np.nonzero(p[PX] < 0)[0]
+    base = p.copy()
+    for k, i in enumerate(dens):
+        if k >= len(free):
+            break
+        plus, minus = split_site(base, stats, target, i, H, W)
+        j = free[k]
+        p[:, i], p[:, j] = plus, minus
+        for arr in (m, v):
+            arr[:, i] = 0.0
+            arr[:, j] = 0.0
+    p[PX, prune] = -1.0
+    p[PY, prune] = -1.0
+    return p, m, v, int((p[PX] >= 0).sum())

@@ -6,40 +6,53 @@
 namespace sad {
 
 // Blend of the K listed sites at point (px, py): max-subtracted softmax of the
-// logits, colour = sum w_i c_i.  Returns false if no listed site is valid.
+// logits, colour = sum w_i c_i; black if no listed site is valid.  Loads use
+// clamped ids so that each batch of gathers is issued before the dependent
+// arithmetic (memory-level parallelism); invalid entries are masked after.
 template <int K>
 __device__ __forceinline__ float3 blend(const uint32_t (&ids)[K], float px, float py, uint32_t ucap,
                                         const float4* __restrict__ geo,
                                         const float4* __restrict__ met,
                                         const float4* __restrict__ col) {
+  constexpr int B = 4;
   float l[K];
   float m = -INFINITY;
   uint32_t valid = 0;
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    l[k] = -INFINITY;
-    const uint32_t id = ids[k];
-    if (id < ucap) {
-      const float4 mt = ldg(&met[id]);
-      if (mt.w != 0.f) {
-        l[k] = score_fast(px, py, ldg(&geo[id]), mt).l;
-        valid |= 1u << k;
-        m = fmaxf(m, l[k]);
-      }
+  for (int k0 = 0; k0 < K; k0 += B) {
+    float4 gk[B], mk[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      const uint32_t id = ids[k0 + j] < ucap ? ids[k0 + j] : 0u;
+      gk[j] = ldg(&geo[id]);
+      mk[j] = ldg(&met[id]);
+    }
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      const bool ok = ids[k0 + j] < ucap && mk[j].w != 0.f;
+      const float lk = score_fast(px, py, gk[j], mk[j]).l;
+      l[k0 + j] = ok ? lk : -INFINITY;
+      valid |= ok ? (1u << (k0 + j)) : 0u;
+      m = ok ? fmaxf(m, lk) : m;
     }
   }
   float3 c = make_float3(0.f, 0.f, 0.f);
   if (!valid) return c;
   float z = 0.f;
+  constexpr int BC = 8;
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    if (valid >> k & 1u) {
-      const float e = __expf(l[k] - m);
-      const float4 ck = ldg(&col[ids[k]]);
+  for (int k0 = 0; k0 < K; k0 += BC) {
+    float4 ck[BC];
+#pragma unroll
+    for (int j = 0; j < BC && k0 + j < K; ++j)
+      ck[j] = ldg(&col[ids[k0 + j] < ucap ? ids[k0 + j] : 0u]);
+#pragma unroll
+    for (int j = 0; j < BC && k0 + j < K; ++j) {
+      const float e = (valid >> (k0 + j) & 1u) ? __expf(l[k0 + j] - m) : 0.f;
       z += e;
-      c.x += e * ck.x;
-      c.y += e * ck.y;
-      c.z += e * ck.z;
+      c.x += e * ck[j].x;
+      c.y += e * ck[j].y;
+      c.z += e * ck[j].z;
     }
   }
   const float iz = 1.f / z;

@@ -55,7 +55,8 @@ def test_autograd_vs_finite_differences_config3(capi, oracle):
         r, c = np.divmod(rows, W)
         sub, gs = ids[rows], g2[rows]
         for j in range(11):
-            h = 1e-4 * max(1.0, abs(p64[j, s]))
+            # positions/radius in pixels: absolute step; others relative
+            h = 1e-3 if j in (0, 1, 3) else 1e-4 * max(1.0, abs(p64[j, s]))
 
             def col_at(d):
                 q = p64.copy()
