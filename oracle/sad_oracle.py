@@ -289,24 +289,38 @@ def removal_delta(params, H, W, ids, target):
     """Per-site removal delta summed over pixels (Sec. 4.5, removal delta).
 
     For each listed site k at pixel x with weight w_k: c' = (c - w_k c_k) /
-    (1 - w_k) and dL(x) = |c' - I|^2 - |c - I|^2, summed per site.  A site
-    that is the only valid entry of a pixel (w_k = 1) adds |I|^2 there, the
-    loss of rendering nothing.  Returns float64[N].
+    (1 - w_k) and dL(x) = |c' - I|^2 - |c - I|^2, summed per site.  c' is
+    the blend of the remaining sites; for the pixel's dominant site (largest
+    logit, where 1 - w_k may be tiny) it is evaluated as that blend directly,
+    with its own max subtracted, which is the same value in exact arithmetic.
+    Removing the only valid site leaves black: dL = |I|^2 - |c - I|^2.
+    Returns float64[N].
     """
     p = np.asarray(params, dtype=np.float64)
-    w, _, valid, sid = weights(p, H, W, ids)
+    w, ell, valid, sid = weights(p, H, W, ids)
     col = np.stack([p[PCR], p[PCG], p[PCB]], axis=1)
     ck = col[sid]
     c = np.einsum("qk,qkc->qc", w, ck)
     I = np.asarray(target, np.float64).reshape(-1, 3)
     base = ((c - I) ** 2).sum(1)
+    Q, K = ids.shape
+    dom = np.argmax(np.where(valid, ell, -np.inf), axis=1)
+    others = valid.copy()
+    others[np.arange(Q), dom] = False
+    has_o = others.any(axis=1)
+    l2 = np.where(others, ell, -np.inf)
+    m2 = np.where(has_o, l2.max(axis=1), 0.0)
+    e2 = np.where(others, np.exp(l2 - m2[:, None]), 0.0)
+    z2 = e2.sum(axis=1)
+    c_dom = np.einsum("qk,qkc->qc", e2, ck) / np.where(z2 > 0, z2, 1.0)[:, None]
+    c_dom = np.where(has_o[:, None], c_dom, 0.0)
     out = np.zeros(p.shape[1])
-    for k in range(ids.shape[1]):
+    for k in range(K):
         wk = w[:, k]
-        alone = wk >= 1.0
-        denom = np.where(alone, 1.0, 1.0 - wk)
-        cprime = (c - wk[:, None] * ck[:, k]) / denom[:, None]
-        dl = np.where(alone, (I ** 2).sum(1), ((cprime - I) ** 2).sum(1)) - base
+        is_dom = dom == k
+        denom = np.where(is_dom, 1.0, 1.0 - wk)
+        cprime = np.where(is_dom[:, None], c_dom, (c - wk[:, None] * ck[:, k]) / denom[:, None])
+        dl = ((cprime - I) ** 2).sum(1) - base
         np.add.at(out, sid[valid[:, k], k], dl[valid[:, k]])
     return out
 

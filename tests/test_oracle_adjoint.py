@@ -83,11 +83,13 @@ def test_rotation_gradient_matches_theta_derivative(oracle):
     assert dth[i] == pytest.approx(fd, rel=1e-7)
 
 
-def test_removal_delta_matches_brute_force(oracle):
-    """Delete site k from each list, renormalise, recompute the loss (Sec. 4.5)."""
+@pytest.mark.parametrize("sharp", [2.0, 14.0])
+def test_removal_delta_matches_brute_force(oracle, sharp):
+    """Delete site k from each list, renormalise, recompute the loss (Sec. 4.5).
+    The sharp case makes 1 - w of the dominant site underflow in fp64."""
     H, W = 8, 9
     p = gen.sites_random_spd(H, W, 12, seed=50).astype(np.float64)
-    p[2] += 2.0
+    p[2] += sharp
     ids = gen.knn_map(p.astype(np.float32), H, W, 4, seed=51)
     img = gen.image_sinusoid_polygons(H, W, seed=52).reshape(-1, 3).astype(np.float64)
     ids[3, 1:] = INV                                  # a single-site pixel
