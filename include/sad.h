@@ -128,8 +128,8 @@ int sad_decode_points(const float* prep, int32_t capacity, int32_t H, int32_t W,
 /*
  * Workspace of sad_render_backward / sad_train_grads, in bytes, for a problem
  * of H x W pixels, list size K and `capacity` sites, able to hold
- * `max_records` per-tile partial records (0 = default H*W*K/4, at least
- * 64 per 16x16 tile).  The caller allocates it (any content; 256-B aligned).
+ * `max_records` per-tile partial records (0 = default H*W*K/8, at least
+ * 128 per 16x16 tile).  The caller allocates it (any content; 256-B aligned).
  */
 size_t sad_backward_workspace_bytes(int32_t H, int32_t W, int32_t K, int32_t capacity,
                                     int64_t max_records);
@@ -139,9 +139,10 @@ size_t sad_backward_workspace_bytes(int32_t H, int32_t W, int32_t K, int32_t cap
  * (App. "Gradient Computation and Reduction", Per-pixel gradients), with the top-K map a frozen index set.
  * Per pixel the softmax is recomputed (nothing from the forward is stored);
  * per 16x16 tile the contributions are reduced per site in a fixed order
- * (atomic-free per-tile partials, replacing the tile hash + global atomics of
- * Sec. 4.8), then a deterministic segmented reduction sums each site's
- * partials in tile order.  Bitwise reproducible run to run.
+ * (per-tile partials, no float atomics; replaces the tile hash + global float
+ * atomics of Sec. 4.8), then each site's partials are summed in exact 64-bit
+ * fixed point (integer atomics: order independent).  Bitwise reproducible
+ * run to run.
  * grad_rgb: float32[H][W][3] = dL/dc.  grads: float32[11][capacity], fully
  * written (zero for sites no pixel lists).  params/prep must describe the
  * same sites.  If more partial records are produced than the workspace holds,
@@ -170,7 +171,7 @@ int sad_train_grads(const float* params, const float* prep, int32_t capacity, in
  * allowed).  The paper has no counterpart; it is a deployment convenience.
  * Scratch is one 64 MiB buffer inside the library (allocated on every device
  * that loads the library, kept until exit).  Limits: H*W <= 4194304 and
- * capacity <= 262144, else SAD_EINVAL; within them about 1.1 million
+ * capacity <= 262144, else SAD_EINVAL; within them about 0.9 million
  * per-tile records fit.  The first call on a device looks up the buffer's
  * device address (make it before any stream capture).  All calls share the
  * buffer: calls that overlap on the GPU race and must be serialised by the
@@ -210,6 +211,63 @@ size_t sad_init_workspace_bytes(int32_t H, int32_t W);
 int sad_init_sites(const float* img, int32_t H, int32_t W, int32_t n, int32_t capacity,
                    float lambda_init, uint64_t seed, float log_tau0, float* params,
                    void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * sad_site_stats -- per-site statistics of one render for the adaptive
+ * budget (Sec. 4.5; App. "Densification and Pruning", densification scores
+ * and pruning): float32[8][capacity] planes
+ *   0 mass    m_i = sum_x w_i(x)
+ *   1 energy  E_i = sum_x w_i(x) |c(x) - I(x)|^2
+ *   2..6      sum omega Dx, sum omega Dy, sum omega Dx^2, sum omega Dx Dy,
+ *             sum omega Dy^2 with omega = w_i(x) |c(x) - I(x)|^2 and
+ *             D = x - p_i (pixel centre minus site position, pixels)
+ *   7 removal sum_x of |c'(x) - I(x)|^2 - |c(x) - I(x)|^2, c' the blend
+ *             without site i (Sec. 4.5 removal delta; black if i was alone)
+ * Same deterministic per-tile reduction and workspace as sad_render_backward.
+ */
+int sad_site_stats(const float* prep, int32_t capacity, int32_t H, int32_t W, int32_t K,
+                   const uint32_t* map, const float* target, float* stats, void* workspace,
+                   size_t workspace_bytes, void* stream);
+
+/* Densify/prune parameters (Sec. 4.5; Sec. 6.1 defaults in brackets). */
+typedef struct sad_dp_params {
+  double densify_pct;      /* fraction of active sites split [0.01] */
+  double prune_pct;        /* fraction of active sites pruned [0.033] */
+  float alpha;             /* score exponent [0.7] */
+  float eps;               /* mass floor in the score [1e-8] */
+  float mass_min;          /* sites with mass <= this are not split [1] */
+  float min_offset, max_offset; /* child offset clamp, px [1.5, 48] */
+  float log_tau_shift;     /* added to log_tau of children [-0.25] */
+  float r_scale;           /* r multiplier of children [0.85] */
+  float a_min, a_max;      /* clamp of a from the covariance [-2, 2] */
+  float a_fallback_scale;  /* a multiplier without statistics [0.8] */
+  float energy_min;        /* below: no covariance (fallback) [1e-6] */
+  float ratio_min;         /* eigenvalue ratio below: fallback [1.01] */
+} sad_dp_params;
+
+/*
+ * sad_densify_prune -- one densify-then-prune event (Sec. 4.5) from
+ * sad_site_stats output: split the floor(densify_pct N_active) sites with the
+ * largest E/max(m,eps)^alpha among those with mass > mass_min and E > 0, and
+ * deactivate the floor(prune_pct N_active) other active sites with the
+ * smallest removal delta (ties to the smaller id in both).  The k-th split
+ * parent (ascending id) keeps its slot for one child and takes the k-th
+ * inactive slot for the other (no split when no slot is left).  Children: at
+ * the residual centroid +- clamp(0.5 sqrt(m), 1.5, 48) px along the major
+ * axis of the residual covariance (u = axis, a = -log(l1/l2)/2 clamped), or
+ * along the 3x3 Sobel gradient of the target at the parent (a scaled by
+ * a_fallback_scale) when the energy or the anisotropy is too small;
+ * log_tau += log_tau_shift, r *= r_scale, colour = target at the child, Adam
+ * m and v zeroed.  If map (uint32[K/4][H*W][4], may be NULL) is given, each
+ * new child is written into the last list slot of its pixel.  Synchronises
+ * the stream; *n_active_out (HOST) receives the active count afterwards.
+ * workspace: sad_densify_workspace_bytes(capacity, H, W) bytes, 256-B aligned.
+ */
+size_t sad_densify_workspace_bytes(int32_t capacity, int32_t H, int32_t W);
+int sad_densify_prune(float* params, float* m, float* v, int32_t capacity, int32_t H, int32_t W,
+                      int32_t K, const float* stats, const float* target, uint32_t* map,
+                      const sad_dp_params* dp, int32_t* n_active_out, void* workspace,
+                      size_t workspace_bytes, void* stream);
 
 /* Adam hyper-parameters (Sec. 6.1; betas/eps after Kingma & Ba 2015). */
 typedef struct sad_adam_hparams {

@@ -788,8 +788,9 @@ def sobel_direction(target, x, y):
 def densify_prune_select(params, stats, densify_pct, prune_pct, alpha=0.7, eps=1e-8):
     """Which sites split and which are pruned (Sec. 4.5).
 
-    Densify: among active sites with mass > 1, the top floor(pct N_active) by
-    s_i = E_i / max(m_i, eps)^alpha (ties to the smaller id).  Prune: among the
+    Densify: among active sites with mass > 1 and residual energy > 0 (a
+    site with no residual has nothing to split), the top floor(pct N_active)
+    by s_i = E_i / max(m_i, eps)^alpha (ties to the smaller id).  Prune: among the
     other active sites, the bottom floor(pct N_active) by removal delta (ties
     to the smaller id).  Returns (densify ids ascending, prune ids ascending).
     """
@@ -797,7 +798,7 @@ def densify_prune_select(params, stats, densify_pct, prune_pct, alpha=0.7, eps=1
     act = np.nonzero(p[PX] >= 0)[0]
     n_act = len(act)
     m, E, R = stats[0], stats[1], stats[7]
-    cand = act[m[act] > 1.0]
+    cand = act[(m[act] > 1.0) & (E[act] > 0.0)]
     score = E[cand] / np.maximum(m[cand], eps) ** alpha
     nd = min(int(math.floor(densify_pct * n_act)), len(cand))
     dens = np.sort(cand[np.lexsort((cand, -score))[:nd]]) if nd > 0 else np.zeros(0, np.int64)
@@ -810,7 +811,8 @@ def densify_prune_select(params, stats, densify_pct, prune_pct, alpha=0.7, eps=1
 def split_site(params, stats, target, i, H, W):
     """The two children of site i (Sec. 4.5; App. "Densification and Pruning"):
     residual-weighted centroid mu and covariance C from the moments; axis =
-    major eigenvector of C and a = -log(l1/l2)/2 clamped to [-2, 2] (u = axis);
+    major eigenvector of C (sign: positive x component, or positive y when x
+    is 0) and a = -log(l1/l2)/2 clamped to [-2, 2] (u = axis);
     if the energy is below 1e-6 or l1/l2 < 1.01 the axis is the Sobel
     gradient direction of the target, the centre the parent position and
     a = 0.8 a_parent (u kept).  Children at centre +- d axis,
@@ -830,6 +832,8 @@ def split_site(params, stats, target, i, H, W):
         if l1 > 0 and l1 / max(l2, 1e-12) >= 1.01:
             use_cov = True
             axis = vec[:, 1]
+            if axis[0] < 0 or (axis[0] == 0 and axis[1] < 0):   # canonical sign
+                axis = -axis
             centre = (p[PX] + mux, p[PY] + muy)
             a_new = float(np.clip(-0.5 * math.log(l1 / max(l2, 1e-12)), -2.0, 2.0))
     if not use_cov:

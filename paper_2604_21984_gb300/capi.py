@@ -32,6 +32,17 @@ class SadError(RuntimeError):
         self.status = status
 
 
+class DpParams(ctypes.Structure):
+    _fields_ = [
+        ("densify_pct", ctypes.c_double), ("prune_pct", ctypes.c_double),
+        ("alpha", ctypes.c_float), ("eps", ctypes.c_float), ("mass_min", ctypes.c_float),
+        ("min_offset", ctypes.c_float), ("max_offset", ctypes.c_float),
+        ("log_tau_shift", ctypes.c_float), ("r_scale", ctypes.c_float),
+        ("a_min", ctypes.c_float), ("a_max", ctypes.c_float), ("a_fallback_scale", ctypes.c_float),
+        ("energy_min", ctypes.c_float), ("ratio_min", ctypes.c_float),
+    ]
+
+
 class AdamHparams(ctypes.Structure):
     _fields_ = [
         ("lr", ctypes.c_float * N_PARAMS),
@@ -86,6 +97,15 @@ _SIGS = {
                                       ctypes.c_int32, ctypes.c_float, ctypes.c_uint64, ctypes.c_float,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                       ctypes.c_void_p]),
+    "sad_site_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "sad_densify_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "sad_densify_prune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(DpParams),
+                                         ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p, ctypes.c_size_t,
+                                         ctypes.c_void_p]),
     "sad_adam_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                      ctypes.c_int32, ctypes.c_int32,
@@ -286,6 +306,49 @@ def sad_init_sites(img, n, capacity, lambda_init, seed, log_tau0, params=None, w
                                 _ptr(ws, torch.uint8, "workspace"), ws.numel(), _stream(stream)),
            "sad_init_sites")
     return params
+
+
+def sad_site_stats(prep, cap, H, W, K, map_in, target, stats, ws, stream=None):
+    """Per-site mass, energy, residual moments and removal delta (float32[8, cap])."""
+    _check(lib().sad_site_stats(_ptr(prep, torch.float32, "prep"), cap, H, W, K,
+                                _ptr(map_in, torch.int32, "map", H * W * K),
+                                _ptr(target, torch.float32, "target", H * W * 3),
+                                _ptr(stats, torch.float32, "stats", 8 * cap),
+                                _ptr(ws, torch.uint8, "workspace"), ws.numel(), _stream(stream)),
+           "sad_site_stats")
+    return stats
+
+
+def dp_params(densify_pct=0.01, prune_pct=0.033, alpha=0.7, eps=1e-8, mass_min=1.0,
+              min_offset=1.5, max_offset=48.0, log_tau_shift=-0.25, r_scale=0.85,
+              a_range=(-2.0, 2.0), a_fallback_scale=0.8, energy_min=1e-6, ratio_min=1.01):
+    """Densify/prune parameters; defaults are the paper's (Sec. 4.5, Sec. 6.1)."""
+    d = DpParams()
+    d.densify_pct, d.prune_pct, d.alpha, d.eps, d.mass_min = densify_pct, prune_pct, alpha, eps, mass_min
+    d.min_offset, d.max_offset, d.log_tau_shift, d.r_scale = min_offset, max_offset, log_tau_shift, r_scale
+    d.a_min, d.a_max = a_range
+    d.a_fallback_scale, d.energy_min, d.ratio_min = a_fallback_scale, energy_min, ratio_min
+    return d
+
+
+def densify_workspace(cap, H, W, device="cuda"):
+    return torch.empty(lib().sad_densify_workspace_bytes(cap, H, W), dtype=torch.uint8, device=device)
+
+
+def sad_densify_prune(params, m, v, H, W, K, stats, target, map_inout, dp, ws, stream=None):
+    """One densify-then-prune event; returns the number of active sites (syncs)."""
+    cap = params.shape[1]
+    n = ctypes.c_int32(0)
+    _check(lib().sad_densify_prune(_ptr(params, torch.float32, "params", N_PARAMS * cap),
+                                   _ptr(m, torch.float32, "m", N_PARAMS * cap),
+                                   _ptr(v, torch.float32, "v", N_PARAMS * cap), cap, H, W, K,
+                                   _ptr(stats, torch.float32, "stats", 8 * cap),
+                                   _ptr(target, torch.float32, "target", H * W * 3),
+                                   _ptr(map_inout, torch.int32, "map", H * W * K),
+                                   ctypes.byref(dp), ctypes.byref(n),
+                                   _ptr(ws, torch.uint8, "workspace"), ws.numel(), _stream(stream)),
+           "sad_densify_prune")
+    return int(n.value)
 
 
 def adam_hparams(lr=None, beta1=0.9, beta2=0.999, eps=1e-8, log_tau_range=(2.0, 20.0),

@@ -19,9 +19,11 @@
 //       sum d dx^2/n, sum d dx dy/n, sum d dy^2/n,   d = dL/dl = w g.(c_k - cbar)
 //     written as one partial record per (site, tile).  If the table fills,
 //     the remaining sites are handled in further rounds.
-// Then a segmented reduction gathers each site's records, orders them by tile
-// index and sums them in that order; the eleven parameter gradients follow
-// from the statistics by the chain rule through G(a, b, u) of Sec. 4.1.
+// Then every record's statistics are added into per-site sums in exact
+// 64-bit fixed point (integer atomics, per-statistic scale from the largest
+// record value), which makes each site's total independent of the order of
+// the additions; the eleven parameter gradients follow from the statistics by
+// the chain rule through G(a, b, u) of Sec. 4.1.
 #include "sad_device.cuh"
 #include "sad_host.h"
 
@@ -34,6 +36,8 @@ constexpr int kTileThreads = kTileSide * kTileSide;
 constexpr int kSlots = 128;  // shared hash table size per round (power of 2)
 constexpr int kLog2Slots = 7;
 constexpr uint32_t kNone = 0xffffffffu;
+constexpr int kModeGrad = 0;
+constexpr int kModeStats = 1;
 
 struct alignas(16) Record {
   uint32_t site;
@@ -43,9 +47,10 @@ struct alignas(16) Record {
 static_assert(sizeof(Record) == 48, "record layout");
 
 struct WsHeader {
-  uint32_t cursor;
-  uint32_t overflow;
-  uint32_t pad[62];
+  uint32_t cursor;     // records written
+  uint32_t overflow;   // records that did not fit
+  uint32_t pmax[10];   // per statistic: bits of the largest |value| of any record
+  uint32_t pad[52];
 };
 static_assert(sizeof(WsHeader) == 256, "header layout");
 
@@ -53,32 +58,28 @@ static_assert(sizeof(WsHeader) == 256, "header layout");
 // workspace layout
 // ---------------------------------------------------------------------------
 struct WsLayout {
-  size_t hdr, tile_loss, records, counts, fill, offs, blocksums, refs, total;
-  uint32_t max_records, n_tiles, n_blocks;
+  size_t hdr, tile_loss, records, acc, total;
+  uint32_t max_records, n_tiles;
 };
 
 static inline size_t align256(size_t v) { return (v + 255) & ~static_cast<size_t>(255); }
 
+// records: 48 B per (site, tile); acc: 10 int64 fixed-point sums per site
 static WsLayout ws_layout(int H, int W, int K, int cap, int64_t max_records) {
   WsLayout L{};
   const uint64_t tiles_x = (W + kTileSide - 1) / kTileSide;
   const uint64_t tiles_y = (H + kTileSide - 1) / kTileSide;
   L.n_tiles = static_cast<uint32_t>(tiles_x * tiles_y);
   uint64_t mr = max_records > 0 ? static_cast<uint64_t>(max_records)
-                                : static_cast<uint64_t>(H) * W * K / 4;
-  if (max_records <= 0 && mr < 64ull * L.n_tiles) mr = 64ull * L.n_tiles;
+                                : static_cast<uint64_t>(H) * W * K / 8;
+  if (max_records <= 0 && mr < 128ull * L.n_tiles) mr = 128ull * L.n_tiles;
   if (mr > 0xfffffff0ull) mr = 0xfffffff0ull;
   L.max_records = static_cast<uint32_t>(mr);
-  L.n_blocks = static_cast<uint32_t>((cap + 1023) / 1024);
   size_t o = 0;
   L.hdr = o;        o = align256(o + sizeof(WsHeader));
   L.tile_loss = o;  o = align256(o + sizeof(float) * L.n_tiles);
+  L.acc = o;        o = align256(o + sizeof(unsigned long long) * 10 * static_cast<size_t>(cap));
   L.records = o;    o = align256(o + sizeof(Record) * L.max_records);
-  L.counts = o;     o = align256(o + sizeof(uint32_t) * cap);
-  L.fill = o;       o = align256(o + sizeof(uint32_t) * cap);
-  L.offs = o;       o = align256(o + sizeof(uint32_t) * cap);
-  L.blocksums = o;  o = align256(o + sizeof(uint32_t) * (L.n_blocks + 1));
-  L.refs = o;       o = align256(o + sizeof(uint64_t) * L.max_records);
   L.total = o;
   return L;
 }
@@ -126,11 +127,33 @@ __device__ __forceinline__ uint32_t probe_slot(uint32_t id, uint32_t* keys) {
   return kNone;
 }
 
+// Sum 10 per-lane values over a warp by recursive halving (padded to 16):
+// each stage sends half of the values to the partner lane and keeps the other
+// half, so 8+4+2+1+1 shuffles replace the 5x10 of a butterfly.  The order of
+// every addition is fixed.  Returns, on lane l, the total of value l/2
+// (values 10..15 are padding).
+__device__ __forceinline__ float warp_sum10_halving(const float (&in)[10], int lane) {
+  float a[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) a[j] = j < 10 ? in[j] : 0.f;
+#pragma unroll
+  for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < h; ++j) {
+      const float keep = up ? a[h + j] : a[j];
+      const float give = up ? a[j] : a[h + j];
+      a[j] = keep + __shfl_xor_sync(0xffffffffu, give, o);
+    }
+  }
+  return a[0] + __shfl_xor_sync(0xffffffffu, a[0], 1);
+}
+
 // ---------------------------------------------------------------------------
 // per-tile kernel
 // ---------------------------------------------------------------------------
-template <int K>
-__global__ void __launch_bounds__(kTileThreads, 4) k_bwd_tile(
+template <int K, int MODE>
+__global__ void __launch_bounds__(kTileThreads, MODE == kModeStats ? 2 : 4) k_bwd_tile(
     const float4* __restrict__ geo, const float4* __restrict__ met,
     const float4* __restrict__ col, int cap, int H, int W, const uint4* __restrict__ map,
     const float* __restrict__ grad_rgb, const float* __restrict__ target, float two_over_P,
@@ -144,11 +167,17 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_bwd_tile(
   __shared__ uint32_t s_off[kSlots];
   __shared__ uint32_t s_rix[kSlots];
   __shared__ uint8_t s_list[kTileThreads * K];
-  __shared__ float4 s_pa[kTileThreads];   // {m, 1/Z, g.cbar, gx}
-  __shared__ float2 s_pb[kTileThreads];   // {gy, gz}
+  // per pixel.  gradient mode: {m, 1/Z, g.cbar, gx}, {gy, gz, -, -};
+  // statistics mode: {m, 1/Z, cbar.x, cbar.y}, {cbar.z, I}, {c' of the
+  // dominant site (blend without it), dominant id}
+  __shared__ float4 s_pa[kTileThreads];
+  __shared__ float2 s_pg[MODE == kModeStats ? 1 : kTileThreads];
+  __shared__ float4 s_pb[MODE == kModeStats ? kTileThreads : 1];
+  __shared__ float4 s_pc[MODE == kModeStats ? kTileThreads : 1];
   __shared__ uint64_t s_scan[kWarps];
   __shared__ float s_red[kWarps];
   __shared__ uint32_t s_base;
+  __shared__ uint32_t s_pmax[10];
 
   const int t = threadIdx.x;
   const int lane = t & 31, warp = t >> 5;
@@ -163,6 +192,7 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_bwd_tile(
   const size_t q = inimg ? static_cast<size_t>(y) * W + x : 0;
   const uint32_t ucap = static_cast<uint32_t>(cap);
   const float px = x + 0.5f, py = y + 0.5f;
+  if (t < 10) s_pmax[t] = 0u;
 
   // ---- 1. per-pixel forward --------------------------------------------
   uint32_t ids[K];
@@ -175,32 +205,62 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_bwd_tile(
     ids[4 * j + 2] = v.z;
     ids[4 * j + 3] = v.w;
   }
-  float l[K];
   float m = -INFINITY;
-  uint32_t vm = 0;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    l[k] = -INFINITY;
-    if (ids[k] < ucap) {
-      const float4 mt = ldg(&met[ids[k]]);
-      if (mt.w != 0.f) {
-        l[k] = score_fast(px, py, ldg(&geo[ids[k]]), mt).l;
-        vm |= 1u << k;
-        m = fmaxf(m, l[k]);
-      }
-    }
-  }
   float z = 0.f;
   float3 cb = make_float3(0.f, 0.f, 0.f);
+  uint32_t vm = 0;
+  float l[MODE == kModeStats ? K : 1];
+  if (MODE == kModeStats) {
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    if (vm >> k & 1u) {
-      const float e = __expf(l[k] - m);
-      const float4 ck = ldg(&col[ids[k]]);
-      z += e;
-      cb.x += e * ck.x;
-      cb.y += e * ck.y;
-      cb.z += e * ck.z;
+    for (int k = 0; k < K; ++k) {
+      l[k] = -INFINITY;
+      if (ids[k] < ucap) {
+        const float4 mt = ldg(&met[ids[k]]);
+        if (mt.w != 0.f) {
+          l[k] = score_fast(px, py, ldg(&geo[ids[k]]), mt).l;
+          vm |= 1u << k;
+          m = fmaxf(m, l[k]);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (vm >> k & 1u) {
+        const float e = __expf(l[k] - m);
+        const float4 ck = ldg(&col[ids[k]]);
+        z += e;
+        cb.x += e * ck.x;
+        cb.y += e * ck.y;
+        cb.z += e * ck.z;
+      }
+    }
+  } else {
+    // online max-subtracted softmax over the list, kB entries at a time
+    constexpr int kB = 1;
+#pragma unroll
+    for (int k0 = 0; k0 < K; k0 += kB) {
+      float4 g[kB], mt[kB], ck[kB];
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        const uint32_t id = ids[k0 + u] < ucap ? ids[k0 + u] : 0u;
+        g[u] = ldg(&geo[id]);
+        mt[u] = ldg(&met[id]);
+        ck[u] = ldg(&col[id]);
+      }
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        const bool ok = ids[k0 + u] < ucap && mt[u].w != 0.f;
+        vm |= ok ? (1u << (k0 + u)) : 0u;
+        const float lk = score_fast(px, py, g[u], mt[u]).l;
+        const float mn = ok ? fmaxf(m, lk) : m;
+        const float a = m == mn ? 1.f : __expf(m - mn);   // unchanged max (or still -inf): 1
+        const float b = ok ? (lk == mn ? 1.f : __expf(lk - mn)) : 0.f;
+        z = z * a + b;
+        cb.x = cb.x * a + b * ck[u].x;
+        cb.y = cb.y * a + b * ck[u].y;
+        cb.z = cb.z * a + b * ck[u].z;
+        m = mn;
+      }
     }
   }
   const float iz = vm ? 1.f / z : 0.f;
@@ -209,12 +269,13 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_bwd_tile(
   cb.z *= iz;
   float3 g = make_float3(0.f, 0.f, 0.f);
   float lpx = 0.f;
+  float3 I = make_float3(0.f, 0.f, 0.f);
   if (inimg) {
     if (grad_rgb) {
       g = make_float3(grad_rgb[3 * q], grad_rgb[3 * q + 1], grad_rgb[3 * q + 2]);
     } else {
-      const float rx = cb.x - target[3 * q], ry = cb.y - target[3 * q + 1],
-                  rz = cb.z - target[3 * q + 2];
+      I = make_float3(target[3 * q], target[3 * q + 1], target[3 * q + 2]);
+      const float rx = cb.x - I.x, ry = cb.y - I.y, rz = cb.z - I.z;
       lpx = rx * rx + ry * ry + rz * rz;
       g = make_float3(two_over_P * rx, two_over_P * ry, two_over_P * rz);
     }
@@ -224,8 +285,49 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_bwd_tile(
       rgb_out[3 * q + 2] = cb.z;
     }
   }
-  s_pa[t] = make_float4(m, iz, g.x * cb.x + g.y * cb.y + g.z * cb.z, g.x);
-  s_pb[t] = make_float2(g.y, g.z);
+  if (MODE == kModeStats) {
+    // dominant site (first largest logit) and the blend of the others with
+    // their own max subtracted
+    int dk = -1;
+    float ld = -INFINITY;
+    uint32_t did = kInvalid;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const bool better = (vm >> k & 1u) && (dk < 0 || l[k] > ld);
+      dk = better ? k : dk;
+      ld = better ? l[k] : ld;
+      did = better ? ids[k] : did;
+    }
+    float m2 = -INFINITY;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if ((vm >> k & 1u) && k != dk) m2 = fmaxf(m2, l[k]);
+    float z2 = 0.f;
+    float3 c2 = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if ((vm >> k & 1u) && k != dk) {
+        const float e = __expf(l[k] - m2);
+        const float4 ck = ldg(&col[ids[k]]);
+        z2 += e;
+        c2.x += e * ck.x;
+        c2.y += e * ck.y;
+        c2.z += e * ck.z;
+      }
+    }
+    if (z2 > 0.f) {
+      const float i2 = 1.f / z2;
+      c2.x *= i2;
+      c2.y *= i2;
+      c2.z *= i2;
+    }
+    s_pa[t] = make_float4(m, iz, cb.x, cb.y);
+    s_pb[t] = make_float4(cb.z, I.x, I.y, I.z);
+    s_pc[t] = make_float4(c2.x, c2.y, c2.z, __uint_as_float(did));
+  } else {
+    s_pa[t] = make_float4(m, iz, g.x * cb.x + g.y * cb.y + g.z * cb.z, g.x);
+    s_pg[t] = make_float2(g.y, g.z);
+  }
   if (tile_loss) {  // deterministic tile sum of the per-pixel squared error
     float v = lpx;
 #pragma unroll
@@ -258,8 +360,9 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_bwd_tile(
         if (sl != kNone) pending &= ~(1u << k);
       }
       slot[k] = sl;
-      const uint32_t peers = __match_any_sync(0xffffffffu, sl);
-      if (sl != kNone && lane == __ffs(peers) - 1) s_mask[warp][sl] |= peers;
+      // the warp's own mask word: OR is order independent, so the masks (and
+      // the pair lists built from them) are deterministic
+      if (sl != kNone) atomicOr(&s_mask[warp][sl], 1u << lane);
     }
     __syncthreads();
     uint64_t packed = 0;
@@ -304,153 +407,148 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_bwd_tile(
       for (uint32_t i = lane; i < cnt; i += 32) {
         const uint32_t p = s_list[off + i];
         const float4 A = s_pa[p];
-        const float2 B = s_pb[p];
         const float dx = (x0 + static_cast<int>(p & (kTileSide - 1)) + 0.5f) - gs.x;
         const float dy = (y0 + static_cast<int>(p >> 4) + 0.5f) - gs.y;
         const float qq = ms.x * dx * dx + 2.f * ms.y * dx * dy + ms.z * dy * dy;
         const float n = sqrtf(fmaxf(qq, 0.f));
         const float w = __expf(gs.z * (gs.w - n) - A.x) * A.y;
-        const float d = w * (A.w * cs.x + B.x * cs.y + B.y * cs.z - A.z);
-        acc[0] += w * A.w;
-        acc[1] += w * B.x;
-        acc[2] += w * B.y;
-        acc[3] += d;
-        acc[4] += d * n;
-        if (n > 0.f) {
-          const float a = d / n;
-          acc[5] += a * dx;
-          acc[6] += a * dy;
-          acc[7] += a * dx * dx;
-          acc[8] += a * dx * dy;
-          acc[9] += a * dy * dy;
-        }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-        for (int j = 0; j < 10; ++j) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
-      }
-      if (lane == 0) {
-        const uint32_t ridx = s_base + s_rix[sl];
-        if (ridx < max_records) {
-          float4* dst = reinterpret_cast<float4*>(&records[ridx]);
-          dst[0] = make_float4(__uint_as_float(id), __uint_as_float(tile), acc[0], acc[1]);
-          dst[1] = make_float4(acc[2], acc[3], acc[4], acc[5]);
-          dst[2] = make_float4(acc[6], acc[7], acc[8], acc[9]);
+        if (MODE == kModeStats) {
+          // A = {m, 1/Z, cbar.x, cbar.y}, B = {cbar.z, I}
+          const float4 B = s_pb[p];
+          const float ex = A.z - B.y, ey = A.w - B.z, ez = B.x - B.w;
+          const float e = ex * ex + ey * ey + ez * ez;
+          const float om = w * e;
+          acc[0] += w;
+          acc[1] += om;
+          acc[2] += om * dx;
+          acc[3] += om * dy;
+          acc[4] += om * dx * dx;
+          acc[5] += om * dx * dy;
+          acc[6] += om * dy * dy;
+          float3 cp;
+          const float4 C = s_pc[p];
+          if (__float_as_uint(C.w) == id) {
+            cp = make_float3(C.x, C.y, C.z);
+          } else {
+            const float inv = 1.f / (1.f - w);
+            cp = make_float3((A.z - w * cs.x) * inv, (A.w - w * cs.y) * inv, (B.x - w * cs.z) * inv);
+          }
+          const float fx = cp.x - B.y, fy = cp.y - B.z, fz = cp.z - B.w;
+          acc[7] += fx * fx + fy * fy + fz * fz - e;
         } else {
-          hdr->overflow = 1u;
+          // A = {m, 1/Z, g.cbar, gx}, B = {gy, gz}
+          const float2 B = s_pg[p];
+          const float d = w * (A.w * cs.x + B.x * cs.y + B.y * cs.z - A.z);
+          acc[0] += w * A.w;
+          acc[1] += w * B.x;
+          acc[2] += w * B.y;
+          acc[3] += d;
+          acc[4] += d * n;
+          if (n > 0.f) {
+            const float a = d / n;
+            acc[5] += a * dx;
+            acc[6] += a * dy;
+            acc[7] += a * dx * dx;
+            acc[8] += a * dx * dy;
+            acc[9] += a * dy * dy;
+          }
         }
+      }
+      // sum the 10 lane partials over the warp by recursive halving (fixed
+      // order): afterwards lanes 2i and 2i+1 hold the total of statistic i
+      const float tot = warp_sum10_halving(acc, lane);
+      const uint32_t ridx = s_base + s_rix[sl];
+      const int stat = lane >> 1;
+      if (ridx < max_records) {
+        float* dst = reinterpret_cast<float*>(&records[ridx]);
+        if (lane == 0) {
+          dst[0] = __uint_as_float(id);
+          dst[1] = __uint_as_float(tile);
+        }
+        if ((lane & 1) == 0 && stat < 10) {
+          const float v = isfinite(tot) ? tot : 0.f;  // non-finite contributions are dropped
+          dst[2 + stat] = v;
+          if (v != 0.f) atomicMax(&s_pmax[stat], __float_as_uint(fabsf(v)));
+        }
+      } else if (lane == 0) {
+        hdr->overflow = 1u;
       }
     }
     if (!__syncthreads_or(pending != 0u)) break;
   }
+  if (t < 10 && s_pmax[t]) atomicMax(&hdr->pmax[t], s_pmax[t]);
 }
 
 // ---------------------------------------------------------------------------
-// segmented reduction of the per-tile records
+// per-site sums of the per-tile records in exact fixed point
+//
+// Statistic j of every record is scaled by 2^S_j, S_j = 61 - e_j - L with
+// max_j |value| < 2^e_j and 2^L > number of records, rounded to an int64 and
+// added with integer atomics: no sum can overflow, integer addition is
+// associative, so each site's total is the same bit pattern whatever the order
+// of the additions, and its rounding error is below 2^-(61-L) of the largest
+// record value of that statistic.
 // ---------------------------------------------------------------------------
-__global__ void k_seg_count(const Record* __restrict__ rec, const WsHeader* __restrict__ hdr,
-                            uint32_t max_records, uint32_t* __restrict__ counts) {
+__device__ __forceinline__ int fixed_shift(uint32_t pmax_bits, uint32_t n_records) {
+  if (pmax_bits == 0u) return 0;
+  int e;
+  frexpf(__uint_as_float(pmax_bits), &e);       // pmax < 2^e
+  int L = 1;
+  while (L < 32 && (1ull << L) <= n_records) ++L;  // 2^L > n_records
+  return 61 - e - L;
+}
+
+template <int NV>
+__global__ void k_seg_accum(const Record* __restrict__ rec, const WsHeader* __restrict__ hdr,
+                            uint32_t max_records, int cap, unsigned long long* __restrict__ acc) {
   const uint32_t n = min(hdr->cursor, max_records);
-  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
-    atomicAdd(&counts[rec[r].site], 1u);
-}
-
-// exclusive scan of counts[cap] -> offs[cap], blocks of 1024
-__global__ void k_scan_blocks(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int n,
-                              uint32_t* __restrict__ block_sums) {
-  __shared__ uint32_t s_w[32];
-  const int i = blockIdx.x * 1024 + threadIdx.x;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t v = i < n ? in[i] : 0u;
-  uint32_t x = v;
+  double scale[NV];
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) s_w[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t w = s_w[lane];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
-    }
-    s_w[lane] = w;
-  }
-  __syncthreads();
-  const uint32_t pre = warp ? s_w[warp - 1] : 0u;
-  if (i < n) out[i] = pre + x - v;
-  if (threadIdx.x == 1023) block_sums[blockIdx.x] = pre + x;
-}
-
-__global__ void k_scan_sums(uint32_t* __restrict__ block_sums, int nb) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    uint32_t run = 0;
-    for (int b = 0; b < nb; ++b) {
-      const uint32_t v = block_sums[b];
-      block_sums[b] = run;
-      run += v;
-    }
-  }
-}
-
-__global__ void k_scan_add(uint32_t* __restrict__ out, int n, const uint32_t* __restrict__ block_sums) {
-  const int i = blockIdx.x * 1024 + threadIdx.x;
-  if (i < n) out[i] += block_sums[blockIdx.x];
-}
-
-__global__ void k_seg_scatter(const Record* __restrict__ rec, const WsHeader* __restrict__ hdr,
-                              uint32_t max_records, const uint32_t* __restrict__ offs,
-                              uint32_t* __restrict__ fill, uint64_t* __restrict__ refs) {
-  const uint32_t n = min(hdr->cursor, max_records);
+  for (int j = 0; j < NV; ++j) scale[j] = ldexp(1.0, fixed_shift(hdr->pmax[j], n));
+  const size_t c = static_cast<size_t>(cap);
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-    const uint32_t s = rec[r].site;
-    const uint32_t pos = offs[s] + atomicAdd(&fill[s], 1u);
-    refs[pos] = (static_cast<uint64_t>(rec[r].tile) << 32) | r;
+    const float4* src = reinterpret_cast<const float4*>(&rec[r]);
+    const float4 r0 = src[0], r1 = src[1], r2 = src[2];
+    const uint32_t site = __float_as_uint(r0.x);
+    const float v[10] = {r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x, r2.y, r2.z, r2.w};
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      if (v[j] != 0.f) {
+        const long long q = __double2ll_rn(static_cast<double>(v[j]) * scale[j]);
+        atomicAdd(&acc[j * c + site], static_cast<unsigned long long>(q));
+      }
+    }
   }
 }
 
-// Per site: sum its records in tile order, then the chain rule to 11 grads.
+// Per site: the exact sums back to float, then the chain rule to 11 grads.
 __global__ void k_site_grads(const float* __restrict__ params, const float4* __restrict__ geo,
                              const float4* __restrict__ met, int cap,
-                             const Record* __restrict__ rec, const uint32_t* __restrict__ counts,
-                             const uint32_t* __restrict__ offs, const uint64_t* __restrict__ refs,
+                             const WsHeader* __restrict__ hdr, uint32_t max_records,
+                             const unsigned long long* __restrict__ accq,
                              float* __restrict__ grads) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= cap) return;
   const size_t c = static_cast<size_t>(cap);
-  const uint32_t cnt = counts[i];
+  const uint32_t n = min(hdr->cursor, max_records);
+  float acc[10];
+  bool any = false;
+#pragma unroll
+  for (int j = 0; j < 10; ++j) {
+    const long long q = static_cast<long long>(accq[j * c + i]);
+    acc[j] = static_cast<float>(static_cast<double>(q) * ldexp(1.0, -fixed_shift(hdr->pmax[j], n)));
+    any |= q != 0;
+  }
   float out[kNParams];
 #pragma unroll
   for (int j = 0; j < kNParams; ++j) out[j] = 0.f;
-  if (cnt > 0) {
-    const uint64_t* seg = refs + offs[i];
-    float acc[10];
-#pragma unroll
-    for (int j = 0; j < 10; ++j) acc[j] = 0.f;
-    uint64_t last = 0;
-    for (uint32_t it = 0; it < cnt; ++it) {
-      uint64_t best = ~0ull;
-      for (uint32_t j = 0; j < cnt; ++j) {
-        const uint64_t v = seg[j];
-        if ((it == 0 || v > last) && v < best) best = v;
-      }
-      last = best;
-      const float4* src = reinterpret_cast<const float4*>(&rec[static_cast<uint32_t>(best)]);
-      const float4 r0 = src[0], r1 = src[1], r2 = src[2];
-      acc[0] += r0.z; acc[1] += r0.w;
-      acc[2] += r1.x; acc[3] += r1.y; acc[4] += r1.z; acc[5] += r1.w;
-      acc[6] += r2.x; acc[7] += r2.y; acc[8] += r2.z; acc[9] += r2.w;
-    }
+  if (any) {
     const float4 gs = geo[i], ms = met[i];
     const float ts = gs.z, r = gs.w;
     const float G00 = ms.x, G01 = ms.y, G11 = ms.z;
     const float rawx = params[PUX * c + i], rawy = params[PUY * c + i];
     const float a = params[PA * c + i], b = params[PB * c + i];
-    float nrm2 = rawx * rawx + rawy * rawy;
+    const float nrm2 = rawx * rawx + rawy * rawy;
     float ux = 1.f, uy = 0.f;
     if (nrm2 > 0.f) {
       const float inv = rsqrtf(nrm2);
@@ -481,6 +579,22 @@ __global__ void k_site_grads(const float* __restrict__ params, const float4* __r
   for (int j = 0; j < kNParams; ++j) grads[j * c + i] = out[j];
 }
 
+// Per site: the exact statistic sums back to float (statistics mode).
+__global__ void k_site_stats(int cap, const WsHeader* __restrict__ hdr, uint32_t max_records,
+                             const unsigned long long* __restrict__ accq,
+                             float* __restrict__ stats) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cap) return;
+  const size_t c = static_cast<size_t>(cap);
+  const uint32_t n = min(hdr->cursor, max_records);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const long long q = static_cast<long long>(accq[j * c + i]);
+    stats[j * c + i] =
+        static_cast<float>(static_cast<double>(q) * ldexp(1.0, -fixed_shift(hdr->pmax[j], n)));
+  }
+}
+
 __global__ void k_loss_final(const float* __restrict__ tile_loss, uint32_t n_tiles, float inv_P,
                              float* __restrict__ loss) {
   __shared__ float s_w[8];
@@ -501,9 +615,11 @@ __global__ void k_loss_final(const float* __restrict__ tile_loss, uint32_t n_til
 static int run_backward(const float* params, const float* prep, int cap, int H, int W, int K,
                         const uint32_t* map, const float* grad_rgb, const float* target,
                         float* grads, float* loss, float* rgb_out, void* ws, size_t ws_bytes,
-                        cudaStream_t st, const char* name) {
+                        cudaStream_t st, const char* name, float* stats = nullptr) {
   if (int e = check_problem(cap, H, W, K, true)) return e;
-  if (!map || !grads || !ws || (!prep && cap > 0) || (!params && cap > 0))
+  const bool stats_mode = stats != nullptr;
+  if (!map || (!grads && !stats_mode) || !ws || (!prep && cap > 0) ||
+      (!params && cap > 0 && !stats_mode))
     return einval("%s: null pointer", name);
   if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return einval("%s: workspace must be 256-byte aligned", name);
   if (!aligned16(map) || !aligned16(prep)) return einval("%s: pointers must be 16-byte aligned", name);
@@ -531,15 +647,11 @@ static int run_backward(const float* params, const float* prep, int cap, int H, 
   WsHeader* hdr = reinterpret_cast<WsHeader*>(base + LL.hdr);
   float* tile_loss = reinterpret_cast<float*>(base + LL.tile_loss);
   Record* rec = reinterpret_cast<Record*>(base + LL.records);
-  uint32_t* counts = reinterpret_cast<uint32_t*>(base + LL.counts);
-  uint32_t* fill = reinterpret_cast<uint32_t*>(base + LL.fill);
-  uint32_t* offs = reinterpret_cast<uint32_t*>(base + LL.offs);
-  uint32_t* bsums = reinterpret_cast<uint32_t*>(base + LL.blocksums);
-  uint64_t* refs = reinterpret_cast<uint64_t*>(base + LL.refs);
+  unsigned long long* accq = reinterpret_cast<unsigned long long*>(base + LL.acc);
 
   cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st);
-  if (e == cudaSuccess && cap > 0) e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * cap, st);
-  if (e == cudaSuccess && cap > 0) e = cudaMemsetAsync(fill, 0, sizeof(uint32_t) * cap, st);
+  if (e == cudaSuccess && cap > 0)
+    e = cudaMemsetAsync(accq, 0, sizeof(unsigned long long) * 10 * static_cast<size_t>(cap), st);
   if (e != cudaSuccess) {
     set_error("%s memset: %s", name, cudaGetErrorString(e));
     return SAD_ECUDA;
@@ -548,37 +660,41 @@ static int run_backward(const float* params, const float* prep, int cap, int H, 
   const float4 *geo = p4, *met = p4 + cap, *col = p4 + 2 * static_cast<size_t>(cap);
   const uint4* m4 = reinterpret_cast<const uint4*>(map);
   const float two_over_P = 2.0f / static_cast<float>(static_cast<double>(H) * W);
-  float* tl = target ? tile_loss : nullptr;
-  switch (K) {
-    case 4:
-      k_bwd_tile<4><<<LL.n_tiles, kTileThreads, 0, st>>>(geo, met, col, cap, H, W, m4, grad_rgb, target,
-                                                         two_over_P, rgb_out, tl, rec, LL.max_records, hdr);
-      break;
-    case 8:
-      k_bwd_tile<8><<<LL.n_tiles, kTileThreads, 0, st>>>(geo, met, col, cap, H, W, m4, grad_rgb, target,
-                                                         two_over_P, rgb_out, tl, rec, LL.max_records, hdr);
-      break;
-    default:
-      k_bwd_tile<16><<<LL.n_tiles, kTileThreads, 0, st>>>(geo, met, col, cap, H, W, m4, grad_rgb, target,
-                                                          two_over_P, rgb_out, tl, rec, LL.max_records, hdr);
-      break;
+  float* tl = (target && loss) ? tile_loss : nullptr;
+#define SAD_TILE_LAUNCH(KK, MM)                                                           \
+  k_bwd_tile<KK, MM><<<LL.n_tiles, kTileThreads, 0, st>>>(geo, met, col, cap, H, W, m4, grad_rgb, \
+                                                          target, two_over_P, rgb_out, tl, rec,  \
+                                                          LL.max_records, hdr)
+  if (stats_mode) {
+    switch (K) {
+      case 4: SAD_TILE_LAUNCH(4, kModeStats); break;
+      case 8: SAD_TILE_LAUNCH(8, kModeStats); break;
+      default: SAD_TILE_LAUNCH(16, kModeStats); break;
+    }
+  } else {
+    switch (K) {
+      case 4: SAD_TILE_LAUNCH(4, kModeGrad); break;
+      case 8: SAD_TILE_LAUNCH(8, kModeGrad); break;
+      default: SAD_TILE_LAUNCH(16, kModeGrad); break;
+    }
   }
+#undef SAD_TILE_LAUNCH
   if (int r = check_launch("k_bwd_tile")) return r;
-  if (target) {
+  if (target && loss) {
     k_loss_final<<<1, 256, 0, st>>>(tile_loss, LL.n_tiles, 1.0f / static_cast<float>(static_cast<double>(H) * W), loss);
     if (int r = check_launch("k_loss_final")) return r;
   }
   if (cap == 0) return SAD_OK;
   const int sgrid = 152 * 8;
-  k_seg_count<<<sgrid, 256, 0, st>>>(rec, hdr, LL.max_records, counts);
-  if (int r = check_launch("k_seg_count")) return r;
-  k_scan_blocks<<<LL.n_blocks, 1024, 0, st>>>(counts, offs, cap, bsums);
-  k_scan_sums<<<1, 32, 0, st>>>(bsums, static_cast<int>(LL.n_blocks));
-  k_scan_add<<<LL.n_blocks, 1024, 0, st>>>(offs, cap, bsums);
-  if (int r = check_launch("k_scan")) return r;
-  k_seg_scatter<<<sgrid, 256, 0, st>>>(rec, hdr, LL.max_records, offs, fill, refs);
-  if (int r = check_launch("k_seg_scatter")) return r;
-  k_site_grads<<<(cap + 255) / 256, 256, 0, st>>>(params, geo, met, cap, rec, counts, offs, refs, grads);
+  if (stats_mode) {
+    k_seg_accum<8><<<sgrid, 256, 0, st>>>(rec, hdr, LL.max_records, cap, accq);
+    if (int r = check_launch("k_seg_accum")) return r;
+    k_site_stats<<<(cap + 255) / 256, 256, 0, st>>>(cap, hdr, LL.max_records, accq, stats);
+    return check_launch("k_site_stats");
+  }
+  k_seg_accum<10><<<sgrid, 256, 0, st>>>(rec, hdr, LL.max_records, cap, accq);
+  if (int r = check_launch("k_seg_accum")) return r;
+  k_site_grads<<<(cap + 255) / 256, 256, 0, st>>>(params, geo, met, cap, hdr, LL.max_records, accq, grads);
   return check_launch("k_site_grads");
 }
 
@@ -609,6 +725,15 @@ int sad_train_grads(const float* params, const float* prep, int32_t capacity, in
   if (!target || !loss) return einval("sad_train_grads: null target or loss");
   return run_backward(params, prep, capacity, H, W, K, map, nullptr, target, grads, loss, rgb_out,
                       workspace, workspace_bytes, as_stream(stream), "sad_train_grads");
+}
+
+int sad_site_stats(const float* prep, int32_t capacity, int32_t H, int32_t W, int32_t K,
+                   const uint32_t* map, const float* target, float* stats, void* workspace,
+                   size_t workspace_bytes, void* stream) {
+  if (!target || !stats) return einval("sad_site_stats: null target or stats");
+  return run_backward(nullptr, prep, capacity, H, W, K, map, nullptr, target, nullptr, nullptr,
+                      nullptr, workspace, workspace_bytes, as_stream(stream), "sad_site_stats",
+                      stats);
 }
 
 int sad_workspace_status(const void* workspace, int64_t* records_used, void* stream) {

@@ -12,6 +12,7 @@
 // fp32 (or integer) operation, so the choice is reproducible.
 #include "sad_device.cuh"
 #include "sad_host.h"
+#include "sad_select.cuh"
 
 namespace sad {
 
@@ -42,10 +43,8 @@ __device__ __forceinline__ float log32_repro(float x) {
 
 struct InitState {
   unsigned long long gsum;  // sum of fixed-point |grad I|
-  uint32_t prefix;          // radix-select prefix
-  uint32_t need;            // keys still to take below/at the prefix
-  uint32_t hist[256];
-  uint32_t pad[60];
+  uint32_t pad[62];
+  SelState sel;             // radix-select state
 };
 
 struct InitLayout {
@@ -64,7 +63,7 @@ static InitLayout init_layout(int H, int W) {
   L.keys = o;  o = al(o + 4 * P);
   L.flag = o;  o = al(o + 4 * P);
   L.scan = o;  o = al(o + 4 * P);
-  L.bsums = o; o = al(o + 4 * (L.nb + 1));
+  L.bsums = o; o = al(o + 4 * (L.nb + 2));
   L.total = o;
   return L;
 }
@@ -73,7 +72,7 @@ __global__ void k_init_state(InitState* __restrict__ st, uint32_t n) {
   uint32_t* w = reinterpret_cast<uint32_t*>(st);
   for (int i = threadIdx.x; i < static_cast<int>(sizeof(InitState) / 4); i += blockDim.x) w[i] = 0u;
   __syncthreads();
-  if (threadIdx.x == 0) st->need = n;
+  if (threadIdx.x == 0) st->sel.need = n;
 }
 
 __global__ void k_init_grad(const float* __restrict__ img, int H, int W, float* __restrict__ g,
@@ -128,102 +127,6 @@ __global__ void k_init_keys(const float* __restrict__ g, size_t P, float lam, ui
   const float E = u == 1.f ? 0.f : -log32_repro(u);
   const float key = w > 0.f ? __fdiv_rn(E, w) : INFINITY;
   keys[i] = __float_as_uint(key);
-}
-
-// radix select pass: histogram of the digit at `shift` among keys whose bits
-// above shift+8 equal the current prefix
-__global__ void k_init_hist(const uint32_t* __restrict__ keys, size_t P, int shift,
-                            InitState* __restrict__ st) {
-  __shared__ uint32_t s_h[256];
-  for (int i = threadIdx.x; i < 256; i += blockDim.x) s_h[i] = 0;
-  __syncthreads();
-  const uint32_t prefix = st->prefix;
-  const int hi = shift + 8;
-  for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < P;
-       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const uint32_t k = keys[i];
-    const bool match = hi >= 32 ? true : ((k >> hi) == prefix);
-    if (match) atomicAdd(&s_h[(k >> shift) & 255u], 1u);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < 256; i += blockDim.x)
-    if (s_h[i]) atomicAdd(&st->hist[i], s_h[i]);
-}
-
-__global__ void k_init_pick(InitState* __restrict__ st) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  uint32_t need = st->need, run = 0;
-  int d = 255;
-  for (int i = 0; i < 256; ++i) {
-    if (run + st->hist[i] >= need) {
-      d = i;
-      break;
-    }
-    run += st->hist[i];
-  }
-  st->prefix = (st->prefix << 8) | static_cast<uint32_t>(d);
-  st->need = need - run;
-  for (int i = 0; i < 256; ++i) st->hist[i] = 0;
-}
-
-__global__ void k_init_flag_eq(const uint32_t* __restrict__ keys, size_t P,
-                               const InitState* __restrict__ st, uint32_t* __restrict__ flag) {
-  const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i < P) flag[i] = keys[i] == st->prefix ? 1u : 0u;
-}
-
-__global__ void k_init_flag_take(const uint32_t* __restrict__ keys, size_t P,
-                                 const InitState* __restrict__ st,
-                                 const uint32_t* __restrict__ eqrank, uint32_t* __restrict__ flag) {
-  const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= P) return;
-  const uint32_t k = keys[i], T = st->prefix;
-  flag[i] = (k < T || (k == T && eqrank[i] < st->need)) ? 1u : 0u;
-}
-
-// exclusive scan, blocks of 1024 (block sums then a serial pass over them)
-__global__ void k_iscan_blocks(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
-                               size_t n, uint32_t* __restrict__ bsums) {
-  __shared__ uint32_t s_w[32];
-  const size_t i = static_cast<size_t>(blockIdx.x) * 1024 + threadIdx.x;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t v = i < n ? in[i] : 0u;
-  uint32_t x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) s_w[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t w = s_w[lane];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
-    }
-    s_w[lane] = w;
-  }
-  __syncthreads();
-  const uint32_t pre = warp ? s_w[warp - 1] : 0u;
-  if (i < n) out[i] = pre + x - v;
-  if (threadIdx.x == 1023) bsums[blockIdx.x] = pre + x;
-}
-
-__global__ void k_iscan_sums(uint32_t* __restrict__ bsums, uint32_t nb) {
-  if (threadIdx.x || blockIdx.x) return;
-  uint32_t run = 0;
-  for (uint32_t b = 0; b < nb; ++b) {
-    const uint32_t v = bsums[b];
-    bsums[b] = run;
-    run += v;
-  }
-}
-
-__global__ void k_iscan_add(uint32_t* __restrict__ out, size_t n, const uint32_t* __restrict__ bsums) {
-  const size_t i = static_cast<size_t>(blockIdx.x) * 1024 + threadIdx.x;
-  if (i < n) out[i] += bsums[blockIdx.x];
 }
 
 __global__ void k_init_write(const float* __restrict__ img, int W, size_t P, uint64_t seed,
@@ -305,18 +208,8 @@ int sad_init_sites(const float* img, int32_t H, int32_t W, int32_t n, int32_t ca
   if (n == 0) return check_launch("k_init_inactive");
   k_init_grad<<<g256, 256, 0, st>>>(img, H, W, g, S);
   k_init_keys<<<g256, 256, 0, st>>>(g, P, lambda_init, seed, S, keys);
-  for (int shift = 24; shift >= 0; shift -= 8) {
-    k_init_hist<<<152 * 4, 256, 0, st>>>(keys, P, shift, S);
-    k_init_pick<<<1, 32, 0, st>>>(S);
-  }
-  k_init_flag_eq<<<g256, 256, 0, st>>>(keys, P, S, flag);
-  k_iscan_blocks<<<L.nb, 1024, 0, st>>>(flag, scan, P, bsums);
-  k_iscan_sums<<<1, 32, 0, st>>>(bsums, L.nb);
-  k_iscan_add<<<L.nb, 1024, 0, st>>>(scan, P, bsums);
-  k_init_flag_take<<<g256, 256, 0, st>>>(keys, P, S, scan, flag);
-  k_iscan_blocks<<<L.nb, 1024, 0, st>>>(flag, scan, P, bsums);
-  k_iscan_sums<<<1, 32, 0, st>>>(bsums, L.nb);
-  k_iscan_add<<<L.nb, 1024, 0, st>>>(scan, P, bsums);
+  run_select_smallest(keys, P, &S->sel, flag, scan, bsums, st);
+  run_xscan(flag, scan, P, bsums, st);
   k_init_write<<<g256, 256, 0, st>>>(img, W, P, seed, log_tau0, flag, scan, params, capacity);
   return check_launch("sad_init_sites");
 }

@@ -5,78 +5,62 @@
 
 namespace sad {
 
-// Blend of the K listed sites at point (px, py): max-subtracted softmax of the
-// logits, colour = sum w_i c_i; black if no listed site is valid.  Loads use
-// clamped ids so that each batch of gathers is issued before the dependent
-// arithmetic (memory-level parallelism); invalid entries are masked after.
-template <int K>
-__device__ __forceinline__ float3 blend(const uint32_t (&ids)[K], float px, float py, uint32_t ucap,
-                                        const float4* __restrict__ geo,
-                                        const float4* __restrict__ met,
-                                        const float4* __restrict__ col) {
-  constexpr int B = 4;
-  float l[K];
-  float m = -INFINITY;
-  uint32_t valid = 0;
-#pragma unroll
-  for (int k0 = 0; k0 < K; k0 += B) {
-    float4 gk[B], mk[B];
-#pragma unroll
-    for (int j = 0; j < B; ++j) {
-      const uint32_t id = ids[k0 + j] < ucap ? ids[k0 + j] : 0u;
-      gk[j] = ldg(&geo[id]);
-      mk[j] = ldg(&met[id]);
-    }
-#pragma unroll
-    for (int j = 0; j < B; ++j) {
-      const bool ok = ids[k0 + j] < ucap && mk[j].w != 0.f;
-      const float lk = score_fast(px, py, gk[j], mk[j]).l;
-      l[k0 + j] = ok ? lk : -INFINITY;
-      valid |= ok ? (1u << (k0 + j)) : 0u;
-      m = ok ? fmaxf(m, lk) : m;
-    }
-  }
+// Blend of the listed sites at point (px, py), streamed two entries at a time
+// with an online max-subtracted softmax: m = running max of the logits,
+// z = sum exp(l - m), c = sum exp(l - m) c_i, rescaled by exp(m_old - m_new)
+// when the max grows (the same w_i = exp(l_i - m)/z in exact arithmetic, no
+// per-entry state kept).  Black if no listed site is valid.
+__device__ __forceinline__ void blend_step(float l, bool ok, float4 ck, float& m, float& z, float3& c) {
+  const float mn = ok ? fmaxf(m, l) : m;
+  const float a = m == mn ? 1.f : __expf(m - mn);   // unchanged max (or still -inf): 1
+  const float b = ok ? (l == mn ? 1.f : __expf(l - mn)) : 0.f;
+  z = z * a + b;
+  c.x = c.x * a + b * ck.x;
+  c.y = c.y * a + b * ck.y;
+  c.z = c.z * a + b * ck.z;
+  m = mn;
+}
+
+template <int NP>
+__device__ __forceinline__ float3 blend_planes(const uint4* __restrict__ map, size_t P, size_t q,
+                                               float px, float py, uint32_t ucap,
+                                               const float4* __restrict__ geo,
+                                               const float4* __restrict__ met,
+                                               const float4* __restrict__ col) {
+  float m = -INFINITY, z = 0.f;
   float3 c = make_float3(0.f, 0.f, 0.f);
-  if (!valid) return c;
-  float z = 0.f;
-  constexpr int BC = 8;
 #pragma unroll
-  for (int k0 = 0; k0 < K; k0 += BC) {
-    float4 ck[BC];
+  for (int j = 0; j < NP; ++j) {
+    const uint4 v = ldg(&map[j * P + q]);
+    const uint32_t id4[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-    for (int j = 0; j < BC && k0 + j < K; ++j)
-      ck[j] = ldg(&col[ids[k0 + j] < ucap ? ids[k0 + j] : 0u]);
+    for (int u0 = 0; u0 < 4; u0 += 2) {
+      float4 g[2], mt[2], ck[2];
 #pragma unroll
-    for (int j = 0; j < BC && k0 + j < K; ++j) {
-      const float e = (valid >> (k0 + j) & 1u) ? __expf(l[k0 + j] - m) : 0.f;
-      z += e;
-      c.x += e * ck[j].x;
-      c.y += e * ck[j].y;
-      c.z += e * ck[j].z;
+      for (int u = 0; u < 2; ++u) {
+        const uint32_t id = id4[u0 + u] < ucap ? id4[u0 + u] : 0u;  // clamped: loads issue early
+        g[u] = ldg(&geo[id]);
+        mt[u] = ldg(&met[id]);
+        ck[u] = ldg(&col[id]);
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const bool ok = id4[u0 + u] < ucap && mt[u].w != 0.f;
+        blend_step(score_fast(px, py, g[u], mt[u]).l, ok, ck[u], m, z, c);
+      }
     }
   }
-  const float iz = 1.f / z;
-  c.x *= iz;
-  c.y *= iz;
-  c.z *= iz;
+  if (z > 0.f) {
+    const float iz = 1.f / z;
+    c.x *= iz;
+    c.y *= iz;
+    c.z *= iz;
+  }
   return c;
 }
 
 template <int K>
-__device__ __forceinline__ void load_list(const uint4* __restrict__ map, size_t P, size_t q,
-                                          uint32_t (&ids)[K]) {
-#pragma unroll
-  for (int j = 0; j < K / 4; ++j) {
-    const uint4 v = ldg(&map[j * P + q]);
-    ids[4 * j] = v.x;
-    ids[4 * j + 1] = v.y;
-    ids[4 * j + 2] = v.z;
-    ids[4 * j + 3] = v.w;
-  }
-}
-
-template <int K>
-__global__ void __launch_bounds__(256) k_render(const float4* __restrict__ geo,
+__global__ void __launch_bounds__(256, 5) k_render(const float4* __restrict__ geo,
                                                 const float4* __restrict__ met,
                                                 const float4* __restrict__ col, int cap, int H,
                                                 int W, const uint4* __restrict__ map,
@@ -86,16 +70,15 @@ __global__ void __launch_bounds__(256) k_render(const float4* __restrict__ geo,
   if (x >= W || y >= H) return;
   const size_t P = static_cast<size_t>(H) * W;
   const size_t q = static_cast<size_t>(y) * W + x;
-  uint32_t ids[K];
-  load_list<K>(map, P, q, ids);
-  const float3 c = blend<K>(ids, x + 0.5f, y + 0.5f, static_cast<uint32_t>(cap), geo, met, col);
+  const float3 c = blend_planes<K / 4>(map, P, q, x + 0.5f, y + 0.5f, static_cast<uint32_t>(cap),
+                                      geo, met, col);
   rgb[3 * q] = c.x;
   rgb[3 * q + 1] = c.y;
   rgb[3 * q + 2] = c.z;
 }
 
 template <int K>
-__global__ void __launch_bounds__(256) k_decode(const float4* __restrict__ geo,
+__global__ void __launch_bounds__(256, 5) k_decode(const float4* __restrict__ geo,
                                                 const float4* __restrict__ met,
                                                 const float4* __restrict__ col, int cap, int H,
                                                 int W, const uint4* __restrict__ map,
@@ -109,9 +92,8 @@ __global__ void __launch_bounds__(256) k_decode(const float4* __restrict__ geo,
   cx = cx < 0 ? 0 : (cx >= W ? W - 1 : cx);
   cy = cy < 0 ? 0 : (cy >= H ? H - 1 : cy);
   const size_t P = static_cast<size_t>(H) * W;
-  uint32_t ids[K];
-  load_list<K>(map, P, static_cast<size_t>(cy) * W + cx, ids);
-  const float3 c = blend<K>(ids, p.x, p.y, static_cast<uint32_t>(cap), geo, met, col);
+  const float3 c = blend_planes<K / 4>(map, P, static_cast<size_t>(cy) * W + cx, p.x, p.y,
+                                       static_cast<uint32_t>(cap), geo, met, col);
   rgb[3 * i] = c.x;
   rgb[3 * i + 1] = c.y;
   rgb[3 * i + 2] = c.z;

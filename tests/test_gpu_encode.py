@@ -1,0 +1,58 @@
+"""The GPU training loop: one iteration against the oracle's sequence of
+steps, and a short encode that must fit the image."""
+import numpy as np
+import pytest
+
+from paper_2604_21984_gb300 import inputs as gen
+from tests.gpu_util import assert_grads_close, dev, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def capi():
+    return require_gpu()
+
+
+def test_one_iteration_matches_oracle(capi, oracle):
+    """prepare -> pass (jump 1) -> fused MSE gradient -> Adam, GPU vs oracle."""
+    torch = pytest.importorskip("torch")
+    from paper_2604_21984_gb300.encode import EncodeConfig, Encoder, jump_code
+    H, W = 48, 64
+    img = gen.image_noise_polygons_lines(H, W, seed=41, n_polygons=5, n_lines=3)
+    enc = Encoder(dev(img), EncodeConfig(n_sites=300, K=8, J=2, iters=1, seed=5))
+    enc.init()
+    p0 = enc.params.cpu().numpy().copy()
+    ids0 = capi.ids_from_map(enc.maps[0])
+    code = jump_code(enc.t_pass, H, W)
+    enc.step()
+    torch.cuda.synchronize()
+    ids1 = oracle.topk_pass_fp32(oracle.prepare_fp32(p0, H, W), ids0, H, W, 8, code, 2, 5 + 0x5AD)
+    assert np.array_equal(capi.ids_from_map(enc.maps[0]), ids1)
+    rgb = oracle.render(p0, H, W, ids1)
+    L, g = oracle.mse_loss_and_grad_rgb(rgb, img)
+    grads = oracle.render_backward(p0, H, W, ids1, g)
+    assert abs(enc.loss.item() - L) <= 1e-5 * L
+    assert_grads_close(enc.grads.cpu().numpy().astype(np.float64), grads)
+    p1, _, _ = oracle.adam_step(p0, enc.grads.cpu().numpy(), np.zeros_like(p0), np.zeros_like(p0), 1, H, W,
+                                lr=dict(zip(oracle.PLANE_NAMES, enc.cfg.lr)))
+    np.testing.assert_allclose(enc.params.cpu().numpy(), p1, rtol=2e-5, atol=2e-5)
+
+
+def test_short_encode_fits_and_densifies(capi):
+    from paper_2604_21984_gb300.encode import EncodeConfig, Encoder
+    H, W = 128, 192
+    img = gen.image_noise_polygons_lines(H, W, seed=42, n_polygons=10, n_lines=6)
+    cfg = EncodeConfig(n_sites=1536, K=16, J=4, iters=400, densify_every=100, densify_start=100,
+                       densify_end=300, seed=3)
+    enc = Encoder(dev(img), cfg)
+    enc.init()
+    p_init = enc.psnr()
+    enc.run(log_every=100)
+    p_end = enc.psnr()
+    print(f"PSNR {p_init:.2f} -> {p_end:.2f} dB, history {enc.history}")
+    assert p_end > p_init + 3.0
+    assert p_end > 24.0
+    n_active = int((enc.params[0] >= 0).sum().item())
+    assert n_active == enc.n_active
+    assert n_active != 1536                      # densify/prune changed the budget
