@@ -292,6 +292,68 @@ typedef struct sad_adam_hparams {
 int sad_adam_step(float* params, const float* grads, float* m, float* v, int32_t capacity,
                   int32_t H, int32_t W, int32_t t, const sad_adam_hparams* hp, void* stream);
 
+/*
+ * Batched training (many images, one launch per stage).  Each image owns a
+ * contiguous range of site slots in the shared site arrays (ascending,
+ * non-overlapping) and a contiguous range of pixels in the packed per-pixel
+ * arrays: targets float32[total_pixels][3] (image b's pixel (x,y) at
+ * pixel_offset + y*W + x) and the map planes uint32[K/4][total_pixels][4].
+ * Site ids in the map are indices into the shared arrays.  At most 64 images.
+ */
+typedef struct sad_batch_image {
+  int32_t H, W;          /* image size */
+  int32_t site_offset;   /* first site slot of the image */
+  int32_t capacity;      /* number of site slots of the image */
+  int64_t pixel_offset;  /* first pixel of the image in the packed arrays */
+  uint64_t seed;         /* injection seed of the image */
+  int32_t t_offset;      /* the image's Adam step is iter[0] + t_offset */
+  int32_t pass_offset;   /* the image's pass index is iter[1] + pass_offset */
+} sad_batch_image;
+
+/* Workspace bytes of sad_train_step (0 = invalid table); same record rule as
+ * sad_backward_workspace_bytes with P = total_pixels. */
+size_t sad_step_workspace_bytes(const sad_batch_image* images, int32_t B, int32_t K,
+                                int32_t total_capacity, int64_t total_pixels,
+                                int64_t max_records);
+
+/* sad_prepare_sites for every image of a batch (each with its own s). */
+int sad_prepare_batch(const sad_batch_image* images, int32_t B, const float* params, float* prep,
+                      int32_t total_capacity, int64_t total_pixels, void* stream);
+
+/*
+ * sad_train_step -- one fused training iteration of every image of a batch
+ * (Sec. 5: no host work inside an iteration).  Per 16x16 tile: one
+ * propagation pass at jump 1 (sad_update_topk semantics with the image's own
+ * site range and seed; pass index = iter[1] + pass_offset) writing map_out,
+ * then, on those
+ * lists, the fused render + MSE + adjoint of sad_train_grads; per site: the
+ * gradient, an Adam step (t = iter[0] + t_offset; sad_adam_step semantics with the
+ * image's H, W) and the prepared table of the new parameters, so `prep` must
+ * hold the prepared table of `params` on entry (sad_prepare_batch) and holds
+ * it again on exit.  loss: device float32[B], the mean loss of each image
+ * before the step (may be NULL).  iter: device int32[2] {t, pass}, both
+ * incremented by the call, so the call sequence can be captured once in a
+ * CUDA graph and replayed.  grads_out: optional float32[11][total_capacity].
+ * map_in and map_out must not overlap; swap them between calls.  Each image's
+ * results are independent of the other images in the batch.
+ */
+int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t J, float* params,
+                   float* m, float* v, float* prep, int32_t total_capacity,
+                   const uint32_t* map_in, uint32_t* map_out, int64_t total_pixels,
+                   const float* targets, float* loss, const sad_adam_hparams* hp, int32_t* iter,
+                   float* grads_out, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * sad_decode_batch -- random-access decode (as sad_decode_points) of queries
+ * against several resident images at once: query i at xy[i] (image pixel
+ * units) uses image query_image[i] of the table (its map cell, its sites).
+ * xy: float32[n][2]; query_image: int32[n]; rgb: float32[n][3].
+ */
+int sad_decode_batch(const sad_batch_image* images, int32_t B, int32_t K, const float* prep,
+                     int32_t total_capacity, const uint32_t* map, int64_t total_pixels,
+                     const float* xy, const int32_t* query_image, int64_t n, float* rgb,
+                     void* stream);
+
 #ifdef __cplusplus
 }
 #endif

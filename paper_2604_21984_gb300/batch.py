@@ -1,0 +1,173 @@
+"""Batched SAD training: many images of uneven sizes in one launch per stage.
+
+All images share one set of device arrays: site parameters / Adam state /
+prepared table ``[11, total_capacity]`` (image b owns a contiguous slot range),
+packed targets ``[total_pixels, 3]`` and top-K map planes
+``[K/4, total_pixels, 4]``.  Each image is initialised and warmed up with the
+single-image calls (gradient-weighted init, JFA warm-up), copied into its
+ranges, and then every training iteration of the whole batch is one
+``sad_train_step`` call (fused propagation + render + MSE + adjoint per tile,
+exact per-site sums, Adam + prepare per site).  The iteration counter lives on
+the device, so two iterations (the map ping-pong) are captured once in a CUDA
+graph and replayed.  An image's trajectory does not depend on the rest of the
+batch (own site range, seed and fixed-point scale).
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass
+
+import torch
+
+from . import capi
+from .encode import EncodeConfig, Encoder
+
+
+@dataclass
+class BatchConfig:
+    K: int = 16
+    J: int = 4
+    sites_per_pixel: float = 0.06
+    lambda_init: float = 0.3
+    seed: int = 0
+    lr: tuple = (1e-3, 1e-3, 1e-2, 1e-3, 5e-3, 5e-3, 5e-3, 1e-2, 1e-2, 1e-2, 0.0)
+    graph: bool = True
+
+
+class BatchTrainer:
+    """Trains a list of float32[H, W, 3] CUDA images jointly."""
+
+    def __init__(self, targets, cfg: BatchConfig | None = None, seeds=None):
+        self.cfg = cfg or BatchConfig()
+        c = self.cfg
+        if not 1 <= len(targets) <= 64:
+            raise ValueError("1..64 images per batch")
+        self.dev = targets[0].device
+        self.images = []
+        site, pix = 0, 0
+        for b, t in enumerate(targets):
+            H, W = int(t.shape[0]), int(t.shape[1])
+            n = max(1, min(H * W, int(round(c.sites_per_pixel * H * W))))
+            sd = seeds[b] if seeds is not None else c.seed * 1000003 + b + 1
+            self.images.append(dict(H=H, W=W, site_offset=site, capacity=n, pixel_offset=pix,
+                                    seed=sd, n=n))
+            site += n
+            pix += H * W
+        self.total_cap, self.total_pixels = site, pix
+        self.table = capi.batch_table(self.images)
+        f32 = dict(dtype=torch.float32, device=self.dev)
+        self.params = torch.empty((capi.N_PARAMS, site), **f32)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.prep = capi.empty_prep(site, self.dev)
+        self.targets = torch.empty((pix, 3), **f32)
+        K = c.K
+        self.maps = [torch.empty((K // 4, pix, 4), dtype=torch.int32, device=self.dev) for _ in range(2)]
+        self.loss = torch.zeros(len(targets), **f32)
+        self.iter = torch.zeros(2, dtype=torch.int32, device=self.dev)
+        self.hp = capi.adam_hparams(lr=c.lr)
+        self.ws = capi.step_workspace(self.table, K, site, pix, device=self.dev)
+        self.graph = None
+        self.steps = 0
+        self._init(targets)
+
+    def _init(self, targets):
+        c = self.cfg
+        for b, (t, im) in enumerate(zip(targets, self.images)):
+            H, W, lo, n, po = im["H"], im["W"], im["site_offset"], im["capacity"], im["pixel_offset"]
+            enc = Encoder(t.contiguous(), EncodeConfig(n_sites=n, K=c.K, J=c.J, capacity_factor=1.0,
+                                                       lambda_init=c.lambda_init,
+                                                       seed=im["seed"]))
+            enc.init()
+            # the single-image warm-up passes used the encoder's seed; from here on the
+            # batch step uses the image's own seed
+            self.params[:, lo:lo + n].copy_(enc.params[:, :n])
+            self.targets[po:po + H * W].copy_(t.reshape(-1, 3))
+            mp = enc.maps[0]
+            # site ids are offset into the shared arrays; sentinels stay sentinels
+            ids = mp.to(torch.int64) & 0xFFFFFFFF
+            shifted = torch.where(ids == 0xFFFFFFFF, ids, ids + lo)
+            self.maps[0][:, po:po + H * W].copy_(self._as_i32(shifted))
+            del enc
+        capi.sad_prepare_batch(self.table, self.params, self.prep, self.total_pixels)
+        # Adam step 1; training passes number from 1024 on (warm-up passes used
+        # indices below 16), the same for every image whatever the batch
+        self.iter.copy_(torch.tensor([1, 1024], dtype=torch.int32))
+
+    @staticmethod
+    def _as_i32(x64):
+        return torch.where(x64 >= 2 ** 31, x64 - 2 ** 32, x64).to(torch.int32)
+
+    def _step(self):
+        capi.sad_train_step(self.table, self.cfg.K, self.cfg.J, self.params, self.m, self.v, self.prep,
+                            self.maps[0], self.maps[1], self.total_pixels, self.targets, self.loss,
+                            self.hp, self.iter, self.ws)
+        self.maps.reverse()
+
+    def _capture(self):
+        """Two iterations (A -> B, B -> A) in one CUDA graph."""
+        s = torch.cuda.Stream(device=self.dev)
+        s.wait_stream(torch.cuda.current_stream(self.dev))
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            # capture records the calls without running them
+            with torch.cuda.graph(g, stream=s):
+                self._step()
+                self._step()
+        torch.cuda.current_stream(self.dev).wait_stream(s)
+        self.graph = g
+
+    def run(self, iters: int):
+        """`iters` training iterations of every image (graph replays when on)."""
+        if self.cfg.graph and iters >= 2:
+            if self.graph is None:
+                self._capture()
+            for _ in range(iters // 2):
+                self.graph.replay()
+            self.steps += 2 * (iters // 2)
+            if iters % 2:
+                self._step()
+                self.steps += 1
+        else:
+            for _ in range(iters):
+                self._step()
+                self.steps += 1
+        return self
+
+    def map_for(self, b):
+        """Current map of image b with image-local site ids (uint32 numpy [P, K])."""
+        im = self.images[b]
+        po, P, lo = im["pixel_offset"], im["H"] * im["W"], im["site_offset"]
+        ids = capi.ids_from_map(self.maps[0][:, po:po + P].contiguous()).astype("int64")
+        import numpy as np
+        return np.where(ids == 0xFFFFFFFF, ids, ids - lo).astype(np.uint32)
+
+    def psnr(self):
+        """Per-image PSNR from the losses of the last step."""
+        return [float("inf") if l <= 0 else 10 * math.log10(3.0 / l) for l in self.loss.tolist()]
+
+
+def autotune(targets, iters: int = 60, candidates=((16, 4), (16, 2), (8, 4), (8, 2)),
+             psnr_tol: float = 0.05, seed: int = 0):
+    """Pick (K, J) for a batch: the fastest candidate whose mean PSNR after a
+    short run is within psnr_tol dB of the first candidate's (the reference).
+    Returns (best (K, J), table of (K, J, ms per iteration, mean PSNR))."""
+    rows = []
+    ref = None
+    for K, J in candidates:
+        tr = BatchTrainer(targets, BatchConfig(K=K, J=J, seed=seed))
+        tr.run(iters - 10)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tr.run(10)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 100.0
+        p = sum(tr.psnr()) / len(targets)
+        rows.append((K, J, ms, p))
+        if ref is None:
+            ref = p
+        del tr
+    ok = [r for r in rows if r[3] >= ref - psnr_tol]
+    best = min(ok, key=lambda r: r[2])
+    return (best[0], best[1]), rows

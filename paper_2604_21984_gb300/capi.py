@@ -43,6 +43,12 @@ class DpParams(ctypes.Structure):
     ]
 
 
+class BatchImage(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int32), ("W", ctypes.c_int32), ("site_offset", ctypes.c_int32),
+                ("capacity", ctypes.c_int32), ("pixel_offset", ctypes.c_int64),
+                ("seed", ctypes.c_uint64), ("t_offset", ctypes.c_int32), ("pass_offset", ctypes.c_int32)]
+
+
 class AdamHparams(ctypes.Structure):
     _fields_ = [
         ("lr", ctypes.c_float * N_PARAMS),
@@ -106,6 +112,19 @@ _SIGS = {
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(DpParams),
                                          ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p, ctypes.c_size_t,
                                          ctypes.c_void_p]),
+    "sad_step_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                                   ctypes.c_int32, ctypes.c_int64, ctypes.c_int64]),
+    "sad_prepare_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p]),
+    "sad_train_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(AdamHparams),
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                      ctypes.c_void_p]),
+    "sad_decode_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                        ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "sad_adam_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                      ctypes.c_int32, ctypes.c_int32,
@@ -377,3 +396,62 @@ def sad_adam_step(params, grads, m, v, H, W, t, hp, stream=None):
                                cap, H, W, t, ctypes.byref(hp), _stream(stream)),
            "sad_adam_step")
     return params
+
+
+# ----------------------------------------------------------------------------
+# batched training (many images per launch)
+# ----------------------------------------------------------------------------
+
+def batch_table(images):
+    """images: list of dicts with H, W, site_offset, capacity, pixel_offset, seed."""
+    arr = (BatchImage * len(images))()
+    for i, d in enumerate(images):
+        arr[i].H, arr[i].W = d["H"], d["W"]
+        arr[i].site_offset, arr[i].capacity = d["site_offset"], d["capacity"]
+        arr[i].pixel_offset, arr[i].seed = d["pixel_offset"], d["seed"] & ((1 << 64) - 1)
+        arr[i].t_offset, arr[i].pass_offset = d.get("t_offset", 0), d.get("pass_offset", 0)
+    return arr
+
+
+def step_workspace(table, K, total_cap, total_pixels, max_records=0, device="cuda"):
+    n = lib().sad_step_workspace_bytes(ctypes.cast(table, ctypes.c_void_p), len(table), K, total_cap,
+                                       total_pixels, max_records)
+    if n == 0:
+        raise ValueError("invalid batch table for sad_step_workspace_bytes")
+    return torch.empty(n, dtype=torch.uint8, device=device)
+
+
+def sad_prepare_batch(table, params, prep, total_pixels, stream=None):
+    cap = params.shape[1]
+    _check(lib().sad_prepare_batch(ctypes.cast(table, ctypes.c_void_p), len(table),
+                                   _ptr(params, torch.float32, "params", N_PARAMS * cap),
+                                   _ptr(prep, torch.float32, "prep"), cap, total_pixels,
+                                   _stream(stream)), "sad_prepare_batch")
+
+
+def sad_train_step(table, K, J, params, m, v, prep, map_in, map_out, total_pixels, targets, loss,
+                   hp, iter_dev, ws, grads_out=None, stream=None):
+    cap = params.shape[1]
+    n = N_PARAMS * cap
+    _check(lib().sad_train_step(ctypes.cast(table, ctypes.c_void_p), len(table), K, J,
+                                _ptr(params, torch.float32, "params", n), _ptr(m, torch.float32, "m", n),
+                                _ptr(v, torch.float32, "v", n), _ptr(prep, torch.float32, "prep"), cap,
+                                _ptr(map_in, torch.int32, "map_in", total_pixels * K),
+                                _ptr(map_out, torch.int32, "map_out", total_pixels * K), total_pixels,
+                                _ptr(targets, torch.float32, "targets", total_pixels * 3),
+                                _ptr(loss, torch.float32, "loss", len(table)), ctypes.byref(hp),
+                                _ptr(iter_dev, torch.int32, "iter", 2),
+                                _ptr(grads_out, torch.float32, "grads_out", n),
+                                _ptr(ws, torch.uint8, "workspace"), ws.numel(), _stream(stream)),
+           "sad_train_step")
+
+
+def sad_decode_batch(table, K, prep, total_cap, map_in, total_pixels, xy, qimg, rgb, stream=None):
+    n = xy.shape[0]
+    _check(lib().sad_decode_batch(ctypes.cast(table, ctypes.c_void_p), len(table), K,
+                                  _ptr(prep, torch.float32, "prep"), total_cap,
+                                  _ptr(map_in, torch.int32, "map", total_pixels * K), total_pixels,
+                                  _ptr(xy, torch.float32, "xy", 2 * n), _ptr(qimg, torch.int32, "qimg", n),
+                                  n, _ptr(rgb, torch.float32, "rgb", 3 * n), _stream(stream)),
+           "sad_decode_batch")
+    return rgb

@@ -1,47 +1,44 @@
 // Adam step with the paper's clamps and direction re-normalisation (Sec. 6.1).
 #include <cmath>
 
-#include "sad_device.cuh"
+#include "sad_adam.cuh"
 #include "sad_host.h"
 
 namespace sad {
 
-struct AdamArgs {
-  float lr[kNParams];
-  float beta1, beta2, eps, bc1, bc2;
-  float lo[kNParams], hi[kNParams];
-  float inv_s;
-};
-
 __global__ void k_adam(float* __restrict__ params, const float* __restrict__ grads,
-                       float* __restrict__ m, float* __restrict__ v, int cap, AdamArgs A) {
+                       float* __restrict__ m, float* __restrict__ v, int cap, int H, int W,
+                       AdamArgs A, float bc1, float bc2) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= cap) return;
   const size_t c = static_cast<size_t>(cap);
   if (!(params[PX * c + i] >= 0.f)) return;  // inactive
-  float p[kNParams];
+  float p[kNParams], g[kNParams];
 #pragma unroll
   for (int j = 0; j < kNParams; ++j) {
-    const size_t o = j * c + i;
-    const bool norm_units = (j == PX || j == PY || j == PR);
-    const float gj = norm_units ? grads[o] * A.inv_s : grads[o];
-    const float mj = A.beta1 * m[o] + (1.f - A.beta1) * gj;
-    const float vj = A.beta2 * v[o] + (1.f - A.beta2) * gj * gj;
-    m[o] = mj;
-    v[o] = vj;
-    const float mhat = mj / A.bc1, vhat = vj / A.bc2;
-    float step = A.lr[j] * mhat / (sqrtf(vhat) + A.eps);
-    if (norm_units) step *= A.inv_s;
-    p[j] = fminf(fmaxf(params[o] - step, A.lo[j]), A.hi[j]);
+    p[j] = params[j * c + i];
+    g[j] = grads[j * c + i];
   }
-  const float n2 = p[PUX] * p[PUX] + p[PUY] * p[PUY];
-  if (n2 > 0.f) {
-    const float inv = 1.f / sqrtf(n2);
-    p[PUX] *= inv;
-    p[PUY] *= inv;
-  }
+  adam_site(p, g, m, v, c, i, A, bc1, bc2, H, W);
 #pragma unroll
   for (int j = 0; j < kNParams; ++j) params[j * c + i] = p[j];
+}
+
+AdamArgs adam_args(const sad_adam_hparams* hp) {
+  AdamArgs A;
+  for (int j = 0; j < kNParams; ++j) A.lr[j] = hp->lr[j];
+  A.beta1 = hp->beta1;
+  A.beta2 = hp->beta2;
+  A.eps = hp->eps;
+  A.log_tau_min = hp->log_tau_min;
+  A.log_tau_max = hp->log_tau_max;
+  A.r_min = hp->r_min;
+  A.r_max = hp->r_max;
+  A.a_min = hp->a_min;
+  A.a_max = hp->a_max;
+  A.b_min = hp->b_min;
+  A.b_max = hp->b_max;
+  return A;
 }
 
 }  // namespace sad
@@ -56,29 +53,11 @@ extern "C" int sad_adam_step(float* params, const float* grads, float* m, float*
   if (t < 1) return einval("sad_adam_step: step t must be >= 1 (got %d)", t);
   if (capacity == 0) return SAD_OK;
   if (!params || !grads || !m || !v) return einval("sad_adam_step: null pointer");
-  AdamArgs A;
-  for (int j = 0; j < kNParams; ++j) {
-    A.lr[j] = hp->lr[j];
-    A.lo[j] = -INFINITY;
-    A.hi[j] = INFINITY;
-  }
-  A.beta1 = hp->beta1;
-  A.beta2 = hp->beta2;
-  A.eps = hp->eps;
-  A.bc1 = static_cast<float>(1.0 - std::pow(static_cast<double>(hp->beta1), t));
-  A.bc2 = static_cast<float>(1.0 - std::pow(static_cast<double>(hp->beta2), t));
-  A.inv_s = static_cast<float>(H > W ? H : W);
-  A.lo[PX] = 0.f; A.hi[PX] = static_cast<float>(W);
-  A.lo[PY] = 0.f; A.hi[PY] = static_cast<float>(H);
-  A.lo[PLOGTAU] = hp->log_tau_min; A.hi[PLOGTAU] = hp->log_tau_max;
-  A.lo[PR] = hp->r_min; A.hi[PR] = hp->r_max;
-  A.lo[PA] = hp->a_min; A.hi[PA] = hp->a_max;
-  A.lo[PB] = hp->b_min; A.hi[PB] = hp->b_max;
-  for (int j = PCR; j <= PCB; ++j) {
-    A.lo[j] = 0.f;
-    A.hi[j] = 1.f;
-  }
+  const AdamArgs A = adam_args(hp);
+  const float bc1 = static_cast<float>(1.0 - std::pow(static_cast<double>(hp->beta1), t));
+  const float bc2 = static_cast<float>(1.0 - std::pow(static_cast<double>(hp->beta2), t));
   const int bs = 256;
-  k_adam<<<(capacity + bs - 1) / bs, bs, 0, as_stream(stream)>>>(params, grads, m, v, capacity, A);
+  k_adam<<<(capacity + bs - 1) / bs, bs, 0, as_stream(stream)>>>(params, grads, m, v, capacity, H, W,
+                                                                 A, bc1, bc2);
   return check_launch("k_adam");
 }

@@ -1,0 +1,64 @@
+// The soft blend of Sec. 4.2 over a pixel's listed sites, shared by the
+// render, decode and batched decode kernels.
+#pragma once
+
+#include "sad_device.cuh"
+#include "sad_topk.cuh"
+
+namespace sad {
+
+// Blend of the listed sites at point (px, py), streamed two entries at a time
+// with an online max-subtracted softmax: m = running max of the logits,
+// z = sum exp(l - m), c = sum exp(l - m) c_i, rescaled by exp(m_old - m_new)
+// when the max grows (the same w_i = exp(l_i - m)/z in exact arithmetic, no
+// per-entry state kept).  Black if no listed site is valid.
+__device__ __forceinline__ void blend_step(float l, bool ok, float4 ck, float& m, float& z, float3& c) {
+  const float mn = ok ? fmaxf(m, l) : m;
+  const float a = m == mn ? 1.f : __expf(m - mn);   // unchanged max (or still -inf): 1
+  const float b = ok ? (l == mn ? 1.f : __expf(l - mn)) : 0.f;
+  z = z * a + b;
+  c.x = c.x * a + b * ck.x;
+  c.y = c.y * a + b * ck.y;
+  c.z = c.z * a + b * ck.z;
+  m = mn;
+}
+
+template <int NP>
+__device__ __forceinline__ float3 blend_planes(const uint4* __restrict__ map, size_t P, size_t q,
+                                               float px, float py, SiteRange sr,
+                                               const float4* __restrict__ geo,
+                                               const float4* __restrict__ met,
+                                               const float4* __restrict__ col) {
+  float m = -INFINITY, z = 0.f;
+  float3 c = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    const uint4 v = ldg(&map[j * P + q]);
+    const uint32_t id4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int u0 = 0; u0 < 4; u0 += 2) {
+      float4 g[2], mt[2], ck[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const uint32_t id = sr.has(id4[u0 + u]) ? id4[u0 + u] : sr.lo;  // clamped: loads issue early
+        g[u] = ldg(&geo[id]);
+        mt[u] = ldg(&met[id]);
+        ck[u] = ldg(&col[id]);
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const bool ok = sr.has(id4[u0 + u]) && mt[u].w != 0.f;
+        blend_step(score_fast(px, py, g[u], mt[u]).l, ok, ck[u], m, z, c);
+      }
+    }
+  }
+  if (z > 0.f) {
+    const float iz = 1.f / z;
+    c.x *= iz;
+    c.y *= iz;
+    c.z *= iz;
+  }
+  return c;
+}
+
+}  // namespace sad

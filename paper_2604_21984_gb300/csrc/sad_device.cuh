@@ -83,6 +83,33 @@ __device__ __forceinline__ bool key_before(float la, uint32_t ia, float lb, uint
   return la > lb || (la == lb && ia < ib);
 }
 
+// Derived table of one site (the "pack" of App. "Data Layout and Packing";
+// metric G of Sec. 4.1), each fp32 operation explicitly rounded so that the
+// result is reproducible: u = (ux,uy)/|(ux,uy)| (or (1,0)), e+ = exp(b+a),
+// e- = exp(b-a), G00 = e+ ux^2 + e- uy^2, G01 = (e+ - e-) ux uy,
+// G11 = e+ uy^2 + e- ux^2, tau s = exp(log_tau) s, active = (x >= 0).
+__device__ __forceinline__ void prepare_site(float x, float y, float logtau, float r, float cr,
+                                             float cg, float cb, float ux, float uy, float a,
+                                             float b, float s, float4& geo, float4& met,
+                                             float4& col) {
+  const float nrm = __fsqrt_rn(__fadd_rn(__fmul_rn(ux, ux), __fmul_rn(uy, uy)));
+  float uxn = 1.f, uyn = 0.f;
+  if (nrm > 0.f) {
+    uxn = __fdiv_rn(ux, nrm);
+    uyn = __fdiv_rn(uy, nrm);
+  }
+  const float ep = exp32_repro(__fadd_rn(b, a));
+  const float em = exp32_repro(__fsub_rn(b, a));
+  const float xx = __fmul_rn(uxn, uxn), yy = __fmul_rn(uyn, uyn), xy = __fmul_rn(uxn, uyn);
+  const float G00 = __fadd_rn(__fmul_rn(ep, xx), __fmul_rn(em, yy));
+  const float G01 = __fmul_rn(__fsub_rn(ep, em), xy);
+  const float G11 = __fadd_rn(__fmul_rn(ep, yy), __fmul_rn(em, xx));
+  const float ts = __fmul_rn(exp32_repro(logtau), s);
+  geo = make_float4(x, y, ts, r);
+  met = make_float4(G00, G01, G11, x >= 0.f ? 1.f : 0.f);
+  col = make_float4(cr, cg, cb, 0.f);
+}
+
 template <typename T>
 __device__ __forceinline__ T ldg(const T* p) {
   return __ldg(p);

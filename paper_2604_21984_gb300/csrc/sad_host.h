@@ -47,4 +47,7 @@ inline int check_problem(int32_t capacity, int32_t H, int32_t W, int32_t K, bool
   return SAD_OK;
 }
 
+struct AdamArgs;
+AdamArgs adam_args(const sad_adam_hparams* hp);
+
 }  // namespace sad

@@ -1,63 +1,10 @@
 // Forward blend (Sec. 4.2) over the cached top-K lists: full-image render and
 // random-access decode at float coordinates.
+#include "sad_blend.cuh"
 #include "sad_device.cuh"
 #include "sad_host.h"
 
 namespace sad {
-
-// Blend of the listed sites at point (px, py), streamed two entries at a time
-// with an online max-subtracted softmax: m = running max of the logits,
-// z = sum exp(l - m), c = sum exp(l - m) c_i, rescaled by exp(m_old - m_new)
-// when the max grows (the same w_i = exp(l_i - m)/z in exact arithmetic, no
-// per-entry state kept).  Black if no listed site is valid.
-__device__ __forceinline__ void blend_step(float l, bool ok, float4 ck, float& m, float& z, float3& c) {
-  const float mn = ok ? fmaxf(m, l) : m;
-  const float a = m == mn ? 1.f : __expf(m - mn);   // unchanged max (or still -inf): 1
-  const float b = ok ? (l == mn ? 1.f : __expf(l - mn)) : 0.f;
-  z = z * a + b;
-  c.x = c.x * a + b * ck.x;
-  c.y = c.y * a + b * ck.y;
-  c.z = c.z * a + b * ck.z;
-  m = mn;
-}
-
-template <int NP>
-__device__ __forceinline__ float3 blend_planes(const uint4* __restrict__ map, size_t P, size_t q,
-                                               float px, float py, uint32_t ucap,
-                                               const float4* __restrict__ geo,
-                                               const float4* __restrict__ met,
-                                               const float4* __restrict__ col) {
-  float m = -INFINITY, z = 0.f;
-  float3 c = make_float3(0.f, 0.f, 0.f);
-#pragma unroll
-  for (int j = 0; j < NP; ++j) {
-    const uint4 v = ldg(&map[j * P + q]);
-    const uint32_t id4[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int u0 = 0; u0 < 4; u0 += 2) {
-      float4 g[2], mt[2], ck[2];
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const uint32_t id = id4[u0 + u] < ucap ? id4[u0 + u] : 0u;  // clamped: loads issue early
-        g[u] = ldg(&geo[id]);
-        mt[u] = ldg(&met[id]);
-        ck[u] = ldg(&col[id]);
-      }
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const bool ok = id4[u0 + u] < ucap && mt[u].w != 0.f;
-        blend_step(score_fast(px, py, g[u], mt[u]).l, ok, ck[u], m, z, c);
-      }
-    }
-  }
-  if (z > 0.f) {
-    const float iz = 1.f / z;
-    c.x *= iz;
-    c.y *= iz;
-    c.z *= iz;
-  }
-  return c;
-}
 
 template <int K>
 __global__ void __launch_bounds__(256, 5) k_render(const float4* __restrict__ geo,
@@ -70,8 +17,8 @@ __global__ void __launch_bounds__(256, 5) k_render(const float4* __restrict__ ge
   if (x >= W || y >= H) return;
   const size_t P = static_cast<size_t>(H) * W;
   const size_t q = static_cast<size_t>(y) * W + x;
-  const float3 c = blend_planes<K / 4>(map, P, q, x + 0.5f, y + 0.5f, static_cast<uint32_t>(cap),
-                                      geo, met, col);
+  const float3 c = blend_planes<K / 4>(map, P, q, x + 0.5f, y + 0.5f,
+                                      SiteRange{0u, static_cast<uint32_t>(cap)}, geo, met, col);
   rgb[3 * q] = c.x;
   rgb[3 * q + 1] = c.y;
   rgb[3 * q + 2] = c.z;
@@ -93,7 +40,7 @@ __global__ void __launch_bounds__(256, 5) k_decode(const float4* __restrict__ ge
   cy = cy < 0 ? 0 : (cy >= H ? H - 1 : cy);
   const size_t P = static_cast<size_t>(H) * W;
   const float3 c = blend_planes<K / 4>(map, P, static_cast<size_t>(cy) * W + cx, p.x, p.y,
-                                       static_cast<uint32_t>(cap), geo, met, col);
+                                       SiteRange{0u, static_cast<uint32_t>(cap)}, geo, met, col);
   rgb[3 * i] = c.x;
   rgb[3 * i + 1] = c.y;
   rgb[3 * i + 2] = c.z;

@@ -1,0 +1,437 @@
+// Fused, batched training step (the paper's GPU-resident iteration, Sec. 5;
+// Sec. 6.3 epoch = one pass over all pixels) over up to kMaxImages images.
+//
+// One iteration is four kernels and two memsets, all on one stream, with the
+// iteration counter in device memory so the whole sequence can be captured
+// once in a CUDA graph and replayed:
+//  1. k_step_tile, one block per 16x16 tile of any image: the tile's pixels
+//     run one propagation pass at jump 1 (Sec. 4.3; reads the neighbours' old
+//     lists, writes the new ones), then - on the lists just computed, still in
+//     registers - the fused render + MSE + adjoint of the tile (per-tile
+//     records, deterministic);
+//  2. k_seg_accum: exact fixed-point per-site sums of the records;
+//  3. k_site_step, one thread per site: the chain rule to the 11 gradients,
+//     Adam with the paper's clamps (Sec. 6.1), and the prepared table of the
+//     updated site for the next iteration;
+//  4. k_step_finish: the per-image mean loss (fixed-order sums) and the
+//     iteration counters advance.
+// Each image uses its own site range, pixel range, injection seed and
+// fixed-point scale, so an image's result does not depend on the rest of the
+// batch.
+#include <cmath>
+
+#include "sad_adam.cuh"
+#include "sad_blend.cuh"
+#include "sad_host.h"
+#include "sad_tile.cuh"
+#include "sad_topk.cuh"
+
+namespace sad {
+
+struct BatchImg {
+  int32_t H, W;
+  uint32_t site_lo, site_n;
+  uint64_t pix_off;
+  uint32_t tile_off, tiles_x;
+  uint64_t seed;
+  float s, two_over_P;
+  int32_t t_off, pass_off;
+};
+
+struct BatchDesc {
+  int32_t B;
+  uint32_t n_tiles;
+  BatchImg img[kMaxImages];
+};
+
+// image of a block's tile (uniform per block)
+__device__ __forceinline__ int image_of_tile(const BatchDesc& d, uint32_t tile) {
+  int lo = 0, hi = d.B - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (d.img[mid].tile_off <= tile) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// image owning a site, or -1
+__device__ __forceinline__ int image_of_site(const BatchDesc& d, uint32_t i) {
+  int lo = 0, hi = d.B - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (d.img[mid].site_lo <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  return (i - d.img[lo].site_lo < d.img[lo].site_n) ? lo : -1;
+}
+
+template <int K>
+__global__ void __launch_bounds__(kTileThreads, 3)
+    k_step_tile(const BatchDesc d, TileIO io, const uint4* __restrict__ map_in,
+                uint4* __restrict__ map_out, size_t Ptot, int J, const int32_t* __restrict__ iter) {
+  __shared__ uint32_t s_q[kQueue][kTileThreads];
+  const int b = image_of_tile(d, blockIdx.x);
+  const BatchImg im = d.img[b];
+  const uint32_t lt = blockIdx.x - im.tile_off;
+  TileCtx c;
+  c.H = im.H;
+  c.W = im.W;
+  c.x0 = static_cast<int>(lt % im.tiles_x) * kTileSide;
+  c.y0 = static_cast<int>(lt / im.tiles_x) * kTileSide;
+  c.pix_off = im.pix_off;
+  c.sr = SiteRange{im.site_lo, im.site_n};
+  c.tile = blockIdx.x;
+  c.img = static_cast<uint32_t>(b);
+  c.two_over_P = im.two_over_P;
+  const int t = threadIdx.x;
+  const int x = c.x0 + (t & (kTileSide - 1)), y = c.y0 + (t >> 4);
+  const bool inimg = x < c.W && y < c.H;
+  const uint32_t code = (1u << 16) | (static_cast<uint32_t>(iter[1] + im.pass_off) & 0xffffu);
+  uint64_t v[K];
+  pixel_update<K, kTileThreads>(v, inimg, x, y, c.H, c.W, c.sr, io.geo, io.met, map_in, Ptot,
+                                im.pix_off, code, J, im.seed, s_q, t);
+  uint32_t ids[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) ids[k] = key_id(v[k]);
+  if (inimg) {
+    const size_t q = im.pix_off + static_cast<size_t>(y) * c.W + x;
+#pragma unroll
+    for (int j = 0; j < K / 4; ++j)
+      map_out[j * Ptot + q] = make_uint4(ids[4 * j], ids[4 * j + 1], ids[4 * j + 2], ids[4 * j + 3]);
+  }
+  tile_body<K, kModeGrad>(c, io, ids);
+}
+
+// The ten exact statistic sums of site i -> 11 gradients -> Adam -> prepared
+// table for the next iteration.  adam = false only prepares.
+__global__ void k_site_step(const BatchDesc d, float* __restrict__ params, float* __restrict__ m,
+                            float* __restrict__ v, float4* __restrict__ geo,
+                            float4* __restrict__ met, float4* __restrict__ col, int cap,
+                            const WsHeader* __restrict__ hdr,
+                            const unsigned long long* __restrict__ accq, AdamArgs A,
+                            const int32_t* __restrict__ iter, float* __restrict__ grads_out,
+                            bool adam) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cap) return;
+  const int b = image_of_site(d, static_cast<uint32_t>(i));
+  if (b < 0) return;
+  const BatchImg im = d.img[b];
+  const size_t c = static_cast<size_t>(cap);
+  float p[kNParams];
+#pragma unroll
+  for (int j = 0; j < kNParams; ++j) p[j] = params[j * c + i];
+  if (adam) {
+    float acc[10];
+    bool any = false;
+#pragma unroll
+    for (int j = 0; j < 10; ++j) {
+      const long long q = static_cast<long long>(accq[j * c + i]);
+      any |= q != 0;
+      acc[j] = static_cast<float>(static_cast<double>(q) * pow2(-fixed_shift(hdr->pmax[b][j])));
+    }
+    float g[kNParams];
+#pragma unroll
+    for (int j = 0; j < kNParams; ++j) g[j] = 0.f;
+    if (any) {
+      const float4 gs = geo[i], ms = met[i];
+      // chain rule through G(a, b, u) (Sec. 4.1), as in the stand-alone backward
+      const float ts = gs.z, r = gs.w;
+      const float G00 = ms.x, G01 = ms.y, G11 = ms.z;
+      const float rawx = p[PUX], rawy = p[PUY];
+      const float nrm2 = rawx * rawx + rawy * rawy;
+      float ux = 1.f, uy = 0.f;
+      if (nrm2 > 0.f) {
+        const float inv = rsqrtf(nrm2);
+        ux = rawx * inv;
+        uy = rawy * inv;
+      }
+      const float ep = expf(p[PB] + p[PA]), em = expf(p[PB] - p[PA]);
+      const float gG00 = -0.5f * ts * acc[7];
+      const float gG01 = -ts * acc[8];
+      const float gG11 = -0.5f * ts * acc[9];
+      g[PX] = ts * (G00 * acc[5] + G01 * acc[6]);
+      g[PY] = ts * (G01 * acc[5] + G11 * acc[6]);
+      g[PLOGTAU] = ts * (r * acc[3] - acc[4]);
+      g[PR] = ts * acc[3];
+      g[PCR] = acc[0];
+      g[PCG] = acc[1];
+      g[PCB] = acc[2];
+      const float xx = ux * ux, yy = uy * uy, xy = ux * uy;
+      g[PA] = gG00 * (ep * xx - em * yy) + gG01 * (ep + em) * xy + gG11 * (ep * yy - em * xx);
+      g[PB] = gG00 * G00 + gG01 * G01 + gG11 * G11;
+      const float gth = (ep - em) * (-2.f * xy * gG00 + (xx - yy) * gG01 + 2.f * xy * gG11);
+      g[PUX] = nrm2 > 0.f ? -gth * rawy / nrm2 : 0.f;
+      g[PUY] = nrm2 > 0.f ? gth * rawx / nrm2 : 0.f;
+    }
+    if (grads_out) {
+#pragma unroll
+      for (int j = 0; j < kNParams; ++j) grads_out[j * c + i] = g[j];
+    }
+    if (p[PX] >= 0.f) {
+      const int t = iter[0] + im.t_off;
+      const float bc1 = static_cast<float>(1.0 - pow(static_cast<double>(A.beta1), t));
+      const float bc2 = static_cast<float>(1.0 - pow(static_cast<double>(A.beta2), t));
+      adam_site(p, g, m, v, c, i, A, bc1, bc2, im.H, im.W);
+#pragma unroll
+      for (int j = 0; j < kNParams; ++j) params[j * c + i] = p[j];
+    }
+  }
+  prepare_site(p[PX], p[PY], p[PLOGTAU], p[PR], p[PCR], p[PCG], p[PCB], p[PUX], p[PUY], p[PA],
+               p[PB], im.s, geo[i], met[i], col[i]);
+}
+
+__global__ void k_step_finish(const BatchDesc d, const float* __restrict__ tile_loss,
+                              float* __restrict__ loss, int32_t* __restrict__ iter) {
+  __shared__ float s_w[8];
+  const int b = blockIdx.x;
+  const BatchImg im = d.img[b];
+  const uint32_t n = (b + 1 < d.B ? d.img[b + 1].tile_off : d.n_tiles) - im.tile_off;
+  float v = 0.f;
+  for (uint32_t i = threadIdx.x; i < n; i += 256) v += tile_loss[im.tile_off + i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float sum = 0.f;
+    for (int w = 0; w < 8; ++w) sum += s_w[w];
+    if (loss) loss[b] = sum / static_cast<float>(static_cast<double>(im.H) * im.W);
+    if (b == 0) {
+      iter[0] += 1;
+      iter[1] += 1;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_decode_batch(const BatchDesc d, const float4* __restrict__ geo,
+                                                      const float4* __restrict__ met,
+                                                      const float4* __restrict__ col,
+                                                      const uint4* __restrict__ map, size_t Ptot,
+                                                      int K, const float2* __restrict__ xy,
+                                                      const int32_t* __restrict__ qimg, int64_t n,
+                                                      float* __restrict__ rgb) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int b = qimg[i];
+  float3 c = make_float3(0.f, 0.f, 0.f);
+  if (b >= 0 && b < d.B) {
+    const BatchImg im = d.img[b];
+    const float2 p = ldg(&xy[i]);
+    int cx = static_cast<int>(floorf(p.x));
+    int cy = static_cast<int>(floorf(p.y));
+    cx = cx < 0 ? 0 : (cx >= im.W ? im.W - 1 : cx);
+    cy = cy < 0 ? 0 : (cy >= im.H ? im.H - 1 : cy);
+    const size_t q = im.pix_off + static_cast<size_t>(cy) * im.W + cx;
+    const SiteRange sr{im.site_lo, im.site_n};
+    switch (K) {
+      case 4: c = blend_planes<1>(map, Ptot, q, p.x, p.y, sr, geo, met, col); break;
+      case 8: c = blend_planes<2>(map, Ptot, q, p.x, p.y, sr, geo, met, col); break;
+      default: c = blend_planes<4>(map, Ptot, q, p.x, p.y, sr, geo, met, col); break;
+    }
+  }
+  rgb[3 * i] = c.x;
+  rgb[3 * i + 1] = c.y;
+  rgb[3 * i + 2] = c.z;
+}
+
+struct StepLayout {
+  size_t hdr, tile_loss, acc, records, total;
+  uint32_t max_records;
+};
+
+static inline size_t al256(size_t v) { return (v + 255) & ~static_cast<size_t>(255); }
+
+static StepLayout step_layout(uint32_t n_tiles, uint64_t total_pixels, int K, int total_cap,
+                              int64_t max_records) {
+  StepLayout L{};
+  uint64_t mr = max_records > 0 ? static_cast<uint64_t>(max_records) : total_pixels * K / 8;
+  if (max_records <= 0 && mr < 128ull * n_tiles) mr = 128ull * n_tiles;
+  if (mr > 0xfffffff0ull) mr = 0xfffffff0ull;
+  L.max_records = static_cast<uint32_t>(mr);
+  size_t o = 0;
+  L.hdr = o;       o = al256(o + sizeof(WsHeader));
+  L.tile_loss = o; o = al256(o + sizeof(float) * n_tiles);
+  L.acc = o;       o = al256(o + sizeof(unsigned long long) * 10 * static_cast<size_t>(total_cap));
+  L.records = o;   o = al256(o + sizeof(Record) * L.max_records);
+  L.total = o;
+  return L;
+}
+
+// Validates the host image table and fills the device descriptor.
+static int make_desc(const sad_batch_image* images, int32_t B, int32_t total_cap,
+                     int64_t total_pixels, BatchDesc& d, const char* name) {
+  if (!images || B < 1 || B > kMaxImages)
+    return einval("%s: need 1 <= B <= %d images", name, kMaxImages);
+  d.B = B;
+  uint32_t tiles = 0;
+  for (int b = 0; b < B; ++b) {
+    const sad_batch_image& im = images[b];
+    if (int e = check_problem(im.capacity, im.H, im.W, 4, false)) return e;
+    if (im.site_offset < 0 || static_cast<int64_t>(im.site_offset) + im.capacity > total_cap)
+      return einval("%s: image %d sites outside [0, %d)", name, b, total_cap);
+    if (b > 0 && im.site_offset < images[b - 1].site_offset + images[b - 1].capacity)
+      return einval("%s: image %d sites overlap the previous image", name, b);
+    if (im.pixel_offset < 0 || im.pixel_offset + static_cast<int64_t>(im.H) * im.W > total_pixels)
+      return einval("%s: image %d pixels outside [0, %lld)", name, b,
+                    static_cast<long long>(total_pixels));
+    BatchImg& o = d.img[b];
+    o.H = im.H;
+    o.W = im.W;
+    o.site_lo = static_cast<uint32_t>(im.site_offset);
+    o.site_n = static_cast<uint32_t>(im.capacity);
+    o.pix_off = static_cast<uint64_t>(im.pixel_offset);
+    o.tiles_x = static_cast<uint32_t>((im.W + kTileSide - 1) / kTileSide);
+    o.tile_off = tiles;
+    o.seed = im.seed;
+    o.s = 1.0f / static_cast<float>(im.H > im.W ? im.H : im.W);
+    o.two_over_P = 2.0f / static_cast<float>(static_cast<double>(im.H) * im.W);
+    o.t_off = im.t_offset;
+    o.pass_off = im.pass_offset;
+    tiles += o.tiles_x * static_cast<uint32_t>((im.H + kTileSide - 1) / kTileSide);
+  }
+  d.n_tiles = tiles;
+  return SAD_OK;
+}
+
+}  // namespace sad
+
+using namespace sad;
+
+extern "C" {
+
+size_t sad_step_workspace_bytes(const sad_batch_image* images, int32_t B, int32_t K,
+                                int32_t total_capacity, int64_t total_pixels,
+                                int64_t max_records) {
+  BatchDesc d;
+  if (K != 4 && K != 8 && K != 16) return 0;
+  if (make_desc(images, B, total_capacity, total_pixels, d, "sad_step_workspace_bytes") != SAD_OK)
+    return 0;
+  return step_layout(d.n_tiles, static_cast<uint64_t>(total_pixels), K, total_capacity, max_records)
+      .total;
+}
+
+int sad_prepare_batch(const sad_batch_image* images, int32_t B, const float* params, float* prep,
+                      int32_t total_capacity, int64_t total_pixels, void* stream) {
+  BatchDesc d;
+  if (int e = make_desc(images, B, total_capacity, total_pixels, d, "sad_prepare_batch")) return e;
+  if (total_capacity == 0) return SAD_OK;
+  if (!params || !prep || !aligned16(prep)) return einval("sad_prepare_batch: bad pointer");
+  float4* p4 = reinterpret_cast<float4*>(prep);
+  AdamArgs A{};
+  k_site_step<<<(total_capacity + 255) / 256, 256, 0, as_stream(stream)>>>(
+      d, const_cast<float*>(params), nullptr, nullptr, p4, p4 + total_capacity,
+      p4 + 2 * static_cast<size_t>(total_capacity), total_capacity, nullptr, nullptr, A, nullptr,
+      nullptr, false);
+  return check_launch("sad_prepare_batch");
+}
+
+int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t J, float* params,
+                   float* m, float* v, float* prep, int32_t total_capacity,
+                   const uint32_t* map_in, uint32_t* map_out, int64_t total_pixels,
+                   const float* targets, float* loss, const sad_adam_hparams* hp, int32_t* iter,
+                   float* grads_out, void* workspace, size_t workspace_bytes, void* stream) {
+  BatchDesc d;
+  if (int e = make_desc(images, B, total_capacity, total_pixels, d, "sad_train_step")) return e;
+  if (K != 4 && K != 8 && K != 16) return einval("sad_train_step: K must be 4, 8 or 16");
+  if (J < 0 || J > 16) return einval("sad_train_step: J must be in [0,16]");
+  if (static_cast<uint64_t>(total_pixels) * static_cast<uint64_t>(J > 0 ? J : 1) >= (1ull << 32))
+    return einval("sad_train_step: pixels * J must be below 2^32");
+  if (!params || !m || !v || !prep || !map_in || !map_out || !targets || !hp || !iter ||
+      !workspace)
+    return einval("sad_train_step: null pointer");
+  if (!aligned16(prep) || !aligned16(map_in) || !aligned16(map_out) ||
+      (reinterpret_cast<uintptr_t>(workspace) & 255u))
+    return einval("sad_train_step: misaligned pointer");
+  const size_t mbytes = static_cast<size_t>(total_pixels) * K * sizeof(uint32_t);
+  const char* a = reinterpret_cast<const char*>(map_in);
+  const char* bb = reinterpret_cast<const char*>(map_out);
+  if (a < bb + mbytes && bb < a + mbytes) return einval("sad_train_step: maps overlap");
+  const StepLayout L1 = step_layout(d.n_tiles, static_cast<uint64_t>(total_pixels), K,
+                                    total_capacity, 1);
+  if (workspace_bytes < L1.total) {
+    set_error("sad_train_step: workspace has %zu bytes, needs at least %zu", workspace_bytes,
+              L1.total);
+    return SAD_EWORKSPACE;
+  }
+  StepLayout L = L1;
+  {
+    const uint64_t per = sizeof(Record);
+    uint64_t mr = 1 + (workspace_bytes - L1.total) / per;
+    if (mr > 0xfffffff0ull) mr = 0xfffffff0ull;
+    for (int it = 0; it < 64 && mr > 1; ++it, --mr) {
+      const StepLayout T = step_layout(d.n_tiles, static_cast<uint64_t>(total_pixels), K,
+                                       total_capacity, static_cast<int64_t>(mr));
+      if (T.total <= workspace_bytes) {
+        L = T;
+        break;
+      }
+    }
+  }
+  cudaStream_t st = as_stream(stream);
+  char* base = static_cast<char*>(workspace);
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(base + L.hdr);
+  float* tile_loss = reinterpret_cast<float*>(base + L.tile_loss);
+  unsigned long long* accq = reinterpret_cast<unsigned long long*>(base + L.acc);
+  Record* rec = reinterpret_cast<Record*>(base + L.records);
+  cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(accq, 0, sizeof(unsigned long long) * 10 * static_cast<size_t>(total_capacity),
+                        st);
+  if (e != cudaSuccess) {
+    set_error("sad_train_step memset: %s", cudaGetErrorString(e));
+    return SAD_ECUDA;
+  }
+  float4* p4 = reinterpret_cast<float4*>(prep);
+  TileIO io;
+  io.geo = p4;
+  io.met = p4 + total_capacity;
+  io.col = p4 + 2 * static_cast<size_t>(total_capacity);
+  io.grad_rgb = nullptr;
+  io.target = targets;
+  io.rgb_out = nullptr;
+  io.tile_loss = tile_loss;
+  io.records = rec;
+  io.max_records = L.max_records;
+  io.hdr = hdr;
+  const uint4* mi = reinterpret_cast<const uint4*>(map_in);
+  uint4* mo = reinterpret_cast<uint4*>(map_out);
+  const size_t Ptot = static_cast<size_t>(total_pixels);
+  switch (K) {
+    case 4: k_step_tile<4><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, iter); break;
+    case 8: k_step_tile<8><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, iter); break;
+    default: k_step_tile<16><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, iter); break;
+  }
+  if (int r = check_launch("k_step_tile")) return r;
+  k_seg_accum<10><<<152 * 8, 256, 0, st>>>(rec, hdr, L.max_records, total_capacity, accq);
+  if (int r = check_launch("k_seg_accum")) return r;
+  const AdamArgs A = adam_args(hp);
+  k_site_step<<<(total_capacity + 255) / 256, 256, 0, st>>>(
+      d, params, m, v, p4, p4 + total_capacity, p4 + 2 * static_cast<size_t>(total_capacity),
+      total_capacity, hdr, accq, A, iter, grads_out, true);
+  if (int r = check_launch("k_site_step")) return r;
+  k_step_finish<<<B, 256, 0, st>>>(d, tile_loss, loss, iter);
+  return check_launch("k_step_finish");
+}
+
+int sad_decode_batch(const sad_batch_image* images, int32_t B, int32_t K, const float* prep,
+                     int32_t total_capacity, const uint32_t* map, int64_t total_pixels,
+                     const float* xy, const int32_t* query_image, int64_t n, float* rgb,
+                     void* stream) {
+  BatchDesc d;
+  if (int e = make_desc(images, B, total_capacity, total_pixels, d, "sad_decode_batch")) return e;
+  if (K != 4 && K != 8 && K != 16) return einval("sad_decode_batch: K must be 4, 8 or 16");
+  if (n < 0) return einval("sad_decode_batch: n must be >= 0");
+  if (n == 0) return SAD_OK;
+  if (!prep || !map || !xy || !query_image || !rgb) return einval("sad_decode_batch: null pointer");
+  if (!aligned16(prep) || !aligned16(map) || (reinterpret_cast<uintptr_t>(xy) & 7u))
+    return einval("sad_decode_batch: misaligned pointer");
+  const float4* p4 = reinterpret_cast<const float4*>(prep);
+  k_decode_batch<<<static_cast<unsigned>((n + 255) / 256), 256, 0, as_stream(stream)>>>(
+      d, p4, p4 + total_capacity, p4 + 2 * static_cast<size_t>(total_capacity),
+      reinterpret_cast<const uint4*>(map), static_cast<size_t>(total_pixels), K,
+      reinterpret_cast<const float2*>(xy), query_image, n, rgb);
+  return check_launch("k_decode_batch");
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+"""Batched fused training step: equals the unfused single-image sequence,
+an image's result does not depend on the batch, graph replay equals eager."""
+import numpy as np
+import pytest
+
+from paper_2604_21984_gb300 import inputs as gen
+from tests.gpu_util import assert_grads_close, dev, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def capi():
+    return require_gpu()
+
+
+def _images(sizes, seed):
+    return [dev(gen.image_noise_polygons_lines(H, W, seed=seed + i, n_polygons=6, n_lines=3))
+            for i, (H, W) in enumerate(sizes)]
+
+
+def test_fused_step_matches_unfused_sequence(capi, oracle):
+    """One batched step on a single image == prepare, pass, train_grads, Adam."""
+    torch = pytest.importorskip("torch")
+    from paper_2604_21984_gb300.batch import BatchConfig, BatchTrainer
+    imgs = _images([(40, 56)], 7)
+    tr = BatchTrainer(imgs, BatchConfig(K=8, J=2, graph=False, seed=3))
+    H, W = 40, 56
+    n = tr.total_cap
+    p0 = tr.params.clone()
+    map0 = capi.ids_from_map(tr.maps[0])
+    t_pass = int(tr.iter[1].item())
+    seed = tr.images[0]["seed"]
+    grads_fused = torch.empty_like(tr.params)
+    capi.sad_train_step(tr.table, 8, 2, tr.params, tr.m, tr.v, tr.prep, tr.maps[0], tr.maps[1],
+                        tr.total_pixels, tr.targets, tr.loss, tr.hp, tr.iter, tr.ws, grads_out=grads_fused)
+    torch.cuda.synchronize()
+    # unfused reference on copies
+    p = p0.clone()
+    prep = capi.empty_prep(n)
+    capi.sad_prepare_sites(p, H, W, prep)
+    a = capi.map_from_ids(map0)
+    b = capi.empty_map(H, W, 8)
+    capi.sad_update_topk(prep, n, H, W, 8, a, b, (1 << 16) | t_pass, 2, seed)
+    assert np.array_equal(capi.ids_from_map(b), capi.ids_from_map(tr.maps[1]))
+    grads = torch.empty_like(p)
+    loss = torch.empty(1, device="cuda")
+    ws = capi.backward_workspace(H, W, 8, n)
+    capi.sad_train_grads(p, prep, H, W, 8, b, imgs[0], grads, loss, ws)
+    assert abs(loss.item() - tr.loss[0].item()) <= 1e-6 * loss.item()
+    assert_grads_close(grads_fused.cpu().numpy().astype(np.float64), grads.cpu().numpy().astype(np.float64))
+    m = torch.zeros_like(p)
+    v = torch.zeros_like(p)
+    capi.sad_adam_step(p, grads_fused, m, v, H, W, 1, tr.hp)
+    np.testing.assert_allclose(tr.params.cpu().numpy(), p.cpu().numpy(), rtol=1e-6, atol=1e-6)
+    # the prepared table was refreshed for the new parameters
+    prep2 = capi.empty_prep(n)
+    capi.sad_prepare_sites(tr.params, H, W, prep2)
+    assert torch.equal(prep2, tr.prep)
+
+
+def test_batch_results_do_not_depend_on_the_batch(capi):
+    """Three uneven images trained together == each trained alone (bitwise)."""
+    torch = pytest.importorskip("torch")
+    from paper_2604_21984_gb300.batch import BatchConfig, BatchTrainer
+    sizes = [(48, 80), (96, 64), (33, 47)]
+    imgs = _images(sizes, 11)
+    cfg = BatchConfig(K=16, J=4, graph=False, seed=5)
+    tr = BatchTrainer(imgs, cfg)
+    tr.run(12)
+    for b, img in enumerate(imgs):
+        solo = BatchTrainer([img], cfg, seeds=[tr.images[b]["seed"]])
+        solo.run(12)
+        lo, n = tr.images[b]["site_offset"], tr.images[b]["capacity"]
+        assert torch.equal(tr.params[:, lo:lo + n], solo.params[:, :n]), b
+        assert np.array_equal(tr.map_for(b), solo.map_for(0)), b
+        assert tr.loss[b].item() == solo.loss[0].item()
+
+
+def test_graph_replay_equals_eager(capi):
+    torch = pytest.importorskip("torch")
+    from paper_2604_21984_gb300.batch import BatchConfig, BatchTrainer
+    imgs = _images([(64, 64), (40, 72)], 21)
+    a = BatchTrainer(imgs, BatchConfig(K=8, J=4, graph=False, seed=2))
+    b = BatchTrainer(imgs, BatchConfig(K=8, J=4, graph=True, seed=2))
+    a.run(10)
+    b.run(10)
+    torch.cuda.synchronize()
+    assert torch.equal(a.params, b.params)
+    assert torch.equal(a.maps[0], b.maps[0])
+    assert int(b.iter[0].item()) == 11 and int(b.iter[1].item()) == 1034
+
+
+def test_batch_training_improves_psnr(capi):
+    from paper_2604_21984_gb300.batch import BatchConfig, BatchTrainer
+    imgs = _images([(96, 128), (128, 96), (80, 80)], 31)
+    tr = BatchTrainer(imgs, BatchConfig(K=16, J=4, seed=1))
+    tr.run(2)
+    p0 = tr.psnr()
+    tr.run(300)
+    p1 = tr.psnr()
+    print("PSNR", p0, "->", p1)
+    assert all(b > a + 3.0 for a, b in zip(p0, p1))
