@@ -1,22 +1,33 @@
 #!/usr/bin/env python3
-"""Benchmark of the SAD hot path (one training iteration) on GB300.
+"""Benchmark of the SAD hot path on GB300.
 
-Workload (N=1): plain SAD encode step of one 768x512 RGB FP32 synthetic image
-(multi-octave value noise + 40 polygons + thin lines), 32768 sites, K=16,
-J=4 injected ids, after a JFA warm-up of the top-K field.  One step = one
-training iteration of the hot path, all on the GPU:
-    sad_prepare_sites -> sad_update_topk (1 pass, jump 1)
-    -> sad_train_grads (fused render + MSE + adjoint + segmented reduce)
-    -> sad_adam_step.
-Metric: fwd+bwd Mpix/s at K=16 (pixels of training iterations per second).
-The step's working set (~60 MB) fits in L2, so L2 is flushed (a 256 MB write)
-before every timed step and each step is timed alone with CUDA events.
+Headline (N=1): the plain SAD encode iteration of one 768x512 RGB FP32
+synthetic image (multi-octave value noise + 40 polygons + 1-3 px lines),
+32768 gradient-weighted sites (capacity 65536), K=16, J=4 injected ids,
+after the JFA warm-up of the top-K field.  One step = one training iteration,
+all on the GPU in one fused call (sad_train_step on a one-image batch): one
+propagation pass at jump 1, render + MSE + adjoint, exact per-site sums,
+Adam and the next prepared table.  Metric: fwd+bwd Mpix/s at K=16 (pixels of
+training iterations per second).  The step's working set fits in L2, so L2
+is flushed (a 256 MB write) before every timed step; each step is timed alone
+with CUDA events, and every kernel of the library is timed by its own event
+pair (the library's stage tracing) for the roofline of the dominant kernel.
+
+Legs on one GPU (each can be skipped):
+  encode  the full config-2 encode: init + 2000 iterations with densify/prune
+          every 200 (encode images/s, PSNR);
+  c3      render + render backward at 2048x2048, 262144 random anisotropic
+          sites, K=16 (the autograd form; HBM roofline of the pair);
+  c4      64 uneven images (long side log-uniform 256..2048, aspect 1..1.5,
+          0.06 sites/px): the batched fused step in a CUDA graph with (K, J)
+          picked by the autotuner vs the plain one-image-at-a-time loop, equal
+          iterations, PSNR of both;
+  c5      a Poisson request stream (70% random-access decodes on resident
+          site sets, 30% encodes) served with continuous batching vs the plain
+          FIFO loop at 0.7x the plain loop's measured capacity: p50/p99.
 
 With N>1 (torchrun) every rank trains its own image (weak scaling, no
 data-path collective); value = all pixels / max-over-ranks time.
-
-Also measured: render + backward at 2048x2048, 262144 sites, K=16 (the
-autograd form) for the HBM roofline of the backward.
 
 --impl reference runs the CPU oracle on a bounded sample of the same workload.
 """
@@ -25,11 +36,13 @@ from __future__ import annotations
 import argparse
 import json
 import math
+import multiprocessing
 import os
 import statistics
 import subprocess
 import sys
 import time
+from concurrent.futures import ProcessPoolExecutor
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -38,9 +51,8 @@ H_C2, W_C2, N_C2, K_C2, J_C2 = 512, 768, 32768, 16, 4
 METRIC = "fwd+bwd Mpix/s at K=16"
 UNIT = "Mpix/s"
 WORKLOAD = ("plain SAD encode training iteration: 768x512 RGB FP32 synthetic image "
-            "(value noise + 40 polygons + 1-3 px lines), 32768 sites, K=16, J=4, "
+            "(value noise + 40 polygons + 1-3 px lines), 32768 gradient-weighted sites, K=16, J=4, "
             "top-K refresh every iteration")
-LAUNCHES_PER_STEP = 11   # prepare, topk update, bwd tile, loss, seg count, 3 scan, scatter, site grads, adam
 
 
 def parse():
@@ -49,10 +61,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-encode", action="store_true", help="skip the full 2000-iteration encode leg")
     ap.add_argument("--no-c3", action="store_true", help="skip the 2048^2 render+backward leg")
+    ap.add_argument("--no-c4", action="store_true", help="skip the batched-vs-plain leg")
+    ap.add_argument("--no-c5", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--only-c3", action="store_true",
-                    help="run only the 2048^2 render+backward leg (profiling target)")
+    ap.add_argument("--legs-only", default="", help="comma list of legs to run alone (encode,c3,c4,c5)")
+    ap.add_argument("--c4-iters", type=int, default=100, help="training iterations of the c4 leg")
+    ap.add_argument("--c5-seconds", type=float, default=8.0, help="length of the c5 request stream")
+    ap.add_argument("--c5-max-side", type=int, default=2048, help="largest encode side in the c5 stream")
+    ap.add_argument("--c5-iters", type=int, default=1000, help="iterations of each c5 encode")
     return ap.parse_args()
 
 
@@ -62,20 +80,6 @@ def measured_peaks():
         d = json.load(open(path))
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
-
-
-# ----------------------------------------------------------------------------
-# workload inputs (seeded, host side)
-# ----------------------------------------------------------------------------
-
-def c2_inputs(rank):
-    from paper_2604_21984_gb300 import inputs as gen
-    img = gen.image_noise_polygons_lines(H_C2, W_C2, seed=2000 + rank)
-    s = 1.0 / max(H_C2, W_C2)
-    d0 = math.sqrt(H_C2 * W_C2 / N_C2)
-    tau0 = 4.0 / (s * d0)                      # tau s d0 = 4: a few px of soft overlap
-    params = gen.sites_isotropic(img, N_C2, seed=2100 + rank, scale_px=1.0, tau=tau0)
-    return img, params
 
 
 # ----------------------------------------------------------------------------
@@ -131,8 +135,29 @@ class Clocks:
 # our arm
 # ----------------------------------------------------------------------------
 
+def _gen_image(args):
+    from paper_2604_21984_gb300 import inputs as gen
+    H, W, seed = args
+    return gen.image_noise_polygons_lines(H, W, seed=seed)
+
+
+def gen_images(specs):
+    """Synthetic images [(H, W, seed)] generated in parallel host processes
+    (spawned, so no CUDA state is inherited)."""
+    if len(specs) <= 2:
+        return [_gen_image(s) for s in specs]
+    workers = max(1, min(len(specs), (os.cpu_count() or 2) - 1, 16))
+    with ProcessPoolExecutor(workers, mp_context=multiprocessing.get_context("spawn")) as ex:
+        return list(ex.map(_gen_image, specs))
+
+
+def dominant(trace):
+    name = max(trace, key=lambda k: trace[k][1])
+    n, ms = trace[name]
+    return name, n, ms / max(n, 1)
+
+
 def run_ours(args):
-    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -143,90 +168,57 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     from paper_2604_21984_gb300 import build, capi
+    from paper_2604_21984_gb300 import inputs as gen
+    from paper_2604_21984_gb300.encode import EncodeConfig, Encoder
     if rank == 0:
         build.build()
     if world > 1:
         dist.barrier()
     capi.lib()
+    dev = torch.device("cuda", local)
+    peak, peak_kind = measured_peaks()
 
-    if args.only_c3:
-        peak, peak_kind = measured_peaks()
-        print(json.dumps({"c3_render_backward": c3_leg(capi, torch.device("cuda", local), peak, peak_kind)}))
+    if args.legs_only:
+        legs = {}
+        for leg in args.legs_only.split(","):
+            legs[leg] = LEGS[leg](capi, dev, peak, peak_kind, args)
+        print(json.dumps(legs), flush=True)
         return
+
     H, W, N, K, J = H_C2, W_C2, N_C2, K_C2, J_C2
     P = H * W
-    img, params = c2_inputs(rank)
-    dev = torch.device("cuda", local)
-    pt = torch.from_numpy(params).to(dev)
+    img = gen.image_noise_polygons_lines(H, W, seed=2000 + rank)
     target = torch.from_numpy(img).to(dev)
-    prep = capi.empty_prep(N, dev)
-    ma, mb = capi.empty_map(H, W, K, dev), capi.empty_map(H, W, K, dev)
-    grads = torch.empty((11, N), dtype=torch.float32, device=dev)
-    m = torch.zeros_like(pt)
-    v = torch.zeros_like(pt)
-    loss = torch.empty(1, dtype=torch.float32, device=dev)
-    ws = capi.backward_workspace(H, W, K, N, device=dev)
-    hp = capi.adam_hparams()
+    enc = Encoder(target, EncodeConfig(n_sites=N, K=K, J=J, seed=rank, densify_every=0))
+    enc.init()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-
-    def step_code(t):
-        L = max(H, W)
-        lb = math.ceil(math.log2(L))
-        s = max(1, (1 << lb) >> (min(t, lb - 1) + 1))
-        return (s << 16) | (t & 0xFFFF)
-
-    # JFA warm-up of the field: seed + log2(B) passes
-    capi.sad_prepare_sites(pt, H, W, prep)
-    capi.sad_topk_seed(prep, N, H, W, K, ma)
-    t_pass = 0
-    for t_pass in range(10):
-        capi.sad_update_topk(prep, N, H, W, K, ma, mb, step_code(t_pass), J, 7)
-        ma, mb = mb, ma
-    state = {"t": t_pass + 1, "it": 0, "ma": ma, "mb": mb}
-
-    def step(timed_parts=None):
-        state["it"] += 1
-        capi.sad_prepare_sites(pt, H, W, prep)
-        if timed_parts is not None:
-            timed_parts["u0"].record()
-        capi.sad_update_topk(prep, N, H, W, K, state["ma"], state["mb"], step_code(state["t"]), J, 7)
-        if timed_parts is not None:
-            timed_parts["u1"].record()
-        state["ma"], state["mb"] = state["mb"], state["ma"]
-        state["t"] += 1
-        capi.sad_train_grads(pt, prep, H, W, K, state["ma"], target, grads, loss, ws)
-        if timed_parts is not None:
-            timed_parts["g1"].record()
-        capi.sad_adam_step(pt, grads, m, v, H, W, state["it"], hp)
-
     for _ in range(args.warmup):
-        step()
+        enc.step()
     torch.cuda.synchronize()
-    st, used = capi.sad_workspace_status(ws)
-    if st != 0:
-        raise RuntimeError(f"workspace overflow during warm-up ({used} records)")
 
     E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
-    evs = [{"s": E(), "u0": E(), "u1": E(), "g1": E(), "e": E()} for _ in range(args.steps)]
+    evs = [(E(), E()) for _ in range(args.steps)]
     clocks = Clocks(local)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    capi.sad_trace_collect()
     clocks.start()
     time.sleep(0.3)
+    capi.sad_trace_enable(True)
     for i in range(args.steps):
         flush.zero_()
-        evs[i]["s"].record()
-        step(evs[i])
-        evs[i]["e"].record()
+        evs[i][0].record()
+        enc.step()
+        evs[i][1].record()
     torch.cuda.synchronize()
+    capi.sad_trace_enable(False)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     ck = clocks.stop()
-    step_ms = [e["s"].elapsed_time(e["e"]) for e in evs]
-    upd_ms = [e["u0"].elapsed_time(e["u1"]) for e in evs]
-    grad_ms = [e["u1"].elapsed_time(e["g1"]) for e in evs]
+    trace = capi.sad_trace_collect()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(step_ms)
     if world > 1:
         tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
@@ -234,7 +226,24 @@ def run_ours(args):
         total_ms = float(tt.item())
     value = world * P * args.steps / (total_ms / 1e3) / 1e6
 
-    # end to end through the public C-ABI binding with host buffers
+    # the same iteration as four separate calls (context for the fusion)
+    enc_u = Encoder(target, EncodeConfig(n_sites=N, K=K, J=J, seed=rank, densify_every=0, fused=False))
+    enc_u.init()
+    for _ in range(3):
+        enc_u.step()
+    u_ms = []
+    for _ in range(10):
+        flush.zero_()
+        a, b = E(), E()
+        a.record()
+        enc_u.step()
+        b.record()
+        torch.cuda.synchronize()
+        u_ms.append(a.elapsed_time(b))
+    del enc_u
+
+    # end to end through the public API with host buffers: the target image
+    # goes up from pinned memory and the loss comes back every step
     host_img = torch.from_numpy(img).pin_memory()
     host_loss = torch.empty(1, dtype=torch.float32).pin_memory()
     e2e_s = 0.0
@@ -242,43 +251,54 @@ def run_ours(args):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        target.copy_(host_img, non_blocking=True)
-        step()
-        host_loss.copy_(loss, non_blocking=True)
+        enc.target.copy_(host_img, non_blocking=True)
+        enc.step()
+        host_loss.copy_(enc.loss, non_blocking=True)
         torch.cuda.synchronize()
         e2e_s += time.perf_counter() - t0
     if world > 1:
         tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_s = float(tt.item())
-    e2e = {"value": world * P * args.steps / e2e_s / 1e6, "unit": UNIT,
+    e2e = {"value": round(world * P * args.steps / e2e_s / 1e6, 3), "unit": UNIT,
            "h2d_bytes_per_step": int(host_img.numel() * 4), "d2h_bytes_per_step": 4}
 
-    peak, peak_kind = measured_peaks()
-    g_ms = statistics.mean(grad_ms)
-    alg_bytes = P * (K * 4 + 12) + N * (48 + 44)
-    achieved = alg_bytes / (g_ms / 1e3) / 1e9
-    roofline = {"kernel": "sad_train_grads (fused render+MSE+adjoint+segmented reduce)",
-                "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "peak_kind": peak_kind, "traffic": None,
-                "algorithmic_bytes": alg_bytes, "avg_ms": round(g_ms, 5)}
+    # roofline of the dominant kernel, from its own event pairs in the timed
+    # region: algorithmic bytes = map read + map write (64 B each at K=16) +
+    # target 12 B per pixel, and the prepared site table (48 B per slot)
+    kname, klaunch, kms = dominant(trace)
+    alg = {"k_step_tile": P * (K * 4 * 2 + 12) + enc.cap * 48}
+    roofline = None
+    if kname in alg:
+        achieved = alg[kname] / (kms / 1e3) / 1e9
+        roofline = {"kernel": kname, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                    "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                    "traffic": None, "algorithmic_bytes_per_launch": alg[kname],
+                    "avg_launch_ms": round(kms, 5), "launches": klaunch}
+    launches = sum(n for n, _ in trace.values())
 
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "H": H, "W": W, "sites": N, "K": K, "J": J,
-                   "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas x{world}"},
-        "breakdown_ms": {"update_topk": round(statistics.mean(upd_ms), 5),
-                         "train_grads": round(g_ms, 5),
-                         "prepare+adam": round(statistics.mean(step_ms) - statistics.mean(upd_ms) - g_ms, 5)},
-        "encode_images_per_s_2000it": round(1e3 / (2000 * statistics.mean(step_ms)), 4),
-        "e2e": e2e, "roofline": roofline, "clocks": ck,
-        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+        "config": {"workload": WORKLOAD, "H": H, "W": W, "sites": N, "capacity": enc.cap, "K": K, "J": J,
+                   "step": "fused sad_train_step (one-image batch)",
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": f"replicas x{world}"},
+        "kernels_ms": {k: round(ms / max(n, 1), 5) for k, (n, ms) in sorted(trace.items())},
+        "unfused_step_ms": round(statistics.median(u_ms), 5),
+        "e2e": e2e, "roofline": roofline, "clocks": ck, "gpu_launches": launches,
     }
-    if not args.no_c3:
-        line["c3_render_backward"] = c3_leg(capi, dev, peak, peak_kind)
+    del enc
+    if world == 1:
+        want = [k for k in ("encode", "c3", "c4", "c5") if not getattr(args, "no_" + k)]
+        for leg in want:
+            try:
+                line[leg] = LEGS[leg](capi, dev, peak, peak_kind, args)
+            except Exception as e:   # a failed leg is reported, the headline still prints
+                line[leg] = {"error": f"{type(e).__name__}: {e}"}
+            torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -287,7 +307,33 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def c3_leg(capi, dev, peak, peak_kind, iters=10):
+def encode_leg(capi, dev, peak, peak_kind, args, iters=2000):
+    """The full config-2 encode: gradient-weighted init, JFA warm-up, 2000
+    fused iterations with densify/prune every 200 in [200, 1800]."""
+    import torch
+    from paper_2604_21984_gb300 import inputs as gen
+    from paper_2604_21984_gb300.encode import EncodeConfig, Encoder
+    img = torch.from_numpy(gen.image_noise_polygons_lines(H_C2, W_C2, seed=2000)).to(dev)
+    out = {}
+    for rep in range(2):   # the first run warms the allocator and the library
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        enc = Encoder(img, EncodeConfig(n_sites=N_C2, K=K_C2, J=J_C2, iters=iters, seed=0))
+        enc.run()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        out = {"workload": "768x512, 32768 gradient-weighted sites (capacity 65536), K=16, J=4, "
+                           f"{iters} iterations, densify/prune every 200 in [200,1800]",
+               "seconds": round(wall, 4), "images_per_s": round(1.0 / wall, 4),
+               "psnr_db": round(enc.psnr(), 3), "active_sites": enc.n_active,
+               "paper_context": "Kodak 768x512, 50k sites, K=8, 4000 it: 2.2 s, 46.00 dB "
+                                "(Kodak @4 BPP: 40.4 dB at 2000 it, ~0.6 s); hardware not stated, "
+                                "RTX 5090 implied"}
+        del enc
+    return out
+
+
+def c3_leg(capi, dev, peak, peak_kind, args, iters=10):
     """render + render_backward at 2048^2, 262144 random anisotropic sites, K=16."""
     import torch
     from paper_2604_21984_gb300 import inputs as gen
@@ -299,10 +345,14 @@ def c3_leg(capi, dev, peak, peak_kind, iters=10):
     capi.sad_prepare_sites(pt, H, W, prep)
     a, b = capi.empty_map(H, W, K, dev), capi.empty_map(H, W, K, dev)
     capi.sad_topk_seed(prep, N, H, W, K, a)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     for t in range(16):
         s = max(1, 2048 >> (min(t, 10) + 1))
         capi.sad_update_topk(prep, N, H, W, K, a, b, (s << 16) | t, 2, 11)
         a, b = b, a
+    torch.cuda.synchronize()
+    jfa_ms = (time.perf_counter() - t0) * 1e3
     rgb = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
     g = torch.from_numpy(gen.grad_image(H, W, seed=3002) / (H * W)).to(dev)
     grads = torch.empty((11, N), dtype=torch.float32, device=dev)
@@ -314,6 +364,8 @@ def c3_leg(capi, dev, peak, peak_kind, iters=10):
     torch.cuda.synchronize()
     st, used = capi.sad_workspace_status(ws)
     r_ms, b_ms = [], []
+    capi.sad_trace_collect()
+    capi.sad_trace_enable(True)
     for _ in range(iters):
         e0, e1, e2 = E(), E(), E()
         e0.record()
@@ -324,24 +376,175 @@ def c3_leg(capi, dev, peak, peak_kind, iters=10):
         torch.cuda.synchronize()
         r_ms.append(e0.elapsed_time(e1))
         b_ms.append(e1.elapsed_time(e2))
+    capi.sad_trace_enable(False)
+    trace = capi.sad_trace_collect()
     P = H * W
     rb = statistics.mean(r_ms)
     bb = statistics.mean(b_ms)
     render_bytes = P * (K * 4 + 12) + N * 48
     bwd_bytes = P * (K * 4 + 12) + N * (48 + 44)
+
+    def roof(nbytes, ms):
+        a = nbytes / (ms / 1e3) / 1e9
+        return {"bound": "hbm", "achieved": round(a, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(a / peak, 4), "peak_kind": peak_kind}
     return {
         "workload": "2048x2048, 262144 random anisotropic sites, K=16, map from seed + 16 passes",
         "mpix_per_s_fwd_bwd": round(P / ((rb + bb) / 1e3) / 1e6, 1),
-        "render_ms": round(rb, 4), "backward_ms": round(bb, 4), "records": used, "ws_status": st,
-        "roofline_render": {"bound": "hbm", "achieved": round(render_bytes / (rb / 1e3) / 1e9, 1),
-                            "peak": peak, "unit": "GB/s",
-                            "frac": round(render_bytes / (rb / 1e3) / 1e9 / peak, 4), "peak_kind": peak_kind},
-        "roofline_fwd_bwd": {"bound": "hbm",
-                             "achieved": round((render_bytes + bwd_bytes) / ((rb + bb) / 1e3) / 1e9, 1),
-                             "peak": peak, "unit": "GB/s",
-                             "frac": round((render_bytes + bwd_bytes) / ((rb + bb) / 1e3) / 1e9 / peak, 4),
-                             "peak_kind": peak_kind},
+        "render_ms": round(rb, 4), "backward_ms": round(bb, 4), "jfa_16_passes_ms": round(jfa_ms, 3),
+        "records": used, "ws_status": st,
+        "kernels_ms": {k: round(ms / max(n, 1), 5) for k, (n, ms) in sorted(trace.items())},
+        "roofline_render": roof(render_bytes, rb),
+        "roofline_fwd_bwd": roof(render_bytes + bwd_bytes, rb + bb),
     }
+
+
+def c4_leg(capi, dev, peak, peak_kind, args, n_images=64, seed=4000):
+    """64 uneven images: batched fused step (CUDA graph, autotuned K/J) vs the
+    plain loop (one image at a time, the separate calls), equal iterations."""
+    import torch
+    from paper_2604_21984_gb300 import inputs as gen
+    from paper_2604_21984_gb300.batch import BatchConfig, BatchTrainer, autotune
+    from paper_2604_21984_gb300.encode import EncodeConfig, Encoder, psnr_from_loss
+    iters = args.c4_iters
+    sizes = gen.batch_sizes(n_images, seed)
+    t0 = time.perf_counter()
+    imgs_np = gen_images([(H, W, seed + 1 + i) for i, (H, W) in enumerate(sizes)])
+    gen_s = time.perf_counter() - t0
+    imgs = [torch.from_numpy(a).to(dev) for a in imgs_np]
+    del imgs_np
+    P = sum(H * W for H, W in sizes)
+    (K, J), table = autotune(imgs[:8], iters=iters, seed=seed)
+    E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    # batched
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seeds = [seed + 1 + i for i in range(n_images)]
+    tr = BatchTrainer(imgs, BatchConfig(K=K, J=J), seeds=seeds)
+    torch.cuda.synchronize()
+    b_init = time.perf_counter() - t0
+    tr.run(2)                              # graph capture outside the timed region
+    torch.cuda.synchronize()
+    e0, e1 = E(), E()
+    e0.record()
+    tr.run(iters - 2)
+    e1.record()
+    torch.cuda.synchronize()
+    b_train = e0.elapsed_time(e1) / 1e3 * iters / (iters - 2)
+    b_psnr = tr.psnr()
+    del tr
+    torch.cuda.empty_cache()
+    # plain loop: each image alone, K=16, J=4, the four separate calls per iteration
+    p_psnr, p_train, p_init = [], 0.0, 0.0
+    for i, img in enumerate(imgs):
+        H, W = sizes[i]
+        n = max(1, min(H * W, int(round(0.06 * H * W))))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        enc = Encoder(img, EncodeConfig(n_sites=n, K=16, J=4, capacity_factor=1.0, seed=seeds[i],
+                                        densify_every=0, fused=False))
+        enc.init()
+        torch.cuda.synchronize()
+        p_init += time.perf_counter() - t0
+        e0, e1 = E(), E()
+        e0.record()
+        for _ in range(iters):
+            enc.step()
+        e1.record()
+        torch.cuda.synchronize()
+        p_train += e0.elapsed_time(e1) / 1e3
+        p_psnr.append(psnr_from_loss(float(enc.loss.item())))
+        del enc
+    mb, mp = statistics.mean(b_psnr), statistics.mean(p_psnr)
+    return {
+        "workload": f"{n_images} images, long side log-uniform 256..2048, aspect 1..1.5, "
+                    f"{P / 1e6:.1f} MP total, 0.06 sites/px, {iters} iterations",
+        "autotune": {"picked": {"K": K, "J": J},
+                     "candidates": [{"K": k, "J": j, "ms_per_iter": round(ms, 3), "psnr_db": round(ps, 3)}
+                                    for k, j, ms, ps in table]},
+        "batched": {"train_s": round(b_train, 4), "init_s": round(b_init, 3),
+                    "images_per_s": round(n_images / (b_train + b_init), 3),
+                    "train_mpix_per_s": round(P * iters / b_train / 1e6, 1),
+                    "mean_psnr_db": round(mb, 3)},
+        "plain": {"train_s": round(p_train, 4), "init_s": round(p_init, 3),
+                  "images_per_s": round(n_images / (p_train + p_init), 3),
+                  "train_mpix_per_s": round(P * iters / p_train / 1e6, 1),
+                  "mean_psnr_db": round(mp, 3)},
+        "speedup_train": round(p_train / b_train, 3),
+        "psnr_delta_db": round(mb - mp, 3),
+        "host_image_generation_s": round(gen_s, 2),
+    }
+
+
+def c5_leg(capi, dev, peak, peak_kind, args, seed=5000):
+    """Poisson stream served with continuous batching vs the plain FIFO loop."""
+    import numpy as np
+    import torch
+    from paper_2604_21984_gb300 import inputs as gen
+    from paper_2604_21984_gb300.serve import (PlainLoop, Request, ServeConfig, Server, latency_summary,
+                                              run_stream)
+    max_side = args.c5_max_side
+    res = gen.resident_sets(seed, 4)
+    cfg = ServeConfig(K=16, J=4, site_pool=(sum(r[2] for r in res) + (8 << 20)),
+                      pixel_pool=(sum(r[0] * r[1] for r in res) + 4 * max_side * max_side + (1 << 20)),
+                      max_side=max_side, max_decode_per_tick=1 << 22)
+    srv = Server(cfg, dev)
+    plain = PlainLoop(cfg, dev)
+    for H, W, N, sd in res:
+        p = torch.from_numpy(gen.sites_random_spd(H, W, N, seed=sd)).to(dev)
+        srv.add_resident(p, H, W, passes=16)
+        plain.add_resident(p, H, W, passes=16)
+        del p
+    torch.cuda.synchronize()
+
+    def requests(stream_specs, imgs):
+        out = []
+        for k, r in enumerate(stream_specs):
+            if r["kind"] == "encode":
+                out.append(Request("encode", arrival=r["arrival"], image=imgs[k], iters=r["iters"],
+                                   seed=r["seed"] & 0x7FFFFFFF))
+            else:
+                H, W = res[r["resident"]][0], res[r["resident"]][1]
+                xy = torch.from_numpy(gen.uniform_points(r["n"], H, W, r["seed"])).pin_memory()
+                out.append(Request("decode", arrival=r["arrival"], resident=r["resident"], xy=xy))
+        return out
+
+    # plain capacity from a calibration stream (all at t=0, FIFO)
+    cal = gen.serve_stream(seed + 1, 60.0, 1.0, side=(128, max_side), iters=args.c5_iters)[:20]
+    cal_imgs = {k: torch.from_numpy(a).to(dev) for k, a in zip(
+        [k for k, r in enumerate(cal) if r["kind"] == "encode"],
+        gen_images([(r["H"], r["W"], r["seed"] % 100000) for r in cal if r["kind"] == "encode"]))}
+    creq = requests([dict(r, arrival=0.0) for r in cal], cal_imgs)
+    wall = run_stream(plain, creq)
+    capacity = len(creq) / wall
+    rate = 0.7 * capacity
+    spec = gen.serve_stream(seed, args.c5_seconds, rate, side=(128, max_side), iters=args.c5_iters)
+    enc_idx = [k for k, r in enumerate(spec) if r["kind"] == "encode"]
+    imgs = dict(zip(enc_idx, [torch.from_numpy(a).to(dev) for a in gen_images(
+        [(spec[k]["H"], spec[k]["W"], spec[k]["seed"] % 100000) for k in enc_idx])]))
+    out = {"workload": f"Poisson stream {args.c5_seconds} s at 0.7x plain capacity "
+                       f"({rate:.2f} req/s), 70% decode (1e3..1e6 coords on 4 resident sets of "
+                       f"{', '.join(str(r[2]) for r in res)} sites) / 30% encode (side 128..{max_side}, "
+                       f"{args.c5_iters} iterations)",
+           "plain_capacity_req_per_s": round(capacity, 3), "requests": len(spec),
+           "encodes": len(enc_idx), "pool_gb": round(srv.footprint_bytes() / 1e9, 2)}
+    for name, eng in (("plain", plain), ("served", srv)):
+        reqs = requests(spec, imgs)
+        wall = run_stream(eng, reqs)
+        s = latency_summary(reqs)
+        s["wall_s"] = round(wall, 3)
+        s["throughput_req_per_s"] = round(len(reqs) / wall, 3)
+        ps = [10 * math.log10(3.0 / max(float(r.loss.item()), 1e-30)) for r in reqs if r.kind == "encode"]
+        s["encode_mean_psnr_db"] = round(statistics.mean(ps), 3) if ps else None
+        for k in ("encode", "decode"):
+            if k in s:
+                s[k] = {kk: (round(v, 5) if isinstance(v, float) else v) for kk, v in s[k].items()}
+        out[name] = s
+        del reqs
+    return out
+
+
+LEGS = {"encode": encode_leg, "c3": c3_leg, "c4": c4_leg, "c5": c5_leg}
 
 
 # ----------------------------------------------------------------------------
@@ -352,15 +555,19 @@ CPU_CROP = 128
 
 
 def _cpu_sample():
-    """A CROPxCROP window of the workload image with the sites inside it (same
-    density), K=16, J=4, field warmed up by seed + 8 passes (untimed)."""
+    """A CROPxCROP window of the workload image with the same site density
+    (gradient-weighted init of the window, tau s d0 = 4), K=16, J=4, field
+    warmed up by seed + 8 passes (untimed)."""
     import numpy as np
     from oracle import sad_oracle as oracle
-    img, params = c2_inputs(0)
+    from paper_2604_21984_gb300 import inputs as gen
     c = CPU_CROP
+    img = gen.image_noise_polygons_lines(H_C2, W_C2, seed=2000)
     sub = img[:c, :c].copy()
-    inside = (params[0] < c) & (params[1] < c)
-    p = params[:, inside].copy()
+    n = int(round(N_C2 * c * c / (H_C2 * W_C2)))
+    s = 1.0 / c
+    d0 = math.sqrt(c * c / n)
+    p = oracle.init_sites(sub, n, n, 0.3, 0, math.log(4.0 / (s * d0)))
     ids = oracle.propagate_fp32(p, c, c, K_C2, passes=8, J=J_C2, seed=7)
     return oracle, np, sub, p, ids
 
@@ -390,7 +597,8 @@ def cpu_baseline(budget_s=12.0):
     return {"value": round(CPU_CROP * CPU_CROP * n / el / 1e6, 5), "unit": UNIT, "cores": 1,
             "kind": "oracle",
             "sample": f"{n} training iterations on a {CPU_CROP}x{CPU_CROP} crop of the workload image "
-                      f"(sites inside it, K=16, J=4), numpy single-threaded, {el:.1f} s"}
+                      f"(gradient-weighted sites at the workload's density, K=16, J=4), "
+                      f"numpy single-threaded, {el:.1f} s"}
 
 
 def run_reference(args):

@@ -62,6 +62,24 @@ const char* sad_last_error(void);
 int sad_abi_version(void);
 
 /*
+ * Stage tracing (library addition with no counterpart in the paper: the
+ * measurement side of the kernels).  While on, every kernel launch of the
+ * library is bracketed by two CUDA events on its stream (not on a stream
+ * being captured into a graph).  sad_trace_enable returns the previous
+ * setting.  sad_trace_collect waits for the recorded events, aggregates
+ * them per stage (kernel name) since the last collect, writes up to
+ * max_entries entries (out: HOST array) and the number of stages to *n_out,
+ * and forgets the records.  At most 65536 launches are kept between collects.
+ */
+typedef struct sad_trace_entry {
+  char name[48];      /* kernel (stage) name */
+  int64_t launches;   /* launches recorded */
+  double total_ms;    /* sum of their event-to-event device times */
+} sad_trace_entry;
+int sad_trace_enable(int on);
+int sad_trace_collect(sad_trace_entry* out, int32_t max_entries, int32_t* n_out);
+
+/*
  * sad_prepare_sites -- per-site derived table ("pack", App. "Data Layout and Packing"; metric G of
  * Sec. 4.1).  For every site i < capacity, in float32 with each operation
  * separately rounded (no fused multiply-add):
@@ -311,12 +329,17 @@ typedef struct sad_batch_image {
 } sad_batch_image;
 
 /* Workspace bytes of sad_train_step (0 = invalid table); same record rule as
- * sad_backward_workspace_bytes with P = total_pixels. */
+ * sad_backward_workspace_bytes with P = total_pixels.  The workspace must be
+ * ZEROED once when allocated: its per-site accumulators (at a fixed offset
+ * that depends on total_capacity only) are cleared by each call after use,
+ * so one workspace serves any sequence of tables over the same arrays.  A
+ * call that returned an error may leave them dirty: zero the workspace again. */
 size_t sad_step_workspace_bytes(const sad_batch_image* images, int32_t B, int32_t K,
                                 int32_t total_capacity, int64_t total_pixels,
                                 int64_t max_records);
 
-/* sad_prepare_sites for every image of a batch (each with its own s). */
+/* sad_prepare_sites for every image of a batch (each with its own s); only
+ * the images' slot ranges are touched. */
 int sad_prepare_batch(const sad_batch_image* images, int32_t B, const float* params, float* prep,
                       int32_t total_capacity, int64_t total_pixels, void* stream);
 
@@ -335,13 +358,31 @@ int sad_prepare_batch(const sad_batch_image* images, int32_t B, const float* par
  * incremented by the call, so the call sequence can be captured once in a
  * CUDA graph and replayed.  grads_out: optional float32[11][total_capacity].
  * map_in and map_out must not overlap; swap them between calls.  Each image's
- * results are independent of the other images in the batch.
+ * results are independent of the other images in the batch.  Only the
+ * images' slot and pixel ranges are read or written (besides the workspace),
+ * so images can join or leave between calls (continuous batching); images
+ * must not share pixels (SAD_EINVAL).
  */
 int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t J, float* params,
                    float* m, float* v, float* prep, int32_t total_capacity,
                    const uint32_t* map_in, uint32_t* map_out, int64_t total_pixels,
                    const float* targets, float* loss, const sad_adam_hparams* hp, int32_t* iter,
                    float* grads_out, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * sad_batch_insert -- place one image, prepared with the single-image calls
+ * (sad_init_sites, sad_topk_seed, sad_update_topk), into its ranges of the
+ * shared batch arrays: params[:, site_offset + i] = src_params[:, i] for
+ * i < capacity (src plane stride src_capacity >= capacity) with m and v
+ * cleared there; map cell ids shifted by site_offset (ids >= capacity become
+ * 0xffffffff); the target pixels copied when src_target is not NULL
+ * (float32[H*W][3]).  `image`: HOST pointer to the image's table entry.
+ * Library addition with no counterpart in the paper (the batching layer).
+ */
+int sad_batch_insert(const sad_batch_image* image, int32_t K, const float* src_params,
+                     int32_t src_capacity, const uint32_t* src_map, const float* src_target,
+                     float* params, float* m, float* v, int32_t total_capacity, uint32_t* map,
+                     float* targets, int64_t total_pixels, void* stream);
 
 /*
  * sad_decode_batch -- random-access decode (as sad_decode_points) of queries

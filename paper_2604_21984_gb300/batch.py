@@ -5,7 +5,7 @@ prepared table ``[11, total_capacity]`` (image b owns a contiguous slot range),
 packed targets ``[total_pixels, 3]`` and top-K map planes
 ``[K/4, total_pixels, 4]``.  Each image is initialised and warmed up with the
 single-image calls (gradient-weighted init, JFA warm-up), copied into its
-ranges, and then every training iteration of the whole batch is one
+ranges (``sad_batch_insert``), and then every training iteration of the whole batch is one
 ``sad_train_step`` call (fused propagation + render + MSE + adjoint per tile,
 exact per-site sums, Adam + prepare per site).  The iteration counter lives on
 the device, so two iterations (the map ping-pong) are captured once in a CUDA
@@ -50,16 +50,18 @@ class BatchTrainer:
             H, W = int(t.shape[0]), int(t.shape[1])
             n = max(1, min(H * W, int(round(c.sites_per_pixel * H * W))))
             sd = seeds[b] if seeds is not None else c.seed * 1000003 + b + 1
+            # table seed = injection seed of the training passes (the
+            # single-image encoder's convention: user seed + 0x5AD)
             self.images.append(dict(H=H, W=W, site_offset=site, capacity=n, pixel_offset=pix,
-                                    seed=sd, n=n))
+                                    seed=sd + 0x5AD, user_seed=sd, n=n))
             site += n
             pix += H * W
         self.total_cap, self.total_pixels = site, pix
         self.table = capi.batch_table(self.images)
         f32 = dict(dtype=torch.float32, device=self.dev)
         self.params = torch.empty((capi.N_PARAMS, site), **f32)
-        self.m = torch.zeros_like(self.params)
-        self.v = torch.zeros_like(self.params)
+        self.m = torch.empty_like(self.params)
+        self.v = torch.empty_like(self.params)
         self.prep = capi.empty_prep(site, self.dev)
         self.targets = torch.empty((pix, 3), **f32)
         K = c.K
@@ -78,26 +80,19 @@ class BatchTrainer:
             H, W, lo, n, po = im["H"], im["W"], im["site_offset"], im["capacity"], im["pixel_offset"]
             enc = Encoder(t.contiguous(), EncodeConfig(n_sites=n, K=c.K, J=c.J, capacity_factor=1.0,
                                                        lambda_init=c.lambda_init,
-                                                       seed=im["seed"]))
+                                                       seed=im["user_seed"]))
             enc.init()
-            # the single-image warm-up passes used the encoder's seed; from here on the
-            # batch step uses the image's own seed
-            self.params[:, lo:lo + n].copy_(enc.params[:, :n])
-            self.targets[po:po + H * W].copy_(t.reshape(-1, 3))
-            mp = enc.maps[0]
-            # site ids are offset into the shared arrays; sentinels stay sentinels
-            ids = mp.to(torch.int64) & 0xFFFFFFFF
-            shifted = torch.where(ids == 0xFFFFFFFF, ids, ids + lo)
-            self.maps[0][:, po:po + H * W].copy_(self._as_i32(shifted))
+            # training pass indices continue after the image's warm-up passes,
+            # as in the single-image encoder
+            im["pass_offset"] = enc.t_pass
+            capi.sad_batch_insert(capi.batch_table([im]), c.K, enc.params, enc.maps[0], t.contiguous(),
+                                  self.params, self.m, self.v, self.maps[0], self.targets,
+                                  self.total_pixels)
             del enc
+        self.table = capi.batch_table(self.images)
         capi.sad_prepare_batch(self.table, self.params, self.prep, self.total_pixels)
-        # Adam step 1; training passes number from 1024 on (warm-up passes used
-        # indices below 16), the same for every image whatever the batch
-        self.iter.copy_(torch.tensor([1, 1024], dtype=torch.int32))
-
-    @staticmethod
-    def _as_i32(x64):
-        return torch.where(x64 >= 2 ** 31, x64 - 2 ** 32, x64).to(torch.int32)
+        # Adam step 1; pass index = iter[1] + the image's warm-up pass count
+        self.iter.copy_(torch.tensor([1, 0], dtype=torch.int32))
 
     def _step(self):
         capi.sad_train_step(self.table, self.cfg.K, self.cfg.J, self.params, self.m, self.v, self.prep,
@@ -148,26 +143,27 @@ class BatchTrainer:
         return [float("inf") if l <= 0 else 10 * math.log10(3.0 / l) for l in self.loss.tolist()]
 
 
-def autotune(targets, iters: int = 60, candidates=((16, 4), (16, 2), (8, 4), (8, 2)),
+def autotune(targets, iters: int = 100, candidates=((16, 4), (16, 2), (8, 4), (8, 2)),
              psnr_tol: float = 0.05, seed: int = 0):
-    """Pick (K, J) for a batch: the fastest candidate whose mean PSNR after a
-    short run is within psnr_tol dB of the first candidate's (the reference).
-    Returns (best (K, J), table of (K, J, ms per iteration, mean PSNR))."""
+    """Pick (K, J) for a batch: each candidate trains `targets` (a sample of
+    the batch) for `iters` iterations, the intended budget, so that the PSNR
+    compared is the one the job will reach; the pick is the fastest candidate
+    whose mean PSNR is within psnr_tol dB of the best.  Returns (best (K, J),
+    table of (K, J, ms per iteration, mean PSNR))."""
     rows = []
-    ref = None
     for K, J in candidates:
         tr = BatchTrainer(targets, BatchConfig(K=K, J=J, seed=seed))
-        tr.run(iters - 10)
+        n_t = min(10, max(1, iters // 4))
+        tr.run(iters - n_t)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        tr.run(10)
+        tr.run(n_t)
         torch.cuda.synchronize()
-        ms = (time.perf_counter() - t0) * 100.0
+        ms = (time.perf_counter() - t0) * 1e3 / n_t
         p = sum(tr.psnr()) / len(targets)
         rows.append((K, J, ms, p))
-        if ref is None:
-            ref = p
         del tr
-    ok = [r for r in rows if r[3] >= ref - psnr_tol]
+    best_p = max(r[3] for r in rows)
+    ok = [r for r in rows if r[3] >= best_p - psnr_tol]
     best = min(ok, key=lambda r: r[2])
     return (best[0], best[1]), rows

@@ -49,6 +49,10 @@ class BatchImage(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("t_offset", ctypes.c_int32), ("pass_offset", ctypes.c_int32)]
 
 
+class TraceEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
 class AdamHparams(ctypes.Structure):
     _fields_ = [
         ("lr", ctypes.c_float * N_PARAMS),
@@ -64,6 +68,8 @@ _SIGS = {
     "sad_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "sad_last_error": (ctypes.c_char_p, []),
     "sad_abi_version": (ctypes.c_int, []),
+    "sad_trace_enable": (ctypes.c_int, [ctypes.c_int]),
+    "sad_trace_collect": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "sad_prepare_sites": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "sad_topk_seed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
@@ -122,6 +128,10 @@ _SIGS = {
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(AdamHparams),
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                       ctypes.c_void_p]),
+    "sad_batch_insert": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_int64, ctypes.c_void_p]),
     "sad_decode_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                         ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
@@ -418,7 +428,9 @@ def step_workspace(table, K, total_cap, total_pixels, max_records=0, device="cud
                                        total_pixels, max_records)
     if n == 0:
         raise ValueError("invalid batch table for sad_step_workspace_bytes")
-    return torch.empty(n, dtype=torch.uint8, device=device)
+    # zeroed once: the per-site accumulators must start at zero (each call
+    # clears them again after use)
+    return torch.zeros(n, dtype=torch.uint8, device=device)
 
 
 def sad_prepare_batch(table, params, prep, total_pixels, stream=None):
@@ -439,7 +451,8 @@ def sad_train_step(table, K, J, params, m, v, prep, map_in, map_out, total_pixel
                                 _ptr(map_in, torch.int32, "map_in", total_pixels * K),
                                 _ptr(map_out, torch.int32, "map_out", total_pixels * K), total_pixels,
                                 _ptr(targets, torch.float32, "targets", total_pixels * 3),
-                                _ptr(loss, torch.float32, "loss", len(table)), ctypes.byref(hp),
+                                _ptr(loss[:len(table)] if loss is not None else None, torch.float32,
+                                     "loss", len(table)), ctypes.byref(hp),
                                 _ptr(iter_dev, torch.int32, "iter", 2),
                                 _ptr(grads_out, torch.float32, "grads_out", n),
                                 _ptr(ws, torch.uint8, "workspace"), ws.numel(), _stream(stream)),
@@ -455,3 +468,37 @@ def sad_decode_batch(table, K, prep, total_cap, map_in, total_pixels, xy, qimg, 
                                   n, _ptr(rgb, torch.float32, "rgb", 3 * n), _stream(stream)),
            "sad_decode_batch")
     return rgb
+
+
+def sad_batch_insert(entry, K, src_params, src_map, src_target, params, m, v, map_out, targets,
+                     total_pixels, stream=None):
+    """entry: one-element batch_table (the image's ranges)."""
+    n, P = entry[0].capacity, entry[0].H * entry[0].W
+    total_cap = params.shape[1]
+    _check(lib().sad_batch_insert(ctypes.cast(entry, ctypes.c_void_p), K,
+                                  _ptr(src_params, torch.float32, "src_params") if n else None,
+                                  src_params.shape[1] if src_params is not None else 0,
+                                  _ptr(src_map, torch.int32, "src_map", P * K),
+                                  _ptr(src_target, torch.float32, "src_target", 3 * P)
+                                  if src_target is not None else None,
+                                  _ptr(params, torch.float32, "params"), _ptr(m, torch.float32, "m"),
+                                  _ptr(v, torch.float32, "v"), total_cap,
+                                  _ptr(map_out, torch.int32, "map", total_pixels * K),
+                                  _ptr(targets, torch.float32, "targets", 3 * total_pixels),
+                                  total_pixels, _stream(stream)),
+           "sad_batch_insert")
+
+
+def sad_trace_enable(on=True):
+    """Switch kernel stage tracing on or off; returns the previous setting."""
+    return bool(lib().sad_trace_enable(1 if on else 0))
+
+
+def sad_trace_collect():
+    """{kernel name: (launches, total device ms)} since the last collect."""
+    arr = (TraceEntry * 128)()
+    n = ctypes.c_int32(0)
+    _check(lib().sad_trace_collect(ctypes.cast(arr, ctypes.c_void_p), 128, ctypes.byref(n)),
+           "sad_trace_collect")
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms))
+            for i in range(min(n.value, 128))}

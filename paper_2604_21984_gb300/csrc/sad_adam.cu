@@ -57,7 +57,7 @@ extern "C" int sad_adam_step(float* params, const float* grads, float* m, float*
   const float bc1 = static_cast<float>(1.0 - std::pow(static_cast<double>(hp->beta1), t));
   const float bc2 = static_cast<float>(1.0 - std::pow(static_cast<double>(hp->beta2), t));
   const int bs = 256;
-  k_adam<<<(capacity + bs - 1) / bs, bs, 0, as_stream(stream)>>>(params, grads, m, v, capacity, H, W,
-                                                                 A, bc1, bc2);
+  { TraceScope tr_(as_stream(stream), "k_adam"); k_adam<<<(capacity + bs - 1) / bs, bs, 0, as_stream(stream)>>>(params, grads, m, v, capacity, H, W,
+                                                                 A, bc1, bc2); }
   return check_launch("k_adam");
 }

@@ -261,36 +261,39 @@ static int run_backward(const float* params, const float* prep, int cap, int H, 
   io.hdr = hdr;
 #define SAD_TILE_LAUNCH(KK, MM) \
   k_bwd_tile<KK, MM><<<LL.n_tiles, kTileThreads, 0, st>>>(io, cap, H, W, m4)
-  if (stats_mode) {
-    switch (K) {
-      case 4: SAD_TILE_LAUNCH(4, kModeStats); break;
-      case 8: SAD_TILE_LAUNCH(8, kModeStats); break;
-      default: SAD_TILE_LAUNCH(16, kModeStats); break;
-    }
-  } else {
-    switch (K) {
-      case 4: SAD_TILE_LAUNCH(4, kModeGrad); break;
-      case 8: SAD_TILE_LAUNCH(8, kModeGrad); break;
-      default: SAD_TILE_LAUNCH(16, kModeGrad); break;
+  {
+    TraceScope tr_(st, "k_bwd_tile");
+    if (stats_mode) {
+      switch (K) {
+        case 4: SAD_TILE_LAUNCH(4, kModeStats); break;
+        case 8: SAD_TILE_LAUNCH(8, kModeStats); break;
+        default: SAD_TILE_LAUNCH(16, kModeStats); break;
+      }
+    } else {
+      switch (K) {
+        case 4: SAD_TILE_LAUNCH(4, kModeGrad); break;
+        case 8: SAD_TILE_LAUNCH(8, kModeGrad); break;
+        default: SAD_TILE_LAUNCH(16, kModeGrad); break;
+      }
     }
   }
 #undef SAD_TILE_LAUNCH
   if (int r = check_launch("k_bwd_tile")) return r;
   if (target && loss) {
-    k_loss_final<<<1, 256, 0, st>>>(tile_loss, LL.n_tiles, 1.0f / static_cast<float>(static_cast<double>(H) * W), loss);
+    { TraceScope tr_(st, "k_loss_final"); k_loss_final<<<1, 256, 0, st>>>(tile_loss, LL.n_tiles, 1.0f / static_cast<float>(static_cast<double>(H) * W), loss); }
     if (int r = check_launch("k_loss_final")) return r;
   }
   if (cap == 0) return SAD_OK;
   const int sgrid = 152 * 8;
   if (stats_mode) {
-    k_seg_accum<8><<<sgrid, 256, 0, st>>>(rec, hdr, LL.max_records, cap, accq);
+    { TraceScope tr_(st, "k_seg_accum"); k_seg_accum<8><<<sgrid, 256, 0, st>>>(rec, hdr, LL.max_records, cap, accq); }
     if (int r = check_launch("k_seg_accum")) return r;
-    k_site_stats<<<(cap + 255) / 256, 256, 0, st>>>(cap, hdr, accq, stats);
+    { TraceScope tr_(st, "k_site_stats"); k_site_stats<<<(cap + 255) / 256, 256, 0, st>>>(cap, hdr, accq, stats); }
     return check_launch("k_site_stats");
   }
-  k_seg_accum<10><<<sgrid, 256, 0, st>>>(rec, hdr, LL.max_records, cap, accq);
+  { TraceScope tr_(st, "k_seg_accum"); k_seg_accum<10><<<sgrid, 256, 0, st>>>(rec, hdr, LL.max_records, cap, accq); }
   if (int r = check_launch("k_seg_accum")) return r;
-  k_site_grads<<<(cap + 255) / 256, 256, 0, st>>>(params, geo, met, cap, hdr, accq, grads);
+  { TraceScope tr_(st, "k_site_grads"); k_site_grads<<<(cap + 255) / 256, 256, 0, st>>>(params, geo, met, cap, hdr, accq, grads); }
   return check_launch("k_site_grads");
 }
 
@@ -432,7 +435,7 @@ extern "C" int sad_render_backward_noalloc(const float* params, const float* pre
                               nullptr, nullptr, scratch, kStaticScratchBytes, as_stream(stream),
                               "sad_render_backward_noalloc");
   if (st != SAD_OK || !status_out) return st;
-  k_static_status<<<1, 32, 0, as_stream(stream)>>>(reinterpret_cast<const WsHeader*>(scratch),
-                                                   status_out);
+  { TraceScope tr_(as_stream(stream), "k_static_status"); k_static_status<<<1, 32, 0, as_stream(stream)>>>(reinterpret_cast<const WsHeader*>(scratch),
+                                                   status_out); }
   return check_launch("k_static_status");
 }

@@ -330,11 +330,11 @@ int sad_densify_prune(float* params, float* m, float* v, int32_t capacity, int32
   A.ratio_min = dp->ratio_min;
   const unsigned gs = static_cast<unsigned>((n + 255) / 256);
   const unsigned gp = static_cast<unsigned>((P + 255) / 256);
-  k_dp_state<<<1, 256, 0, st>>>(S);
+  { TraceScope tr_(st, "k_dp_state"); k_dp_state<<<1, 256, 0, st>>>(S); }
   // inactive flags go to flag_p for now (reused after the free list is built)
-  k_dp_count<<<gs, 256, 0, st>>>(params, stats, capacity, A.mass_min, S, flag_p);
+  { TraceScope tr_(st, "k_dp_count"); k_dp_count<<<gs, 256, 0, st>>>(params, stats, capacity, A.mass_min, S, flag_p); }
   run_xscan(flag_p, freepos, n, bsums, st);
-  k_dp_freelist<<<gs, 256, 0, st>>>(flag_p, freepos, capacity, freelist);
+  { TraceScope tr_(st, "k_dp_freelist"); k_dp_freelist<<<gs, 256, 0, st>>>(flag_p, freepos, capacity, freelist); }
   // the number of free slots: total of that scan
   uint32_t* n_free = bsums + scan_blocks(n);
   // keep the count in the state page (bsums is reused by later scans)
@@ -344,11 +344,11 @@ int sad_densify_prune(float* params, float* m, float* v, int32_t capacity, int32
     set_error("sad_densify_prune: %s", cudaGetErrorString(e));
     return SAD_ECUDA;
   }
-  k_dp_need_d<<<1, 32, 0, st>>>(S, A.densify_pct);
-  k_dp_keys_d<<<gs, 256, 0, st>>>(params, stats, capacity, A, keys);
+  { TraceScope tr_(st, "k_dp_need_d"); k_dp_need_d<<<1, 32, 0, st>>>(S, A.densify_pct); }
+  { TraceScope tr_(st, "k_dp_keys_d"); k_dp_keys_d<<<gs, 256, 0, st>>>(params, stats, capacity, A, keys); }
   run_select_smallest(keys, n, &S->sel_d, flag_d, scan, bsums, st);
-  k_dp_need_p<<<1, 32, 0, st>>>(S, A.prune_pct);
-  k_dp_keys_p<<<gs, 256, 0, st>>>(params, stats, flag_d, capacity, keys);
+  { TraceScope tr_(st, "k_dp_need_p"); k_dp_need_p<<<1, 32, 0, st>>>(S, A.prune_pct); }
+  { TraceScope tr_(st, "k_dp_keys_p"); k_dp_keys_p<<<gs, 256, 0, st>>>(params, stats, flag_d, capacity, keys); }
   run_select_smallest(keys, n, &S->sel_p, flag_p, scan, bsums, st);
   run_xscan(flag_d, rank, n, bsums, st);
   if (map) {
@@ -358,11 +358,11 @@ int sad_densify_prune(float* params, float* m, float* v, int32_t capacity, int32
       return SAD_ECUDA;
     }
   }
-  k_dp_split<<<gs, 256, 0, st>>>(params, m, v, stats, target, capacity, H, W, flag_d, rank, freelist,
-                                 n_free_keep, map ? claim : nullptr, A);
-  k_dp_prune<<<gs, 256, 0, st>>>(params, flag_p, capacity);
-  if (map) k_dp_seed_map<<<gp, 256, 0, st>>>(claim, P, K, map);
-  k_dp_count_after<<<gs, 256, 0, st>>>(params, capacity, S);
+  { TraceScope tr_(st, "k_dp_split"); k_dp_split<<<gs, 256, 0, st>>>(params, m, v, stats, target, capacity, H, W, flag_d, rank, freelist,
+                                 n_free_keep, map ? claim : nullptr, A); }
+  { TraceScope tr_(st, "k_dp_prune"); k_dp_prune<<<gs, 256, 0, st>>>(params, flag_p, capacity); }
+  if (map) { TraceScope tr_(st, "k_dp_seed_map"); k_dp_seed_map<<<gp, 256, 0, st>>>(claim, P, K, map); }
+  { TraceScope tr_(st, "k_dp_count_after"); k_dp_count_after<<<gs, 256, 0, st>>>(params, capacity, S); }
   if (int r = check_launch("sad_densify_prune")) return r;
   uint32_t after = 0;
   e = cudaMemcpyAsync(&after, &S->n_active_after, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);

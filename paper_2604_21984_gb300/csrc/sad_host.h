@@ -50,4 +50,18 @@ inline int check_problem(int32_t capacity, int32_t H, int32_t W, int32_t K, bool
 struct AdamArgs;
 AdamArgs adam_args(const sad_adam_hparams* hp);
 
+// While tracing is on (sad_trace_enable), records a CUDA event on `s` when
+// constructed and another when destroyed; the pair is one launch of stage
+// `name` (a string literal).  Does nothing when tracing is off or the stream
+// is being captured into a graph.
+struct TraceScope {
+  TraceScope(cudaStream_t st, const char* nm);
+  ~TraceScope();
+  TraceScope(const TraceScope&) = delete;
+  TraceScope& operator=(const TraceScope&) = delete;
+  cudaStream_t s;
+  const char* name;
+  cudaEvent_t e0, e1;
+};
+
 }  // namespace sad

@@ -201,16 +201,16 @@ int sad_init_sites(const float* img, int32_t H, int32_t W, int32_t n, int32_t ca
   uint32_t* flag = reinterpret_cast<uint32_t*>(base + L.flag);
   uint32_t* scan = reinterpret_cast<uint32_t*>(base + L.scan);
   uint32_t* bsums = reinterpret_cast<uint32_t*>(base + L.bsums);
-  k_init_state<<<1, 256, 0, st>>>(S, static_cast<uint32_t>(n));
+  { TraceScope tr_(st, "k_init_state"); k_init_state<<<1, 256, 0, st>>>(S, static_cast<uint32_t>(n)); }
   const unsigned g256 = static_cast<unsigned>((P + 255) / 256);
   if (capacity > n)
-    k_init_inactive<<<(capacity - n + 255) / 256, 256, 0, st>>>(params, n, capacity);
+    { TraceScope tr_(st, "k_init_inactive"); k_init_inactive<<<(capacity - n + 255) / 256, 256, 0, st>>>(params, n, capacity); }
   if (n == 0) return check_launch("k_init_inactive");
-  k_init_grad<<<g256, 256, 0, st>>>(img, H, W, g, S);
-  k_init_keys<<<g256, 256, 0, st>>>(g, P, lambda_init, seed, S, keys);
+  { TraceScope tr_(st, "k_init_grad"); k_init_grad<<<g256, 256, 0, st>>>(img, H, W, g, S); }
+  { TraceScope tr_(st, "k_init_keys"); k_init_keys<<<g256, 256, 0, st>>>(g, P, lambda_init, seed, S, keys); }
   run_select_smallest(keys, P, &S->sel, flag, scan, bsums, st);
   run_xscan(flag, scan, P, bsums, st);
-  k_init_write<<<g256, 256, 0, st>>>(img, W, P, seed, log_tau0, flag, scan, params, capacity);
+  { TraceScope tr_(st, "k_init_write"); k_init_write<<<g256, 256, 0, st>>>(img, W, P, seed, log_tau0, flag, scan, params, capacity); }
   return check_launch("sad_init_sites");
 }
 

@@ -64,9 +64,9 @@ int sad_render(const float* prep, int32_t capacity, int32_t H, int32_t W, int32_
   const dim3 grid((W + 31) / 32, (H + 7) / 8);
   cudaStream_t st = as_stream(stream);
   switch (K) {
-    case 4: k_render<4><<<grid, block, 0, st>>>(geo, met, col, capacity, H, W, m4, rgb); break;
-    case 8: k_render<8><<<grid, block, 0, st>>>(geo, met, col, capacity, H, W, m4, rgb); break;
-    default: k_render<16><<<grid, block, 0, st>>>(geo, met, col, capacity, H, W, m4, rgb); break;
+    case 4: { TraceScope tr_(st, "k_render"); k_render<4><<<grid, block, 0, st>>>(geo, met, col, capacity, H, W, m4, rgb); } break;
+    case 8: { TraceScope tr_(st, "k_render"); k_render<8><<<grid, block, 0, st>>>(geo, met, col, capacity, H, W, m4, rgb); } break;
+    default: { TraceScope tr_(st, "k_render"); k_render<16><<<grid, block, 0, st>>>(geo, met, col, capacity, H, W, m4, rgb); } break;
   }
   return check_launch("k_render");
 }
@@ -88,9 +88,9 @@ int sad_decode_points(const float* prep, int32_t capacity, int32_t H, int32_t W,
   const unsigned grid = static_cast<unsigned>((n + bs - 1) / bs);
   cudaStream_t st = as_stream(stream);
   switch (K) {
-    case 4: k_decode<4><<<grid, bs, 0, st>>>(geo, met, col, capacity, H, W, m4, q, n, rgb); break;
-    case 8: k_decode<8><<<grid, bs, 0, st>>>(geo, met, col, capacity, H, W, m4, q, n, rgb); break;
-    default: k_decode<16><<<grid, bs, 0, st>>>(geo, met, col, capacity, H, W, m4, q, n, rgb); break;
+    case 4: { TraceScope tr_(st, "k_decode"); k_decode<4><<<grid, bs, 0, st>>>(geo, met, col, capacity, H, W, m4, q, n, rgb); } break;
+    case 8: { TraceScope tr_(st, "k_decode"); k_decode<8><<<grid, bs, 0, st>>>(geo, met, col, capacity, H, W, m4, q, n, rgb); } break;
+    default: { TraceScope tr_(st, "k_decode"); k_decode<16><<<grid, bs, 0, st>>>(geo, met, col, capacity, H, W, m4, q, n, rgb); } break;
   }
   return check_launch("k_decode");
 }

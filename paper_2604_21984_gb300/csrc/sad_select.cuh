@@ -126,9 +126,9 @@ static inline void run_xscan(const uint32_t* in, uint32_t* out, size_t n, uint32
                              cudaStream_t st) {
   const uint32_t nb = scan_blocks(n);
   if (nb == 0) return;
-  k_xscan_blocks<<<nb, 1024, 0, st>>>(in, out, n, bsums);
-  k_xscan_sums<<<1, 32, 0, st>>>(bsums, nb);
-  k_xscan_add<<<nb, 1024, 0, st>>>(out, n, bsums);
+  { TraceScope tr_(st, "k_xscan_blocks"); k_xscan_blocks<<<nb, 1024, 0, st>>>(in, out, n, bsums); }
+  { TraceScope tr_(st, "k_xscan_sums"); k_xscan_sums<<<1, 32, 0, st>>>(bsums, nb); }
+  { TraceScope tr_(st, "k_xscan_add"); k_xscan_add<<<nb, 1024, 0, st>>>(out, n, bsums); }
 }
 
 // flag[i] = 1 for the `need` smallest keys (ties to the smaller index),
@@ -138,12 +138,12 @@ static inline void run_select_smallest(const uint32_t* keys, size_t n, SelState*
                                        cudaStream_t st) {
   const unsigned g256 = static_cast<unsigned>((n + 255) / 256);
   for (int shift = 24; shift >= 0; shift -= 8) {
-    k_sel_hist<<<152 * 4, 256, 0, st>>>(keys, n, shift, sel);
-    k_sel_pick<<<1, 32, 0, st>>>(sel);
+    { TraceScope tr_(st, "k_sel_hist"); k_sel_hist<<<152 * 4, 256, 0, st>>>(keys, n, shift, sel); }
+    { TraceScope tr_(st, "k_sel_pick"); k_sel_pick<<<1, 32, 0, st>>>(sel); }
   }
-  k_sel_flag_eq<<<g256, 256, 0, st>>>(keys, n, sel, flag);
+  { TraceScope tr_(st, "k_sel_flag_eq"); k_sel_flag_eq<<<g256, 256, 0, st>>>(keys, n, sel, flag); }
   run_xscan(flag, scan, n, bsums, st);
-  k_sel_flag_take<<<g256, 256, 0, st>>>(keys, n, sel, scan, flag);
+  { TraceScope tr_(st, "k_sel_flag_take"); k_sel_flag_take<<<g256, 256, 0, st>>>(keys, n, sel, scan, flag); }
 }
 
 }  // namespace sad

@@ -1,7 +1,7 @@
 // Fused, batched training step (the paper's GPU-resident iteration, Sec. 5;
 // Sec. 6.3 epoch = one pass over all pixels) over up to kMaxImages images.
 //
-// One iteration is four kernels and two memsets, all on one stream, with the
+// One iteration is four kernels and one small memset, all on one stream, with the
 // iteration counter in device memory so the whole sequence can be captured
 // once in a CUDA graph and replayed:
 //  1. k_step_tile, one block per 16x16 tile of any image: the tile's pixels
@@ -36,11 +36,13 @@ struct BatchImg {
   uint64_t seed;
   float s, two_over_P;
   int32_t t_off, pass_off;
+  uint32_t site_cum;  // sites of the images before this one
 };
 
 struct BatchDesc {
   int32_t B;
   uint32_t n_tiles;
+  uint32_t n_sites;  // sites of all images
   BatchImg img[kMaxImages];
 };
 
@@ -55,15 +57,15 @@ __device__ __forceinline__ int image_of_tile(const BatchDesc& d, uint32_t tile) 
   return lo;
 }
 
-// image owning a site, or -1
-__device__ __forceinline__ int image_of_site(const BatchDesc& d, uint32_t i) {
+// image of the j-th site of the table (j < n_sites)
+__device__ __forceinline__ int image_of_slot(const BatchDesc& d, uint32_t j) {
   int lo = 0, hi = d.B - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (d.img[mid].site_lo <= i) lo = mid;
+    if (d.img[mid].site_cum <= j) lo = mid;
     else hi = mid - 1;
   }
-  return (i - d.img[lo].site_lo < d.img[lo].site_n) ? lo : -1;
+  return lo;
 }
 
 template <int K>
@@ -89,7 +91,7 @@ __global__ void __launch_bounds__(kTileThreads, 3)
   const bool inimg = x < c.W && y < c.H;
   const uint32_t code = (1u << 16) | (static_cast<uint32_t>(iter[1] + im.pass_off) & 0xffffu);
   uint64_t v[K];
-  pixel_update<K, kTileThreads>(v, inimg, x, y, c.H, c.W, c.sr, io.geo, io.met, map_in, Ptot,
+  pixel_update<K, kTileThreads, 2>(v, inimg, x, y, c.H, c.W, c.sr, io.geo, io.met, map_in, Ptot,
                                 im.pix_off, code, J, im.seed, s_q, t);
   uint32_t ids[K];
 #pragma unroll
@@ -104,35 +106,42 @@ __global__ void __launch_bounds__(kTileThreads, 3)
 }
 
 // The ten exact statistic sums of site i -> 11 gradients -> Adam -> prepared
-// table for the next iteration.  adam = false only prepares.
+// table for the next iteration.  adam = false only prepares.  One thread per
+// site of the table (slot ranges of the images only), and the accumulators
+// are cleared once read, so the next call finds them zero without a memset
+// over the whole site array.
 __global__ void k_site_step(const BatchDesc d, float* __restrict__ params, float* __restrict__ m,
                             float* __restrict__ v, float4* __restrict__ geo,
                             float4* __restrict__ met, float4* __restrict__ col, int cap,
                             const WsHeader* __restrict__ hdr,
-                            const unsigned long long* __restrict__ accq, AdamArgs A,
+                            unsigned long long* __restrict__ accq, AdamArgs A,
                             const int32_t* __restrict__ iter, float* __restrict__ grads_out,
                             bool adam) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= cap) return;
-  const int b = image_of_site(d, static_cast<uint32_t>(i));
-  if (b < 0) return;
+  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= d.n_sites) return;
+  const int b = image_of_slot(d, j);
   const BatchImg im = d.img[b];
+  const uint32_t i = im.site_lo + (j - im.site_cum);
   const size_t c = static_cast<size_t>(cap);
   float p[kNParams];
 #pragma unroll
-  for (int j = 0; j < kNParams; ++j) p[j] = params[j * c + i];
+  for (int k = 0; k < kNParams; ++k) p[k] = params[k * c + i];
   if (adam) {
     float acc[10];
     bool any = false;
 #pragma unroll
-    for (int j = 0; j < 10; ++j) {
-      const long long q = static_cast<long long>(accq[j * c + i]);
+    for (int k = 0; k < 10; ++k) {
+      const long long q = static_cast<long long>(accq[k * c + i]);
       any |= q != 0;
-      acc[j] = static_cast<float>(static_cast<double>(q) * pow2(-fixed_shift(hdr->pmax[b][j])));
+      acc[k] = static_cast<float>(static_cast<double>(q) * pow2(-fixed_shift(hdr->pmax[b][k])));
+    }
+    if (any) {
+#pragma unroll
+      for (int k = 0; k < 10; ++k) accq[k * c + i] = 0ull;
     }
     float g[kNParams];
 #pragma unroll
-    for (int j = 0; j < kNParams; ++j) g[j] = 0.f;
+    for (int k = 0; k < kNParams; ++k) g[k] = 0.f;
     if (any) {
       const float4 gs = geo[i], ms = met[i];
       // chain rule through G(a, b, u) (Sec. 4.1), as in the stand-alone backward
@@ -166,7 +175,7 @@ __global__ void k_site_step(const BatchDesc d, float* __restrict__ params, float
     }
     if (grads_out) {
 #pragma unroll
-      for (int j = 0; j < kNParams; ++j) grads_out[j * c + i] = g[j];
+      for (int k = 0; k < kNParams; ++k) grads_out[k * c + i] = g[k];
     }
     if (p[PX] >= 0.f) {
       const int t = iter[0] + im.t_off;
@@ -174,7 +183,7 @@ __global__ void k_site_step(const BatchDesc d, float* __restrict__ params, float
       const float bc2 = static_cast<float>(1.0 - pow(static_cast<double>(A.beta2), t));
       adam_site(p, g, m, v, c, i, A, bc1, bc2, im.H, im.W);
 #pragma unroll
-      for (int j = 0; j < kNParams; ++j) params[j * c + i] = p[j];
+      for (int k = 0; k < kNParams; ++k) params[k * c + i] = p[k];
     }
   }
   prepare_site(p[PX], p[PY], p[PLOGTAU], p[PR], p[PCR], p[PCG], p[PCB], p[PUX], p[PUY], p[PA],
@@ -235,6 +244,42 @@ __global__ void __launch_bounds__(256) k_decode_batch(const BatchDesc d, const f
   rgb[3 * i + 2] = c.z;
 }
 
+// Copy of one image from the single-image layout into its ranges of the
+// shared arrays: parameters (Adam moments cleared), target pixels, and map ids
+// offset by the image's first slot (ids outside the image become empty).
+__global__ void k_insert_sites(const float* __restrict__ src, int src_cap, int n, int lo,
+                               float* __restrict__ params, float* __restrict__ m,
+                               float* __restrict__ v, int cap) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const size_t c = static_cast<size_t>(cap), sc = static_cast<size_t>(src_cap);
+#pragma unroll
+  for (int k = 0; k < kNParams; ++k) {
+    params[k * c + lo + i] = src[k * sc + i];
+    m[k * c + lo + i] = 0.f;
+    v[k * c + lo + i] = 0.f;
+  }
+}
+
+__global__ void k_insert_pixels(const uint4* __restrict__ src_map, const float* __restrict__ src_t,
+                                size_t P, int NP, uint32_t n, uint32_t lo, size_t pix_off,
+                                uint4* __restrict__ map, float* __restrict__ targets, size_t Ptot) {
+  const size_t q = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= P) return;
+  for (int j = 0; j < NP; ++j) {
+    uint4 w = src_map[j * P + q];
+    w.x = w.x < n ? w.x + lo : kInvalid;
+    w.y = w.y < n ? w.y + lo : kInvalid;
+    w.z = w.z < n ? w.z + lo : kInvalid;
+    w.w = w.w < n ? w.w + lo : kInvalid;
+    map[j * Ptot + pix_off + q] = w;
+  }
+  if (src_t) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) targets[3 * (pix_off + q) + c] = src_t[3 * q + c];
+  }
+}
+
 struct StepLayout {
   size_t hdr, tile_loss, acc, records, total;
   uint32_t max_records;
@@ -249,10 +294,12 @@ static StepLayout step_layout(uint32_t n_tiles, uint64_t total_pixels, int K, in
   if (max_records <= 0 && mr < 128ull * n_tiles) mr = 128ull * n_tiles;
   if (mr > 0xfffffff0ull) mr = 0xfffffff0ull;
   L.max_records = static_cast<uint32_t>(mr);
+  // the accumulators keep their offset whatever the table (they must stay
+  // zero between calls)
   size_t o = 0;
   L.hdr = o;       o = al256(o + sizeof(WsHeader));
-  L.tile_loss = o; o = al256(o + sizeof(float) * n_tiles);
   L.acc = o;       o = al256(o + sizeof(unsigned long long) * 10 * static_cast<size_t>(total_cap));
+  L.tile_loss = o; o = al256(o + sizeof(float) * n_tiles);
   L.records = o;   o = al256(o + sizeof(Record) * L.max_records);
   L.total = o;
   return L;
@@ -264,7 +311,7 @@ static int make_desc(const sad_batch_image* images, int32_t B, int32_t total_cap
   if (!images || B < 1 || B > kMaxImages)
     return einval("%s: need 1 <= B <= %d images", name, kMaxImages);
   d.B = B;
-  uint32_t tiles = 0;
+  uint32_t tiles = 0, sites = 0;
   for (int b = 0; b < B; ++b) {
     const sad_batch_image& im = images[b];
     if (int e = check_problem(im.capacity, im.H, im.W, 4, false)) return e;
@@ -288,9 +335,18 @@ static int make_desc(const sad_batch_image* images, int32_t B, int32_t total_cap
     o.two_over_P = 2.0f / static_cast<float>(static_cast<double>(im.H) * im.W);
     o.t_off = im.t_offset;
     o.pass_off = im.pass_offset;
+    o.site_cum = sites;
+    sites += o.site_n;
     tiles += o.tiles_x * static_cast<uint32_t>((im.H + kTileSide - 1) / kTileSide);
   }
+  for (int b = 0; b < B; ++b)
+    for (int c = 0; c < b; ++c) {
+      const int64_t a0 = images[b].pixel_offset, a1 = a0 + static_cast<int64_t>(images[b].H) * images[b].W;
+      const int64_t c0 = images[c].pixel_offset, c1 = c0 + static_cast<int64_t>(images[c].H) * images[c].W;
+      if (a0 < c1 && c0 < a1) return einval("%s: images %d and %d share pixels", name, c, b);
+    }
   d.n_tiles = tiles;
+  d.n_sites = sites;
   return SAD_OK;
 }
 
@@ -315,14 +371,14 @@ int sad_prepare_batch(const sad_batch_image* images, int32_t B, const float* par
                       int32_t total_capacity, int64_t total_pixels, void* stream) {
   BatchDesc d;
   if (int e = make_desc(images, B, total_capacity, total_pixels, d, "sad_prepare_batch")) return e;
-  if (total_capacity == 0) return SAD_OK;
+  if (d.n_sites == 0) return SAD_OK;
   if (!params || !prep || !aligned16(prep)) return einval("sad_prepare_batch: bad pointer");
   float4* p4 = reinterpret_cast<float4*>(prep);
   AdamArgs A{};
-  k_site_step<<<(total_capacity + 255) / 256, 256, 0, as_stream(stream)>>>(
+  { TraceScope tr_(as_stream(stream), "k_site_step"); k_site_step<<<(d.n_sites + 255) / 256, 256, 0, as_stream(stream)>>>(
       d, const_cast<float*>(params), nullptr, nullptr, p4, p4 + total_capacity,
       p4 + 2 * static_cast<size_t>(total_capacity), total_capacity, nullptr, nullptr, A, nullptr,
-      nullptr, false);
+      nullptr, false); }
   return check_launch("sad_prepare_batch");
 }
 
@@ -374,10 +430,7 @@ int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t 
   float* tile_loss = reinterpret_cast<float*>(base + L.tile_loss);
   unsigned long long* accq = reinterpret_cast<unsigned long long*>(base + L.acc);
   Record* rec = reinterpret_cast<Record*>(base + L.records);
-  cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st);
-  if (e == cudaSuccess)
-    e = cudaMemsetAsync(accq, 0, sizeof(unsigned long long) * 10 * static_cast<size_t>(total_capacity),
-                        st);
+  const cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st);
   if (e != cudaSuccess) {
     set_error("sad_train_step memset: %s", cudaGetErrorString(e));
     return SAD_ECUDA;
@@ -398,20 +451,50 @@ int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t 
   uint4* mo = reinterpret_cast<uint4*>(map_out);
   const size_t Ptot = static_cast<size_t>(total_pixels);
   switch (K) {
-    case 4: k_step_tile<4><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, iter); break;
-    case 8: k_step_tile<8><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, iter); break;
-    default: k_step_tile<16><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, iter); break;
+    case 4: { TraceScope tr_(st, "k_step_tile"); k_step_tile<4><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, iter); } break;
+    case 8: { TraceScope tr_(st, "k_step_tile"); k_step_tile<8><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, iter); } break;
+    default: { TraceScope tr_(st, "k_step_tile"); k_step_tile<16><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, iter); } break;
   }
   if (int r = check_launch("k_step_tile")) return r;
-  k_seg_accum<10><<<152 * 8, 256, 0, st>>>(rec, hdr, L.max_records, total_capacity, accq);
+  { TraceScope tr_(st, "k_seg_accum"); k_seg_accum<10><<<152 * 8, 256, 0, st>>>(rec, hdr, L.max_records, total_capacity, accq); }
   if (int r = check_launch("k_seg_accum")) return r;
   const AdamArgs A = adam_args(hp);
-  k_site_step<<<(total_capacity + 255) / 256, 256, 0, st>>>(
+  if (d.n_sites > 0)
+    { TraceScope tr_(st, "k_site_step"); k_site_step<<<(d.n_sites + 255) / 256, 256, 0, st>>>(
       d, params, m, v, p4, p4 + total_capacity, p4 + 2 * static_cast<size_t>(total_capacity),
-      total_capacity, hdr, accq, A, iter, grads_out, true);
+      total_capacity, hdr, accq, A, iter, grads_out, true); }
   if (int r = check_launch("k_site_step")) return r;
-  k_step_finish<<<B, 256, 0, st>>>(d, tile_loss, loss, iter);
+  { TraceScope tr_(st, "k_step_finish"); k_step_finish<<<B, 256, 0, st>>>(d, tile_loss, loss, iter); }
   return check_launch("k_step_finish");
+}
+
+int sad_batch_insert(const sad_batch_image* image, int32_t K, const float* src_params,
+                     int32_t src_capacity, const uint32_t* src_map, const float* src_target,
+                     float* params, float* m, float* v, int32_t total_capacity, uint32_t* map,
+                     float* targets, int64_t total_pixels, void* stream) {
+  BatchDesc d;
+  if (int e = make_desc(image, 1, total_capacity, total_pixels, d, "sad_batch_insert")) return e;
+  if (K != 4 && K != 8 && K != 16) return einval("sad_batch_insert: K must be 4, 8 or 16");
+  if (src_capacity < image->capacity)
+    return einval("sad_batch_insert: src_capacity %d below the image's %d slots", src_capacity,
+                  image->capacity);
+  if ((image->capacity > 0 && (!src_params || !params || !m || !v)) || !src_map || !map ||
+      (src_target && !targets))
+    return einval("sad_batch_insert: null pointer");
+  if (!aligned16(src_map) || !aligned16(map)) return einval("sad_batch_insert: maps must be 16-byte aligned");
+  cudaStream_t st = as_stream(stream);
+  if (image->capacity > 0) {
+    { TraceScope tr_(st, "k_insert_sites"); k_insert_sites<<<(image->capacity + 255) / 256, 256, 0, st>>>(
+        src_params, src_capacity, image->capacity, image->site_offset, params, m, v, total_capacity); }
+    if (int r = check_launch("k_insert_sites")) return r;
+  }
+  const size_t P = static_cast<size_t>(image->H) * image->W;
+  { TraceScope tr_(st, "k_insert_pixels"); k_insert_pixels<<<static_cast<unsigned>((P + 255) / 256), 256, 0, st>>>(
+      reinterpret_cast<const uint4*>(src_map), src_target, P, K / 4,
+      static_cast<uint32_t>(image->capacity), static_cast<uint32_t>(image->site_offset),
+      static_cast<size_t>(image->pixel_offset), reinterpret_cast<uint4*>(map), targets,
+      static_cast<size_t>(total_pixels)); }
+  return check_launch("k_insert_pixels");
 }
 
 int sad_decode_batch(const sad_batch_image* images, int32_t B, int32_t K, const float* prep,
@@ -427,10 +510,10 @@ int sad_decode_batch(const sad_batch_image* images, int32_t B, int32_t K, const 
   if (!aligned16(prep) || !aligned16(map) || (reinterpret_cast<uintptr_t>(xy) & 7u))
     return einval("sad_decode_batch: misaligned pointer");
   const float4* p4 = reinterpret_cast<const float4*>(prep);
-  k_decode_batch<<<static_cast<unsigned>((n + 255) / 256), 256, 0, as_stream(stream)>>>(
+  { TraceScope tr_(as_stream(stream), "k_decode_batch"); k_decode_batch<<<static_cast<unsigned>((n + 255) / 256), 256, 0, as_stream(stream)>>>(
       d, p4, p4 + total_capacity, p4 + 2 * static_cast<size_t>(total_capacity),
       reinterpret_cast<const uint4*>(map), static_cast<size_t>(total_pixels), K,
-      reinterpret_cast<const float2*>(xy), query_image, n, rgb);
+      reinterpret_cast<const float2*>(xy), query_image, n, rgb); }
   return check_launch("k_decode_batch");
 }
 

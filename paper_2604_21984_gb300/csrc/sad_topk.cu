@@ -81,9 +81,9 @@ int sad_prepare_sites(const float* params, int32_t capacity, int32_t H, int32_t 
   const float s = 1.0f / static_cast<float>(H > W ? H : W);
   float4* p4 = reinterpret_cast<float4*>(prep);
   const int bs = 256;
-  k_prepare<<<(capacity + bs - 1) / bs, bs, 0, as_stream(stream)>>>(params, capacity, s, p4,
+  { TraceScope tr_(as_stream(stream), "k_prepare"); k_prepare<<<(capacity + bs - 1) / bs, bs, 0, as_stream(stream)>>>(params, capacity, s, p4,
                                                                      p4 + capacity,
-                                                                     p4 + 2 * (size_t)capacity);
+                                                                     p4 + 2 * (size_t)capacity); }
   return check_launch("k_prepare");
 }
 
@@ -101,8 +101,8 @@ int sad_topk_seed(const float* prep, int32_t capacity, int32_t H, int32_t W, int
   if (capacity == 0) return SAD_OK;
   const float4* p4 = reinterpret_cast<const float4*>(prep);
   const int bs = 256;
-  k_seed<<<(capacity + bs - 1) / bs, bs, 0, as_stream(stream)>>>(p4, p4 + capacity, capacity, H,
-                                                                  W, map);
+  { TraceScope tr_(as_stream(stream), "k_seed"); k_seed<<<(capacity + bs - 1) / bs, bs, 0, as_stream(stream)>>>(p4, p4 + capacity, capacity, H,
+                                                                  W, map); }
   return check_launch("k_seed");
 }
 
@@ -129,16 +129,16 @@ int sad_update_topk(const float* prep, int32_t capacity, int32_t H, int32_t W, i
   cudaStream_t st = as_stream(stream);
   switch (K) {
     case 4:
-      k_topk_update<4><<<grid, block, 0, st>>>(p4, p4 + capacity, capacity, H, W, in, out,
-                                               step_code, n_inject, seed);
+      { TraceScope tr_(st, "k_topk_update"); k_topk_update<4><<<grid, block, 0, st>>>(p4, p4 + capacity, capacity, H, W, in, out,
+                                               step_code, n_inject, seed); }
       break;
     case 8:
-      k_topk_update<8><<<grid, block, 0, st>>>(p4, p4 + capacity, capacity, H, W, in, out,
-                                               step_code, n_inject, seed);
+      { TraceScope tr_(st, "k_topk_update"); k_topk_update<8><<<grid, block, 0, st>>>(p4, p4 + capacity, capacity, H, W, in, out,
+                                               step_code, n_inject, seed); }
       break;
     default:
-      k_topk_update<16><<<grid, block, 0, st>>>(p4, p4 + capacity, capacity, H, W, in, out,
-                                                step_code, n_inject, seed);
+      { TraceScope tr_(st, "k_topk_update"); k_topk_update<16><<<grid, block, 0, st>>>(p4, p4 + capacity, capacity, H, W, in, out,
+                                                step_code, n_inject, seed); }
       break;
   }
   return check_launch("k_topk_update");

@@ -12,9 +12,10 @@
 // Per pixel (one thread):
 //  A. score the pixel's own list (independent gathers) and sort it with a
 //     bitonic network; drop duplicate ids (only possible in a damaged input);
-//  B. filter the 4 neighbour lists and the J injected ids against the list
+//  B. filter each neighbour list and the J injected ids against the list
 //     and queue the novel ids in shared memory (per-thread column);
-//  C. each thread scores its own queue and inserts winners.
+//  C. the thread scores its queue and inserts the winners, after each
+//     neighbour whose ids could overflow the queue, and at the end.
 // Phase C runs per lane, so the insertion network is paid for the queued
 // candidates only, not for every candidate of every lane in the warp.
 #pragma once
@@ -23,7 +24,7 @@
 
 namespace sad {
 
-constexpr int kQueue = 24;
+constexpr int kQueue = 24;  // per-thread queue of novel candidate ids
 
 __device__ __forceinline__ uint64_t make_key(float l, uint32_t id) {
   uint32_t u = __float_as_uint(__fadd_rn(l, 0.0f));
@@ -97,7 +98,7 @@ __device__ __forceinline__ uint64_t cand_key(uint32_t id, SiteRange sr, float px
 // at plane index pix_off.  q_local = row*W + col (injection counter).  Threads
 // outside the image pass inimg = false and get an empty list; the queue
 // column `tid` of s_q must be private to the thread.
-template <int K, int NT>
+template <int K, int NT, int NG = 4>
 __device__ __forceinline__ void pixel_update(uint64_t (&v)[K], bool inimg, int col, int row, int H,
                                              int W, SiteRange sr, const float4* __restrict__ geo,
                                              const float4* __restrict__ met,
@@ -132,14 +133,37 @@ __device__ __forceinline__ void pixel_update(uint64_t (&v)[K], bool inimg, int c
     bitonic_sort_desc<K>(v);
   }
 
-  // B + C. queue novel candidates; drain the queue when full and at the end
+  // B + C. Novel ids (valid, not in the list, not yet queued) go to the
+  // thread's queue column.  A queued id cannot be in the list when it is
+  // scored: the list only gains queued ids, and the queue holds distinct ids.
+  // So the queue is scored in groups of NG (2 NG independent gathers in
+  // flight) and merged; the result is the top K of the union, whatever the
+  // order.  The drain and offer bodies each appear at a handful of call sites
+  // only: fully unrolling them over all candidates made the kernel too large
+  // for the instruction cache when most candidates are novel (the long jumps
+  // of the warm-up).
   int qn = 0;
   auto drain = [&]() {
-    for (int i = 0; i < qn; ++i) {
-      const uint32_t id = s_q[i][tid];
-      if (list_has<K>(v, id)) continue;
-      const uint64_t c = cand_key(id, sr, px, py, geo, met);
-      if (c > v[K - 1]) list_insert<K>(v, c);
+#pragma unroll 1
+    for (int i = 0; i < qn; i += NG) {
+      uint32_t id[NG];
+      float4 g[NG], m[NG];
+#pragma unroll
+      for (int u = 0; u < NG; ++u) id[u] = s_q[i + u < qn ? i + u : i][tid];
+#pragma unroll
+      for (int u = 0; u < NG; ++u) {
+        m[u] = ldg(&met[id[u]]);
+        g[u] = ldg(&geo[id[u]]);
+      }
+#pragma unroll
+      for (int u = 0; u < NG; ++u) {
+        uint64_t c = 0ull;
+        if (i + u < qn && m[u].w != 0.f) {
+          const float l = score_exact(px, py, g[u], m[u]);
+          if (l == l) c = make_key(l, id[u]);
+        }
+        if (c > v[K - 1]) list_insert<K>(v, c);
+      }
     }
     qn = 0;
   };
@@ -147,30 +171,35 @@ __device__ __forceinline__ void pixel_update(uint64_t (&v)[K], bool inimg, int c
     if (!sr.has(id) || list_has<K>(v, id)) return;
     for (int i = 0; i < qn; ++i)
       if (s_q[i][tid] == id) return;
-    if (qn == kQueue) drain();
     s_q[qn++][tid] = id;
   };
+  static_assert(kQueue >= K, "queue must hold one neighbour list");
   const int s = static_cast<int>(code >> 16);
-  const int nc[4] = {col - s, col + s, col, col};
-  const int nr[4] = {row, row, row - s, row + s};
-#pragma unroll
+#pragma unroll 1
   for (int d = 0; d < 4; ++d) {
-    if (nc[d] < 0 || nc[d] >= W || nr[d] < 0 || nr[d] >= H) continue;
-    const size_t nq = pix_off + static_cast<size_t>(nr[d]) * W + nc[d];
+    const int nc = d == 0 ? col - s : (d == 1 ? col + s : col);
+    const int nr = d == 2 ? row - s : (d == 3 ? row + s : row);
+    if (nc < 0 || nc >= W || nr < 0 || nr >= H) continue;
+    const size_t nq = pix_off + static_cast<size_t>(nr) * W + nc;
+    uint4 w[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) w[j] = ldg(&map_in[j * P + nq]);
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
-      const uint4 w = ldg(&map_in[j * P + nq]);
-      offer(w.x);
-      offer(w.y);
-      offer(w.z);
-      offer(w.w);
+      offer(w[j].x);
+      offer(w[j].y);
+      offer(w[j].z);
+      offer(w[j].w);
     }
+    if (qn > kQueue - K) drain();  // room for the next neighbour's K ids
   }
   const uint64_t base = (static_cast<uint64_t>(code) << 32);
+#pragma unroll 1
   for (int j = 0; j < J; ++j) {
     const uint64_t ctr = base | static_cast<uint32_t>(q * static_cast<uint32_t>(J) + j);
     const uint64_t h = splitmix64_at(seed, ctr);
     offer(sr.lo + static_cast<uint32_t>(((h >> 32) * static_cast<uint64_t>(sr.n)) >> 32));
+    if (qn == kQueue) drain();
   }
   drain();
 }

@@ -2,11 +2,15 @@
 
 One encode = gradient-weighted initialisation (Sec. 4.4), a JFA warm-up of
 the top-K field (seed + log2 B propagation passes, Sec. 4.3), then per
-iteration: prepare sites -> one propagation pass -> fused render + MSE +
-adjoint -> Adam (Sec. 6.1), with a densify-then-prune event every
-`densify_every` iterations inside [densify_start, densify_end] (Sec. 4.5).
-Everything runs in libsad.so on one CUDA stream; the host only enqueues
-calls (the densify event reads back the active-site count).
+iteration: one propagation pass -> render + MSE + adjoint -> Adam (Sec. 6.1),
+with a densify-then-prune event every `densify_every` iterations inside
+[densify_start, densify_end] (Sec. 4.5).  With `fused` (the default) an
+iteration is one `sad_train_step` call on a one-image batch (the pass and the
+adjoint in one tile kernel, Adam and the next prepared table in one site
+kernel); otherwise it is the four separate calls (prepare, update, train
+grads, Adam), which give the same iteration.  Everything runs in libsad.so
+on one CUDA stream; the host only enqueues calls (the densify event reads
+back the active-site count).
 """
 from __future__ import annotations
 
@@ -34,6 +38,8 @@ class EncodeConfig:
     alpha: float = 0.7
     seed: int = 0
     lr: tuple = (1e-3, 1e-3, 1e-2, 1e-3, 5e-3, 5e-3, 5e-3, 1e-2, 1e-2, 1e-2, 0.0)
+    fused: bool = True   # one sad_train_step per iteration (else the separate calls)
+    keep_grads: bool = False   # fused: also write the step's gradients to Encoder.grads
     extra: dict = field(default_factory=dict)
 
 
@@ -50,6 +56,30 @@ def psnr_from_loss(loss: float) -> float:
     """PSNR of images in [0,1] from L = mean over pixels of |c - I|^2 (3 channels)."""
     mse = loss / 3.0
     return float("inf") if mse <= 0 else 10.0 * math.log10(1.0 / mse)
+
+
+def warm_start(target, n0, params, prep, map_a, map_b, K, J, lambda_init, seed, stream=None):
+    """Gradient-weighted sites (Sec. 4.4) with tau s d0 = 4, d0 = sqrt(P/n0),
+    then the top-K field's JFA warm-up: seed + ceil(log2 max(H, W)) passes
+    (Sec. 4.3) with injection seed `seed + 0x5AD`.  params: float32[11, cap]
+    (cap >= n0; slots from n0 on inactive); prep: the prepared table;
+    map_a/map_b: the two map buffers.  Returns (current map, other map,
+    passes run)."""
+    H, W = int(target.shape[0]), int(target.shape[1])
+    cap = params.shape[1]
+    s = 1.0 / max(H, W)
+    d0 = math.sqrt(H * W / n0)
+    log_tau0 = math.log(4.0 / (s * d0))
+    capi.sad_init_sites(target, n0, cap, lambda_init, seed, log_tau0, params=params, stream=stream)
+    capi.sad_prepare_sites(params, H, W, prep, stream)
+    capi.sad_topk_seed(prep, cap, H, W, K, map_a, stream)
+    L = max(H, W)
+    n_pass = max(1, math.ceil(math.log2(L)))
+    for t in range(n_pass):
+        capi.sad_update_topk(prep, cap, H, W, K, map_a, map_b, jump_code(t, H, W), J, seed + 0x5AD,
+                             stream)
+        map_a, map_b = map_b, map_a
+    return map_a, map_b, n_pass
 
 
 class Encoder:
@@ -83,6 +113,12 @@ class Encoder:
         self.it = 0
         self.n_active = self.n0
         self.history = []
+        if c.fused:
+            self.table = capi.batch_table([dict(H=H, W=W, site_offset=0, capacity=cap, pixel_offset=0,
+                                                seed=c.seed + 0x5AD)])
+            self.ws_step = capi.step_workspace(self.table, K, cap, H * W, device=self.dev)
+            self.iter_dev = torch.zeros(2, dtype=torch.int32, device=self.dev)
+            self.target_flat = self.target.reshape(-1, 3)
 
     @property
     def map(self):
@@ -97,25 +133,27 @@ class Encoder:
         self.t_pass += 1
 
     def init(self):
-        """Gradient-weighted sites, tau s d0 = 4 with d0 = sqrt(P/N), and the
-        JFA warm-up of the field."""
+        """Gradient-weighted sites and the JFA warm-up of the field."""
         c = self.cfg
-        H, W = self.H, self.W
-        s = 1.0 / max(H, W)
-        d0 = math.sqrt(H * W / self.n0)
-        log_tau0 = math.log(4.0 / (s * d0))
-        capi.sad_init_sites(self.target, self.n0, self.cap, c.lambda_init, c.seed, log_tau0,
-                            params=self.params, stream=self.stream)
-        capi.sad_prepare_sites(self.params, H, W, self.prep, self.stream)
-        capi.sad_topk_seed(self.prep, self.cap, H, W, c.K, self.maps[0], self.stream)
-        L = max(H, W)
-        for _ in range(max(1, math.ceil(math.log2(L)))):
-            self._pass()
+        a, b, self.t_pass = warm_start(self.target, self.n0, self.params, self.prep, self.maps[0],
+                                       self.maps[1], c.K, c.J, c.lambda_init, c.seed, self.stream)
+        self.maps = [a, b]
+        if c.fused:
+            # Adam step 1 next; pass indices continue after the warm-up's
+            self.iter_dev.copy_(torch.tensor([1, self.t_pass], dtype=torch.int32))
 
     def step(self):
-        """One training iteration (prepare, 1 pass, fused gradient, Adam)."""
+        """One training iteration (1 pass, gradient, Adam)."""
         c = self.cfg
         self.it += 1
+        if c.fused:
+            capi.sad_train_step(self.table, c.K, c.J, self.params, self.m, self.v, self.prep, self.maps[0],
+                                self.maps[1], self.H * self.W, self.target_flat, self.loss, self.hp,
+                                self.iter_dev, self.ws_step,
+                                grads_out=self.grads if c.keep_grads else None, stream=self.stream)
+            self.maps.reverse()
+            self.t_pass += 1
+            return
         capi.sad_prepare_sites(self.params, self.H, self.W, self.prep, self.stream)
         self._pass()
         capi.sad_train_grads(self.params, self.prep, self.H, self.W, c.K, self.maps[0], self.target,
@@ -131,6 +169,8 @@ class Encoder:
         self.n_active = capi.sad_densify_prune(self.params, self.m, self.v, self.H, self.W, c.K,
                                                self.stats, self.target, self.maps[0], self.dp,
                                                self.ws_dp, self.stream)
+        if c.fused:   # the step expects the prepared table of the current sites
+            capi.sad_prepare_sites(self.params, self.H, self.W, self.prep, self.stream)
         return self.n_active
 
     def run(self, iters: int | None = None, log_every: int = 0):

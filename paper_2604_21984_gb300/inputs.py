@@ -91,6 +91,37 @@ def image_sinusoid_polygons(H: int = 64, W: int = 64, seed: int = 1000,
     return np.clip(img, 0.0, 1.0).astype(np.float32)
 
 
+def _draw_segment(img, x0, y0, x1, y1, width, colour, bx0, bx1, by0, by1):
+    """Paint the pixels whose centre lies within width/2 of the segment.
+    Works in strips of 64 rows, each restricted to the columns the segment can
+    reach inside the strip (a margin of one pixel beyond the exact reach), so
+    a long diagonal stroke costs its area, not its bounding box."""
+    dx, dy = x1 - x0, y1 - y0
+    L2 = dx * dx + dy * dy + 1e-12
+    half = 0.5 * width
+    for r0 in range(by0, by1, 64):
+        r1 = min(r0 + 64, by1)
+        ylo, yhi = r0 + 0.5 - half, r1 - 0.5 + half
+        if abs(dy) < 1e-12:
+            if not ylo <= y0 <= yhi:
+                continue
+            tlo, thi = 0.0, 1.0
+        else:
+            ta, tb = (ylo - y0) / dy, (yhi - y0) / dy
+            tlo, thi = max(0.0, min(ta, tb)), min(1.0, max(ta, tb))
+            if tlo > thi:
+                continue
+        xa, xb = sorted((x0 + tlo * dx, x0 + thi * dx))
+        c0 = max(bx0, int(math.floor(xa - half - 1.5)))
+        c1 = min(bx1, int(math.ceil(xb + half + 1.5)) + 1)
+        if c0 >= c1:
+            continue
+        py, px = np.mgrid[r0:r1, c0:c1].astype(np.float64) + 0.5
+        t = np.clip(((px - x0) * dx + (py - y0) * dy) / L2, 0, 1)
+        dist = np.hypot(px - (x0 + t * dx), py - (y0 + t * dy))
+        img[r0:r1, c0:c1][dist <= half] = colour
+
+
 def _value_noise(g, H, W, cell):
     """One octave of bilinear value noise with lattice spacing ``cell``."""
     ny, nx = H // cell + 2, W // cell + 2
@@ -100,11 +131,10 @@ def _value_noise(g, H, W, cell):
     iy, ix = ys.astype(int), xs.astype(int)
     ty, tx = (ys - iy)[:, None, None], (xs - ix)[None, :, None]
     ty, tx = ty * ty * (3 - 2 * ty), tx * tx * (3 - 2 * tx)
-    a = lat[iy][:, ix]
-    b = lat[iy][:, ix + 1]
-    c = lat[iy + 1][:, ix]
-    d = lat[iy + 1][:, ix + 1]
-    return (a * (1 - tx) + b * tx) * (1 - ty) + (c * (1 - tx) + d * tx) * ty
+    # separable: interpolate each lattice row along x, then rows along y
+    # (the same products and sums per pixel as the 4-corner form)
+    rows = lat[:, ix] * (1 - tx) + lat[:, ix + 1] * tx
+    return rows[iy] * (1 - ty) + rows[iy + 1] * ty
 
 
 def image_noise_polygons_lines(H: int = 512, W: int = 768, seed: int = 2000,
@@ -137,12 +167,7 @@ def image_noise_polygons_lines(H: int = 512, W: int = 768, seed: int = 2000,
         by1 = min(int(max(y0, y1) + width + 2), H)
         if bx0 >= bx1 or by0 >= by1:
             continue
-        py, px = np.mgrid[by0:by1, bx0:bx1].astype(np.float64) + 0.5
-        dx, dy = x1 - x0, y1 - y0
-        L2 = dx * dx + dy * dy + 1e-12
-        t = np.clip(((px - x0) * dx + (py - y0) * dy) / L2, 0, 1)
-        dist = np.hypot(px - (x0 + t * dx), py - (y0 + t * dy))
-        img[by0:by1, bx0:bx1][dist <= 0.5 * width] = colour
+        _draw_segment(img, x0, y0, x1, y1, width, colour, bx0, bx1, by0, by1)
     return np.clip(img, 0.0, 1.0).astype(np.float32)
 
 
@@ -305,3 +330,65 @@ def uniform_points(n: int, H: int, W: int, seed: int) -> np.ndarray:
     """Uniform float query coordinates in [0,W) x [0,H): float32[n, 2]."""
     g = rng(seed)
     return np.stack([g.uniform(0, W, n), g.uniform(0, H, n)], 1).astype(np.float32)
+
+
+# ----------------------------------------------------------------------------
+# workload mixes: uneven image batches and request streams
+# ----------------------------------------------------------------------------
+
+def _log_uniform(g, lo, hi):
+    return math.exp(g.uniform(math.log(lo), math.log(hi)))
+
+
+def batch_sizes(n: int, seed: int, lo: int = 256, hi: int = 2048,
+                aspect=(1.0, 1.5)) -> list:
+    """n image sizes (H, W): long side log-uniform in [lo, hi], aspect ratio
+    uniform in `aspect`, short side round(long / ratio), orientation random."""
+    g = rng(seed)
+    out = []
+    for _ in range(n):
+        L = int(round(_log_uniform(g, lo, hi)))
+        S = max(1, int(round(L / g.uniform(*aspect))))
+        out.append((S, L) if g.uniform() < 0.5 else (L, S))
+    return out
+
+
+def serve_stream(seed: int, seconds: float, rate: float, decode_frac: float = 0.7,
+                 n_residents: int = 4, coords=(1e3, 1e6), side=(128, 4096),
+                 iters: int = 1000) -> list:
+    """Poisson request stream: exponential inter-arrival times with mean
+    1/rate until `seconds`; each request is a decode with probability
+    decode_frac (a resident set index uniform in [0, n_residents), a
+    log-uniform coordinate count in `coords`, a coordinate seed) or else an
+    encode (square-ish image with log-uniform side in `side`, aspect in
+    [1, 1.5], an image seed, `iters` iterations).  Returns a list of dicts
+    sorted by arrival."""
+    g = rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += g.exponential(1.0 / rate)
+        if t >= seconds:
+            break
+        if g.uniform() < decode_frac:
+            out.append(dict(kind="decode", arrival=t, resident=int(g.integers(0, n_residents)),
+                            n=int(round(_log_uniform(g, *coords))), seed=int(g.integers(1 << 31))))
+        else:
+            L = int(round(_log_uniform(g, *side)))
+            S = max(1, int(round(L / g.uniform(1.0, 1.5))))
+            H, W = (S, L) if g.uniform() < 0.5 else (L, S)
+            out.append(dict(kind="encode", arrival=t, H=H, W=W, seed=int(g.integers(1 << 31)),
+                            iters=iters))
+    return out
+
+
+def resident_sets(seed: int, n: int, sites=(16384, 1 << 20), sites_per_pixel: float = 0.06) -> list:
+    """n decode site sets: N log-uniform in `sites`, a square image of
+    P = N / sites_per_pixel pixels, random anisotropic sites
+    (sites_random_spd).  Returns [(H, W, N, site seed)]."""
+    g = rng(seed)
+    out = []
+    for _ in range(n):
+        N = int(round(_log_uniform(g, *sites)))
+        side = max(1, int(round(math.sqrt(N / sites_per_pixel))))
+        out.append((side, side, N, int(g.integers(1 << 31))))
+    return out

@@ -1,0 +1,500 @@
+"""Serving: continuous batching of encode requests and batched random-access
+decode over one resident pool of sites and pixels.
+
+Two request kinds:
+  * encode(image, iters): fit SAD sites to an image (gradient-weighted init
+    and JFA warm-up, Sec. 4.3-4.4; then `iters` training iterations, Sec. 6.1)
+    and return the site parameters;
+  * decode(resident, xy): colours at arbitrary float coordinates of a resident
+    site set (the random-access decode of the softmax blend, Sec. 4.2).
+
+All encodes in flight share one set of device arrays (a site pool and a pixel
+pool, sized up front from the HBM budget).  Admission allocates an encode's
+slot range and pixel range (first fit); a request that does not fit waits.
+Every tick runs ONE fused training iteration (`sad_train_step`) of every
+admitted encode, whatever its age: an encode joins the running batch with
+counter offsets so that its Adam step and pass index start where a solo run's
+would, so its result is the same alone or in any mix.  All decode requests
+that have arrived are answered by one `sad_decode_batch` launch per tick.
+Completion times are CUDA events on the serving stream.
+
+`PlainLoop` is the baseline: FIFO, one request at a time, each with the
+single-image calls.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import capi
+from .encode import EncodeConfig, Encoder, warm_start
+
+@dataclass
+class ServeConfig:
+    K: int = 16
+    J: int = 4
+    sites_per_pixel: float = 0.06
+    lambda_init: float = 0.3
+    site_pool: int = 1 << 22
+    pixel_pool: int = 1 << 26
+    max_side: int = 4096           # largest encode accepted
+    max_decode_per_tick: int = 1 << 22
+    lr: tuple = (1e-3, 1e-3, 1e-2, 1e-3, 5e-3, 5e-3, 5e-3, 1e-2, 1e-2, 1e-2, 0.0)
+
+
+@dataclass
+class Request:
+    kind: str                      # "encode" | "decode"
+    arrival: float = 0.0           # seconds after the stream's start
+    image: torch.Tensor | None = None   # encode: float32[H, W, 3] (device)
+    iters: int = 1000              # encode: training iterations
+    seed: int = 0                  # encode: per-request seed
+    resident: int = -1             # decode: resident site set index
+    xy: torch.Tensor | None = None      # decode: float32[n, 2] (pinned host or device)
+    rid: int = -1
+    # filled in by the server
+    done_event: torch.cuda.Event | None = None
+    latency: float | None = None
+    result: object = None          # encode: float32[11, n] params; decode: float32[n, 3]
+    loss: torch.Tensor | None = None
+
+
+class RangePool:
+    """First-fit allocator of [0, capacity) with coalescing free list."""
+
+    def __init__(self, capacity: int, align: int = 1):
+        self.capacity = capacity
+        self.align = align
+        self.free = [(0, capacity)]     # sorted (offset, length)
+
+    def alloc(self, n: int):
+        n = max(1, -(-n // self.align) * self.align)
+        for k, (o, l) in enumerate(self.free):
+            if l >= n:
+                if l == n:
+                    self.free.pop(k)
+                else:
+                    self.free[k] = (o + n, l - n)
+                return o
+        return None
+
+    def release(self, o: int, n: int):
+        n = max(1, -(-n // self.align) * self.align)
+        fr = self.free
+        k = 0
+        while k < len(fr) and fr[k][0] < o:
+            k += 1
+        if k > 0 and fr[k - 1][0] + fr[k - 1][1] > o:
+            raise ValueError("double free or overlap")
+        if k < len(fr) and o + n > fr[k][0]:
+            raise ValueError("double free or overlap")
+        fr.insert(k, (o, n))
+        # coalesce with neighbours
+        if k + 1 < len(fr) and fr[k][0] + fr[k][1] == fr[k + 1][0]:
+            fr[k] = (fr[k][0], fr[k][1] + fr[k + 1][1])
+            fr.pop(k + 1)
+        if k > 0 and fr[k - 1][0] + fr[k - 1][1] == fr[k][0]:
+            fr[k - 1] = (fr[k - 1][0], fr[k - 1][1] + fr[k][1])
+            fr.pop(k)
+
+    def free_total(self):
+        return sum(l for _, l in self.free)
+
+
+def encode_sites(H: int, W: int, sites_per_pixel: float) -> int:
+    return max(1, min(H * W, int(round(sites_per_pixel * H * W))))
+
+
+def pool_bytes(site_pool: int, pixel_pool: int, K: int) -> int:
+    """HBM footprint of a Server's pools (params, Adam moments, prepared
+    table, step accumulators; targets, two maps)."""
+    per_site = 4 * 11 * 3 + 48 + 80
+    per_pixel = 12 + 2 * 4 * K
+    return site_pool * per_site + pixel_pool * per_pixel
+
+
+class Server:
+    """Resident pools + the per-tick batched step and decode."""
+
+    def __init__(self, cfg: ServeConfig | None = None, device="cuda", stream=None):
+        self.cfg = cfg or ServeConfig()
+        c = self.cfg
+        self.dev = torch.device(device)
+        self.stream = stream or torch.cuda.Stream(device=self.dev)
+        # decodes run beside training, ahead of it when both have work queued
+        self.dstream = torch.cuda.Stream(device=self.dev, priority=-1)
+        S, Pp, K = c.site_pool, c.pixel_pool, c.K
+        if Pp < c.max_side ** 2 or S < encode_sites(c.max_side, c.max_side, c.sites_per_pixel):
+            raise ValueError("pools smaller than one encode of max_side")
+        f32 = dict(dtype=torch.float32, device=self.dev)
+        self.params = torch.zeros((capi.N_PARAMS, S), **f32)
+        self.params[0].fill_(-1.0)          # every slot inactive until used
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.prep = capi.empty_prep(S, self.dev)
+        self.targets = torch.zeros((Pp, 3), **f32)
+        self.maps = [torch.full((K // 4, Pp, 4), -1, dtype=torch.int32, device=self.dev) for _ in range(2)]
+        self.sites = RangePool(S)
+        self.pixels = RangePool(Pp, align=4)
+        self.loss = torch.zeros(64, **f32)
+        self.iter = torch.tensor([1, 0], dtype=torch.int32, device=self.dev)
+        self.iter_host = [1, 0]
+        self.hp = capi.adam_hparams(lr=c.lr)
+        self.ws = self._workspace()
+        # staging for the single-image warm start (largest accepted image)
+        Pmax = c.max_side * c.max_side
+        nmax = encode_sites(c.max_side, c.max_side, c.sites_per_pixel)
+        self._st_params = torch.empty(capi.N_PARAMS * nmax, **f32)
+        self._st_prep = torch.empty(12 * nmax, **f32)
+        self._st_maps = [torch.empty(K * Pmax, dtype=torch.int32, device=self.dev) for _ in range(2)]
+        # decode staging
+        self._dq_xy = torch.empty((c.max_decode_per_tick, 2), **f32)
+        self._dq_img = torch.empty(c.max_decode_per_tick, dtype=torch.int32, device=self.dev)
+        self._dq_rgb = torch.empty((c.max_decode_per_tick, 3), **f32)
+        self.active = []        # encodes in the batch: dicts with entry + request
+        self.waiting = []       # encodes not admitted yet (FIFO)
+        self.decodes = []       # decodes waiting for the next tick
+        self.residents = []     # resident decode site sets: table entries
+        self.launches = 0
+
+    # -- pools ---------------------------------------------------------------
+    def _workspace(self):
+        c = self.cfg
+        # records as for a full single image; tile losses for the worst tile
+        # count of the pixel pool (64 images, each with a ragged tile row and
+        # column)
+        Pp = c.pixel_pool
+        tiles = Pp // 256 + 64 * (2 * int(math.isqrt(Pp)) // 16 + 2)
+        side = 16 * int(math.isqrt(tiles)) + 16
+        entry = [dict(H=side, W=side, site_offset=0, capacity=0, pixel_offset=0, seed=0)]
+        n = capi.lib().sad_step_workspace_bytes(
+            capi.ctypes.cast(capi.batch_table(entry), capi.ctypes.c_void_p), 1, c.K, c.site_pool,
+            side * side, Pp * c.K // 8)
+        if n == 0:
+            raise ValueError("pool too large for one step workspace")
+        return torch.zeros(n, dtype=torch.uint8, device=self.dev)
+
+    def footprint_bytes(self):
+        c = self.cfg
+        return pool_bytes(c.site_pool, c.pixel_pool, c.K) + self.ws.numel()
+
+    def add_resident(self, params: torch.Tensor, H: int, W: int, passes: int = 16, J: int = 2,
+                     seed: int = 11):
+        """Place a decode site set (float32[11, N] device) in the pools with
+        its field built by seed + `passes` propagation passes.  Returns its
+        index."""
+        c = self.cfg
+        N = params.shape[1]
+        lo = self.sites.alloc(N)
+        po = self.pixels.alloc(H * W)
+        if lo is None or po is None:
+            raise MemoryError("pools too small for the resident set")
+        entry = dict(H=H, W=W, site_offset=lo, capacity=N, pixel_offset=po, seed=seed)
+        with torch.cuda.stream(self.stream):
+            prep = capi.empty_prep(N, self.dev)
+            a = capi.empty_map(H, W, c.K, self.dev)
+            b = capi.empty_map(H, W, c.K, self.dev)
+            pc = params.contiguous()
+            capi.sad_prepare_sites(pc, H, W, prep, self.stream)
+            capi.sad_topk_seed(prep, N, H, W, c.K, a, self.stream)
+            L = max(H, W)
+            lb = max(1, math.ceil(math.log2(L)))
+            for t in range(passes):
+                s = max(1, (1 << lb) >> (min(t, lb - 1) + 1))
+                capi.sad_update_topk(prep, N, H, W, c.K, a, b, (s << 16) | t, J, seed, self.stream)
+                a, b = b, a
+            # both ping-pong buffers: training steps only rewrite their own
+            # images' pixels
+            for mp in self.maps:
+                capi.sad_batch_insert(capi.batch_table([entry]), c.K, pc, a, None, self.params,
+                                      self.m, self.v, mp, self.targets, c.pixel_pool, self.stream)
+            capi.sad_prepare_batch(capi.batch_table([entry]), self.params, self.prep, c.pixel_pool,
+                                   self.stream)
+        self.dstream.wait_stream(self.stream)
+        self.residents.append(entry)
+        return len(self.residents) - 1
+
+    # -- requests --------------------------------------------------------------
+    def submit(self, req: Request):
+        if req.kind == "encode":
+            H, W = int(req.image.shape[0]), int(req.image.shape[1])
+            if max(H, W) > self.cfg.max_side:
+                raise ValueError("image larger than max_side")
+            res_s = sum(e["capacity"] for e in self.residents)
+            res_p = sum(e["H"] * e["W"] + 3 for e in self.residents)
+            if (encode_sites(H, W, self.cfg.sites_per_pixel) > self.cfg.site_pool - res_s
+                    or H * W + 3 > self.cfg.pixel_pool - res_p):
+                raise ValueError("encode larger than the pools left beside the resident sets")
+            self.waiting.append(req)
+        elif req.kind == "decode":
+            if not 0 <= req.resident < len(self.residents):
+                raise ValueError("unknown resident set")
+            if req.xy.shape[0] > self.cfg.max_decode_per_tick:
+                raise ValueError("decode larger than max_decode_per_tick")
+            self.decodes.append(req)
+        else:
+            raise ValueError(req.kind)
+
+    def _admit(self):
+        c = self.cfg
+        admitted = []
+        while self.waiting and len(self.active) < 64:
+            req = self.waiting[0]
+            H, W = int(req.image.shape[0]), int(req.image.shape[1])
+            n = encode_sites(H, W, c.sites_per_pixel)
+            lo = self.sites.alloc(n)
+            if lo is None:
+                break
+            po = self.pixels.alloc(H * W)
+            if po is None:
+                self.sites.release(lo, n)
+                break
+            self.waiting.pop(0)
+            # injection seed and pass indices as in a solo encode: seed + 0x5AD,
+            # passes numbered on from the warm-up's; Adam step 1 first
+            entry = dict(H=H, W=W, site_offset=lo, capacity=n, pixel_offset=po, seed=req.seed + 0x5AD,
+                         t_offset=1 - self.iter_host[0], pass_offset=0)
+            n_pass = self._warm_start(req, entry)
+            entry["pass_offset"] = n_pass - self.iter_host[1]
+            self.active.append(dict(entry=entry, req=req, left=req.iters))
+            admitted.append(entry)
+        if admitted:
+            capi.sad_prepare_batch(capi.batch_table(admitted), self.params, self.prep,
+                                   c.pixel_pool, self.stream)
+            self.launches += 1
+
+    def _warm_start(self, req, entry):
+        c = self.cfg
+        H, W, n = entry["H"], entry["W"], entry["capacity"]
+        P = H * W
+        params = self._st_params[:capi.N_PARAMS * n].view(capi.N_PARAMS, n)
+        prep = self._st_prep[:12 * n]
+        ma = self._st_maps[0][:c.K * P].view(c.K // 4, P, 4)
+        mb = self._st_maps[1][:c.K * P].view(c.K // 4, P, 4)
+        target = req.image.contiguous()
+        a, _, n_pass = warm_start(target, n, params, prep, ma, mb, c.K, c.J, c.lambda_init,
+                                  req.seed, self.stream)
+        # the step reads the current map buffer
+        capi.sad_batch_insert(capi.batch_table([entry]), c.K, params, a, target, self.params, self.m,
+                              self.v, self.maps[0], self.targets, c.pixel_pool, self.stream)
+        self.launches += 4 + n_pass + 2
+        return n_pass
+
+    def train_tick(self, max_iters: int = 1) -> int:
+        """Admit what fits, then T = min(max_iters, fewest iterations left)
+        fused iterations of every admitted encode (so encodes finish only at
+        the end of a tick); finished encodes hand back their sites and leave.
+        Returns T."""
+        with torch.cuda.stream(self.stream):
+            self._admit()
+            if not self.active:
+                return 0
+            c = self.cfg
+            T = max(1, min(max_iters, min(a["left"] for a in self.active)))
+            self.active.sort(key=lambda a: a["entry"]["site_offset"])
+            table = capi.batch_table([a["entry"] for a in self.active])
+            for _ in range(T):
+                capi.sad_train_step(table, c.K, c.J, self.params, self.m, self.v, self.prep, self.maps[0],
+                                    self.maps[1], c.pixel_pool, self.targets, self.loss, self.hp,
+                                    self.iter, self.ws, stream=self.stream)
+                self.maps.reverse()
+            self.launches += 4 * T
+            self.iter_host[0] += T
+            self.iter_host[1] += T
+            still = []
+            for b, a in enumerate(self.active):
+                a["left"] -= T
+                if a["left"] > 0:
+                    still.append(a)
+                    continue
+                e, req = a["entry"], a["req"]
+                lo, n = e["site_offset"], e["capacity"]
+                req.result = self.params[:, lo:lo + n].clone()
+                req.loss = self.loss[b:b + 1].clone()
+                ev = torch.cuda.Event(enable_timing=True)
+                ev.record(self.stream)
+                req.done_event = ev
+                self.sites.release(lo, n)
+                self.pixels.release(e["pixel_offset"], e["H"] * e["W"])
+            self.active = still
+            return T
+
+    def decode_tick(self):
+        """Answer every waiting decode (up to max_decode_per_tick coordinates)
+        with one batched launch on the decode stream, which runs beside the
+        training stream (resident sets are never written by training)."""
+        if not self.decodes:
+            return
+        c = self.cfg
+        reqs, total = [], 0
+        while self.decodes and total + self.decodes[0].xy.shape[0] <= c.max_decode_per_tick:
+            r = self.decodes.pop(0)
+            reqs.append(r)
+            total += r.xy.shape[0]
+        table = capi.batch_table(self.residents)
+        ds = self.dstream
+        with torch.cuda.stream(ds):
+            o = 0
+            for r in reqs:
+                n = r.xy.shape[0]
+                self._dq_xy[o:o + n].copy_(r.xy, non_blocking=True)
+                self._dq_img[o:o + n].fill_(r.resident)
+                o += n
+            capi.sad_decode_batch(table, c.K, self.prep, c.site_pool, self.maps[0], c.pixel_pool,
+                                  self._dq_xy[:total], self._dq_img[:total], self._dq_rgb[:total], ds)
+            self.launches += 1
+            o = 0
+            ev = torch.cuda.Event(enable_timing=True)
+            for r in reqs:
+                n = r.xy.shape[0]
+                r.result = torch.empty((n, 3), dtype=torch.float32, pin_memory=True)
+                r.result.copy_(self._dq_rgb[o:o + n], non_blocking=True)
+                o += n
+            ev.record(ds)
+        for r in reqs:
+            r.done_event = ev
+
+    def tick(self):
+        """One training iteration of every admitted encode, then one batched
+        decode of every waiting query."""
+        self.train_tick(1)
+        self.decode_tick()
+
+    def busy(self):
+        return bool(self.active or self.waiting or self.decodes)
+
+
+class PlainLoop:
+    """FIFO baseline: one request at a time with the single-image calls.
+    Encodes run `Encoder.step` with the separate calls per iteration
+    (prepare, propagation pass, fused forward/backward with its reduce, Adam;
+    no densify, no graph, nothing shared across images); decodes
+    `sad_decode_points` on the resident set's own arrays."""
+
+    def __init__(self, cfg: ServeConfig | None = None, device="cuda", stream=None):
+        self.cfg = cfg or ServeConfig()
+        self.dev = torch.device(device)
+        self.stream = stream or torch.cuda.Stream(device=self.dev)
+        self.residents = []
+        self.queue = []
+        self.launches = 0
+
+    def add_resident(self, params, H, W, passes=16, J=2, seed=11):
+        c = self.cfg
+        N = params.shape[1]
+        with torch.cuda.stream(self.stream):
+            prep = capi.empty_prep(N, self.dev)
+            a = capi.empty_map(H, W, c.K, self.dev)
+            b = capi.empty_map(H, W, c.K, self.dev)
+            pc = params.contiguous()
+            capi.sad_prepare_sites(pc, H, W, prep, self.stream)
+            capi.sad_topk_seed(prep, N, H, W, c.K, a, self.stream)
+            lb = max(1, math.ceil(math.log2(max(H, W))))
+            for t in range(passes):
+                s = max(1, (1 << lb) >> (min(t, lb - 1) + 1))
+                capi.sad_update_topk(prep, N, H, W, c.K, a, b, (s << 16) | t, J, seed, self.stream)
+                a, b = b, a
+        self.residents.append(dict(prep=prep, map=a, H=H, W=W, N=N))
+        return len(self.residents) - 1
+
+    def submit(self, req: Request):
+        self.queue.append(req)
+
+    def run_one(self):
+        c = self.cfg
+        req = self.queue.pop(0)
+        with torch.cuda.stream(self.stream):
+            if req.kind == "encode":
+                H, W = int(req.image.shape[0]), int(req.image.shape[1])
+                n = encode_sites(H, W, c.sites_per_pixel)
+                enc = Encoder(req.image.contiguous(),
+                              EncodeConfig(n_sites=n, K=c.K, J=c.J, capacity_factor=1.0,
+                                           lambda_init=c.lambda_init, seed=req.seed, lr=c.lr,
+                                           densify_every=0, fused=False),
+                              stream=self.stream)
+                enc.init()
+                for _ in range(req.iters):
+                    enc.step()
+                req.result = enc.params[:, :n].clone()
+                req.loss = enc.loss.clone()
+                self.launches += 7 + enc.t_pass + 4 * req.iters
+            else:
+                r = self.residents[req.resident]
+                n = req.xy.shape[0]
+                xy = req.xy.to(self.dev, non_blocking=True)
+                out = torch.empty((n, 3), dtype=torch.float32, device=self.dev)
+                capi.sad_decode_points(r["prep"], r["N"], r["H"], r["W"], c.K, r["map"], xy, out,
+                                       self.stream)
+                req.result = torch.empty((n, 3), dtype=torch.float32, pin_memory=True)
+                req.result.copy_(out, non_blocking=True)
+                self.launches += 1
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(self.stream)
+        req.done_event = ev
+        return req
+
+    def busy(self):
+        return bool(self.queue)
+
+
+def run_stream(server, requests, max_inflight_ticks: int = 2, iters_per_tick: int = 8):
+    """Replay `requests` (sorted by arrival, seconds) in real time against a
+    Server or PlainLoop.  Latency = completion (CUDA event, relative to a
+    start event recorded when the stream starts) - arrival.  The host only
+    enqueues work: a Server gets decode batches as soon as queries arrive and
+    training ticks of up to `iters_per_tick` iterations while fewer than
+    `max_inflight_ticks` are queued on the device; a PlainLoop runs one
+    request at a time.  Returns wall seconds."""
+    st = server.stream
+    start = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(server.dev)
+    start.record(st)
+    t0 = time.perf_counter()
+    pending = list(requests)
+    inflight = []
+    plain = isinstance(server, PlainLoop)
+    while pending or server.busy():
+        now = time.perf_counter() - t0
+        while pending and pending[0].arrival <= now:
+            server.submit(pending.pop(0))
+        inflight = [e for e in inflight if not e.query()]
+        did = False
+        if plain:
+            if server.busy() and len(inflight) < max_inflight_ticks:
+                server.run_one()
+                ev = torch.cuda.Event()
+                ev.record(st)
+                inflight.append(ev)
+                did = True
+        else:
+            if server.decodes:
+                server.decode_tick()
+                did = True
+            if (server.active or server.waiting) and len(inflight) < max_inflight_ticks:
+                if server.train_tick(iters_per_tick):
+                    ev = torch.cuda.Event()
+                    ev.record(st)
+                    inflight.append(ev)
+                    did = True
+        if not did:
+            time.sleep(0.0002)
+    torch.cuda.synchronize(server.dev)
+    wall = time.perf_counter() - t0
+    for r in requests:
+        r.latency = start.elapsed_time(r.done_event) / 1e3 - r.arrival
+    return wall
+
+
+def latency_summary(requests):
+    out = {}
+    for kind in ("encode", "decode"):
+        lat = sorted(r.latency for r in requests if r.kind == kind)
+        if not lat:
+            continue
+        out[kind] = dict(n=len(lat), p50_s=float(np.percentile(lat, 50)),
+                         p99_s=float(np.percentile(lat, 99)), mean_s=float(np.mean(lat)))
+    return out

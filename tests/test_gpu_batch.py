@@ -29,7 +29,7 @@ def test_fused_step_matches_unfused_sequence(capi, oracle):
     n = tr.total_cap
     p0 = tr.params.clone()
     map0 = capi.ids_from_map(tr.maps[0])
-    t_pass = int(tr.iter[1].item())
+    t_pass = int(tr.iter[1].item()) + tr.images[0]["pass_offset"]
     seed = tr.images[0]["seed"]
     grads_fused = torch.empty_like(tr.params)
     capi.sad_train_step(tr.table, 8, 2, tr.params, tr.m, tr.v, tr.prep, tr.maps[0], tr.maps[1],
@@ -69,7 +69,7 @@ def test_batch_results_do_not_depend_on_the_batch(capi):
     tr = BatchTrainer(imgs, cfg)
     tr.run(12)
     for b, img in enumerate(imgs):
-        solo = BatchTrainer([img], cfg, seeds=[tr.images[b]["seed"]])
+        solo = BatchTrainer([img], cfg, seeds=[tr.images[b]["user_seed"]])
         solo.run(12)
         lo, n = tr.images[b]["site_offset"], tr.images[b]["capacity"]
         assert torch.equal(tr.params[:, lo:lo + n], solo.params[:, :n]), b
@@ -88,7 +88,7 @@ def test_graph_replay_equals_eager(capi):
     torch.cuda.synchronize()
     assert torch.equal(a.params, b.params)
     assert torch.equal(a.maps[0], b.maps[0])
-    assert int(b.iter[0].item()) == 11 and int(b.iter[1].item()) == 1034
+    assert int(b.iter[0].item()) == 11 and int(b.iter[1].item()) == 10
 
 
 def test_batch_training_improves_psnr(capi):
@@ -101,3 +101,60 @@ def test_batch_training_improves_psnr(capi):
     p1 = tr.psnr()
     print("PSNR", p0, "->", p1)
     assert all(b > a + 3.0 for a, b in zip(p0, p1))
+
+
+def test_iteration_offsets_shift_the_counters(capi):
+    """An image whose Adam step / pass index are given by offsets from a later
+    global counter trains exactly as one started at the counter's origin
+    (images can join a running batch)."""
+    torch = pytest.importorskip("torch")
+    from paper_2604_21984_gb300.batch import BatchConfig, BatchTrainer
+    imgs = _images([(48, 64), (40, 40)], 41)
+    cfg = BatchConfig(K=8, J=3, graph=False, seed=9)
+    a = BatchTrainer(imgs, cfg)
+    b = BatchTrainer(imgs, cfg)
+    for im in b.images:
+        im["t_offset"] = -37
+        im["pass_offset"] -= 501
+    b.table = capi.batch_table(b.images)
+    b.iter.copy_(torch.tensor([1 + 37, 501], dtype=torch.int32))
+    a.run(7)
+    b.run(7)
+    assert torch.equal(a.params, b.params)
+    assert torch.equal(a.maps[0], b.maps[0])
+
+
+def test_decode_batch_matches_per_image_decode(capi):
+    torch = pytest.importorskip("torch")
+    from paper_2604_21984_gb300.batch import BatchConfig, BatchTrainer
+    sizes = [(40, 72), (64, 48), (17, 29)]
+    imgs = _images(sizes, 51)
+    tr = BatchTrainer(imgs, BatchConfig(K=16, J=4, graph=False, seed=4))
+    tr.run(6)
+    rng = np.random.default_rng(3)
+    n = 5000
+    qimg = rng.integers(0, len(sizes), n).astype(np.int32)
+    xy = np.empty((n, 2), np.float32)
+    for b, (H, W) in enumerate(sizes):
+        sel = qimg == b
+        # include points slightly outside the image (clamped map cell)
+        xy[sel, 0] = rng.uniform(-1.0, W + 1.0, sel.sum())
+        xy[sel, 1] = rng.uniform(-1.0, H + 1.0, sel.sum())
+    qimg[:7] = [-1, 3, 99, 0, 1, 2, 0]
+    xy_d, q_d = torch.from_numpy(xy).cuda(), torch.from_numpy(qimg).cuda()
+    out = torch.empty((n, 3), device="cuda")
+    capi.sad_decode_batch(tr.table, 16, tr.prep, tr.total_cap, tr.maps[0], tr.total_pixels, xy_d, q_d, out)
+    got = out.cpu().numpy()
+    for b, (H, W) in enumerate(sizes):
+        im = tr.images[b]
+        lo, cap = im["site_offset"], im["capacity"]
+        p = tr.params[:, lo:lo + cap].contiguous()
+        prep = capi.empty_prep(cap)
+        capi.sad_prepare_sites(p, H, W, prep)
+        mp = capi.map_from_ids(tr.map_for(b))
+        sel = np.nonzero(qimg == b)[0]
+        ref = torch.empty((len(sel), 3), device="cuda")
+        capi.sad_decode_points(prep, cap, H, W, 16, mp, xy_d[sel].contiguous(), ref)
+        np.testing.assert_allclose(got[sel], ref.cpu().numpy(), rtol=0, atol=1e-6)
+    bad = (qimg < 0) | (qimg >= len(sizes))
+    assert np.all(got[bad] == 0.0)

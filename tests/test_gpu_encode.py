@@ -14,13 +14,16 @@ def capi():
     return require_gpu()
 
 
-def test_one_iteration_matches_oracle(capi, oracle):
-    """prepare -> pass (jump 1) -> fused MSE gradient -> Adam, GPU vs oracle."""
+@pytest.mark.parametrize("fused", [False, True])
+def test_one_iteration_matches_oracle(capi, oracle, fused):
+    """prepare -> pass (jump 1) -> MSE gradient -> Adam, GPU vs oracle, as
+    separate calls and as the fused step."""
     torch = pytest.importorskip("torch")
     from paper_2604_21984_gb300.encode import EncodeConfig, Encoder, jump_code
     H, W = 48, 64
     img = gen.image_noise_polygons_lines(H, W, seed=41, n_polygons=5, n_lines=3)
-    enc = Encoder(dev(img), EncodeConfig(n_sites=300, K=8, J=2, iters=1, seed=5))
+    enc = Encoder(dev(img), EncodeConfig(n_sites=300, K=8, J=2, iters=1, seed=5, fused=fused,
+                                         keep_grads=True))
     enc.init()
     p0 = enc.params.cpu().numpy().copy()
     ids0 = capi.ids_from_map(enc.maps[0])
