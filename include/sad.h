@@ -326,6 +326,8 @@ typedef struct sad_batch_image {
   uint64_t seed;         /* injection seed of the image */
   int32_t t_offset;      /* the image's Adam step is iter[0] + t_offset */
   int32_t pass_offset;   /* the image's pass index is iter[1] + pass_offset */
+  int32_t swap_maps;     /* sad_train_step: 0 = read map_in, write map_out; else the reverse */
+  int32_t reserved;      /* must be 0 */
 } sad_batch_image;
 
 /* Workspace bytes of sad_train_step (0 = invalid table); same record rule as
@@ -357,7 +359,10 @@ int sad_prepare_batch(const sad_batch_image* images, int32_t B, const float* par
  * before the step (may be NULL).  iter: device int32[2] {t, pass}, both
  * incremented by the call, so the call sequence can be captured once in a
  * CUDA graph and replayed.  grads_out: optional float32[11][total_capacity].
- * map_in and map_out must not overlap; swap them between calls.  Each image's
+ * map_in and map_out must not overlap; swap them between calls.  An image
+ * whose swap_maps is set reads map_out and writes map_in instead, so images
+ * that skipped calls (a scheduler choosing which images step) keep their
+ * current map wherever it is.  Each image's
  * results are independent of the other images in the batch.  Only the
  * images' slot and pixel ranges are read or written (besides the workspace),
  * so images can join or leave between calls (continuous batching); images
@@ -365,7 +370,7 @@ int sad_prepare_batch(const sad_batch_image* images, int32_t B, const float* par
  */
 int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t J, float* params,
                    float* m, float* v, float* prep, int32_t total_capacity,
-                   const uint32_t* map_in, uint32_t* map_out, int64_t total_pixels,
+                   uint32_t* map_in, uint32_t* map_out, int64_t total_pixels,
                    const float* targets, float* loss, const sad_adam_hparams* hp, int32_t* iter,
                    float* grads_out, void* workspace, size_t workspace_bytes, void* stream);
 

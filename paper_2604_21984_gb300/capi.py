@@ -46,7 +46,8 @@ class DpParams(ctypes.Structure):
 class BatchImage(ctypes.Structure):
     _fields_ = [("H", ctypes.c_int32), ("W", ctypes.c_int32), ("site_offset", ctypes.c_int32),
                 ("capacity", ctypes.c_int32), ("pixel_offset", ctypes.c_int64),
-                ("seed", ctypes.c_uint64), ("t_offset", ctypes.c_int32), ("pass_offset", ctypes.c_int32)]
+                ("seed", ctypes.c_uint64), ("t_offset", ctypes.c_int32), ("pass_offset", ctypes.c_int32),
+                ("swap_maps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class TraceEntry(ctypes.Structure):
@@ -420,6 +421,7 @@ def batch_table(images):
         arr[i].site_offset, arr[i].capacity = d["site_offset"], d["capacity"]
         arr[i].pixel_offset, arr[i].seed = d["pixel_offset"], d["seed"] & ((1 << 64) - 1)
         arr[i].t_offset, arr[i].pass_offset = d.get("t_offset", 0), d.get("pass_offset", 0)
+        arr[i].swap_maps = 1 if d.get("swap_maps", 0) else 0
     return arr
 
 

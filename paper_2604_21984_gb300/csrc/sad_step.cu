@@ -37,6 +37,7 @@ struct BatchImg {
   float s, two_over_P;
   int32_t t_off, pass_off;
   uint32_t site_cum;  // sites of the images before this one
+  int32_t swap;       // read map_out / write map_in
 };
 
 struct BatchDesc {
@@ -70,11 +71,13 @@ __device__ __forceinline__ int image_of_slot(const BatchDesc& d, uint32_t j) {
 
 template <int K>
 __global__ void __launch_bounds__(kTileThreads, 3)
-    k_step_tile(const BatchDesc d, TileIO io, const uint4* __restrict__ map_in,
-                uint4* __restrict__ map_out, size_t Ptot, int J, const int32_t* __restrict__ iter) {
+    k_step_tile(const BatchDesc d, TileIO io, uint4* map_a, uint4* map_b, size_t Ptot, int J,
+                const int32_t* __restrict__ iter) {
   __shared__ uint32_t s_q[kQueue][kTileThreads];
   const int b = image_of_tile(d, blockIdx.x);
   const BatchImg im = d.img[b];
+  const uint4* map_in = im.swap ? map_b : map_a;
+  uint4* map_out = im.swap ? map_a : map_b;
   const uint32_t lt = blockIdx.x - im.tile_off;
   TileCtx c;
   c.H = im.H;
@@ -336,6 +339,8 @@ static int make_desc(const sad_batch_image* images, int32_t B, int32_t total_cap
     o.t_off = im.t_offset;
     o.pass_off = im.pass_offset;
     o.site_cum = sites;
+    o.swap = im.swap_maps != 0;
+    if (im.reserved != 0) return einval("%s: image %d reserved field must be 0", name, b);
     sites += o.site_n;
     tiles += o.tiles_x * static_cast<uint32_t>((im.H + kTileSide - 1) / kTileSide);
   }
@@ -384,7 +389,7 @@ int sad_prepare_batch(const sad_batch_image* images, int32_t B, const float* par
 
 int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t J, float* params,
                    float* m, float* v, float* prep, int32_t total_capacity,
-                   const uint32_t* map_in, uint32_t* map_out, int64_t total_pixels,
+                   uint32_t* map_in, uint32_t* map_out, int64_t total_pixels,
                    const float* targets, float* loss, const sad_adam_hparams* hp, int32_t* iter,
                    float* grads_out, void* workspace, size_t workspace_bytes, void* stream) {
   BatchDesc d;
@@ -447,7 +452,7 @@ int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t 
   io.records = rec;
   io.max_records = L.max_records;
   io.hdr = hdr;
-  const uint4* mi = reinterpret_cast<const uint4*>(map_in);
+  uint4* mi = reinterpret_cast<uint4*>(map_in);
   uint4* mo = reinterpret_cast<uint4*>(map_out);
   const size_t Ptot = static_cast<size_t>(total_pixels);
   switch (K) {

@@ -43,6 +43,7 @@ class ServeConfig:
     pixel_pool: int = 1 << 26
     max_side: int = 4096           # largest encode accepted
     max_decode_per_tick: int = 1 << 22
+    pixels_per_call: int = 1 << 21    # encodes joined per step, shortest remaining work first
     lr: tuple = (1e-3, 1e-3, 1e-2, 1e-3, 5e-3, 5e-3, 5e-3, 1e-2, 1e-2, 1e-2, 0.0)
 
 
@@ -160,6 +161,7 @@ class Server:
         self.decodes = []       # decodes waiting for the next tick
         self.residents = []     # resident decode site sets: table entries
         self.launches = 0
+        self._seq = 0
 
     # -- pools ---------------------------------------------------------------
     def _workspace(self):
@@ -256,11 +258,11 @@ class Server:
             self.waiting.pop(0)
             # injection seed and pass indices as in a solo encode: seed + 0x5AD,
             # passes numbered on from the warm-up's; Adam step 1 first
-            entry = dict(H=H, W=W, site_offset=lo, capacity=n, pixel_offset=po, seed=req.seed + 0x5AD,
-                         t_offset=1 - self.iter_host[0], pass_offset=0)
+            entry = dict(H=H, W=W, site_offset=lo, capacity=n, pixel_offset=po, seed=req.seed + 0x5AD)
             n_pass = self._warm_start(req, entry)
-            entry["pass_offset"] = n_pass - self.iter_host[1]
-            self.active.append(dict(entry=entry, req=req, left=req.iters))
+            self._seq += 1
+            self.active.append(dict(entry=entry, req=req, left=req.iters, done=0, n_pass=n_pass,
+                                    parity=0, P=H * W, seq=self._seq))
             admitted.append(entry)
         if admitted:
             capi.sad_prepare_batch(capi.batch_table(admitted), self.params, self.prep,
@@ -285,31 +287,49 @@ class Server:
         return n_pass
 
     def train_tick(self, max_iters: int = 1) -> int:
-        """Admit what fits, then T = min(max_iters, fewest iterations left)
-        fused iterations of every admitted encode (so encodes finish only at
-        the end of a tick); finished encodes hand back their sites and leave.
-        Returns T."""
+        """Admit what fits, pick the encodes to step, run T fused iterations
+        of them and retire the finished ones.  Returns T (0 if idle).
+
+        Selection: shortest remaining work (iterations left x pixels) first,
+        until `pixels_per_call` pixels are in the batch (at most 64 images),
+        so small encodes are batched together and are not held to the pace of
+        a large one; T = min(max_iters, fewest iterations left among them).
+        Each image's Adam step, pass index and map buffer come from its own
+        progress (the counter offsets and the swap flag of its table entry),
+        so skipping calls does not change its trajectory."""
         with torch.cuda.stream(self.stream):
             self._admit()
             if not self.active:
                 return 0
             c = self.cfg
-            T = max(1, min(max_iters, min(a["left"] for a in self.active)))
-            self.active.sort(key=lambda a: a["entry"]["site_offset"])
-            table = capi.batch_table([a["entry"] for a in self.active])
+            order = sorted(self.active, key=lambda a: (a["left"] * a["P"], a["seq"]))
+            sel, tot = [], 0
+            for a in order[:64]:
+                sel.append(a)
+                tot += a["P"]
+                if tot >= c.pixels_per_call:
+                    break
+            sel.sort(key=lambda a: a["entry"]["site_offset"])
+            T = max(1, min(max_iters, min(a["left"] for a in sel)))
             for _ in range(T):
-                capi.sad_train_step(table, c.K, c.J, self.params, self.m, self.v, self.prep, self.maps[0],
-                                    self.maps[1], c.pixel_pool, self.targets, self.loss, self.hp,
-                                    self.iter, self.ws, stream=self.stream)
-                self.maps.reverse()
+                for a in sel:
+                    e = a["entry"]
+                    e["t_offset"] = a["done"] + 1 - self.iter_host[0]
+                    e["pass_offset"] = a["n_pass"] + a["done"] - self.iter_host[1]
+                    e["swap_maps"] = a["parity"]
+                capi.sad_train_step(capi.batch_table([a["entry"] for a in sel]), c.K, c.J, self.params,
+                                    self.m, self.v, self.prep, self.maps[0], self.maps[1], c.pixel_pool,
+                                    self.targets, self.loss, self.hp, self.iter, self.ws,
+                                    stream=self.stream)
+                self.iter_host[0] += 1
+                self.iter_host[1] += 1
+                for a in sel:
+                    a["done"] += 1
+                    a["left"] -= 1
+                    a["parity"] ^= 1
             self.launches += 4 * T
-            self.iter_host[0] += T
-            self.iter_host[1] += T
-            still = []
-            for b, a in enumerate(self.active):
-                a["left"] -= T
+            for b, a in enumerate(sel):
                 if a["left"] > 0:
-                    still.append(a)
                     continue
                 e, req = a["entry"], a["req"]
                 lo, n = e["site_offset"], e["capacity"]
@@ -320,7 +340,7 @@ class Server:
                 req.done_event = ev
                 self.sites.release(lo, n)
                 self.pixels.release(e["pixel_offset"], e["H"] * e["W"])
-            self.active = still
+            self.active = [a for a in self.active if a["left"] > 0]
             return T
 
     def decode_tick(self):

@@ -19,17 +19,21 @@ def _img(H, W, seed):
     return dev(gen.image_noise_polygons_lines(H, W, seed=seed, n_polygons=5, n_lines=2))
 
 
-def _small_cfg():
+def _small_cfg(**kw):
     from paper_2604_21984_gb300.serve import ServeConfig
     return ServeConfig(K=16, J=4, site_pool=40000, pixel_pool=1 << 18, max_side=256,
-                       max_decode_per_tick=1 << 16)
+                       max_decode_per_tick=1 << 16, **kw)
 
 
-def test_encode_in_a_mix_equals_encode_alone(capi):
+@pytest.mark.parametrize("pixels_per_call", [1 << 21, 1])
+def test_encode_in_a_mix_equals_encode_alone(capi, pixels_per_call):
+    """pixels_per_call=1 steps only the encode with the least remaining work
+    in each call, so the others skip calls (their own counters and map
+    buffer carry their state)."""
     torch = pytest.importorskip("torch")
     from paper_2604_21984_gb300.batch import BatchConfig, BatchTrainer
     from paper_2604_21984_gb300.serve import Request, Server
-    srv = Server(_small_cfg())
+    srv = Server(_small_cfg(pixels_per_call=pixels_per_call))
     specs = [((48, 64), 11, 9), ((80, 40), 12, 14), ((33, 57), 13, 6), ((64, 64), 14, 10)]
     reqs = [Request("encode", image=_img(H, W, sd), iters=it, seed=1000 + sd) for (H, W), sd, it in specs]
     # staggered joins: 0 at tick 0, 1 at tick 2, 2 and 3 at tick 5
