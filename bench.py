@@ -151,6 +151,23 @@ def gen_images(specs):
         return list(ex.map(_gen_image, specs))
 
 
+def reduce_max(x, dist, world, device):
+    """Max over ranks of a host float (the slowest replica's time)."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, units_per_rank, steps, seconds):
+    """Whole-job throughput in millions of units per second: every rank
+    processes its own units each step (weak scaling), the job takes as long
+    as the slowest rank."""
+    return world * units_per_rank * steps / seconds / 1e6
+
+
 def dominant(trace):
     name = max(trace, key=lambda k: trace[k][1])
     n, ms = trace[name]
@@ -219,12 +236,8 @@ def run_ours(args):
     ck = clocks.stop()
     trace = capi.sad_trace_collect()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(step_ms)
-    if world > 1:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = world * P * args.steps / (total_ms / 1e3) / 1e6
+    total_ms = reduce_max(sum(step_ms), dist, world, dev)
+    value = whole_job_value(world, P, args.steps, total_ms / 1e3)
 
     # the same iteration as four separate calls (context for the fusion)
     enc_u = Encoder(target, EncodeConfig(n_sites=N, K=K, J=J, seed=rank, densify_every=0, fused=False))
@@ -256,11 +269,8 @@ def run_ours(args):
         host_loss.copy_(enc.loss, non_blocking=True)
         torch.cuda.synchronize()
         e2e_s += time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e = {"value": round(world * P * args.steps / e2e_s / 1e6, 3), "unit": UNIT,
+    e2e_s = reduce_max(e2e_s, dist, world, dev)
+    e2e = {"value": round(whole_job_value(world, P, args.steps, e2e_s), 3), "unit": UNIT,
            "h2d_bytes_per_step": int(host_img.numel() * 4), "d2h_bytes_per_step": 4}
 
     # roofline of the dominant kernel, from its own event pairs in the timed
