@@ -486,7 +486,7 @@ def c4_leg(capi, dev, peak, peak_kind, args, n_images=64, seed=4000):
     }
 
 
-def c5_leg(capi, dev, peak, peak_kind, args, seed=5000):
+def c5_leg(capi, dev, peak, peak_kind, args, seed=5000, details=False):
     """Poisson stream served with continuous batching vs the plain FIFO loop."""
     import numpy as np
     import torch
@@ -516,7 +516,9 @@ def c5_leg(capi, dev, peak, peak_kind, args, seed=5000):
             else:
                 H, W = res[r["resident"]][0], res[r["resident"]][1]
                 xy = torch.from_numpy(gen.uniform_points(r["n"], H, W, r["seed"])).pin_memory()
-                out.append(Request("decode", arrival=r["arrival"], resident=r["resident"], xy=xy))
+                res_buf = torch.empty((r["n"], 3), dtype=torch.float32, pin_memory=True)
+                out.append(Request("decode", arrival=r["arrival"], resident=r["resident"], xy=xy,
+                                   out=res_buf))
         return out
 
     # plain capacity from a calibration stream (all at t=0, FIFO)
@@ -549,6 +551,10 @@ def c5_leg(capi, dev, peak, peak_kind, args, seed=5000):
         for k in ("encode", "decode"):
             if k in s:
                 s[k] = {kk: (round(v, 5) if isinstance(v, float) else v) for kk, v in s[k].items()}
+        if details:
+            s["requests"] = [(r.kind, round(r.arrival, 4), round(r.latency, 4),
+                              int(r.image.shape[0] * r.image.shape[1]) if r.kind == "encode"
+                              else int(r.xy.shape[0])) for r in reqs]
         out[name] = s
         del reqs
     return out

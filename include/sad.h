@@ -324,9 +324,7 @@ typedef struct sad_batch_image {
   int32_t capacity;      /* number of site slots of the image */
   int64_t pixel_offset;  /* first pixel of the image in the packed arrays */
   uint64_t seed;         /* injection seed of the image */
-  int32_t t_offset;      /* the image's Adam step is iter[0] + t_offset */
-  int32_t pass_offset;   /* the image's pass index is iter[1] + pass_offset */
-  int32_t swap_maps;     /* sad_train_step: 0 = read map_in, write map_out; else the reverse */
+  int32_t state_index;   /* sad_train_step: the image's row of image_state */
   int32_t reserved;      /* must be 0 */
 } sad_batch_image;
 
@@ -349,30 +347,34 @@ int sad_prepare_batch(const sad_batch_image* images, int32_t B, const float* par
  * sad_train_step -- one fused training iteration of every image of a batch
  * (Sec. 5: no host work inside an iteration).  Per 16x16 tile: one
  * propagation pass at jump 1 (sad_update_topk semantics with the image's own
- * site range and seed; pass index = iter[1] + pass_offset) writing map_out,
- * then, on those
- * lists, the fused render + MSE + adjoint of sad_train_grads; per site: the
- * gradient, an Adam step (t = iter[0] + t_offset; sad_adam_step semantics with the
- * image's H, W) and the prepared table of the new parameters, so `prep` must
- * hold the prepared table of `params` on entry (sad_prepare_batch) and holds
- * it again on exit.  loss: device float32[B], the mean loss of each image
- * before the step (may be NULL).  iter: device int32[2] {t, pass}, both
- * incremented by the call, so the call sequence can be captured once in a
- * CUDA graph and replayed.  grads_out: optional float32[11][total_capacity].
- * map_in and map_out must not overlap; swap them between calls.  An image
- * whose swap_maps is set reads map_out and writes map_in instead, so images
- * that skipped calls (a scheduler choosing which images step) keep their
- * current map wherever it is.  Each image's
- * results are independent of the other images in the batch.  Only the
- * images' slot and pixel ranges are read or written (besides the workspace),
- * so images can join or leave between calls (continuous batching); images
- * must not share pixels (SAD_EINVAL).
+ * site range and seed) writing the image's next map, then, on those lists,
+ * the fused render + MSE + adjoint of sad_train_grads; per site: the
+ * gradient, an Adam step (sad_adam_step semantics with the image's H, W) and
+ * the prepared table of the new parameters, so `prep` must hold the
+ * prepared table of `params` on entry (sad_prepare_batch) and holds it again
+ * on exit.
+ * image_state: device int32[n_states][4]; image b uses row
+ * images[b].state_index (distinct rows) = {t, pass, parity, 0}: t is the
+ * Adam step (1-based), pass the pass index of the propagation (step code
+ * (1 << 16) | (pass & 0xffff)), parity 0 = its current map is in map_in
+ * (then it writes map_out), 1 = the reverse.  The call advances the rows of
+ * the images it steps (t + 1, pass + 1, parity ^ 1), so a fixed batch always
+ * makes the same call (capture it once in a CUDA graph and replay it), and
+ * an image left out of some calls keeps its own counters and map.
+ * loss: device float32[B], the mean loss of each image before the step (may
+ * be NULL).  grads_out: optional float32[11][total_capacity].  map_in and
+ * map_out must not overlap.  Each image's results are independent of the
+ * other images in the batch.  Only the images' slot and pixel ranges and
+ * state rows are read or written (besides the workspace), so images can
+ * join or leave between calls (continuous batching); images must not share
+ * pixels (SAD_EINVAL).
  */
 int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t J, float* params,
                    float* m, float* v, float* prep, int32_t total_capacity,
                    uint32_t* map_in, uint32_t* map_out, int64_t total_pixels,
-                   const float* targets, float* loss, const sad_adam_hparams* hp, int32_t* iter,
-                   float* grads_out, void* workspace, size_t workspace_bytes, void* stream);
+                   const float* targets, float* loss, const sad_adam_hparams* hp,
+                   int32_t* image_state, int32_t n_states, float* grads_out, void* workspace,
+                   size_t workspace_bytes, void* stream);
 
 /*
  * sad_batch_insert -- place one image, prepared with the single-image calls

@@ -7,10 +7,12 @@ packed targets ``[total_pixels, 3]`` and top-K map planes
 single-image calls (gradient-weighted init, JFA warm-up), copied into its
 ranges (``sad_batch_insert``), and then every training iteration of the whole batch is one
 ``sad_train_step`` call (fused propagation + render + MSE + adjoint per tile,
-exact per-site sums, Adam + prepare per site).  The iteration counter lives on
-the device, so two iterations (the map ping-pong) are captured once in a CUDA
-graph and replayed.  An image's trajectory does not depend on the rest of the
-batch (own site range, seed and fixed-point scale).
+exact per-site sums, Adam + prepare per site).  Each image's counters (Adam
+step, pass index, current map buffer) live in a device state row advanced by
+the step, so one iteration is captured once in a CUDA graph and replayed.
+An image's trajectory does not depend on the rest of the batch (own site
+range, seed, state row and fixed-point scale) and equals the single-image
+encoder's (same seeds, same pass numbering).
 """
 from __future__ import annotations
 
@@ -65,14 +67,23 @@ class BatchTrainer:
         self.prep = capi.empty_prep(site, self.dev)
         self.targets = torch.empty((pix, 3), **f32)
         K = c.K
-        self.maps = [torch.empty((K // 4, pix, 4), dtype=torch.int32, device=self.dev) for _ in range(2)]
+        self.bufs = [torch.empty((K // 4, pix, 4), dtype=torch.int32, device=self.dev) for _ in range(2)]
         self.loss = torch.zeros(len(targets), **f32)
-        self.iter = torch.zeros(2, dtype=torch.int32, device=self.dev)
+        self.state = torch.zeros((len(targets), 4), dtype=torch.int32, device=self.dev)
         self.hp = capi.adam_hparams(lr=c.lr)
         self.ws = capi.step_workspace(self.table, K, site, pix, device=self.dev)
         self.graph = None
         self.steps = 0
         self._init(targets)
+        self._call = capi.TrainStepCall(self.table, c.K, c.J, self.params, self.m, self.v, self.prep,
+                                        self.bufs[0], self.bufs[1], self.total_pixels, self.targets,
+                                        self.loss, self.hp, self.state, self.ws)
+
+    @property
+    def maps(self):
+        """[current map buffer, other] (every image steps every call, so all
+        share the parity of the step count)."""
+        return [self.bufs[self.steps & 1], self.bufs[1 - (self.steps & 1)]]
 
     def _init(self, targets):
         c = self.cfg
@@ -84,50 +95,45 @@ class BatchTrainer:
             enc.init()
             # training pass indices continue after the image's warm-up passes,
             # as in the single-image encoder
-            im["pass_offset"] = enc.t_pass
+            im["state_index"] = b
+            im["n_pass"] = enc.t_pass
             capi.sad_batch_insert(capi.batch_table([im]), c.K, enc.params, enc.maps[0], t.contiguous(),
-                                  self.params, self.m, self.v, self.maps[0], self.targets,
+                                  self.params, self.m, self.v, self.bufs[0], self.targets,
                                   self.total_pixels)
             del enc
         self.table = capi.batch_table(self.images)
         capi.sad_prepare_batch(self.table, self.params, self.prep, self.total_pixels)
-        # Adam step 1; pass index = iter[1] + the image's warm-up pass count
-        self.iter.copy_(torch.tensor([1, 0], dtype=torch.int32))
+        # state rows: Adam step 1, passes numbered on from the warm-up's, map in bufs[0]
+        self.state.copy_(torch.tensor([[1, im["n_pass"], 0, 0] for im in self.images], dtype=torch.int32))
 
     def _step(self):
-        capi.sad_train_step(self.table, self.cfg.K, self.cfg.J, self.params, self.m, self.v, self.prep,
-                            self.maps[0], self.maps[1], self.total_pixels, self.targets, self.loss,
-                            self.hp, self.iter, self.ws)
-        self.maps.reverse()
+        self._call()
+        self.steps += 1
 
     def _capture(self):
-        """Two iterations (A -> B, B -> A) in one CUDA graph."""
+        """One iteration in a CUDA graph (the call never changes: the state
+        rows on the device carry the counters and the map parity)."""
         s = torch.cuda.Stream(device=self.dev)
         s.wait_stream(torch.cuda.current_stream(self.dev))
         g = torch.cuda.CUDAGraph()
         with torch.cuda.stream(s):
-            # capture records the calls without running them
+            # capture records the call without running it
             with torch.cuda.graph(g, stream=s):
-                self._step()
-                self._step()
+                self._call(s)
         torch.cuda.current_stream(self.dev).wait_stream(s)
         self.graph = g
 
     def run(self, iters: int):
         """`iters` training iterations of every image (graph replays when on)."""
-        if self.cfg.graph and iters >= 2:
+        if self.cfg.graph and iters >= 1:
             if self.graph is None:
                 self._capture()
-            for _ in range(iters // 2):
+            for _ in range(iters):
                 self.graph.replay()
-            self.steps += 2 * (iters // 2)
-            if iters % 2:
-                self._step()
-                self.steps += 1
+            self.steps += iters
         else:
             for _ in range(iters):
                 self._step()
-                self.steps += 1
         return self
 
     def map_for(self, b):

@@ -46,8 +46,7 @@ class DpParams(ctypes.Structure):
 class BatchImage(ctypes.Structure):
     _fields_ = [("H", ctypes.c_int32), ("W", ctypes.c_int32), ("site_offset", ctypes.c_int32),
                 ("capacity", ctypes.c_int32), ("pixel_offset", ctypes.c_int64),
-                ("seed", ctypes.c_uint64), ("t_offset", ctypes.c_int32), ("pass_offset", ctypes.c_int32),
-                ("swap_maps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("seed", ctypes.c_uint64), ("state_index", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class TraceEntry(ctypes.Structure):
@@ -127,8 +126,8 @@ _SIGS = {
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(AdamHparams),
-                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
-                                      ctypes.c_void_p]),
+                                      ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_size_t, ctypes.c_void_p]),
     "sad_batch_insert": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
@@ -420,8 +419,7 @@ def batch_table(images):
         arr[i].H, arr[i].W = d["H"], d["W"]
         arr[i].site_offset, arr[i].capacity = d["site_offset"], d["capacity"]
         arr[i].pixel_offset, arr[i].seed = d["pixel_offset"], d["seed"] & ((1 << 64) - 1)
-        arr[i].t_offset, arr[i].pass_offset = d.get("t_offset", 0), d.get("pass_offset", 0)
-        arr[i].swap_maps = 1 if d.get("swap_maps", 0) else 0
+        arr[i].state_index = d.get("state_index", i)
     return arr
 
 
@@ -444,7 +442,8 @@ def sad_prepare_batch(table, params, prep, total_pixels, stream=None):
 
 
 def sad_train_step(table, K, J, params, m, v, prep, map_in, map_out, total_pixels, targets, loss,
-                   hp, iter_dev, ws, grads_out=None, stream=None):
+                   hp, state, ws, grads_out=None, stream=None):
+    """state: device int32[n_states, 4] per-image rows {t, pass, parity, 0}."""
     cap = params.shape[1]
     n = N_PARAMS * cap
     _check(lib().sad_train_step(ctypes.cast(table, ctypes.c_void_p), len(table), K, J,
@@ -455,10 +454,38 @@ def sad_train_step(table, K, J, params, m, v, prep, map_in, map_out, total_pixel
                                 _ptr(targets, torch.float32, "targets", total_pixels * 3),
                                 _ptr(loss[:len(table)] if loss is not None else None, torch.float32,
                                      "loss", len(table)), ctypes.byref(hp),
-                                _ptr(iter_dev, torch.int32, "iter", 2),
+                                _ptr(state, torch.int32, "state"), state.shape[0],
                                 _ptr(grads_out, torch.float32, "grads_out", n),
                                 _ptr(ws, torch.uint8, "workspace"), ws.numel(), _stream(stream)),
            "sad_train_step")
+
+
+class TrainStepCall:
+    """A prepared sad_train_step: the arguments are marshalled once, so a
+    call (eager or while being captured into a graph) is one ctypes call."""
+
+    def __init__(self, table, K, J, params, m, v, prep, map_in, map_out, total_pixels, targets, loss,
+                 hp, state, ws, grads_out=None):
+        cap = params.shape[1]
+        n = N_PARAMS * cap
+        self.table = table
+        self.hp = hp
+        self.keep = (params, m, v, prep, map_in, map_out, targets, loss, state, ws, grads_out)
+        self.args = [ctypes.cast(table, ctypes.c_void_p), len(table), K, J,
+                     _ptr(params, torch.float32, "params", n), _ptr(m, torch.float32, "m", n),
+                     _ptr(v, torch.float32, "v", n), _ptr(prep, torch.float32, "prep"), cap,
+                     _ptr(map_in, torch.int32, "map_in", total_pixels * K),
+                     _ptr(map_out, torch.int32, "map_out", total_pixels * K), total_pixels,
+                     _ptr(targets, torch.float32, "targets", total_pixels * 3),
+                     _ptr(loss[:len(table)] if loss is not None else None, torch.float32, "loss",
+                          len(table)), ctypes.byref(hp),
+                     _ptr(state, torch.int32, "state"), state.shape[0],
+                     _ptr(grads_out, torch.float32, "grads_out", n),
+                     _ptr(ws, torch.uint8, "workspace"), ws.numel()]
+        self.fn = lib().sad_train_step
+
+    def __call__(self, stream=None):
+        _check(self.fn(*self.args, _stream(stream)), "sad_train_step")
 
 
 def sad_decode_batch(table, K, prep, total_cap, map_in, total_pixels, xy, qimg, rgb, stream=None):

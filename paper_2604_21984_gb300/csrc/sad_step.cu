@@ -1,9 +1,11 @@
 // Fused, batched training step (the paper's GPU-resident iteration, Sec. 5;
 // Sec. 6.3 epoch = one pass over all pixels) over up to kMaxImages images.
 //
-// One iteration is four kernels and one small memset, all on one stream, with the
-// iteration counter in device memory so the whole sequence can be captured
-// once in a CUDA graph and replayed:
+// One iteration is four kernels and one small memset, all on one stream.  Each
+// image's counters (Adam step, pass index, which map buffer is current) live
+// in a device state row that the step itself advances, so a fixed set of
+// images always makes the same call, which is captured once in a CUDA graph
+// and replayed:
 //  1. k_step_tile, one block per 16x16 tile of any image: the tile's pixels
 //     run one propagation pass at jump 1 (Sec. 4.3; reads the neighbours' old
 //     lists, writes the new ones), then - on the lists just computed, still in
@@ -13,8 +15,8 @@
 //  3. k_site_step, one thread per site: the chain rule to the 11 gradients,
 //     Adam with the paper's clamps (Sec. 6.1), and the prepared table of the
 //     updated site for the next iteration;
-//  4. k_step_finish: the per-image mean loss (fixed-order sums) and the
-//     iteration counters advance.
+//  4. k_step_finish: the per-image mean loss (fixed-order sums) and each
+//     image's state row advances.
 // Each image uses its own site range, pixel range, injection seed and
 // fixed-point scale, so an image's result does not depend on the rest of the
 // batch.
@@ -35,10 +37,11 @@ struct BatchImg {
   uint32_t tile_off, tiles_x;
   uint64_t seed;
   float s, two_over_P;
-  int32_t t_off, pass_off;
+  int32_t state;      // row of the image in the per-image state array
   uint32_t site_cum;  // sites of the images before this one
-  int32_t swap;       // read map_out / write map_in
 };
+
+constexpr int kStateWords = 4;  // per image: {Adam step t, pass index, map parity, reserved}
 
 struct BatchDesc {
   int32_t B;
@@ -72,12 +75,14 @@ __device__ __forceinline__ int image_of_slot(const BatchDesc& d, uint32_t j) {
 template <int K>
 __global__ void __launch_bounds__(kTileThreads, 3)
     k_step_tile(const BatchDesc d, TileIO io, uint4* map_a, uint4* map_b, size_t Ptot, int J,
-                const int32_t* __restrict__ iter) {
+                const int32_t* __restrict__ state) {
   __shared__ uint32_t s_q[kQueue][kTileThreads];
   const int b = image_of_tile(d, blockIdx.x);
   const BatchImg im = d.img[b];
-  const uint4* map_in = im.swap ? map_b : map_a;
-  uint4* map_out = im.swap ? map_a : map_b;
+  const int32_t* st = state + kStateWords * im.state;
+  const bool swap = st[2] & 1;
+  const uint4* map_in = swap ? map_b : map_a;
+  uint4* map_out = swap ? map_a : map_b;
   const uint32_t lt = blockIdx.x - im.tile_off;
   TileCtx c;
   c.H = im.H;
@@ -92,7 +97,7 @@ __global__ void __launch_bounds__(kTileThreads, 3)
   const int t = threadIdx.x;
   const int x = c.x0 + (t & (kTileSide - 1)), y = c.y0 + (t >> 4);
   const bool inimg = x < c.W && y < c.H;
-  const uint32_t code = (1u << 16) | (static_cast<uint32_t>(iter[1] + im.pass_off) & 0xffffu);
+  const uint32_t code = (1u << 16) | (static_cast<uint32_t>(st[1]) & 0xffffu);
   uint64_t v[K];
   pixel_update<K, kTileThreads, 2>(v, inimg, x, y, c.H, c.W, c.sr, io.geo, io.met, map_in, Ptot,
                                 im.pix_off, code, J, im.seed, s_q, t);
@@ -118,7 +123,7 @@ __global__ void k_site_step(const BatchDesc d, float* __restrict__ params, float
                             float4* __restrict__ met, float4* __restrict__ col, int cap,
                             const WsHeader* __restrict__ hdr,
                             unsigned long long* __restrict__ accq, AdamArgs A,
-                            const int32_t* __restrict__ iter, float* __restrict__ grads_out,
+                            const int32_t* __restrict__ state, float* __restrict__ grads_out,
                             bool adam) {
   const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= d.n_sites) return;
@@ -181,7 +186,7 @@ __global__ void k_site_step(const BatchDesc d, float* __restrict__ params, float
       for (int k = 0; k < kNParams; ++k) grads_out[k * c + i] = g[k];
     }
     if (p[PX] >= 0.f) {
-      const int t = iter[0] + im.t_off;
+      const int t = state[kStateWords * im.state];
       const float bc1 = static_cast<float>(1.0 - pow(static_cast<double>(A.beta1), t));
       const float bc2 = static_cast<float>(1.0 - pow(static_cast<double>(A.beta2), t));
       adam_site(p, g, m, v, c, i, A, bc1, bc2, im.H, im.W);
@@ -194,7 +199,7 @@ __global__ void k_site_step(const BatchDesc d, float* __restrict__ params, float
 }
 
 __global__ void k_step_finish(const BatchDesc d, const float* __restrict__ tile_loss,
-                              float* __restrict__ loss, int32_t* __restrict__ iter) {
+                              float* __restrict__ loss, int32_t* __restrict__ state) {
   __shared__ float s_w[8];
   const int b = blockIdx.x;
   const BatchImg im = d.img[b];
@@ -209,10 +214,10 @@ __global__ void k_step_finish(const BatchDesc d, const float* __restrict__ tile_
     float sum = 0.f;
     for (int w = 0; w < 8; ++w) sum += s_w[w];
     if (loss) loss[b] = sum / static_cast<float>(static_cast<double>(im.H) * im.W);
-    if (b == 0) {
-      iter[0] += 1;
-      iter[1] += 1;
-    }
+    int32_t* st = state + kStateWords * im.state;  // the image's step is done
+    st[0] += 1;
+    st[1] += 1;
+    st[2] ^= 1;
   }
 }
 
@@ -310,7 +315,7 @@ static StepLayout step_layout(uint32_t n_tiles, uint64_t total_pixels, int K, in
 
 // Validates the host image table and fills the device descriptor.
 static int make_desc(const sad_batch_image* images, int32_t B, int32_t total_cap,
-                     int64_t total_pixels, BatchDesc& d, const char* name) {
+                     int64_t total_pixels, BatchDesc& d, const char* name, int32_t n_states = -1) {
   if (!images || B < 1 || B > kMaxImages)
     return einval("%s: need 1 <= B <= %d images", name, kMaxImages);
   d.B = B;
@@ -336,11 +341,14 @@ static int make_desc(const sad_batch_image* images, int32_t B, int32_t total_cap
     o.seed = im.seed;
     o.s = 1.0f / static_cast<float>(im.H > im.W ? im.H : im.W);
     o.two_over_P = 2.0f / static_cast<float>(static_cast<double>(im.H) * im.W);
-    o.t_off = im.t_offset;
-    o.pass_off = im.pass_offset;
-    o.site_cum = sites;
-    o.swap = im.swap_maps != 0;
+    o.state = im.state_index;
+    if (n_states >= 0 && (im.state_index < 0 || im.state_index >= n_states))
+      return einval("%s: image %d state_index %d outside [0, %d)", name, b, im.state_index, n_states);
+    for (int c = 0; c < b && n_states >= 0; ++c)
+      if (images[c].state_index == im.state_index)
+        return einval("%s: images %d and %d share state row %d", name, c, b, im.state_index);
     if (im.reserved != 0) return einval("%s: image %d reserved field must be 0", name, b);
+    o.site_cum = sites;
     sites += o.site_n;
     tiles += o.tiles_x * static_cast<uint32_t>((im.H + kTileSide - 1) / kTileSide);
   }
@@ -390,15 +398,17 @@ int sad_prepare_batch(const sad_batch_image* images, int32_t B, const float* par
 int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t J, float* params,
                    float* m, float* v, float* prep, int32_t total_capacity,
                    uint32_t* map_in, uint32_t* map_out, int64_t total_pixels,
-                   const float* targets, float* loss, const sad_adam_hparams* hp, int32_t* iter,
-                   float* grads_out, void* workspace, size_t workspace_bytes, void* stream) {
+                   const float* targets, float* loss, const sad_adam_hparams* hp,
+                   int32_t* image_state, int32_t n_states, float* grads_out, void* workspace,
+                   size_t workspace_bytes, void* stream) {
   BatchDesc d;
-  if (int e = make_desc(images, B, total_capacity, total_pixels, d, "sad_train_step")) return e;
+  if (int e = make_desc(images, B, total_capacity, total_pixels, d, "sad_train_step", n_states))
+    return e;
   if (K != 4 && K != 8 && K != 16) return einval("sad_train_step: K must be 4, 8 or 16");
   if (J < 0 || J > 16) return einval("sad_train_step: J must be in [0,16]");
   if (static_cast<uint64_t>(total_pixels) * static_cast<uint64_t>(J > 0 ? J : 1) >= (1ull << 32))
     return einval("sad_train_step: pixels * J must be below 2^32");
-  if (!params || !m || !v || !prep || !map_in || !map_out || !targets || !hp || !iter ||
+  if (!params || !m || !v || !prep || !map_in || !map_out || !targets || !hp || !image_state ||
       !workspace)
     return einval("sad_train_step: null pointer");
   if (!aligned16(prep) || !aligned16(map_in) || !aligned16(map_out) ||
@@ -456,9 +466,9 @@ int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t 
   uint4* mo = reinterpret_cast<uint4*>(map_out);
   const size_t Ptot = static_cast<size_t>(total_pixels);
   switch (K) {
-    case 4: { TraceScope tr_(st, "k_step_tile"); k_step_tile<4><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, iter); } break;
-    case 8: { TraceScope tr_(st, "k_step_tile"); k_step_tile<8><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, iter); } break;
-    default: { TraceScope tr_(st, "k_step_tile"); k_step_tile<16><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, iter); } break;
+    case 4: { TraceScope tr_(st, "k_step_tile"); k_step_tile<4><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, image_state); } break;
+    case 8: { TraceScope tr_(st, "k_step_tile"); k_step_tile<8><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, image_state); } break;
+    default: { TraceScope tr_(st, "k_step_tile"); k_step_tile<16><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, image_state); } break;
   }
   if (int r = check_launch("k_step_tile")) return r;
   { TraceScope tr_(st, "k_seg_accum"); k_seg_accum<10><<<152 * 8, 256, 0, st>>>(rec, hdr, L.max_records, total_capacity, accq); }
@@ -467,9 +477,9 @@ int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t 
   if (d.n_sites > 0)
     { TraceScope tr_(st, "k_site_step"); k_site_step<<<(d.n_sites + 255) / 256, 256, 0, st>>>(
       d, params, m, v, p4, p4 + total_capacity, p4 + 2 * static_cast<size_t>(total_capacity),
-      total_capacity, hdr, accq, A, iter, grads_out, true); }
+      total_capacity, hdr, accq, A, image_state, grads_out, true); }
   if (int r = check_launch("k_site_step")) return r;
-  { TraceScope tr_(st, "k_step_finish"); k_step_finish<<<B, 256, 0, st>>>(d, tile_loss, loss, iter); }
+  { TraceScope tr_(st, "k_step_finish"); k_step_finish<<<B, 256, 0, st>>>(d, tile_loss, loss, image_state); }
   return check_launch("k_step_finish");
 }
 

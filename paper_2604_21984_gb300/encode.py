@@ -117,8 +117,9 @@ class Encoder:
             self.table = capi.batch_table([dict(H=H, W=W, site_offset=0, capacity=cap, pixel_offset=0,
                                                 seed=c.seed + 0x5AD)])
             self.ws_step = capi.step_workspace(self.table, K, cap, H * W, device=self.dev)
-            self.iter_dev = torch.zeros(2, dtype=torch.int32, device=self.dev)
+            self.state = torch.zeros((1, 4), dtype=torch.int32, device=self.dev)
             self.target_flat = self.target.reshape(-1, 3)
+            self._call = None
 
     @property
     def map(self):
@@ -139,19 +140,24 @@ class Encoder:
                                        self.maps[1], c.K, c.J, c.lambda_init, c.seed, self.stream)
         self.maps = [a, b]
         if c.fused:
-            # Adam step 1 next; pass indices continue after the warm-up's
-            self.iter_dev.copy_(torch.tensor([1, self.t_pass], dtype=torch.int32))
+            # Adam step 1 next; pass indices continue after the warm-up's; the
+            # current map is bufs[0] (state parity 0)
+            self.state.copy_(torch.tensor([[1, self.t_pass, 0, 0]], dtype=torch.int32))
+            self.bufs = (self.maps[0], self.maps[1])
+            self._par = 0
+            self._call = capi.TrainStepCall(self.table, c.K, c.J, self.params, self.m, self.v, self.prep,
+                                            self.bufs[0], self.bufs[1], self.H * self.W, self.target_flat,
+                                            self.loss, self.hp, self.state, self.ws_step,
+                                            grads_out=self.grads if c.keep_grads else None)
 
     def step(self):
         """One training iteration (1 pass, gradient, Adam)."""
         c = self.cfg
         self.it += 1
         if c.fused:
-            capi.sad_train_step(self.table, c.K, c.J, self.params, self.m, self.v, self.prep, self.maps[0],
-                                self.maps[1], self.H * self.W, self.target_flat, self.loss, self.hp,
-                                self.iter_dev, self.ws_step,
-                                grads_out=self.grads if c.keep_grads else None, stream=self.stream)
-            self.maps.reverse()
+            self._call(self.stream)
+            self._par ^= 1
+            self.maps = [self.bufs[self._par], self.bufs[1 - self._par]]
             self.t_pass += 1
             return
         capi.sad_prepare_sites(self.params, self.H, self.W, self.prep, self.stream)

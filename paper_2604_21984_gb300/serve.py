@@ -11,12 +11,14 @@ Two request kinds:
 All encodes in flight share one set of device arrays (a site pool and a pixel
 pool, sized up front from the HBM budget).  Admission allocates an encode's
 slot range and pixel range (first fit); a request that does not fit waits.
-Every tick runs ONE fused training iteration (`sad_train_step`) of every
-admitted encode, whatever its age: an encode joins the running batch with
-counter offsets so that its Adam step and pass index start where a solo run's
-would, so its result is the same alone or in any mix.  All decode requests
-that have arrived are answered by one `sad_decode_batch` launch per tick.
-Completion times are CUDA events on the serving stream.
+Admitted encodes are trained by fused batched steps (`sad_train_step`) in
+two lanes, chosen by least remaining work (see `Server`); each image's Adam
+step, pass index and current map live in its own device state row, so an
+image that joins late or sits out some calls follows exactly the trajectory
+it would follow alone: its result is the same alone or in any mix.  A lane
+whose set of images is unchanged replays its call as a CUDA graph.  All
+decode requests that have arrived are answered by one `sad_decode_batch`
+launch on their own stream.  Completion times are CUDA events.
 
 `PlainLoop` is the baseline: FIFO, one request at a time, each with the
 single-image calls.
@@ -43,7 +45,8 @@ class ServeConfig:
     pixel_pool: int = 1 << 26
     max_side: int = 4096           # largest encode accepted
     max_decode_per_tick: int = 1 << 22
-    pixels_per_call: int = 1 << 21    # encodes joined per step, shortest remaining work first
+    pixels_per_call: int = 1 << 19    # fast-lane pixels per call (least remaining work first)
+    bulk_pixels_per_call: int = 1 << 21   # bulk-lane pixels per call (arrival order)
     lr: tuple = (1e-3, 1e-3, 1e-2, 1e-3, 5e-3, 5e-3, 5e-3, 1e-2, 1e-2, 1e-2, 0.0)
 
 
@@ -56,6 +59,7 @@ class Request:
     seed: int = 0                  # encode: per-request seed
     resident: int = -1             # decode: resident site set index
     xy: torch.Tensor | None = None      # decode: float32[n, 2] (pinned host or device)
+    out: torch.Tensor | None = None     # decode: optional float32[n, 3] result buffer (pinned host)
     rid: int = -1
     # filled in by the server
     done_event: torch.cuda.Event | None = None
@@ -118,15 +122,111 @@ def pool_bytes(site_pool: int, pixel_pool: int, K: int) -> int:
     return site_pool * per_site + pixel_pool * per_pixel
 
 
+class _Lane:
+    """A stream of fused training calls over a subset of the admitted encodes,
+    with its own workspace and loss buffer.  A lane whose set of images is
+    unchanged for a second tick captures its call in a CUDA graph and
+    replays it (the per-image state rows on the device carry the counters)."""
+
+    def __init__(self, srv, priority):
+        self.srv = srv
+        self.stream = torch.cuda.Stream(device=srv.dev, priority=priority)
+        self.ws = srv._workspace()
+        self.loss = torch.zeros(64, dtype=torch.float32, device=srv.dev)
+        self.members = []
+        self.key = None
+        self.call = None
+        self.graph = None
+        self.ticks_same = 0
+        self.inflight = []
+        self.retired = []
+
+    def assign(self, members):
+        members = sorted(members, key=lambda a: a["entry"]["site_offset"])
+        key = tuple(a["seq"] for a in members)
+        if key != self.key:
+            if self.graph is not None and self.inflight:
+                # replays may still be queued: keep the graph until they ran
+                self.retired.append((self.graph, self.inflight[-1]))
+            self.key, self.members, self.graph, self.ticks_same = key, members, None, 0
+            self.call = None
+            if members:
+                srv, c = self.srv, self.srv.cfg
+                self.call = capi.TrainStepCall(
+                    capi.batch_table([a["entry"] for a in members]), c.K, c.J, srv.params, srv.m, srv.v,
+                    srv.prep, srv.maps[0], srv.maps[1], c.pixel_pool, srv.targets, self.loss, srv.hp,
+                    srv.state, self.ws)
+
+    def busy(self):
+        self.inflight = [e for e in self.inflight if not e.query()]
+        self.retired = [(g, e) for g, e in self.retired if not e.query()]
+        return len(self.inflight)
+
+    def tick(self, max_iters):
+        """T = min(max_iters, fewest iterations left) calls; finished encodes
+        hand back their ranges.  Returns T."""
+        if not self.members:
+            return 0
+        srv = self.srv
+        st = self.stream
+        T = max(1, min(max_iters, min(a["left"] for a in self.members)))
+        for a in self.members:   # order after the image's previous work
+            if a["last_lane"] is not self and a["last_event"] is not None:
+                st.wait_event(a["last_event"])
+        with torch.cuda.stream(st):
+            if self.graph is None and self.ticks_same >= 1:
+                g = torch.cuda.CUDAGraph()
+                g.capture_begin(capture_error_mode="thread_local")
+                self.call(st)
+                g.capture_end()
+                self.graph = g
+            for _ in range(T):
+                if self.graph is not None:
+                    self.graph.replay()
+                else:
+                    self.call(st)
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(st)
+            done = []
+            for b, a in enumerate(self.members):
+                a["left"] -= T
+                a["last_lane"], a["last_event"] = self, ev
+                if a["left"] <= 0:
+                    e, req = a["entry"], a["req"]
+                    lo, n = e["site_offset"], e["capacity"]
+                    req.result = srv.params[:, lo:lo + n].clone()
+                    req.loss = self.loss[b:b + 1].clone()
+                    done.append(a)
+            if done:
+                fin = torch.cuda.Event(enable_timing=True)
+                fin.record(st)
+                for a in done:
+                    a["req"].done_event = fin
+                    srv._retire(a, fin)
+        self.ticks_same += 1
+        srv.launches += 4 * T
+        self.inflight.append(ev)
+        return T
+
+
 class Server:
-    """Resident pools + the per-tick batched step and decode."""
+    """Resident pools, admission, two training lanes and the batched decode.
+
+    The `fast` lane (high priority stream) takes small encodes, least
+    remaining work first, within `pixels_per_call`; the `bulk` lane (normal
+    priority) takes the others first come first served within
+    `bulk_pixels_per_call`.  The two lanes' calls overlap on the GPU, the
+    fast one ahead, so small encodes are not held to the pace of a large one
+    and large ones keep their arrival order.  Decodes run on a third stream at high
+    priority (resident sets are never written by training)."""
 
     def __init__(self, cfg: ServeConfig | None = None, device="cuda", stream=None):
         self.cfg = cfg or ServeConfig()
         c = self.cfg
         self.dev = torch.device(device)
-        self.stream = stream or torch.cuda.Stream(device=self.dev)
-        # decodes run beside training, ahead of it when both have work queued
+        # admission (warm starts, inserts); the completion events and the
+        # stream the latencies are measured on
+        self.stream = stream or torch.cuda.Stream(device=self.dev, priority=-1)
         self.dstream = torch.cuda.Stream(device=self.dev, priority=-1)
         S, Pp, K = c.site_pool, c.pixel_pool, c.K
         if Pp < c.max_side ** 2 or S < encode_sites(c.max_side, c.max_side, c.sites_per_pixel):
@@ -141,11 +241,11 @@ class Server:
         self.maps = [torch.full((K // 4, Pp, 4), -1, dtype=torch.int32, device=self.dev) for _ in range(2)]
         self.sites = RangePool(S)
         self.pixels = RangePool(Pp, align=4)
-        self.loss = torch.zeros(64, **f32)
-        self.iter = torch.tensor([1, 0], dtype=torch.int32, device=self.dev)
-        self.iter_host = [1, 0]
+        self.state = torch.zeros((128, 4), dtype=torch.int32, device=self.dev)
+        self.free_rows = list(range(128))
         self.hp = capi.adam_hparams(lr=c.lr)
-        self.ws = self._workspace()
+        self.fast = _Lane(self, -1)
+        self.bulk = _Lane(self, 0)
         # staging for the single-image warm start (largest accepted image)
         Pmax = c.max_side * c.max_side
         nmax = encode_sites(c.max_side, c.max_side, c.sites_per_pixel)
@@ -156,12 +256,14 @@ class Server:
         self._dq_xy = torch.empty((c.max_decode_per_tick, 2), **f32)
         self._dq_img = torch.empty(c.max_decode_per_tick, dtype=torch.int32, device=self.dev)
         self._dq_rgb = torch.empty((c.max_decode_per_tick, 3), **f32)
-        self.active = []        # encodes in the batch: dicts with entry + request
+        self.active = []        # admitted encodes
         self.waiting = []       # encodes not admitted yet (FIFO)
         self.decodes = []       # decodes waiting for the next tick
         self.residents = []     # resident decode site sets: table entries
         self.launches = 0
         self._seq = 0
+        self._freed = []        # completion events of ranges handed back
+        torch.cuda.synchronize(self.dev)
 
     # -- pools ---------------------------------------------------------------
     def _workspace(self):
@@ -182,7 +284,7 @@ class Server:
 
     def footprint_bytes(self):
         c = self.cfg
-        return pool_bytes(c.site_pool, c.pixel_pool, c.K) + self.ws.numel()
+        return pool_bytes(c.site_pool, c.pixel_pool, c.K) + self.fast.ws.numel() + self.bulk.ws.numel()
 
     def add_resident(self, params: torch.Tensor, H: int, W: int, passes: int = 16, J: int = 2,
                      seed: int = 11):
@@ -209,8 +311,7 @@ class Server:
                 s = max(1, (1 << lb) >> (min(t, lb - 1) + 1))
                 capi.sad_update_topk(prep, N, H, W, c.K, a, b, (s << 16) | t, J, seed, self.stream)
                 a, b = b, a
-            # both ping-pong buffers: training steps only rewrite their own
-            # images' pixels
+            # both ping-pong buffers: training only rewrites its own images' pixels
             for mp in self.maps:
                 capi.sad_batch_insert(capi.batch_table([entry]), c.K, pc, a, None, self.params,
                                       self.m, self.v, mp, self.targets, c.pixel_pool, self.stream)
@@ -241,10 +342,20 @@ class Server:
         else:
             raise ValueError(req.kind)
 
+    def _retire(self, a, ev):
+        e = a["entry"]
+        self.sites.release(e["site_offset"], e["capacity"])
+        self.pixels.release(e["pixel_offset"], e["H"] * e["W"])
+        self.free_rows.append(e["state_index"])
+        self._freed.append(ev)
+        a["left"] = 0
+
     def _admit(self):
+        """Admit waiting encodes (FIFO) while their ranges fit: warm start in
+        the staging buffers, insert into the pools, set the state row."""
         c = self.cfg
-        admitted = []
-        while self.waiting and len(self.active) < 64:
+        st = self.stream
+        while self.waiting and len(self.active) < 128 and self.free_rows:
             req = self.waiting[0]
             H, W = int(req.image.shape[0]), int(req.image.shape[1])
             n = encode_sites(H, W, c.sites_per_pixel)
@@ -256,17 +367,28 @@ class Server:
                 self.sites.release(lo, n)
                 break
             self.waiting.pop(0)
+            # ranges and rows handed back by finished encodes are reused only
+            # after the work that last touched them
+            for ev in self._freed:
+                st.wait_event(ev)
+            self._freed = []
+            row = self.free_rows.pop(0)
             # injection seed and pass indices as in a solo encode: seed + 0x5AD,
             # passes numbered on from the warm-up's; Adam step 1 first
-            entry = dict(H=H, W=W, site_offset=lo, capacity=n, pixel_offset=po, seed=req.seed + 0x5AD)
-            n_pass = self._warm_start(req, entry)
+            entry = dict(H=H, W=W, site_offset=lo, capacity=n, pixel_offset=po, seed=req.seed + 0x5AD,
+                         state_index=row)
+            with torch.cuda.stream(st):
+                n_pass = self._warm_start(req, entry)
+                capi.sad_prepare_batch(capi.batch_table([entry]), self.params, self.prep,
+                                       c.pixel_pool, st)
+                self.state[row, 0].fill_(1)
+                self.state[row, 1].fill_(n_pass)
+                self.state[row, 2].fill_(0)
+                ready = torch.cuda.Event()
+                ready.record(st)
             self._seq += 1
-            self.active.append(dict(entry=entry, req=req, left=req.iters, done=0, n_pass=n_pass,
-                                    parity=0, P=H * W, seq=self._seq))
-            admitted.append(entry)
-        if admitted:
-            capi.sad_prepare_batch(capi.batch_table(admitted), self.params, self.prep,
-                                   c.pixel_pool, self.stream)
+            self.active.append(dict(entry=entry, req=req, left=req.iters, P=H * W, seq=self._seq,
+                                    last_lane=None, last_event=ready))
             self.launches += 1
 
     def _warm_start(self, req, entry):
@@ -280,73 +402,59 @@ class Server:
         target = req.image.contiguous()
         a, _, n_pass = warm_start(target, n, params, prep, ma, mb, c.K, c.J, c.lambda_init,
                                   req.seed, self.stream)
-        # the step reads the current map buffer
+        # the image's current map goes to buffer 0 (state parity 0)
         capi.sad_batch_insert(capi.batch_table([entry]), c.K, params, a, target, self.params, self.m,
                               self.v, self.maps[0], self.targets, c.pixel_pool, self.stream)
         self.launches += 4 + n_pass + 2
         return n_pass
 
-    def train_tick(self, max_iters: int = 1) -> int:
-        """Admit what fits, pick the encodes to step, run T fused iterations
-        of them and retire the finished ones.  Returns T (0 if idle).
+    def _plan(self):
+        """Split the admitted encodes between the lanes.  The fast lane takes
+        encodes in order of least remaining work (iterations left x pixels)
+        while their pixels fit in pixels_per_call (an encode larger than that
+        never goes there); the bulk lane takes the others in arrival order
+        while they fit in bulk_pixels_per_call (at least one).  At most 64
+        per lane; the rest wait.  Large encodes thus run first come first
+        served, as in the plain loop, while small ones pass them on the fast
+        lane; one large encode already fills the GPU, so stepping several
+        together would only make each finish later."""
+        c = self.cfg
+        fast, tot = [], 0
+        for a in sorted(self.active, key=lambda a: (a["left"] * a["P"], a["seq"])):
+            if len(fast) == 64 or tot + a["P"] > c.pixels_per_call:
+                break
+            fast.append(a)
+            tot += a["P"]
+        taken = {a["seq"] for a in fast}
+        bulk, tot = [], 0
+        for a in sorted(self.active, key=lambda a: a["seq"]):
+            if a["seq"] in taken:
+                continue
+            if len(bulk) == 64 or (bulk and tot + a["P"] > c.bulk_pixels_per_call):
+                break
+            bulk.append(a)
+            tot += a["P"]
+        self.fast.assign(fast)
+        self.bulk.assign(bulk)
 
-        Selection: shortest remaining work (iterations left x pixels) first,
-        until `pixels_per_call` pixels are in the batch (at most 64 images),
-        so small encodes are batched together and are not held to the pace of
-        a large one; T = min(max_iters, fewest iterations left among them).
-        Each image's Adam step, pass index and map buffer come from its own
-        progress (the counter offsets and the swap flag of its table entry),
-        so skipping calls does not change its trajectory."""
-        with torch.cuda.stream(self.stream):
-            self._admit()
-            if not self.active:
-                return 0
-            c = self.cfg
-            order = sorted(self.active, key=lambda a: (a["left"] * a["P"], a["seq"]))
-            sel, tot = [], 0
-            for a in order[:64]:
-                sel.append(a)
-                tot += a["P"]
-                if tot >= c.pixels_per_call:
-                    break
-            sel.sort(key=lambda a: a["entry"]["site_offset"])
-            T = max(1, min(max_iters, min(a["left"] for a in sel)))
-            for _ in range(T):
-                for a in sel:
-                    e = a["entry"]
-                    e["t_offset"] = a["done"] + 1 - self.iter_host[0]
-                    e["pass_offset"] = a["n_pass"] + a["done"] - self.iter_host[1]
-                    e["swap_maps"] = a["parity"]
-                capi.sad_train_step(capi.batch_table([a["entry"] for a in sel]), c.K, c.J, self.params,
-                                    self.m, self.v, self.prep, self.maps[0], self.maps[1], c.pixel_pool,
-                                    self.targets, self.loss, self.hp, self.iter, self.ws,
-                                    stream=self.stream)
-                self.iter_host[0] += 1
-                self.iter_host[1] += 1
-                for a in sel:
-                    a["done"] += 1
-                    a["left"] -= 1
-                    a["parity"] ^= 1
-            self.launches += 4 * T
-            for b, a in enumerate(sel):
-                if a["left"] > 0:
-                    continue
-                e, req = a["entry"], a["req"]
-                lo, n = e["site_offset"], e["capacity"]
-                req.result = self.params[:, lo:lo + n].clone()
-                req.loss = self.loss[b:b + 1].clone()
-                ev = torch.cuda.Event(enable_timing=True)
-                ev.record(self.stream)
-                req.done_event = ev
-                self.sites.release(lo, n)
-                self.pixels.release(e["pixel_offset"], e["H"] * e["W"])
-            self.active = [a for a in self.active if a["left"] > 0]
-            return T
+    def train_tick(self, max_iters: int = 1, max_inflight: int = 0) -> int:
+        """Admit what fits, re-plan the lanes, and tick every lane that has
+        fewer than max_inflight ticks queued (0: no limit).  Returns the
+        number of iterations enqueued."""
+        self._admit()
+        if not self.active:
+            return 0
+        self._plan()
+        n = 0
+        for lane in (self.fast, self.bulk):
+            if lane.members and (max_inflight <= 0 or lane.busy() < max_inflight):
+                n += lane.tick(max_iters)
+        self.active = [a for a in self.active if a["left"] > 0]
+        return n
 
     def decode_tick(self):
         """Answer every waiting decode (up to max_decode_per_tick coordinates)
-        with one batched launch on the decode stream, which runs beside the
-        training stream (resident sets are never written by training)."""
+        with one batched launch on the decode stream."""
         if not self.decodes:
             return
         c = self.cfg
@@ -371,7 +479,8 @@ class Server:
             ev = torch.cuda.Event(enable_timing=True)
             for r in reqs:
                 n = r.xy.shape[0]
-                r.result = torch.empty((n, 3), dtype=torch.float32, pin_memory=True)
+                r.result = r.out if r.out is not None else torch.empty((n, 3), dtype=torch.float32,
+                                                                        pin_memory=True)
                 r.result.copy_(self._dq_rgb[o:o + n], non_blocking=True)
                 o += n
             ev.record(ds)
@@ -379,7 +488,7 @@ class Server:
             r.done_event = ev
 
     def tick(self):
-        """One training iteration of every admitted encode, then one batched
+        """One training iteration of the planned encodes, then one batched
         decode of every waiting query."""
         self.train_tick(1)
         self.decode_tick()
@@ -449,7 +558,8 @@ class PlainLoop:
                 out = torch.empty((n, 3), dtype=torch.float32, device=self.dev)
                 capi.sad_decode_points(r["prep"], r["N"], r["H"], r["W"], c.K, r["map"], xy, out,
                                        self.stream)
-                req.result = torch.empty((n, 3), dtype=torch.float32, pin_memory=True)
+                req.result = req.out if req.out is not None else torch.empty(
+                    (n, 3), dtype=torch.float32, pin_memory=True)
                 req.result.copy_(out, non_blocking=True)
                 self.launches += 1
             ev = torch.cuda.Event(enable_timing=True)
@@ -466,9 +576,10 @@ def run_stream(server, requests, max_inflight_ticks: int = 2, iters_per_tick: in
     Server or PlainLoop.  Latency = completion (CUDA event, relative to a
     start event recorded when the stream starts) - arrival.  The host only
     enqueues work: a Server gets decode batches as soon as queries arrive and
-    training ticks of up to `iters_per_tick` iterations while fewer than
-    `max_inflight_ticks` are queued on the device; a PlainLoop runs one
-    request at a time.  Returns wall seconds."""
+    training ticks of up to `iters_per_tick` iterations on each lane that has
+    fewer than `max_inflight_ticks` queued on the device; a PlainLoop runs one
+    request at a time (the next is enqueued while fewer than
+    `max_inflight_ticks` are queued).  Returns wall seconds."""
     st = server.stream
     start = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(server.dev)
@@ -494,11 +605,8 @@ def run_stream(server, requests, max_inflight_ticks: int = 2, iters_per_tick: in
             if server.decodes:
                 server.decode_tick()
                 did = True
-            if (server.active or server.waiting) and len(inflight) < max_inflight_ticks:
-                if server.train_tick(iters_per_tick):
-                    ev = torch.cuda.Event()
-                    ev.record(st)
-                    inflight.append(ev)
+            if server.active or server.waiting:
+                if server.train_tick(iters_per_tick, max_inflight=max_inflight_ticks):
                     did = True
         if not did:
             time.sleep(0.0002)

@@ -29,11 +29,12 @@ def test_fused_step_matches_unfused_sequence(capi, oracle):
     n = tr.total_cap
     p0 = tr.params.clone()
     map0 = capi.ids_from_map(tr.maps[0])
-    t_pass = int(tr.iter[1].item()) + tr.images[0]["pass_offset"]
+    t_pass = int(tr.state[0, 1].item())
+    assert t_pass == tr.images[0]["n_pass"]
     seed = tr.images[0]["seed"]
     grads_fused = torch.empty_like(tr.params)
     capi.sad_train_step(tr.table, 8, 2, tr.params, tr.m, tr.v, tr.prep, tr.maps[0], tr.maps[1],
-                        tr.total_pixels, tr.targets, tr.loss, tr.hp, tr.iter, tr.ws, grads_out=grads_fused)
+                        tr.total_pixels, tr.targets, tr.loss, tr.hp, tr.state, tr.ws, grads_out=grads_fused)
     torch.cuda.synchronize()
     # unfused reference on copies
     p = p0.clone()
@@ -88,7 +89,9 @@ def test_graph_replay_equals_eager(capi):
     torch.cuda.synchronize()
     assert torch.equal(a.params, b.params)
     assert torch.equal(a.maps[0], b.maps[0])
-    assert int(b.iter[0].item()) == 11 and int(b.iter[1].item()) == 10
+    st = b.state.cpu().numpy()
+    assert (st[:, 0] == 11).all() and (st[:, 2] == 0).all()
+    assert [int(x) for x in st[:, 1]] == [im["n_pass"] + 10 for im in b.images]
 
 
 def test_batch_training_improves_psnr(capi):
@@ -103,25 +106,41 @@ def test_batch_training_improves_psnr(capi):
     assert all(b > a + 3.0 for a, b in zip(p0, p1))
 
 
-def test_iteration_offsets_shift_the_counters(capi):
-    """An image whose Adam step / pass index are given by offsets from a later
-    global counter trains exactly as one started at the counter's origin
-    (images can join a running batch)."""
+def test_state_rows_carry_each_images_counters(capi):
+    """Any distinct state rows give the same training; an image left out of
+    some calls resumes from its own row (Adam step, pass index, map parity)."""
     torch = pytest.importorskip("torch")
+    from paper_2604_21984_gb300 import capi as C
     from paper_2604_21984_gb300.batch import BatchConfig, BatchTrainer
     imgs = _images([(48, 64), (40, 40)], 41)
     cfg = BatchConfig(K=8, J=3, graph=False, seed=9)
     a = BatchTrainer(imgs, cfg)
-    b = BatchTrainer(imgs, cfg)
-    for im in b.images:
-        im["t_offset"] = -37
-        im["pass_offset"] -= 501
-    b.table = capi.batch_table(b.images)
-    b.iter.copy_(torch.tensor([1 + 37, 501], dtype=torch.int32))
     a.run(7)
-    b.run(7)
+    b = BatchTrainer(imgs, cfg)
+    rows = torch.zeros((5, 4), dtype=torch.int32, device="cuda")
+    rows[3] = b.state[0]
+    rows[1] = b.state[1]
+    b.images[0]["state_index"], b.images[1]["state_index"] = 3, 1
+    full = C.batch_table(b.images)
+    only0 = C.batch_table([b.images[0]])
+
+    def call(table, B):
+        C.sad_train_step(table, 8, 3, b.params, b.m, b.v, b.prep, b.bufs[0], b.bufs[1], b.total_pixels,
+                         b.targets, b.loss[:B], b.hp, rows, b.ws)
+
+    for _ in range(3):
+        call(full, 2)
+    for _ in range(2):      # image 1 sits these out
+        call(only0, 1)
+    for _ in range(2):
+        call(full, 2)
+    for _ in range(2):      # image 1 catches up alone
+        call(C.batch_table([b.images[1]]), 1)
+    torch.cuda.synchronize()
     assert torch.equal(a.params, b.params)
-    assert torch.equal(a.maps[0], b.maps[0])
+    assert rows[3, 0].item() == 8 and rows[1, 0].item() == 8
+    # 7 steps each: both current maps are in bufs[1]
+    assert torch.equal(a.maps[0], b.bufs[1])
 
 
 def test_decode_batch_matches_per_image_decode(capi):
