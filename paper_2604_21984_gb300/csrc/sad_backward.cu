@@ -92,7 +92,10 @@ __global__ void __launch_bounds__(kTileThreads, MODE == kModeStats ? 2 : 4)
     ids[4 * j + 2] = v.z;
     ids[4 * j + 3] = v.w;
   }
-  tile_body<K, MODE>(c, io, ids);
+  float lk[K];  // unused without HAVE_L
+#pragma unroll
+  for (int k = 0; k < K; ++k) lk[k] = 0.f;
+  tile_body<K, MODE>(c, io, ids, lk);
 }
 
 // ---------------------------------------------------------------------------

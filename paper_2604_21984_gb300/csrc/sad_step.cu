@@ -102,15 +102,19 @@ __global__ void __launch_bounds__(kTileThreads, 3)
   pixel_update<K, kTileThreads, 2>(v, inimg, x, y, c.H, c.W, c.sr, io.geo, io.met, map_in, Ptot,
                                 im.pix_off, code, J, im.seed, s_q, t);
   uint32_t ids[K];
+  float lk[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) ids[k] = key_id(v[k]);
+  for (int k = 0; k < K; ++k) {
+    ids[k] = key_id(v[k]);
+    lk[k] = key_logit(v[k]);
+  }
   if (inimg) {
     const size_t q = im.pix_off + static_cast<size_t>(y) * c.W + x;
 #pragma unroll
     for (int j = 0; j < K / 4; ++j)
       map_out[j * Ptot + q] = make_uint4(ids[4 * j], ids[4 * j + 1], ids[4 * j + 2], ids[4 * j + 3]);
   }
-  tile_body<K, kModeGrad>(c, io, ids);
+  tile_body<K, kModeGrad, true>(c, io, ids, lk);
 }
 
 // The ten exact statistic sums of site i -> 11 gradients -> Adam -> prepared

@@ -137,9 +137,14 @@ struct TileIO {
 
 // Adjoint (MODE = kModeGrad) or budget statistics (kModeStats) of one tile
 // whose pixels' lists are ids[] (thread t = pixel (t%16, t/16) of the tile).
+// With HAVE_L (gradient mode), lk[] holds the logits of the listed sites in
+// descending order (the propagation pass just computed them exactly; invalid
+// entries are the empty tail), so the forward takes them instead of
+// re-gathering and re-scoring, and the first entry is the maximum.
 // Every thread of the 256-thread block must call it.
-template <int K, int MODE>
-__device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, uint32_t (&ids)[K]) {
+template <int K, int MODE, bool HAVE_L = false>
+__device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, uint32_t (&ids)[K],
+                                          const float (&lk)[K]) {
   const float4* __restrict__ geo = io.geo;
   const float4* __restrict__ met = io.met;
   const float4* __restrict__ col = io.col;
@@ -208,6 +213,21 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
     for (int k = 0; k < K; ++k) {
       if (vm >> k & 1u) {
         const float e = __expf(l[k] - m);
+        const float4 ck = ldg(&col[ids[k]]);
+        z += e;
+        cb.x += e * ck.x;
+        cb.y += e * ck.y;
+        cb.z += e * ck.z;
+      }
+    }
+  } else if (HAVE_L) {
+    // sorted logits: the first valid entry is the maximum
+    m = ids[0] != kInvalid ? lk[0] : -INFINITY;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (ids[k] != kInvalid) {
+        vm |= 1u << k;
+        const float e = __expf(lk[k] - m);
         const float4 ck = ldg(&col[ids[k]]);
         z += e;
         cb.x += e * ck.x;

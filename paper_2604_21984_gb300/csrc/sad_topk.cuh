@@ -34,6 +34,12 @@ __device__ __forceinline__ uint64_t make_key(float l, uint32_t id) {
 
 __device__ __forceinline__ uint32_t key_id(uint64_t k) { return ~static_cast<uint32_t>(k); }
 
+// The logit a (non-empty) key was made from.
+__device__ __forceinline__ float key_logit(uint64_t k) {
+  const uint32_t u = static_cast<uint32_t>(k >> 32);
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
 template <int K>
 __device__ __forceinline__ void bitonic_sort_desc(uint64_t (&v)[K]) {
 #pragma unroll
