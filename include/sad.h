@@ -325,8 +325,14 @@ typedef struct sad_batch_image {
   int64_t pixel_offset;  /* first pixel of the image in the packed arrays */
   uint64_t seed;         /* injection seed of the image */
   int32_t state_index;   /* sad_train_step: the image's row of image_state */
-  int32_t reserved;      /* must be 0 */
+  int32_t flags;         /* sad_train_step: 0, or SAD_STEP_KEEP_LISTS */
 } sad_batch_image;
+
+/* Batch-image flag: this call skips the image's propagation pass and runs
+ * the adjoint on its current lists (candidate update period f_cand > 1,
+ * App. "Candidate Field and Jump Schedule", Candidate update frequency);
+ * only the image's Adam step t advances. */
+#define SAD_STEP_KEEP_LISTS 1
 
 /* Workspace bytes of sad_train_step (0 = invalid table); same record rule as
  * sad_backward_workspace_bytes with P = total_pixels.  The workspace must be
@@ -358,9 +364,11 @@ int sad_prepare_batch(const sad_batch_image* images, int32_t B, const float* par
  * Adam step (1-based), pass the pass index of the propagation (step code
  * (1 << 16) | (pass & 0xffff)), parity 0 = its current map is in map_in
  * (then it writes map_out), 1 = the reverse.  The call advances the rows of
- * the images it steps (t + 1, pass + 1, parity ^ 1), so a fixed batch always
- * makes the same call (capture it once in a CUDA graph and replay it), and
- * an image left out of some calls keeps its own counters and map.
+ * the images it steps (t + 1, pass + 1, parity ^ 1; only t + 1 for an image
+ * flagged SAD_STEP_KEEP_LISTS, whose propagation is skipped), so a fixed
+ * batch always makes the same call (capture it once in a CUDA graph and
+ * replay it), and an image left out of some calls keeps its own counters
+ * and map.
  * loss: device float32[B], the mean loss of each image before the step (may
  * be NULL).  grads_out: optional float32[11][total_capacity].  map_in and
  * map_out must not overlap.  Each image's results are independent of the
@@ -375,6 +383,18 @@ int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t 
                    const float* targets, float* loss, const sad_adam_hparams* hp,
                    int32_t* image_state, int32_t n_states, float* grads_out, void* workspace,
                    size_t workspace_bytes, void* stream);
+
+/*
+ * sad_batch_update -- one propagation pass at jump 1 (sad_update_topk
+ * semantics, each image with its own site range, seed, pass index and
+ * current map from its state row) for every image of the table, advancing
+ * each row's pass index and parity (t unchanged): the extra passes of a
+ * candidate update with n_cand > 1 (App. "Candidate Field and Jump
+ * Schedule", Candidate update frequency).  Arguments as sad_train_step.
+ */
+int sad_batch_update(const sad_batch_image* images, int32_t B, int32_t K, int32_t J,
+                     const float* prep, int32_t total_capacity, uint32_t* map_in, uint32_t* map_out,
+                     int64_t total_pixels, int32_t* image_state, int32_t n_states, void* stream);
 
 /*
  * sad_batch_insert -- place one image, prepared with the single-image calls

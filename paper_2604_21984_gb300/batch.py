@@ -35,6 +35,7 @@ class BatchConfig:
     seed: int = 0
     lr: tuple = (1e-3, 1e-3, 1e-2, 1e-3, 5e-3, 5e-3, 5e-3, 1e-2, 1e-2, 1e-2, 0.0)
     graph: bool = True
+    cand_every: int = 1   # f_cand: candidate refresh every this many iterations
 
 
 class BatchTrainer:
@@ -74,16 +75,22 @@ class BatchTrainer:
         self.ws = capi.step_workspace(self.table, K, site, pix, device=self.dev)
         self.graph = None
         self.steps = 0
+        self.refreshes = 0
         self._init(targets)
         self._call = capi.TrainStepCall(self.table, c.K, c.J, self.params, self.m, self.v, self.prep,
                                         self.bufs[0], self.bufs[1], self.total_pixels, self.targets,
                                         self.loss, self.hp, self.state, self.ws)
+        keep = capi.batch_table([dict(im, flags=capi.STEP_KEEP_LISTS) for im in self.images])
+        self._call_keep = capi.TrainStepCall(keep, c.K, c.J, self.params, self.m, self.v, self.prep,
+                                             self.bufs[0], self.bufs[1], self.total_pixels, self.targets,
+                                             self.loss, self.hp, self.state, self.ws)
 
     @property
     def maps(self):
-        """[current map buffer, other] (every image steps every call, so all
-        share the parity of the step count)."""
-        return [self.bufs[self.steps & 1], self.bufs[1 - (self.steps & 1)]]
+        """[current map buffer, other] (every image refreshes on the same
+        calls, so all share the parity of the refresh count)."""
+        p = self.refreshes & 1
+        return [self.bufs[p], self.bufs[1 - p]]
 
     def _init(self, targets):
         c = self.cfg
@@ -106,34 +113,51 @@ class BatchTrainer:
         # state rows: Adam step 1, passes numbered on from the warm-up's, map in bufs[0]
         self.state.copy_(torch.tensor([[1, im["n_pass"], 0, 0] for im in self.images], dtype=torch.int32))
 
-    def _step(self):
-        self._call()
+    def _step(self, stream=None):
+        """One iteration: a candidate refresh on the first of every
+        cand_every iterations, the current lists on the others."""
+        if self.steps % max(1, self.cfg.cand_every) == 0:
+            self._call(stream)
+            self.refreshes += 1
+        else:
+            self._call_keep(stream)
         self.steps += 1
 
     def _capture(self):
-        """One iteration in a CUDA graph (the call never changes: the state
-        rows on the device carry the counters and the map parity)."""
+        """One candidate period (cand_every iterations) in a CUDA graph: the
+        calls never change, the state rows on the device carry the counters
+        and the map parity."""
         s = torch.cuda.Stream(device=self.dev)
         s.wait_stream(torch.cuda.current_stream(self.dev))
         g = torch.cuda.CUDAGraph()
+        steps, refreshes = self.steps, self.refreshes
         with torch.cuda.stream(s):
-            # capture records the call without running it
+            # capture records the calls without running them
             with torch.cuda.graph(g, stream=s):
-                self._call(s)
+                for _ in range(max(1, self.cfg.cand_every)):
+                    self._step(s)
+        self.steps, self.refreshes = steps, refreshes
         torch.cuda.current_stream(self.dev).wait_stream(s)
         self.graph = g
 
     def run(self, iters: int):
-        """`iters` training iterations of every image (graph replays when on)."""
-        if self.cfg.graph and iters >= 1:
-            if self.graph is None:
-                self._capture()
-            for _ in range(iters):
-                self.graph.replay()
-            self.steps += iters
-        else:
-            for _ in range(iters):
+        """`iters` training iterations of every image (graph replays of whole
+        candidate periods when on, single calls for the rest)."""
+        F = max(1, self.cfg.cand_every)
+        if self.cfg.graph:
+            while iters > 0 and self.steps % F != 0:
                 self._step()
+                iters -= 1
+            if iters >= F:
+                if self.graph is None:
+                    self._capture()
+                for _ in range(iters // F):
+                    self.graph.replay()
+                self.steps += F * (iters // F)
+                self.refreshes += iters // F
+                iters -= F * (iters // F)
+        for _ in range(iters):
+            self._step()
         return self
 
     def map_for(self, b):

@@ -24,6 +24,7 @@ _lib = None
 
 N_PARAMS = 11
 INVALID = 0xFFFFFFFF
+STEP_KEEP_LISTS = 1   # batch-image flag (include/sad.h SAD_STEP_KEEP_LISTS)
 
 
 class SadError(RuntimeError):
@@ -46,7 +47,7 @@ class DpParams(ctypes.Structure):
 class BatchImage(ctypes.Structure):
     _fields_ = [("H", ctypes.c_int32), ("W", ctypes.c_int32), ("site_offset", ctypes.c_int32),
                 ("capacity", ctypes.c_int32), ("pixel_offset", ctypes.c_int64),
-                ("seed", ctypes.c_uint64), ("state_index", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("seed", ctypes.c_uint64), ("state_index", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 class TraceEntry(ctypes.Structure):
@@ -128,6 +129,9 @@ _SIGS = {
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(AdamHparams),
                                       ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_size_t, ctypes.c_void_p]),
+    "sad_batch_update": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_int64, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "sad_batch_insert": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
@@ -420,6 +424,7 @@ def batch_table(images):
         arr[i].site_offset, arr[i].capacity = d["site_offset"], d["capacity"]
         arr[i].pixel_offset, arr[i].seed = d["pixel_offset"], d["seed"] & ((1 << 64) - 1)
         arr[i].state_index = d.get("state_index", i)
+        arr[i].flags = d.get("flags", 0)
     return arr
 
 
@@ -531,3 +536,13 @@ def sad_trace_collect():
            "sad_trace_collect")
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms))
             for i in range(min(n.value, 128))}
+
+
+def sad_batch_update(table, K, J, prep, total_cap, map_in, map_out, total_pixels, state, stream=None):
+    """One propagation pass of every image of the table (state rows advance)."""
+    _check(lib().sad_batch_update(ctypes.cast(table, ctypes.c_void_p), len(table), K, J,
+                                  _ptr(prep, torch.float32, "prep"), total_cap,
+                                  _ptr(map_in, torch.int32, "map_in", total_pixels * K),
+                                  _ptr(map_out, torch.int32, "map_out", total_pixels * K), total_pixels,
+                                  _ptr(state, torch.int32, "state"), state.shape[0], _stream(stream)),
+           "sad_batch_update")

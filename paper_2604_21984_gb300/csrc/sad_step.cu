@@ -39,6 +39,7 @@ struct BatchImg {
   float s, two_over_P;
   int32_t state;      // row of the image in the per-image state array
   uint32_t site_cum;  // sites of the images before this one
+  int32_t flags;      // SAD_STEP_KEEP_LISTS: no propagation this call
 };
 
 constexpr int kStateWords = 4;  // per image: {Adam step t, pass index, map parity, reserved}
@@ -72,18 +73,9 @@ __device__ __forceinline__ int image_of_slot(const BatchDesc& d, uint32_t j) {
   return lo;
 }
 
-template <int K>
-__global__ void __launch_bounds__(kTileThreads, 3)
-    k_step_tile(const BatchDesc d, TileIO io, uint4* map_a, uint4* map_b, size_t Ptot, int J,
-                const int32_t* __restrict__ state) {
-  __shared__ uint32_t s_q[kQueue][kTileThreads];
-  const int b = image_of_tile(d, blockIdx.x);
-  const BatchImg im = d.img[b];
-  const int32_t* st = state + kStateWords * im.state;
-  const bool swap = st[2] & 1;
-  const uint4* map_in = swap ? map_b : map_a;
-  uint4* map_out = swap ? map_a : map_b;
-  const uint32_t lt = blockIdx.x - im.tile_off;
+__device__ __forceinline__ TileCtx tile_ctx(const BatchDesc& d, int b, uint32_t tile) {
+  const BatchImg& im = d.img[b];
+  const uint32_t lt = tile - im.tile_off;
   TileCtx c;
   c.H = im.H;
   c.W = im.W;
@@ -91,9 +83,29 @@ __global__ void __launch_bounds__(kTileThreads, 3)
   c.y0 = static_cast<int>(lt / im.tiles_x) * kTileSide;
   c.pix_off = im.pix_off;
   c.sr = SiteRange{im.site_lo, im.site_n};
-  c.tile = blockIdx.x;
+  c.tile = tile;
   c.img = static_cast<uint32_t>(b);
   c.two_over_P = im.two_over_P;
+  return c;
+}
+
+constexpr int kKeepLists = SAD_STEP_KEEP_LISTS;
+
+// Propagation pass + adjoint of the tiles of images that refresh their lists
+// this call (UPDATE_ONLY: the pass alone, for extra passes between steps).
+template <int K, bool UPDATE_ONLY>
+__global__ void __launch_bounds__(kTileThreads, 3)
+    k_step_tile(const BatchDesc d, TileIO io, uint4* map_a, uint4* map_b, size_t Ptot, int J,
+                const int32_t* __restrict__ state) {
+  __shared__ uint32_t s_q[kQueue][kTileThreads];
+  const int b = image_of_tile(d, blockIdx.x);
+  const BatchImg im = d.img[b];
+  if (!UPDATE_ONLY && (im.flags & kKeepLists)) return;  // whole block: handled by k_keep_tile
+  const int32_t* st = state + kStateWords * im.state;
+  const bool swap = st[2] & 1;
+  const uint4* map_in = swap ? map_b : map_a;
+  uint4* map_out = swap ? map_a : map_b;
+  const TileCtx c = tile_ctx(d, b, blockIdx.x);
   const int t = threadIdx.x;
   const int x = c.x0 + (t & (kTileSide - 1)), y = c.y0 + (t >> 4);
   const bool inimg = x < c.W && y < c.H;
@@ -114,7 +126,46 @@ __global__ void __launch_bounds__(kTileThreads, 3)
     for (int j = 0; j < K / 4; ++j)
       map_out[j * Ptot + q] = make_uint4(ids[4 * j], ids[4 * j + 1], ids[4 * j + 2], ids[4 * j + 3]);
   }
-  tile_body<K, kModeGrad, true>(c, io, ids, lk);
+  if (!UPDATE_ONLY) tile_body<K, kModeGrad, true>(c, io, ids, lk);
+}
+
+// Adjoint of the tiles of images that keep their lists this call: the lists
+// are read from the image's current map (candidate update period > 1).
+template <int K>
+__global__ void __launch_bounds__(kTileThreads, 3)
+    k_keep_tile(const BatchDesc d, TileIO io, const uint4* map_a, const uint4* map_b, size_t Ptot,
+                const int32_t* __restrict__ state) {
+  const int b = image_of_tile(d, blockIdx.x);
+  const BatchImg im = d.img[b];
+  if (!(im.flags & kKeepLists)) return;
+  const int32_t* st = state + kStateWords * im.state;
+  const uint4* map = (st[2] & 1) ? map_b : map_a;
+  const TileCtx c = tile_ctx(d, b, blockIdx.x);
+  const int t = threadIdx.x;
+  const int x = c.x0 + (t & (kTileSide - 1)), y = c.y0 + (t >> 4);
+  uint32_t ids[K];
+#pragma unroll
+  for (int j = 0; j < K / 4; ++j) {
+    uint4 w = make_uint4(kInvalid, kInvalid, kInvalid, kInvalid);
+    if (x < c.W && y < c.H) w = ldg(&map[j * Ptot + im.pix_off + static_cast<size_t>(y) * c.W + x]);
+    ids[4 * j] = w.x;
+    ids[4 * j + 1] = w.y;
+    ids[4 * j + 2] = w.z;
+    ids[4 * j + 3] = w.w;
+  }
+  float lk[K];  // unused without HAVE_L
+#pragma unroll
+  for (int k = 0; k < K; ++k) lk[k] = 0.f;
+  tile_body<K, kModeGrad>(c, io, ids, lk);
+}
+
+// After a propagation-only pass: every image's pass index and map parity advance.
+__global__ void k_state_pass(const BatchDesc d, int32_t* __restrict__ state) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= d.B) return;
+  int32_t* st = state + kStateWords * d.img[b].state;
+  st[1] += 1;
+  st[2] ^= 1;
 }
 
 // The ten exact statistic sums of site i -> 11 gradients -> Adam -> prepared
@@ -220,8 +271,10 @@ __global__ void k_step_finish(const BatchDesc d, const float* __restrict__ tile_
     if (loss) loss[b] = sum / static_cast<float>(static_cast<double>(im.H) * im.W);
     int32_t* st = state + kStateWords * im.state;  // the image's step is done
     st[0] += 1;
-    st[1] += 1;
-    st[2] ^= 1;
+    if (!(im.flags & kKeepLists)) {
+      st[1] += 1;
+      st[2] ^= 1;
+    }
   }
 }
 
@@ -351,7 +404,8 @@ static int make_desc(const sad_batch_image* images, int32_t B, int32_t total_cap
     for (int c = 0; c < b && n_states >= 0; ++c)
       if (images[c].state_index == im.state_index)
         return einval("%s: images %d and %d share state row %d", name, c, b, im.state_index);
-    if (im.reserved != 0) return einval("%s: image %d reserved field must be 0", name, b);
+    if (im.flags & ~SAD_STEP_KEEP_LISTS) return einval("%s: image %d has unknown flags", name, b);
+    o.flags = im.flags;
     o.site_cum = sites;
     sites += o.site_n;
     tiles += o.tiles_x * static_cast<uint32_t>((im.H + kTileSide - 1) / kTileSide);
@@ -469,12 +523,28 @@ int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t 
   uint4* mi = reinterpret_cast<uint4*>(map_in);
   uint4* mo = reinterpret_cast<uint4*>(map_out);
   const size_t Ptot = static_cast<size_t>(total_pixels);
-  switch (K) {
-    case 4: { TraceScope tr_(st, "k_step_tile"); k_step_tile<4><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, image_state); } break;
-    case 8: { TraceScope tr_(st, "k_step_tile"); k_step_tile<8><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, image_state); } break;
-    default: { TraceScope tr_(st, "k_step_tile"); k_step_tile<16><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, image_state); } break;
+  bool any_keep = false, any_refresh = false;
+  for (int b = 0; b < B; ++b) {
+    any_keep |= (images[b].flags & SAD_STEP_KEEP_LISTS) != 0;
+    any_refresh |= (images[b].flags & SAD_STEP_KEEP_LISTS) == 0;
   }
-  if (int r = check_launch("k_step_tile")) return r;
+  if (any_refresh) {
+    TraceScope tr_(st, "k_step_tile");
+    switch (K) {
+      case 4: k_step_tile<4, false><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, image_state); break;
+      case 8: k_step_tile<8, false><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, image_state); break;
+      default: k_step_tile<16, false><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, image_state); break;
+    }
+  }
+  if (any_keep) {
+    TraceScope tr_(st, "k_keep_tile");
+    switch (K) {
+      case 4: k_keep_tile<4><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, image_state); break;
+      case 8: k_keep_tile<8><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, image_state); break;
+      default: k_keep_tile<16><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, image_state); break;
+    }
+  }
+  if (int r = check_launch("k_step_tile / k_keep_tile")) return r;
   { TraceScope tr_(st, "k_seg_accum"); k_seg_accum<10><<<152 * 8, 256, 0, st>>>(rec, hdr, L.max_records, total_capacity, accq); }
   if (int r = check_launch("k_seg_accum")) return r;
   const AdamArgs A = adam_args(hp);
@@ -485,6 +555,45 @@ int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t 
   if (int r = check_launch("k_site_step")) return r;
   { TraceScope tr_(st, "k_step_finish"); k_step_finish<<<B, 256, 0, st>>>(d, tile_loss, loss, image_state); }
   return check_launch("k_step_finish");
+}
+
+int sad_batch_update(const sad_batch_image* images, int32_t B, int32_t K, int32_t J,
+                     const float* prep, int32_t total_capacity, uint32_t* map_in, uint32_t* map_out,
+                     int64_t total_pixels, int32_t* image_state, int32_t n_states, void* stream) {
+  BatchDesc d;
+  if (int e = make_desc(images, B, total_capacity, total_pixels, d, "sad_batch_update", n_states))
+    return e;
+  if (K != 4 && K != 8 && K != 16) return einval("sad_batch_update: K must be 4, 8 or 16");
+  if (J < 0 || J > 16) return einval("sad_batch_update: J must be in [0,16]");
+  if (static_cast<uint64_t>(total_pixels) * static_cast<uint64_t>(J > 0 ? J : 1) >= (1ull << 32))
+    return einval("sad_batch_update: pixels * J must be below 2^32");
+  if (!prep || !map_in || !map_out || !image_state) return einval("sad_batch_update: null pointer");
+  if (!aligned16(prep) || !aligned16(map_in) || !aligned16(map_out))
+    return einval("sad_batch_update: misaligned pointer");
+  const size_t mbytes = static_cast<size_t>(total_pixels) * K * sizeof(uint32_t);
+  const char* a = reinterpret_cast<const char*>(map_in);
+  const char* bb = reinterpret_cast<const char*>(map_out);
+  if (a < bb + mbytes && bb < a + mbytes) return einval("sad_batch_update: maps overlap");
+  cudaStream_t st = as_stream(stream);
+  const float4* p4 = reinterpret_cast<const float4*>(prep);
+  TileIO io{};
+  io.geo = p4;
+  io.met = p4 + total_capacity;
+  io.col = p4 + 2 * static_cast<size_t>(total_capacity);
+  uint4* mi = reinterpret_cast<uint4*>(map_in);
+  uint4* mo = reinterpret_cast<uint4*>(map_out);
+  const size_t Ptot = static_cast<size_t>(total_pixels);
+  {
+    TraceScope tr_(st, "k_update_tile");
+    switch (K) {
+      case 4: k_step_tile<4, true><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, image_state); break;
+      case 8: k_step_tile<8, true><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, image_state); break;
+      default: k_step_tile<16, true><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, image_state); break;
+    }
+  }
+  if (int r = check_launch("k_update_tile")) return r;
+  { TraceScope tr_(st, "k_state_pass"); k_state_pass<<<1, 64, 0, st>>>(d, image_state); }
+  return check_launch("k_state_pass");
 }
 
 int sad_batch_insert(const sad_batch_image* image, int32_t K, const float* src_params,

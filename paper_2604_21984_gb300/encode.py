@@ -39,6 +39,8 @@ class EncodeConfig:
     seed: int = 0
     lr: tuple = (1e-3, 1e-3, 1e-2, 1e-3, 5e-3, 5e-3, 5e-3, 1e-2, 1e-2, 1e-2, 0.0)
     fused: bool = True   # one sad_train_step per iteration (else the separate calls)
+    cand_every: int = 1  # f_cand: refresh the candidate lists every this many iterations
+    cand_passes: int = 1  # n_cand: propagation passes per refresh
     keep_grads: bool = False   # fused: also write the step's gradients to Encoder.grads
     extra: dict = field(default_factory=dict)
 
@@ -149,19 +151,38 @@ class Encoder:
                                             self.bufs[0], self.bufs[1], self.H * self.W, self.target_flat,
                                             self.loss, self.hp, self.state, self.ws_step,
                                             grads_out=self.grads if c.keep_grads else None)
+            e = dict(H=self.H, W=self.W, site_offset=0, capacity=self.cap, pixel_offset=0,
+                     seed=c.seed + 0x5AD, flags=capi.STEP_KEEP_LISTS)
+            self._call_keep = capi.TrainStepCall(capi.batch_table([e]), c.K, c.J, self.params, self.m,
+                                                 self.v, self.prep, self.bufs[0], self.bufs[1],
+                                                 self.H * self.W, self.target_flat, self.loss, self.hp,
+                                                 self.state, self.ws_step,
+                                                 grads_out=self.grads if c.keep_grads else None)
 
     def step(self):
-        """One training iteration (1 pass, gradient, Adam)."""
+        """One training iteration: a candidate refresh (cand_passes passes)
+        every cand_every iterations, then gradient and Adam."""
         c = self.cfg
         self.it += 1
+        refresh = (self.it - 1) % max(1, c.cand_every) == 0
         if c.fused:
-            self._call(self.stream)
-            self._par ^= 1
+            if refresh:
+                for _ in range(c.cand_passes - 1):
+                    capi.sad_batch_update(self.table, c.K, c.J, self.prep, self.cap, self.bufs[0],
+                                          self.bufs[1], self.H * self.W, self.state, self.stream)
+                    self._par ^= 1
+                    self.t_pass += 1
+                self._call(self.stream)
+                self._par ^= 1
+                self.t_pass += 1
+            else:
+                self._call_keep(self.stream)
             self.maps = [self.bufs[self._par], self.bufs[1 - self._par]]
-            self.t_pass += 1
             return
         capi.sad_prepare_sites(self.params, self.H, self.W, self.prep, self.stream)
-        self._pass()
+        if refresh:
+            for _ in range(c.cand_passes):
+                self._pass()
         capi.sad_train_grads(self.params, self.prep, self.H, self.W, c.K, self.maps[0], self.target,
                              self.grads, self.loss, self.ws, stream=self.stream)
         capi.sad_adam_step(self.params, self.grads, self.m, self.v, self.H, self.W, self.it, self.hp,

@@ -177,3 +177,69 @@ def test_decode_batch_matches_per_image_decode(capi):
         np.testing.assert_allclose(got[sel], ref.cpu().numpy(), rtol=0, atol=1e-6)
     bad = (qimg < 0) | (qimg >= len(sizes))
     assert np.all(got[bad] == 0.0)
+
+
+def test_keep_lists_step_and_batch_update(capi, oracle):
+    """A step flagged to keep its lists = train_grads on the current map +
+    Adam; sad_batch_update = sad_update_topk per image (bit-exact)."""
+    torch = pytest.importorskip("torch")
+    from paper_2604_21984_gb300.batch import BatchConfig, BatchTrainer
+    imgs = _images([(40, 56), (33, 47)], 61)
+    tr = BatchTrainer(imgs, BatchConfig(K=16, J=4, graph=False, seed=6))
+    tr.run(2)
+    torch.cuda.synchronize()
+    # propagation-only pass of both images vs the single-image pass
+    before = [tr.map_for(b) for b in range(2)]
+    pass_idx = tr.state[:, 1].cpu().numpy().copy()
+    cur, other = tr.maps
+    capi.sad_batch_update(tr.table, 16, 4, tr.prep, tr.total_cap, tr.bufs[0], tr.bufs[1], tr.total_pixels,
+                          tr.state)
+    torch.cuda.synchronize()
+    tr.refreshes += 1
+    for b, (H, W) in enumerate([(40, 56), (33, 47)]):
+        im = tr.images[b]
+        lo, n = im["site_offset"], im["capacity"]
+        prep = capi.empty_prep(n)
+        capi.sad_prepare_sites(tr.params[:, lo:lo + n].contiguous(), H, W, prep)
+        a = capi.map_from_ids(before[b])
+        out = capi.empty_map(H, W, 16)
+        capi.sad_update_topk(prep, n, H, W, 16, a, out, (1 << 16) | int(pass_idx[b]), 4, im["seed"])
+        assert np.array_equal(capi.ids_from_map(out), tr.map_for(b)), b
+    assert (tr.state[:, 1].cpu().numpy() == pass_idx + 1).all()
+    # a keep-lists step: gradients of the current lists, t advances only
+    H, W = 40, 56
+    im = tr.images[0]
+    lo, n = im["site_offset"], im["capacity"]
+    p_before = tr.params[:, lo:lo + n].contiguous()
+    st_before = tr.state.clone()
+    keep = capi.batch_table([dict(x, flags=capi.STEP_KEEP_LISTS) for x in tr.images])
+    grads = torch.zeros_like(tr.params)
+    capi.sad_train_step(keep, 16, 4, tr.params, tr.m, tr.v, tr.prep, tr.bufs[0], tr.bufs[1], tr.total_pixels,
+                        tr.targets, tr.loss, tr.hp, tr.state, tr.ws, grads_out=grads)
+    torch.cuda.synchronize()
+    st = tr.state.cpu().numpy()
+    assert (st[:, 0] == st_before.cpu().numpy()[:, 0] + 1).all()
+    assert (st[:, 1:] == st_before.cpu().numpy()[:, 1:]).all()
+    prep = capi.empty_prep(n)
+    capi.sad_prepare_sites(p_before, H, W, prep)
+    g_ref = torch.empty_like(p_before)
+    loss = torch.empty(1, device="cuda")
+    capi.sad_train_grads(p_before, prep, H, W, 16, capi.map_from_ids(tr.map_for(0)), imgs[0], g_ref, loss,
+                         capi.backward_workspace(H, W, 16, n))
+    assert abs(loss.item() - tr.loss[0].item()) <= 1e-6 * loss.item()
+    assert_grads_close(grads[:, lo:lo + n].cpu().numpy().astype(np.float64), g_ref.cpu().numpy().astype(np.float64))
+
+
+def test_candidate_period_graph_equals_eager(capi):
+    torch = pytest.importorskip("torch")
+    from paper_2604_21984_gb300.batch import BatchConfig, BatchTrainer
+    imgs = _images([(48, 48), (32, 64)], 71)
+    a = BatchTrainer(imgs, BatchConfig(K=8, J=2, graph=False, seed=3, cand_every=3))
+    b = BatchTrainer(imgs, BatchConfig(K=8, J=2, graph=True, seed=3, cand_every=3))
+    a.run(11)
+    b.run(1)
+    b.run(10)
+    torch.cuda.synchronize()
+    assert torch.equal(a.params, b.params)
+    assert torch.equal(a.maps[0], b.maps[0])
+    assert a.refreshes == b.refreshes == 4

@@ -59,3 +59,20 @@ def test_short_encode_fits_and_densifies(capi):
     n_active = int((enc.params[0] >= 0).sum().item())
     assert n_active == enc.n_active
     assert n_active != 1536                      # densify/prune changed the budget
+
+
+def test_candidate_period_fused_matches_separate_calls(capi):
+    """cand_every = 3, cand_passes = 2: the fused step (update-only batch
+    pass + keep-lists steps) trains like the separate calls."""
+    torch = pytest.importorskip("torch")
+    from paper_2604_21984_gb300.encode import EncodeConfig, Encoder
+    img = dev(gen.image_noise_polygons_lines(64, 80, seed=44, n_polygons=6, n_lines=3))
+    kw = dict(n_sites=400, K=16, J=4, seed=8, densify_every=0, cand_every=3, cand_passes=2)
+    a = Encoder(img, EncodeConfig(fused=True, **kw)).run(14)
+    b = Encoder(img, EncodeConfig(fused=False, **kw)).run(14)
+    torch.cuda.synchronize()
+    assert a.t_pass == b.t_pass
+    pa, pb = a.psnr(), b.psnr()
+    assert abs(pa - pb) < 0.02, (pa, pb)
+    same = (capi.ids_from_map(a.maps[0]) == capi.ids_from_map(b.maps[0])).mean()
+    assert same > 0.95
