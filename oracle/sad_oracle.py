@@ -28,6 +28,10 @@ Part 2 (fp32, the top-K propagation as the kernel's precision decides it):
   splitmix64 / inject_ids   App. "Candidate Field and Jump Schedule" seeded stochastic injection (counter-based)
   topk_seed_fp32    App. "Candidate Field and Jump Schedule", JFA prepass seed pass
   topk_pass_fp32    Sec. 4.3 update C_t = topK(C_{t-1} U P_t U G_t)
+Part 3: gradient-weighted initialisation (Sec. 4.4).
+Part 4: adaptive budget: statistics, densify split, prune (Sec. 4.5).
+Part 5: packed 16-byte evaluation sites (App. "Data Layout and Packing",
+  Packed storage for evaluation): pack_eval / unpack_eval.
 """
 from __future__ import annotations
 
@@ -883,3 +887,93 @@ def densify_prune(params, m, v, stats, target, H, W, densify_pct, prune_pct, alp
     p[PX, prune] = -1.0
     p[PY, prune] = -1.0
     return p, m, v, int((p[PX] >= 0).sum())
+
+
+# ---------------------------------------------------------------------------
+# Part 5: packed 16-byte evaluation sites (App. "Data Layout and Packing",
+# Packed storage for evaluation)
+# ---------------------------------------------------------------------------
+# Four 32-bit words per site:
+#   w0  x, y as 15-bit UNORM of x/W, y/H (bits 0-14, 15-29), active flag bit 31
+#   w1  colour r, g, b as 11/11/10-bit UNORM with per-image min/scale
+#   w2  (log tau, r) as 16/16-bit UNORM with per-image min/scale
+#   w3  bits 0-15: the angle of u as a 16-bit UNORM code over [-pi, pi];
+#       bits 16-31: a as float16
+# The per-image min and max of log tau, r and the colour channels (over the
+# active sites) are kept beside the words: q = float32[10] (lo, hi) x 5.
+# The paper's sites have no b; b is folded into (log tau, r) exactly, since
+# tau s (r - e^{b/2} n0) = (tau e^{b/2}) s (r e^{-b/2} - n0): log tau' =
+# log tau + b/2, r' = r e^{-b/2}, b' = 0.  Quantisation arithmetic is carried
+# out in float64 from the float32 inputs (codes = round half to even).
+
+PACK_BITS = (16, 16, 11, 11, 10)   # log tau, r, colour r, g, b
+
+
+def _fold_b(p):
+    """float32 (log tau', r') with b folded in (float64 arithmetic)."""
+    lt = (p[PLOGTAU].astype(np.float64) + p[PB].astype(np.float64) / 2.0).astype(np.float32)
+    rr = (p[PR].astype(np.float64) * np.exp(-p[PB].astype(np.float64) / 2.0)).astype(np.float32)
+    return lt, rr
+
+
+def _code(v, lo, hi, bits):
+    """UNORM code of float32 v in [lo, hi] (float64 arithmetic)."""
+    top = float((1 << bits) - 1)
+    d = float(hi) - float(lo)
+    if d <= 0.0:
+        return np.zeros(np.shape(v), dtype=np.uint32)
+    t = (np.asarray(v, np.float64) - float(lo)) / d * top
+    return np.rint(np.clip(t, 0.0, top)).astype(np.uint32)
+
+
+def _uncode(c, lo, hi, bits):
+    top = float((1 << bits) - 1)
+    return (float(lo) + np.asarray(c, np.float64) / top * (float(hi) - float(lo))).astype(np.float32)
+
+
+def pack_eval(params, H, W):
+    """Pack float32[11, N] sites: returns (uint32[N, 4] words, float32[10] q)."""
+    p = np.asarray(params, dtype=np.float32)
+    N = p.shape[1]
+    act = p[PX] >= 0
+    lt, rr = _fold_b(p)
+    vals = (lt, rr, p[PCR], p[PCG], p[PCB])
+    q = np.zeros(10, dtype=np.float32)
+    for i, v in enumerate(vals):
+        if act.any():
+            q[2 * i], q[2 * i + 1] = v[act].min(), v[act].max()
+    codes = [_code(v, q[2 * i], q[2 * i + 1], PACK_BITS[i]) for i, v in enumerate(vals)]
+    xq = np.rint(np.clip(p[PX].astype(np.float64) / W, 0.0, 1.0) * 32767.0).astype(np.uint32)
+    yq = np.rint(np.clip(p[PY].astype(np.float64) / H, 0.0, 1.0) * 32767.0).astype(np.uint32)
+    th = np.arctan2(p[PUY].astype(np.float64), p[PUX].astype(np.float64))
+    aq = np.rint(np.clip((th + math.pi) / (2.0 * math.pi), 0.0, 1.0) * 65535.0).astype(np.uint32)
+    ah = p[PA].astype(np.float16).view(np.uint16).astype(np.uint32)
+    w = np.zeros((N, 4), dtype=np.uint32)
+    w[:, 0] = xq | (yq << np.uint32(15)) | (np.uint32(1) << np.uint32(31))
+    w[:, 1] = codes[2] | (codes[3] << np.uint32(11)) | (codes[4] << np.uint32(22))
+    w[:, 2] = codes[0] | (codes[1] << np.uint32(16))
+    w[:, 3] = aq | (ah << np.uint32(16))
+    w[~act] = 0
+    return w, q
+
+
+def unpack_eval(words, q, H, W):
+    """float32[11, N] sites from packed words (b = 0; inactive: x = y = -1)."""
+    w = np.asarray(words, dtype=np.uint32)
+    N = w.shape[0]
+    p = np.zeros((N_PARAMS, N), dtype=np.float32)
+    act = (w[:, 0] >> np.uint32(31)) & np.uint32(1) == 1
+    p[PX] = ((w[:, 0] & np.uint32(0x7FFF)).astype(np.float64) / 32767.0 * W).astype(np.float32)
+    p[PY] = (((w[:, 0] >> np.uint32(15)) & np.uint32(0x7FFF)).astype(np.float64) / 32767.0 * H).astype(np.float32)
+    p[PLOGTAU] = _uncode(w[:, 2] & np.uint32(0xFFFF), q[0], q[1], 16)
+    p[PR] = _uncode(w[:, 2] >> np.uint32(16), q[2], q[3], 16)
+    p[PCR] = _uncode(w[:, 1] & np.uint32(0x7FF), q[4], q[5], 11)
+    p[PCG] = _uncode((w[:, 1] >> np.uint32(11)) & np.uint32(0x7FF), q[6], q[7], 11)
+    p[PCB] = _uncode(w[:, 1] >> np.uint32(22), q[8], q[9], 10)
+    th = (w[:, 3] & np.uint32(0xFFFF)).astype(np.float64) / 65535.0 * (2.0 * math.pi) - math.pi
+    p[PUX] = np.cos(th).astype(np.float32)
+    p[PUY] = np.sin(th).astype(np.float32)
+    p[PA] = (w[:, 3] >> np.uint32(16)).astype(np.uint16).view(np.float16).astype(np.float32)
+    p[PX, ~act] = -1.0
+    p[PY, ~act] = -1.0
+    return p
