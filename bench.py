@@ -24,7 +24,9 @@ Legs on one GPU (each can be skipped):
           iterations, PSNR of both;
   c5      a Poisson request stream (70% random-access decodes on resident
           site sets, 30% encodes) served with continuous batching vs the plain
-          FIFO loop at 0.7x the plain loop's measured capacity: p50/p99.
+          FIFO loop at 0.7x the plain loop's measured capacity: p50/p99;
+  decode  random-access decode on a 1M-site resident set from the prepared
+          48-byte table vs the packed 16-byte evaluation records.
 
 With N>1 (torchrun) every rank trains its own image (weak scaling, no
 data-path collective); value = all pixels / max-over-ranks time.
@@ -65,6 +67,7 @@ def parse():
     ap.add_argument("--no-c3", action="store_true", help="skip the 2048^2 render+backward leg")
     ap.add_argument("--no-c4", action="store_true", help="skip the batched-vs-plain leg")
     ap.add_argument("--no-c5", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-decode", action="store_true", help="skip the packed-decode leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--legs-only", default="", help="comma list of legs to run alone (encode,c3,c4,c5)")
     ap.add_argument("--c4-iters", type=int, default=100, help="training iterations of the c4 leg")
@@ -302,7 +305,7 @@ def run_ours(args):
     }
     del enc
     if world == 1:
-        want = [k for k in ("encode", "c3", "c4", "c5") if not getattr(args, "no_" + k)]
+        want = [k for k in ("encode", "c3", "c4", "c5", "decode") if not getattr(args, "no_" + k)]
         for leg in want:
             try:
                 line[leg] = LEGS[leg](capi, dev, peak, peak_kind, args)
@@ -396,6 +399,20 @@ def c3_leg(capi, dev, peak, peak_kind, args, iters=10):
         b_ms.append(e1.elapsed_time(e2))
     capi.sad_trace_enable(False)
     trace = capi.sad_trace_collect()
+    # the paper's evaluation render from the packed 16-byte records
+    words, q = capi.sad_pack_sites(pt, H, W)
+    qh = q.cpu()
+    rgb_p = torch.empty_like(rgb)
+    for _ in range(3):
+        capi.sad_render_packed(words, qh, N, H, W, K, a, rgb_p)
+    pk_ms = []
+    for _ in range(iters):
+        e0, e1 = E(), E()
+        e0.record()
+        capi.sad_render_packed(words, qh, N, H, W, K, a, rgb_p)
+        e1.record()
+        torch.cuda.synchronize()
+        pk_ms.append(e0.elapsed_time(e1))
     P = H * W
     rb = statistics.mean(r_ms)
     bb = statistics.mean(b_ms)
@@ -410,6 +427,8 @@ def c3_leg(capi, dev, peak, peak_kind, args, iters=10):
         "workload": "2048x2048, 262144 random anisotropic sites, K=16, map from seed + 16 passes",
         "mpix_per_s_fwd_bwd": round(P / ((rb + bb) / 1e3) / 1e6, 1),
         "render_ms": round(rb, 4), "backward_ms": round(bb, 4), "jfa_16_passes_ms": round(jfa_ms, 3),
+        "render_packed_16B_ms": round(statistics.mean(pk_ms), 4),
+        "render_packed_max_abs_diff": round(float((rgb - rgb_p).abs().max().item()), 5),
         "records": used, "ws_status": st,
         "kernels_ms": {k: round(ms / max(n, 1), 5) for k, (n, ms) in sorted(trace.items())},
         "roofline_render": roof(render_bytes, rb),
@@ -568,7 +587,54 @@ def c5_leg(capi, dev, peak, peak_kind, args, seed=5000, details=False):
     return out
 
 
-LEGS = {"encode": encode_leg, "c3": c3_leg, "c4": c4_leg, "c5": c5_leg}
+def decode_leg(capi, dev, peak, peak_kind, args, n_query=1 << 20, n_sites=1 << 20):
+    """Random-access decode on the largest config-5 resident set (1M random
+    anisotropic sites, P = N/0.06): the prepared 48-byte table vs the packed
+    16-byte evaluation records (App. "Data Layout and Packing")."""
+    import torch
+    from paper_2604_21984_gb300 import inputs as gen
+    side = int(round(math.sqrt(n_sites / 0.06)))
+    H = W = side
+    K = 16
+    pt = torch.from_numpy(gen.sites_random_spd(H, W, n_sites, seed=6000)).to(dev)
+    prep = capi.empty_prep(n_sites, dev)
+    capi.sad_prepare_sites(pt, H, W, prep)
+    a, b = capi.empty_map(H, W, K, dev), capi.empty_map(H, W, K, dev)
+    capi.sad_topk_seed(prep, n_sites, H, W, K, a)
+    lb = math.ceil(math.log2(side))
+    for t in range(16):
+        s = max(1, (1 << lb) >> (min(t, lb - 1) + 1))
+        capi.sad_update_topk(prep, n_sites, H, W, K, a, b, (s << 16) | t, 2, 11)
+        a, b = b, a
+    words, q = capi.sad_pack_sites(pt, H, W)
+    qh = q.cpu()
+    xy = torch.from_numpy(gen.uniform_points(n_query, H, W, seed=6001)).to(dev)
+    r1 = torch.empty((n_query, 3), dtype=torch.float32, device=dev)
+    r2 = torch.empty_like(r1)
+    E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    res = {}
+    for name, fn in (("prepared_48B", lambda: capi.sad_decode_points(prep, n_sites, H, W, K, a, xy, r1)),
+                     ("packed_16B", lambda: capi.sad_decode_packed(words, qh, n_sites, H, W, K, a, xy, r2))):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(10):
+            e0, e1 = E(), E()
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        res[name] = {"ms": round(statistics.median(ms), 4),
+                     "mqueries_per_s": round(n_query / statistics.median(ms) / 1e3, 1)}
+    return {"workload": f"{n_query} uniform queries on {n_sites} random anisotropic sites, "
+                        f"{H}x{W} map from 16 passes, K=16",
+            **res, "site_bytes": {"prepared": 48, "packed": 16},
+            "max_abs_colour_diff_packed_vs_prepared": round(float((r1 - r2).abs().max().item()), 5)}
+
+
+LEGS = {"encode": encode_leg, "c3": c3_leg, "c4": c4_leg, "c5": c5_leg, "decode": decode_leg}
 
 
 # ----------------------------------------------------------------------------

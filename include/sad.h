@@ -422,6 +422,39 @@ int sad_decode_batch(const sad_batch_image* images, int32_t B, int32_t K, const 
                      const float* xy, const int32_t* query_image, int64_t n, float* rgb,
                      void* stream);
 
+/*
+ * Packed 16-byte evaluation sites (App. "Data Layout and Packing", Packed
+ * storage for evaluation).  Per site four 32-bit words:
+ *   w0 = x/W, y/H as 15-bit UNORM (bits 0-14, 15-29), active flag bit 31
+ *   w1 = colour r, g, b as 11/11/10-bit UNORM over the per-image ranges
+ *   w2 = (log tau', r') as 16/16-bit UNORM over the per-image ranges
+ *   w3 = angle of u as a 16-bit UNORM code over [-pi, pi] (bits 0-15), a as
+ *        float16 (bits 16-31)
+ * with b folded in exactly: log tau' = log tau + b/2, r' = r e^{-b/2} (the
+ * unpacked sites have b = 0).  q = float32[10]: (lo, hi) of log tau', r',
+ * colour r, g, b over the active sites.  Codes are round-half-even of
+ * (v - lo)/(hi - lo) * (2^bits - 1) computed in double; inactive sites pack
+ * to four zero words and unpack with x = y = -1.
+ *
+ * sad_pack_sites: params float32[11][capacity] -> packed uint32[capacity][4]
+ *   (16-byte aligned) and q (DEVICE float32[10]).
+ * sad_unpack_sites: packed + q (DEVICE) -> params float32[11][capacity].
+ * sad_decode_packed: sad_decode_points reading the packed records (each
+ *   listed site unpacked in float32 on the fly); q_host: HOST float32[10].
+ * sad_render_packed: sad_render reading the packed records (the paper's
+ *   evaluation render); q_host: HOST float32[10].
+ * Library additions with no counterpart in the paper beyond the format.
+ */
+int sad_pack_sites(const float* params, int32_t capacity, int32_t H, int32_t W, uint32_t* packed,
+                   float* q, void* stream);
+int sad_unpack_sites(const uint32_t* packed, const float* q, int32_t capacity, int32_t H, int32_t W,
+                     float* params, void* stream);
+int sad_decode_packed(const uint32_t* packed, const float* q_host, int32_t capacity, int32_t H,
+                      int32_t W, int32_t K, const uint32_t* map, const float* xy, int64_t n,
+                      float* rgb, void* stream);
+int sad_render_packed(const uint32_t* packed, const float* q_host, int32_t capacity, int32_t H,
+                      int32_t W, int32_t K, const uint32_t* map, float* rgb, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -129,6 +129,16 @@ _SIGS = {
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(AdamHparams),
                                       ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_size_t, ctypes.c_void_p]),
+    "sad_pack_sites": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "sad_unpack_sites": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "sad_decode_packed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
+    "sad_render_packed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p]),
     "sad_batch_update": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                         ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_int64, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
@@ -546,3 +556,46 @@ def sad_batch_update(table, K, J, prep, total_cap, map_in, map_out, total_pixels
                                   _ptr(map_out, torch.int32, "map_out", total_pixels * K), total_pixels,
                                   _ptr(state, torch.int32, "state"), state.shape[0], _stream(stream)),
            "sad_batch_update")
+
+
+def sad_pack_sites(params, H, W, packed=None, q=None, stream=None):
+    """Packed 16-byte evaluation records: (int32[cap, 4] words, float32[10] q) on the device."""
+    cap = params.shape[1]
+    if packed is None:
+        packed = torch.empty((max(cap, 1), 4), dtype=torch.int32, device=params.device)
+    if q is None:
+        q = torch.empty(10, dtype=torch.float32, device=params.device)
+    _check(lib().sad_pack_sites(_ptr(params, torch.float32, "params", N_PARAMS * cap), cap, H, W,
+                                _ptr(packed, torch.int32, "packed"), _ptr(q, torch.float32, "q", 10),
+                                _stream(stream)), "sad_pack_sites")
+    return packed, q
+
+
+def sad_unpack_sites(packed, q, cap, H, W, params=None, stream=None):
+    if params is None:
+        params = torch.empty((N_PARAMS, cap), dtype=torch.float32, device=packed.device)
+    _check(lib().sad_unpack_sites(_ptr(packed, torch.int32, "packed"), _ptr(q, torch.float32, "q", 10), cap,
+                                  H, W, _ptr(params, torch.float32, "params", N_PARAMS * cap),
+                                  _stream(stream)), "sad_unpack_sites")
+    return params
+
+
+def sad_decode_packed(packed, q, cap, H, W, K, map_in, xy, rgb, stream=None):
+    """q: the 10 range floats (a host sequence or tensor; read on the host)."""
+    qh = (ctypes.c_float * 10)(*[float(v) for v in (q.tolist() if hasattr(q, "tolist") else q)])
+    n = xy.shape[0]
+    _check(lib().sad_decode_packed(_ptr(packed, torch.int32, "packed"), ctypes.cast(qh, ctypes.c_void_p), cap,
+                                   H, W, K, _ptr(map_in, torch.int32, "map", H * W * K),
+                                   _ptr(xy, torch.float32, "xy", 2 * n), n,
+                                   _ptr(rgb, torch.float32, "rgb", 3 * n), _stream(stream)),
+           "sad_decode_packed")
+    return rgb
+
+
+def sad_render_packed(packed, q, cap, H, W, K, map_in, rgb, stream=None):
+    qh = (ctypes.c_float * 10)(*[float(v) for v in (q.tolist() if hasattr(q, "tolist") else q)])
+    _check(lib().sad_render_packed(_ptr(packed, torch.int32, "packed"), ctypes.cast(qh, ctypes.c_void_p), cap,
+                                   H, W, K, _ptr(map_in, torch.int32, "map", H * W * K),
+                                   _ptr(rgb, torch.float32, "rgb", H * W * 3), _stream(stream)),
+           "sad_render_packed")
+    return rgb
