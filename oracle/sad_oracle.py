@@ -28,6 +28,7 @@ Part 2 (fp32, the top-K propagation as the kernel's precision decides it):
   splitmix64 / inject_ids   App. "Candidate Field and Jump Schedule" seeded stochastic injection (counter-based)
   topk_seed_fp32    App. "Candidate Field and Jump Schedule", JFA prepass seed pass
   topk_pass_fp32    Sec. 4.3 update C_t = topK(C_{t-1} U P_t U G_t)
+  jfa_flood_fp32    App. "Candidate Field and Jump Schedule", JFA prepass flood pass (3x3, first 4 slots)
 Part 3: gradient-weighted initialisation (Sec. 4.4).
 Part 4: adaptive budget: statistics, densify split, prune (Sec. 4.5).
 Part 5: packed 16-byte evaluation sites (App. "Data Layout and Packing",
@@ -580,6 +581,42 @@ def topk_pass_fp32(prep, ids_in, H, W, K, code, J, seed, pixels=None):
     ell = score_fp32(prep, safe, px, py)
     valid &= ~np.isnan(ell)
     return select_topk(pool, ell, valid, K)
+
+
+def jfa_flood_fp32(prep, ids_in, H, W, code, slots=4):
+    """One flood pass of the JFA prepass (App. "Candidate Field and Jump
+    Schedule", JFA prepass): each pixel pools the first ``slots`` entries
+    (the first candidate texture) of the lists of the 3x3 pixels at offsets
+    {-s, 0, s}^2 around it, itself included (s = jump distance in ``code``;
+    pixels outside the image are skipped), drops the sentinel, out-of-range,
+    inactive and NaN-score entries, collapses duplicates, and writes the
+    ``slots`` best by (l descending, id ascending) into its first ``slots``
+    entries; the rest of its list is copied unchanged.  No injection.  Reads
+    ``ids_in`` only (Jacobi).  Returns uint32[P, K]."""
+    ids_in = np.asarray(ids_in, dtype=np.uint32)
+    cap = len(prep["x"])
+    pixels = np.arange(H * W, dtype=np.int64)
+    s = (code >> 16) & 0xFFFF
+    row, col = np.divmod(pixels, W)
+    pools = []
+    for ddy in (-s, 0, s):
+        for ddx in (-s, 0, s):
+            nc, nr = col + ddx, row + ddy
+            inside = (nc >= 0) & (nc < W) & (nr >= 0) & (nr < H)
+            nb = np.where(inside, nr * W + nc, 0)
+            lst = ids_in[nb, :slots].astype(np.int64)
+            pools.append(np.where(inside[:, None], lst, INVALID))
+    pool = np.concatenate(pools, axis=1)
+    valid = (pool != INVALID) & (pool >= 0) & (pool < cap)
+    safe = np.where(valid, pool, 0)
+    valid &= prep["active"][safe]
+    px = (col.astype(F32) + F32(0.5)).astype(F32)[:, None]
+    py = (row.astype(F32) + F32(0.5)).astype(F32)[:, None]
+    ell = score_fp32(prep, safe, px, py)
+    valid &= ~np.isnan(ell)
+    out = ids_in.copy()
+    out[:, :slots] = select_topk(pool, ell, valid, slots)
+    return out
 
 
 def propagate_fp32(params, H, W, K, passes, J, seed, ids_in=None, t0=0):

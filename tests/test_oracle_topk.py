@@ -194,3 +194,63 @@ def test_convergence_like_paper_table(oracle):
             em[t + 1] = oracle.topk_match_stats(ids[sample], ex)[1]
     assert em[16] >= em[8] - 0.02
     assert em[16] >= min(low_density) - 0.08
+
+
+def _flood_brute(oracle, prep, ids, H, W, code, slots=4):
+    """Per pixel, in plain Python: pool the first `slots` entries of the 3x3
+    neighbourhood at step s, score each distinct valid active id, keep the
+    best `slots` by (logit desc, id asc)."""
+    s = code >> 16
+    cap = len(prep["x"])
+    out = ids.copy()
+    for r in range(H):
+        for c in range(W):
+            cand = set()
+            for dy in (-s, 0, s):
+                for dx in (-s, 0, s):
+                    rr, cc = r + dy, c + dx
+                    if 0 <= rr < H and 0 <= cc < W:
+                        for i in ids[rr * W + cc, :slots]:
+                            i = int(i)
+                            if i < cap and prep["active"][i]:
+                                cand.add(i)
+            scored = []
+            for i in cand:
+                l = oracle.score_fp32(prep, np.array([[i]]), np.float32([[c + 0.5]]), np.float32([[r + 0.5]]))[0, 0]
+                if not np.isnan(l):
+                    scored.append((-float(l), i))
+            scored.sort()
+            row = [i for _, i in scored[:slots]] + [oracle.INVALID] * (slots - min(slots, len(scored)))
+            out[r * W + c, :slots] = row
+    return out
+
+
+def test_jfa_flood_matches_brute_force(oracle):
+    H, W, K = 12, 17, 8
+    p = gen.sites_isotropic(gen.image_sinusoid_polygons(H, W, seed=5), 30, seed=6)
+    p = gen.deactivate_random(p, 0.2, seed=7)
+    prep = oracle.prepare_fp32(p, H, W)
+    ids = gen.random_map(H * W, K, 30, seed=8, invalid_frac=0.3)
+    for s in (1, 2, 4):
+        code = (s << 16) | 3
+        got = oracle.jfa_flood_fp32(prep, ids, H, W, code)
+        ref = _flood_brute(oracle, prep, ids, H, W, code)
+        np.testing.assert_array_equal(got, ref)
+        np.testing.assert_array_equal(got[:, 4:], ids[:, 4:])   # other slots untouched
+
+
+def test_jfa_flood_reaches_nearest_site(oracle):
+    """Seed + log2 passes of the flood (jump schedule B/2 ... 1): with
+    isotropic unit-scale sites, slot 0 is the Euclidean-nearest site for
+    nearly every pixel (the JFA property)."""
+    H, W = 48, 64
+    img = gen.image_sinusoid_polygons(H, W, seed=9)
+    p = gen.sites_isotropic(img, 60, seed=10, scale_px=1.0)
+    prep = oracle.prepare_fp32(p, H, W)
+    ids = oracle.topk_seed_fp32(prep, H, W, 4)
+    lb = int(np.ceil(np.log2(max(H, W))))
+    for t in range(lb):
+        ids = oracle.jfa_flood_fp32(prep, ids, H, W, oracle.step_code(t, H, W))
+    exact, _ = oracle.exact_topk(p, H, W, 4)
+    frac = (ids[:, 0] == exact[:, 0]).mean()
+    assert frac >= 0.97, frac
