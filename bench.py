@@ -374,6 +374,20 @@ def c3_leg(capi, dev, peak, peak_kind, args, iters=10):
         a, b = b, a
     torch.cuda.synchronize()
     jfa_ms = (time.perf_counter() - t0) * 1e3
+    # the JFA 3x3 flood prepass (seed + 11 flood passes) + 4 propagation passes
+    fa, fb = capi.empty_map(H, W, K, dev), capi.empty_map(H, W, K, dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    capi.sad_topk_seed(prep, N, H, W, K, fa)
+    for t in range(11):
+        capi.sad_jfa_flood(prep, N, H, W, K, fa, fb, ((2048 >> (t + 1)) << 16) | t)
+        fa, fb = fb, fa
+    for t in range(4):
+        capi.sad_update_topk(prep, N, H, W, K, fa, fb, (1 << 16) | (100 + t), 2, 11)
+        fa, fb = fb, fa
+    torch.cuda.synchronize()
+    flood_ms = (time.perf_counter() - t0) * 1e3
+    del fa, fb
     rgb = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
     g = torch.from_numpy(gen.grad_image(H, W, seed=3002) / (H * W)).to(dev)
     grads = torch.empty((11, N), dtype=torch.float32, device=dev)
@@ -427,6 +441,7 @@ def c3_leg(capi, dev, peak, peak_kind, args, iters=10):
         "workload": "2048x2048, 262144 random anisotropic sites, K=16, map from seed + 16 passes",
         "mpix_per_s_fwd_bwd": round(P / ((rb + bb) / 1e3) / 1e6, 1),
         "render_ms": round(rb, 4), "backward_ms": round(bb, 4), "jfa_16_passes_ms": round(jfa_ms, 3),
+        "flood_prepass_11_plus_4_passes_ms": round(flood_ms, 3),
         "render_packed_16B_ms": round(statistics.mean(pk_ms), 4),
         "render_packed_max_abs_diff": round(float((rgb - rgb_p).abs().max().item()), 5),
         "records": used, "ws_status": st,

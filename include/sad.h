@@ -104,6 +104,21 @@ int sad_topk_seed(const float* prep, int32_t capacity, int32_t H, int32_t W, int
                   uint32_t* map, void* stream);
 
 /*
+ * sad_jfa_flood -- one flood pass of the JFA prepass (App. "Candidate Field
+ * and Jump Schedule", JFA prepass): every pixel pools slots 0..3 (the first
+ * candidate plane) of the lists of the 3x3 pixels at offsets {-s, 0, s}^2
+ * around it, itself included (s = step_code >> 16; outside pixels skipped),
+ * drops invalid / inactive / NaN entries and duplicates, and writes the 4
+ * best by (logit descending, id ascending) -- the R2/R13 order and fp32
+ * score of sad_update_topk -- into its slots 0..3; the other planes are
+ * copied.  No injection.  A full refresh is sad_topk_seed, ceil(log2
+ * max(W, H)) flood passes at the jump schedule, then propagation passes.
+ * map_in / map_out: K/4 uint4 planes, must not overlap.
+ */
+int sad_jfa_flood(const float* prep, int32_t capacity, int32_t H, int32_t W, int32_t K,
+                  const uint32_t* map_in, uint32_t* map_out, uint32_t step_code, void* stream);
+
+/*
  * sad_update_topk -- one propagation pass of the per-pixel top-K field
  * (Sec. 4.3, update C_t = topK over C_{t-1} U P_t U G_t).  Pool of pixel x:
  * its own list in map_in, the lists of the 4 neighbours at (+-s,0), (0,+-s)

@@ -80,6 +80,9 @@ _SIGS = {
                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int32,
                                        ctypes.c_uint64, ctypes.c_void_p]),
+    "sad_jfa_flood": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
+                                     ctypes.c_void_p]),
     "sad_render": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                   ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_void_p]),
@@ -599,3 +602,11 @@ def sad_render_packed(packed, q, cap, H, W, K, map_in, rgb, stream=None):
                                    _ptr(rgb, torch.float32, "rgb", H * W * 3), _stream(stream)),
            "sad_render_packed")
     return rgb
+
+
+def sad_jfa_flood(prep, cap, H, W, K, map_in, map_out, step_code, stream=None):
+    _check(lib().sad_jfa_flood(_ptr(prep, torch.float32, "prep"), cap, H, W, K,
+                               _ptr(map_in, torch.int32, "map_in", H * W * K),
+                               _ptr(map_out, torch.int32, "map_out", H * W * K), step_code & 0xFFFFFFFF,
+                               _stream(stream)), "sad_jfa_flood")
+    return map_out

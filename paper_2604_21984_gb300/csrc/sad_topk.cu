@@ -66,6 +66,44 @@ __global__ void __launch_bounds__(kUpdThreads) k_topk_update(const float4* __res
                                     key_id(v[4 * j + 3]));
 }
 
+// ---------------------------------------------------------------------------
+// JFA prepass flood pass: the 3x3 neighbourhood's first four slots -> the
+// best four in slot 0..3 (App. "Candidate Field and Jump Schedule", JFA
+// prepass); the other slots are copied.
+// ---------------------------------------------------------------------------
+template <int K>
+__global__ void __launch_bounds__(kUpdThreads) k_jfa_flood(const float4* __restrict__ geo,
+                                                           const float4* __restrict__ met, int cap,
+                                                           int H, int W,
+                                                           const uint4* __restrict__ map_in,
+                                                           uint4* __restrict__ map_out, int s) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = blockIdx.y * blockDim.y + threadIdx.y;
+  if (col >= W || row >= H) return;
+  const size_t P = static_cast<size_t>(H) * W;
+  const size_t q = static_cast<size_t>(row) * W + col;
+  const float px = __fadd_rn(static_cast<float>(col), 0.5f);
+  const float py = __fadd_rn(static_cast<float>(row), 0.5f);
+  const SiteRange sr{0u, static_cast<uint32_t>(cap)};
+  uint64_t v[4] = {0ull, 0ull, 0ull, 0ull};
+#pragma unroll 1
+  for (int d = 0; d < 9; ++d) {
+    const int nc = col + (d % 3 - 1) * s, nr = row + (d / 3 - 1) * s;
+    if (nc < 0 || nc >= W || nr < 0 || nr >= H) continue;
+    const uint4 w = ldg(&map_in[static_cast<size_t>(nr) * W + nc]);
+    const uint32_t id4[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (list_has<4>(v, id4[u])) continue;
+      const uint64_t c = cand_key(id4[u], sr, px, py, geo, met);
+      if (c > v[3]) list_insert<4>(v, c);
+    }
+  }
+  map_out[q] = make_uint4(key_id(v[0]), key_id(v[1]), key_id(v[2]), key_id(v[3]));
+#pragma unroll
+  for (int j = 1; j < K / 4; ++j) map_out[j * P + q] = ldg(&map_in[j * P + q]);
+}
+
 }  // namespace sad
 
 using namespace sad;
@@ -104,6 +142,34 @@ int sad_topk_seed(const float* prep, int32_t capacity, int32_t H, int32_t W, int
   { TraceScope tr_(as_stream(stream), "k_seed"); k_seed<<<(capacity + bs - 1) / bs, bs, 0, as_stream(stream)>>>(p4, p4 + capacity, capacity, H,
                                                                   W, map); }
   return check_launch("k_seed");
+}
+
+int sad_jfa_flood(const float* prep, int32_t capacity, int32_t H, int32_t W, int32_t K,
+                  const uint32_t* map_in, uint32_t* map_out, uint32_t step_code, void* stream) {
+  if (int st = check_problem(capacity, H, W, K, true)) return st;
+  if (!map_in || !map_out || (!prep && capacity > 0)) return einval("sad_jfa_flood: null pointer");
+  if (!aligned16(map_in) || !aligned16(map_out) || !aligned16(prep))
+    return einval("sad_jfa_flood: pointers must be 16-byte aligned");
+  const size_t P = static_cast<size_t>(H) * W;
+  const char* a = reinterpret_cast<const char*>(map_in);
+  const char* b = reinterpret_cast<const char*>(map_out);
+  if (a < b + P * K * 4 && b < a + P * K * 4) return einval("sad_jfa_flood: maps overlap");
+  const float4* p4 = reinterpret_cast<const float4*>(prep);
+  const dim3 block(32, 8);
+  const dim3 grid((W + 31) / 32, (H + 7) / 8);
+  const int s = static_cast<int>(step_code >> 16);
+  cudaStream_t st = as_stream(stream);
+  const uint4* in = reinterpret_cast<const uint4*>(map_in);
+  uint4* out = reinterpret_cast<uint4*>(map_out);
+  {
+    TraceScope tr_(st, "k_jfa_flood");
+    switch (K) {
+      case 4: k_jfa_flood<4><<<grid, block, 0, st>>>(p4, p4 + capacity, capacity, H, W, in, out, s); break;
+      case 8: k_jfa_flood<8><<<grid, block, 0, st>>>(p4, p4 + capacity, capacity, H, W, in, out, s); break;
+      default: k_jfa_flood<16><<<grid, block, 0, st>>>(p4, p4 + capacity, capacity, H, W, in, out, s); break;
+    }
+  }
+  return check_launch("k_jfa_flood");
 }
 
 int sad_update_topk(const float* prep, int32_t capacity, int32_t H, int32_t W, int32_t K,

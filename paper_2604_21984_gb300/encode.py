@@ -41,6 +41,7 @@ class EncodeConfig:
     fused: bool = True   # one sad_train_step per iteration (else the separate calls)
     cand_every: int = 1  # f_cand: refresh the candidate lists every this many iterations
     cand_passes: int = 1  # n_cand: propagation passes per refresh
+    prepass: str = "propagate"   # warm-up: "propagate" (jump schedule) or "flood" (JFA 3x3 prepass)
     keep_grads: bool = False   # fused: also write the step's gradients to Encoder.grads
     extra: dict = field(default_factory=dict)
 
@@ -60,13 +61,17 @@ def psnr_from_loss(loss: float) -> float:
     return float("inf") if mse <= 0 else 10.0 * math.log10(1.0 / mse)
 
 
-def warm_start(target, n0, params, prep, map_a, map_b, K, J, lambda_init, seed, stream=None):
+def warm_start(target, n0, params, prep, map_a, map_b, K, J, lambda_init, seed, stream=None,
+               prepass="propagate", passes_after=4):
     """Gradient-weighted sites (Sec. 4.4) with tau s d0 = 4, d0 = sqrt(P/n0),
-    then the top-K field's JFA warm-up: seed + ceil(log2 max(H, W)) passes
-    (Sec. 4.3) with injection seed `seed + 0x5AD`.  params: float32[11, cap]
+    then the top-K field's warm-up: seed + ceil(log2 max(H, W)) propagation
+    passes at the jump schedule (Sec. 4.3), or with prepass="flood" the JFA
+    prepass (seed + ceil(log2 max(H, W)) 3x3 flood passes, App. "Candidate
+    Field and Jump Schedule") followed by `passes_after` propagation passes
+    at jump 1; injection seed `seed + 0x5AD`.  params: float32[11, cap]
     (cap >= n0; slots from n0 on inactive); prep: the prepared table;
     map_a/map_b: the two map buffers.  Returns (current map, other map,
-    passes run)."""
+    propagation passes run)."""
     H, W = int(target.shape[0]), int(target.shape[1])
     cap = params.shape[1]
     s = 1.0 / max(H, W)
@@ -76,12 +81,18 @@ def warm_start(target, n0, params, prep, map_a, map_b, K, J, lambda_init, seed, 
     capi.sad_prepare_sites(params, H, W, prep, stream)
     capi.sad_topk_seed(prep, cap, H, W, K, map_a, stream)
     L = max(H, W)
-    n_pass = max(1, math.ceil(math.log2(L)))
-    for t in range(n_pass):
-        capi.sad_update_topk(prep, cap, H, W, K, map_a, map_b, jump_code(t, H, W), J, seed + 0x5AD,
-                             stream)
+    lb = max(1, math.ceil(math.log2(L)))
+    if prepass == "flood":
+        for t in range(lb):
+            capi.sad_jfa_flood(prep, cap, H, W, K, map_a, map_b, jump_code(t, H, W), stream)
+            map_a, map_b = map_b, map_a
+        codes = [(1 << 16) | t for t in range(passes_after)]
+    else:
+        codes = [jump_code(t, H, W) for t in range(lb)]
+    for code in codes:
+        capi.sad_update_topk(prep, cap, H, W, K, map_a, map_b, code, J, seed + 0x5AD, stream)
         map_a, map_b = map_b, map_a
-    return map_a, map_b, n_pass
+    return map_a, map_b, len(codes)
 
 
 class Encoder:
@@ -139,7 +150,8 @@ class Encoder:
         """Gradient-weighted sites and the JFA warm-up of the field."""
         c = self.cfg
         a, b, self.t_pass = warm_start(self.target, self.n0, self.params, self.prep, self.maps[0],
-                                       self.maps[1], c.K, c.J, c.lambda_init, c.seed, self.stream)
+                                       self.maps[1], c.K, c.J, c.lambda_init, c.seed, self.stream,
+                                       prepass=c.prepass)
         self.maps = [a, b]
         if c.fused:
             # Adam step 1 next; pass indices continue after the warm-up's; the

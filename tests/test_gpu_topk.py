@@ -132,3 +132,48 @@ def test_full_size_sampled_pixels(capi, oracle):
     capi.sad_update_topk(prep, p.shape[1], H, W, K, mi, mo, code, J, 99)
     ref = oracle.topk_pass_fp32(oracle.prepare_fp32(p, H, W), ids, H, W, K, code, J, 99, sample)
     assert np.array_equal(capi.ids_from_map(mo)[sample], ref)
+
+
+@pytest.mark.parametrize("K,s", [(4, 1), (8, 3), (16, 8), (16, 1)])
+def test_jfa_flood_bit_exact(capi, oracle, K, s):
+    H, W = 41, 58
+    p = gen.sites_random_spd(H, W, 500, seed=K + s)
+    p = gen.deactivate_random(p, 0.15, seed=5)
+    _, prep = prepare(capi, p, H, W)
+    ids = gen.random_map(H * W, K, p.shape[1] + 20, seed=6, invalid_frac=0.25)   # some ids out of range
+    out = capi.empty_map(H, W, K)
+    capi.sad_jfa_flood(prep, p.shape[1], H, W, K, capi.map_from_ids(ids), out, (s << 16) | 5)
+    ref = oracle.jfa_flood_fp32(oracle.prepare_fp32(p, H, W), ids, H, W, (s << 16) | 5)
+    np.testing.assert_array_equal(capi.ids_from_map(out), ref)
+
+
+def test_flood_prepass_then_propagation(capi, oracle):
+    """seed, log2 flood passes and two propagation passes, step for step
+    against the oracle; the flood prepass gives the propagation a head start
+    (higher recall of the exact top-K than as many propagation passes alone)."""
+    H, W, K, J = 64, 80, 8, 2
+    p = gen.sites_random_spd(H, W, 400, seed=77)
+    _, prep = prepare(capi, p, H, W)
+    op = oracle.prepare_fp32(p, H, W)
+    a, b = capi.empty_map(H, W, K), capi.empty_map(H, W, K)
+    capi.sad_topk_seed(prep, p.shape[1], H, W, K, a)
+    ref = oracle.topk_seed_fp32(op, H, W, K)
+    lb = int(np.ceil(np.log2(max(H, W))))
+    for t in range(lb):
+        code = oracle.step_code(t, H, W)
+        capi.sad_jfa_flood(prep, p.shape[1], H, W, K, a, b, code)
+        a, b = b, a
+        ref = oracle.jfa_flood_fp32(op, ref, H, W, code)
+    np.testing.assert_array_equal(capi.ids_from_map(a), ref)
+    for t in range(lb, lb + 2):
+        code = (1 << 16) | t
+        capi.sad_update_topk(prep, p.shape[1], H, W, K, a, b, code, J, 9)
+        a, b = b, a
+        ref = oracle.topk_pass_fp32(op, ref, H, W, K, code, J, 9)
+    np.testing.assert_array_equal(capi.ids_from_map(a), ref)
+    exact, _ = oracle.exact_topk(p, H, W, K)
+    flood_recall = oracle.topk_match_stats(ref, exact)[0]
+    vpt = oracle.propagate_fp32(p, H, W, K, lb + 2, J, 9)
+    vpt_recall = oracle.topk_match_stats(vpt, exact)[0]
+    print("recall flood+2 %.4f, propagation alone %.4f" % (flood_recall, vpt_recall))
+    assert flood_recall > 0.5
