@@ -76,3 +76,34 @@ def test_candidate_period_fused_matches_separate_calls(capi):
     assert abs(pa - pb) < 0.02, (pa, pb)
     same = (capi.ids_from_map(a.maps[0]) == capi.ids_from_map(b.maps[0])).mean()
     assert same > 0.95
+
+
+def test_full_size_fused_step_as_benchmarked(capi, oracle):
+    """The benchmark's configuration: 768x512, 32768 gradient-weighted sites
+    (capacity 65536), K=16, J=4, one fused step after three.  The new map on
+    4096 sampled pixels equals the oracle's pass bit for bit; the loss and
+    every site's gradient match the oracle's fp64 render and adjoint on the
+    new lists over the whole image."""
+    torch = pytest.importorskip("torch")
+    from paper_2604_21984_gb300.encode import EncodeConfig, Encoder
+    H, W = 512, 768
+    img = gen.image_noise_polygons_lines(H, W, seed=2000)
+    enc = Encoder(dev(img), EncodeConfig(n_sites=32768, K=16, J=4, seed=0, densify_every=0, keep_grads=True))
+    enc.init()
+    for _ in range(3):
+        enc.step()
+    torch.cuda.synchronize()
+    p0 = enc.params.cpu().numpy().copy()
+    ids0 = capi.ids_from_map(enc.maps[0])
+    code = (1 << 16) | (enc.t_pass & 0xFFFF)
+    enc.step()
+    torch.cuda.synchronize()
+    ids1 = capi.ids_from_map(enc.maps[0])
+    sample = np.random.default_rng(11).choice(H * W, 4096, replace=False)
+    ref = oracle.topk_pass_fp32(oracle.prepare_fp32(p0, H, W), ids0, H, W, 16, code, 4, 0x5AD, sample)
+    assert np.array_equal(ids1[sample], ref)
+    rgb = oracle.render(p0, H, W, ids1)
+    L, g = oracle.mse_loss_and_grad_rgb(rgb, img)
+    assert abs(enc.loss.item() - L) <= 1e-5 * L
+    grads = oracle.render_backward(p0, H, W, ids1, g)
+    assert_grads_close(enc.grads.cpu().numpy().astype(np.float64), grads)

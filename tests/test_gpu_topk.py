@@ -177,3 +177,25 @@ def test_flood_prepass_then_propagation(capi, oracle):
     vpt_recall = oracle.topk_match_stats(vpt, exact)[0]
     print("recall flood+2 %.4f, propagation alone %.4f" % (flood_recall, vpt_recall))
     assert flood_recall > 0.5
+
+
+def test_maximum_image_side(capi, oracle):
+    """An image of the largest accepted side (32768 x 12): a pass at a long
+    jump and at jump 1 on sampled pixels, bit-exact; a side above the limit
+    is rejected before any launch."""
+    H, W, K, J = 32768, 12, 8, 2
+    p = gen.sites_random_spd(H, W, 20000, seed=81)
+    ids = gen.knn_map(p, H, W, K, seed=82)
+    _, prep = prepare(capi, p, H, W)
+    mi = capi.map_from_ids(ids)
+    mo = capi.empty_map(H, W, K)
+    sample = np.random.default_rng(3).choice(H * W, 2048, replace=False)
+    op = oracle.prepare_fp32(p, H, W)
+    for t in (1, 14):
+        code = oracle.step_code(t, H, W)
+        capi.sad_update_topk(prep, p.shape[1], H, W, K, mi, mo, code, J, 5)
+        ref = oracle.topk_pass_fp32(op, ids, H, W, K, code, J, 5, sample)
+        assert np.array_equal(capi.ids_from_map(mo)[sample], ref), t
+    with pytest.raises(capi.SadError):
+        capi.sad_update_topk(prep, p.shape[1], H + 1, W, K, capi.empty_map(H + 1, W, K),
+                             capi.empty_map(H + 1, W, K), 1 << 16, J, 5)
