@@ -154,6 +154,31 @@ def gen_images(specs):
         return list(ex.map(_gen_image, specs))
 
 
+# DRAM traffic and warp instructions per launch of the timed step's dominant
+# kernel, from one ncu capture of the build whose kernel sources hash to
+# `sha` (profiles/k_step_tile_768x512_k16.md).  Reported only while the
+# sources still hash the same (a changed kernel has no counters until it is
+# captured again).
+NCU_COUNTERS = {
+    "k_step_tile": {"sources": ["sad_step.cu", "sad_tile.cuh", "sad_topk.cuh", "sad_device.cuh",
+                                "sad_adam.cuh", "sad_blend.cuh"],
+                    "sha": "417c345137b568a9", "dram_bytes": 33945856, "warp_inst": 150208379},
+}
+ISSUE_PEAK = 152 * 4 * 2.07e9   # warp instructions / s: 152 SMs x 4 schedulers x 1 issue/clk x 2070 MHz
+
+
+def ncu_counters(kernel):
+    import hashlib
+    c = NCU_COUNTERS.get(kernel)
+    if c is None:
+        return None
+    h = hashlib.sha256()
+    for f in c["sources"]:
+        with open(os.path.join(ROOT, "paper_2604_21984_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return c if h.hexdigest()[:16] == c["sha"] else None
+
+
 def reduce_max(x, dist, world, device):
     """Max over ranks of a host float (the slowest replica's time)."""
     if world <= 1:
@@ -284,10 +309,19 @@ def run_ours(args):
     roofline = None
     if kname in alg:
         achieved = alg[kname] / (kms / 1e3) / 1e9
+        ctr = ncu_counters(kname)
         roofline = {"kernel": kname, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                     "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-                    "traffic": None, "algorithmic_bytes_per_launch": alg[kname],
+                    "traffic": ctr["dram_bytes"] if ctr else None,
+                    "algorithmic_bytes_per_launch": alg[kname],
                     "avg_launch_ms": round(kms, 5), "launches": klaunch}
+        if ctr:
+            # the kernel is issue bound: its ncu instruction count over the
+            # live launch time, against the schedulers' issue rate
+            ips = ctr["warp_inst"] / (kms / 1e3)
+            roofline["issue"] = {"achieved_warp_inst_per_s": round(ips / 1e9, 1), "peak": round(ISSUE_PEAK / 1e9, 1),
+                                 "unit": "G warp-inst/s", "frac": round(ips / ISSUE_PEAK, 4),
+                                 "warp_inst_per_launch": ctr["warp_inst"]}
     launches = sum(n for n, _ in trace.values())
 
     line = {
