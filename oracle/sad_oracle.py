@@ -29,6 +29,7 @@ Part 2 (fp32, the top-K propagation as the kernel's precision decides it):
   topk_seed_fp32    App. "Candidate Field and Jump Schedule", JFA prepass seed pass
   topk_pass_fp32    Sec. 4.3 update C_t = topK(C_{t-1} U P_t U G_t)
   jfa_flood_fp32    App. "Candidate Field and Jump Schedule", JFA prepass flood pass (3x3, first 4 slots)
+  grid_dims / expand_grid   App. "Candidate Field and Jump Schedule", downscaled candidate grid
 Part 3: gradient-weighted initialisation (Sec. 4.4).
 Part 4: adaptive budget: statistics, densify split, prune (Sec. 4.5).
 Part 5: packed 16-byte evaluation sites (App. "Data Layout and Packing",
@@ -533,21 +534,44 @@ def inject_ids(seed: int, code: int, pixels, J: int, capacity: int):
     return ids.astype(np.int64)
 
 
-def topk_seed_fp32(prep, H, W, K):
+def topk_seed_fp32(prep, H, W, K, cell=1, image=None):
     """Seed pass of the JFA prepass (App. "Candidate Field and Jump Schedule"): every active site writes its id
     into slot 0 of the pixel that contains it; on a collision the smaller id
-    wins.  All other entries are the sentinel.  Returns uint32[P, K]."""
+    wins.  All other entries are the sentinel.  With a candidate grid of
+    cell x cell pixels (App. "Candidate Field and Jump Schedule", Downscaled
+    candidate grid) H, W are the grid's size, ``image`` = (H, W) of the
+    image, and the site's pixel (clamped to the image) maps to cell
+    (col // cell, row // cell).  Returns uint32[H*W, K]."""
+    Hi, Wi = (H, W) if image is None else image
     out = np.full((H * W, K), INVALID, dtype=np.uint32)
     for i in np.nonzero(prep["active"])[0]:
-        col = min(max(int(math.floor(float(prep["x"][i]))), 0), W - 1)
-        row = min(max(int(math.floor(float(prep["y"][i]))), 0), H - 1)
+        col = min(max(int(math.floor(float(prep["x"][i]))), 0), Wi - 1) // cell
+        row = min(max(int(math.floor(float(prep["y"][i]))), 0), Hi - 1) // cell
         pix = row * W + col
         out[pix, 0] = min(int(out[pix, 0]), int(i))
     return out
 
 
-def topk_pass_fp32(prep, ids_in, H, W, K, code, J, seed, pixels=None):
+def grid_dims(H, W, cell):
+    """Size of the candidate grid of an H x W image with cell x cell cells."""
+    return (H + cell - 1) // cell, (W + cell - 1) // cell
+
+
+def expand_grid(ids_grid, H, W, cell):
+    """Per-pixel lists from a candidate grid: pixel (x, y) takes the list of
+    cell (x // cell, y // cell) (integer mapping, no interpolation)."""
+    Hc, Wc = grid_dims(H, W, cell)
+    rows, cols = np.divmod(np.arange(H * W), W)
+    return np.asarray(ids_grid)[(rows // cell) * Wc + cols // cell]
+
+
+def topk_pass_fp32(prep, ids_in, H, W, K, code, J, seed, pixels=None, cell=1):
     """One propagation pass (Sec. 4.3, update of C_t), for all or some pixels.
+    With a candidate grid (cell > 1) H, W are the grid's size, the "pixels"
+    are its cells, and a cell's scores are taken at its centre
+    ((col + 0.5) cell, (row + 0.5) cell) in image pixels (App. "Candidate
+    Field and Jump Schedule", Downscaled candidate grid: the centred UV of
+    the cell).
 
     Pool = C_{t-1}(x) (the pixel's own list) U P_t(x) (the lists of the four
     neighbours at (+-s, 0), (0, +-s), s = jump distance in ``code``; neighbours
@@ -576,8 +600,8 @@ def topk_pass_fp32(prep, ids_in, H, W, K, code, J, seed, pixels=None):
     valid = (pool != INVALID) & (pool >= 0) & (pool < cap)
     safe = np.where(valid, pool, 0)
     valid &= prep["active"][safe]
-    px = (col.astype(F32) + F32(0.5)).astype(F32)[:, None]
-    py = (row.astype(F32) + F32(0.5)).astype(F32)[:, None]
+    px = ((col.astype(F32) + F32(0.5)).astype(F32) * F32(cell)).astype(F32)[:, None]
+    py = ((row.astype(F32) + F32(0.5)).astype(F32) * F32(cell)).astype(F32)[:, None]
     ell = score_fp32(prep, safe, px, py)
     valid &= ~np.isnan(ell)
     return select_topk(pool, ell, valid, K)

@@ -79,8 +79,10 @@ def test_seed_pass(oracle):
     assert len(set(m[:, 0][m[:, 0] != INV].tolist())) == (m[:, 0] != INV).sum()
 
 
-def _brute_force_pass(oracle, p, ids_in, H, W, K, t, J, seed, pixels):
-    """Per-pixel loops: gather the pool by explicit offsets, score in fp64."""
+def _brute_force_pass(oracle, p, ids_in, H, W, K, t, J, seed, pixels, cell=1, image=None):
+    """Per-pixel (per-cell) loops: gather the pool by explicit offsets, score
+    in fp64 at the pixel centre (the cell centre)."""
+    Hi, Wi = (H, W) if image is None else image
     s = oracle.jump_step(t, H, W)
     code = oracle.step_code(t, H, W)
     cap = p.shape[1]
@@ -95,7 +97,8 @@ def _brute_force_pass(oracle, p, ids_in, H, W, K, t, J, seed, pixels):
         pool += list(oracle.inject_ids(seed, code, [pix], J, cap)[0])
         cand = {int(i) for i in pool if int(i) != INV and int(i) < cap and p[0, int(i)] >= 0}
         ids = np.array(sorted(cand), dtype=np.int64)
-        ell = oracle.logits(p, H, W, ids[None, :], [col + 0.5], [row + 0.5])[0] if len(ids) else np.array([])
+        ell = (oracle.logits(p, Hi, Wi, ids[None, :], [(col + 0.5) * cell], [(row + 0.5) * cell])[0]
+               if len(ids) else np.array([]))
         order = sorted(range(len(ids)), key=lambda k: (-ell[k], ids[k]))[:K]
         out.append(([int(ids[k]) for k in order], [float(ell[k]) for k in order],
                     sorted(((float(l), int(i)) for l, i in zip(ell, ids)), reverse=True)))
@@ -254,3 +257,46 @@ def test_jfa_flood_reaches_nearest_site(oracle):
     exact, _ = oracle.exact_topk(p, H, W, 4)
     frac = (ids[:, 0] == exact[:, 0]).mean()
     assert frac >= 0.97, frac
+
+
+
+@pytest.mark.parametrize("cell", [2, 3])
+def test_grid_pass_matches_brute_force(oracle, cell):
+    """Candidate grid: the pass over cells scores at the cell centres."""
+    Hi, Wi, K, J = 23, 31, 6, 2
+    H, W = oracle.grid_dims(Hi, Wi, cell)
+    p = gen.sites_random_spd(Hi, Wi, 60, seed=80 + cell)
+    prep = oracle.prepare_fp32(p, Hi, Wi)
+    ids_in = gen.random_map(H * W, K, 60, seed=81, invalid_frac=0.2)
+    pixels = np.arange(H * W)
+    for t in (0, 2):
+        code = oracle.step_code(t, H, W)
+        got = oracle.topk_pass_fp32(prep, ids_in, H, W, K, code, J, 7, pixels, cell=cell)
+        # the brute force takes the jump from the grid's schedule too
+        ref = _brute_force_pass(oracle, p.astype(np.float64), ids_in, H, W, K, t, J, 7, pixels,
+                                cell=cell, image=(Hi, Wi))
+        mism = sum(1 for q, (r, _, _) in enumerate(ref) if [int(v) for v in got[q] if v != INV] != r)
+        assert mism <= 2, mism
+
+
+def test_grid_seed_and_expand(oracle):
+    Hi, Wi, cell = 21, 34, 4
+    H, W = oracle.grid_dims(Hi, Wi, cell)
+    assert (H, W) == (6, 9)
+    p = gen.sites_random_spd(Hi, Wi, 40, seed=90)
+    p[0, :3] = [-5.0, Wi + 7.0, 5.5]         # clamped into the image first
+    prep = oracle.prepare_fp32(p, Hi, Wi)
+    seed = oracle.topk_seed_fp32(prep, H, W, 4, cell=cell, image=(Hi, Wi))
+    for i in range(40):
+        if not prep["active"][i]:
+            continue
+        c = min(max(int(np.floor(prep["x"][i])), 0), Wi - 1) // cell
+        r = min(max(int(np.floor(prep["y"][i])), 0), Hi - 1) // cell
+        assert seed[r * W + c, 0] <= i
+    ex = oracle.expand_grid(seed, Hi, Wi, cell)
+    assert ex.shape == (Hi * Wi, 4)
+    for y in (0, 5, Hi - 1):
+        for x in (0, 7, Wi - 1):
+            np.testing.assert_array_equal(ex[y * Wi + x], seed[(y // cell) * W + x // cell])
+    # cell = 1 is the plain map
+    np.testing.assert_array_equal(oracle.expand_grid(ex, Hi, Wi, 1), ex)
