@@ -385,6 +385,7 @@ def encode_leg(capi, dev, peak, peak_kind, args, iters=2000):
                             "(Kodak @4 BPP: 40.4 dB at 2000 it, ~0.6 s); hardware not stated, "
                             "RTX 5090 implied"}
     res["cand_every_8"] = run(cand_every=8)
+    res["s_grid_2"] = run(s_grid=2)   # lists on a 2x2-pixel candidate grid (separate calls)
     return res
 
 

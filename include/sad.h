@@ -140,6 +140,28 @@ int sad_update_topk(const float* prep, int32_t capacity, int32_t H, int32_t W, i
                     int32_t n_inject, uint64_t seed, void* stream);
 
 /*
+ * Downscaled candidate grid (App. "Candidate Field and Jump Schedule",
+ * Downscaled candidate grid): the lists live on a ceil(H/s) x ceil(W/s)
+ * grid of s x s pixel cells, and a cell's candidates are scored at its
+ * centre ((col + 0.5) s, (row + 0.5) s) in image pixels; pixels map to cells
+ * by integer division (no interpolation).  H, W: the image; s_grid in
+ * [1, 64]; grid maps are K/4 uint4 planes over the cells.
+ * sad_grid_seed   -- sad_topk_seed onto the grid (a site's clamped pixel's cell).
+ * sad_grid_update -- sad_update_topk over the cells (jumps, injection counters
+ *                    and the jump schedule are in cells).
+ * sad_grid_expand -- per-pixel map (K/4 planes over H*W) from the grid, for
+ *                    the render, adjoint and statistics calls.
+ * s_grid = 1 reproduces sad_topk_seed / sad_update_topk exactly.
+ */
+int sad_grid_seed(const float* prep, int32_t capacity, int32_t H, int32_t W, int32_t s_grid,
+                  int32_t K, uint32_t* map, void* stream);
+int sad_grid_update(const float* prep, int32_t capacity, int32_t H, int32_t W, int32_t s_grid,
+                    int32_t K, const uint32_t* map_in, uint32_t* map_out, uint32_t step_code,
+                    int32_t n_inject, uint64_t seed, void* stream);
+int sad_grid_expand(const uint32_t* map_grid, int32_t H, int32_t W, int32_t s_grid, int32_t K,
+                    uint32_t* map_pixels, void* stream);
+
+/*
  * sad_render -- soft anisotropic additively weighted render (Sec. 4.2):
  * c(x) = sum_i w_i(x) c_i, w = softmax over the listed sites of
  * l_i(x) = -tau_i d_mix(x,i) (max-subtracted).  Pixels whose list holds no

@@ -83,6 +83,13 @@ _SIGS = {
     "sad_jfa_flood": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                      ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
                                      ctypes.c_void_p]),
+    "sad_grid_seed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "sad_grid_update": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_uint32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p]),
+    "sad_grid_expand": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "sad_render": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                   ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_void_p]),
@@ -610,3 +617,32 @@ def sad_jfa_flood(prep, cap, H, W, K, map_in, map_out, step_code, stream=None):
                                _ptr(map_out, torch.int32, "map_out", H * W * K), step_code & 0xFFFFFFFF,
                                _stream(stream)), "sad_jfa_flood")
     return map_out
+
+
+def grid_dims(H, W, s_grid):
+    return (H + s_grid - 1) // s_grid, (W + s_grid - 1) // s_grid
+
+
+def sad_grid_seed(prep, cap, H, W, s_grid, K, map_grid, stream=None):
+    Hc, Wc = grid_dims(H, W, s_grid)
+    _check(lib().sad_grid_seed(_ptr(prep, torch.float32, "prep"), cap, H, W, s_grid, K,
+                               _ptr(map_grid, torch.int32, "map", Hc * Wc * K), _stream(stream)),
+           "sad_grid_seed")
+    return map_grid
+
+
+def sad_grid_update(prep, cap, H, W, s_grid, K, map_in, map_out, step_code, n_inject, seed, stream=None):
+    Hc, Wc = grid_dims(H, W, s_grid)
+    _check(lib().sad_grid_update(_ptr(prep, torch.float32, "prep"), cap, H, W, s_grid, K,
+                                 _ptr(map_in, torch.int32, "map_in", Hc * Wc * K),
+                                 _ptr(map_out, torch.int32, "map_out", Hc * Wc * K), step_code & 0xFFFFFFFF,
+                                 n_inject, seed & ((1 << 64) - 1), _stream(stream)), "sad_grid_update")
+    return map_out
+
+
+def sad_grid_expand(map_grid, H, W, s_grid, K, map_pixels, stream=None):
+    Hc, Wc = grid_dims(H, W, s_grid)
+    _check(lib().sad_grid_expand(_ptr(map_grid, torch.int32, "map_grid", Hc * Wc * K), H, W, s_grid, K,
+                                 _ptr(map_pixels, torch.int32, "map", H * W * K), _stream(stream)),
+           "sad_grid_expand")
+    return map_pixels

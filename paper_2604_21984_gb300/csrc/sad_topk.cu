@@ -25,7 +25,7 @@ __global__ void k_prepare(const float* __restrict__ params, int cap, float s,
 // seed: slot 0 of the pixel holding each active site <- min id
 // ---------------------------------------------------------------------------
 __global__ void k_seed(const float4* __restrict__ geo, const float4* __restrict__ met, int cap,
-                       int H, int W, uint32_t* __restrict__ plane0) {
+                       int H, int W, int cell, int Wc, uint32_t* __restrict__ plane0) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= cap) return;
   if (met[i].w == 0.f) return;
@@ -34,7 +34,7 @@ __global__ void k_seed(const float4* __restrict__ geo, const float4* __restrict_
   int row = static_cast<int>(floorf(g.y));
   col = col < 0 ? 0 : (col >= W ? W - 1 : col);
   row = row < 0 ? 0 : (row >= H ? H - 1 : row);
-  const size_t q = static_cast<size_t>(row) * W + col;
+  const size_t q = static_cast<size_t>(row / cell) * Wc + col / cell;  // cell of a candidate grid
   atomicMin(&plane0[q * 4], static_cast<uint32_t>(i));
 }
 
@@ -49,7 +49,8 @@ __global__ void __launch_bounds__(kUpdThreads) k_topk_update(const float4* __res
                                                              int H, int W,
                                                              const uint4* __restrict__ map_in,
                                                              uint4* __restrict__ map_out,
-                                                             uint32_t code, int J, uint64_t seed) {
+                                                             uint32_t code, int J, uint64_t seed,
+                                                             float cell) {
   __shared__ uint32_t s_q[kQueue][kUpdThreads];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int col = blockIdx.x * blockDim.x + threadIdx.x;
@@ -59,7 +60,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_topk_update(const float4* __res
   const size_t q = static_cast<size_t>(row) * W + col;
   uint64_t v[K];
   pixel_update<K, kUpdThreads>(v, true, col, row, H, W, SiteRange{0u, static_cast<uint32_t>(cap)},
-                               geo, met, map_in, P, 0, code, J, seed, s_q, tid);
+                               geo, met, map_in, P, 0, code, J, seed, s_q, tid, cell);
 #pragma unroll
   for (int j = 0; j < K / 4; ++j)
     map_out[j * P + q] = make_uint4(key_id(v[4 * j]), key_id(v[4 * j + 1]), key_id(v[4 * j + 2]),
@@ -104,6 +105,52 @@ __global__ void __launch_bounds__(kUpdThreads) k_jfa_flood(const float4* __restr
   for (int j = 1; j < K / 4; ++j) map_out[j * P + q] = ldg(&map_in[j * P + q]);
 }
 
+// Candidate grid -> per-pixel lists: pixel (x, y) takes cell (x / s, y / s).
+__global__ void k_grid_expand(const uint4* __restrict__ grid, int H, int W, int s, int NP,
+                              uint4* __restrict__ out) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= W || y >= H) return;
+  const int Wc = (W + s - 1) / s, Hc = (H + s - 1) / s;
+  const size_t P = static_cast<size_t>(H) * W, Pc = static_cast<size_t>(Hc) * Wc;
+  const size_t qc = static_cast<size_t>(y / s) * Wc + x / s;
+  const size_t q = static_cast<size_t>(y) * W + x;
+  for (int j = 0; j < NP; ++j) out[j * P + q] = ldg(&grid[j * Pc + qc]);
+}
+
+// One propagation pass over an H x W grid of lists whose entries are scored
+// at ((col + 0.5) cell, (row + 0.5) cell).
+static int run_update(const float* prep, int32_t capacity, int32_t H, int32_t W, int32_t K,
+                      const uint32_t* map_in, uint32_t* map_out, uint32_t step_code,
+                      int32_t n_inject, uint64_t seed, float cell, void* stream, const char* name) {
+  if (!map_in || !map_out || (!prep && capacity > 0)) return einval("%s: null pointer", name);
+  if (!aligned16(map_in) || !aligned16(map_out) || !aligned16(prep))
+    return einval("%s: pointers must be 16-byte aligned", name);
+  if (n_inject < 0 || n_inject > 16) return einval("%s: n_inject must be in [0,16]", name);
+  const size_t P = static_cast<size_t>(H) * W;
+  if (static_cast<uint64_t>(P) * static_cast<uint64_t>(n_inject > 0 ? n_inject : 1) >= (1ull << 32))
+    return einval("%s: H*W*n_inject must be below 2^32", name);
+  const char* a = reinterpret_cast<const char*>(map_in);
+  const char* b = reinterpret_cast<const char*>(map_out);
+  const size_t bytes = P * K * sizeof(uint32_t);
+  if (a < b + bytes && b < a + bytes) return einval("%s: map_in and map_out overlap", name);
+  const float4* p4 = reinterpret_cast<const float4*>(prep);
+  const dim3 block(32, 8);
+  const dim3 grid((W + 31) / 32, (H + 7) / 8);
+  const uint4* in = reinterpret_cast<const uint4*>(map_in);
+  uint4* out = reinterpret_cast<uint4*>(map_out);
+  cudaStream_t st = as_stream(stream);
+  {
+    TraceScope tr_(st, "k_topk_update");
+    switch (K) {
+      case 4: k_topk_update<4><<<grid, block, 0, st>>>(p4, p4 + capacity, capacity, H, W, in, out, step_code, n_inject, seed, cell); break;
+      case 8: k_topk_update<8><<<grid, block, 0, st>>>(p4, p4 + capacity, capacity, H, W, in, out, step_code, n_inject, seed, cell); break;
+      default: k_topk_update<16><<<grid, block, 0, st>>>(p4, p4 + capacity, capacity, H, W, in, out, step_code, n_inject, seed, cell); break;
+    }
+  }
+  return check_launch(name);
+}
+
 }  // namespace sad
 
 using namespace sad;
@@ -140,7 +187,7 @@ int sad_topk_seed(const float* prep, int32_t capacity, int32_t H, int32_t W, int
   const float4* p4 = reinterpret_cast<const float4*>(prep);
   const int bs = 256;
   { TraceScope tr_(as_stream(stream), "k_seed"); k_seed<<<(capacity + bs - 1) / bs, bs, 0, as_stream(stream)>>>(p4, p4 + capacity, capacity, H,
-                                                                  W, map); }
+                                                                  W, 1, W, map); }
   return check_launch("k_seed");
 }
 
@@ -176,38 +223,59 @@ int sad_update_topk(const float* prep, int32_t capacity, int32_t H, int32_t W, i
                     const uint32_t* map_in, uint32_t* map_out, uint32_t step_code,
                     int32_t n_inject, uint64_t seed, void* stream) {
   if (int st = check_problem(capacity, H, W, K, true)) return st;
-  if (!map_in || !map_out || (!prep && capacity > 0)) return einval("sad_update_topk: null pointer");
-  if (!aligned16(map_in) || !aligned16(map_out) || !aligned16(prep))
-    return einval("sad_update_topk: pointers must be 16-byte aligned");
-  if (n_inject < 0 || n_inject > 16) return einval("sad_update_topk: n_inject must be in [0,16]");
-  const size_t P = static_cast<size_t>(H) * W;
-  if (static_cast<uint64_t>(P) * static_cast<uint64_t>(n_inject > 0 ? n_inject : 1) >= (1ull << 32))
-    return einval("sad_update_topk: H*W*n_inject must be below 2^32");
-  const char* a = reinterpret_cast<const char*>(map_in);
-  const char* b = reinterpret_cast<const char*>(map_out);
-  const size_t bytes = P * K * sizeof(uint32_t);
-  if (a < b + bytes && b < a + bytes) return einval("sad_update_topk: map_in and map_out overlap");
+  return run_update(prep, capacity, H, W, K, map_in, map_out, step_code, n_inject, seed, 1.f, stream,
+                    "sad_update_topk");
+}
+
+int sad_grid_seed(const float* prep, int32_t capacity, int32_t H, int32_t W, int32_t s_grid,
+                  int32_t K, uint32_t* map, void* stream) {
+  if (int st = check_problem(capacity, H, W, K, true)) return st;
+  if (s_grid < 1 || s_grid > 64) return einval("sad_grid_seed: s_grid must be in [1, 64]");
+  if (!map || (!prep && capacity > 0)) return einval("sad_grid_seed: null pointer");
+  if (!aligned16(map) || !aligned16(prep)) return einval("sad_grid_seed: pointers must be 16-byte aligned");
+  const int Hc = (H + s_grid - 1) / s_grid, Wc = (W + s_grid - 1) / s_grid;
+  const size_t Pc = static_cast<size_t>(Hc) * Wc;
+  cudaError_t e = cudaMemsetAsync(map, 0xff, Pc * K * sizeof(uint32_t), as_stream(stream));
+  if (e != cudaSuccess) {
+    set_error("sad_grid_seed memset: %s", cudaGetErrorString(e));
+    return SAD_ECUDA;
+  }
+  if (capacity == 0) return SAD_OK;
   const float4* p4 = reinterpret_cast<const float4*>(prep);
+  {
+    TraceScope tr_(as_stream(stream), "k_seed");
+    k_seed<<<(capacity + 255) / 256, 256, 0, as_stream(stream)>>>(p4, p4 + capacity, capacity, H, W,
+                                                                  s_grid, Wc, map);
+  }
+  return check_launch("k_seed");
+}
+
+int sad_grid_update(const float* prep, int32_t capacity, int32_t H, int32_t W, int32_t s_grid,
+                    int32_t K, const uint32_t* map_in, uint32_t* map_out, uint32_t step_code,
+                    int32_t n_inject, uint64_t seed, void* stream) {
+  if (int st = check_problem(capacity, H, W, K, true)) return st;
+  if (s_grid < 1 || s_grid > 64) return einval("sad_grid_update: s_grid must be in [1, 64]");
+  return run_update(prep, capacity, (H + s_grid - 1) / s_grid, (W + s_grid - 1) / s_grid, K, map_in,
+                    map_out, step_code, n_inject, seed, static_cast<float>(s_grid), stream,
+                    "sad_grid_update");
+}
+
+int sad_grid_expand(const uint32_t* map_grid, int32_t H, int32_t W, int32_t s_grid, int32_t K,
+                    uint32_t* map_pixels, void* stream) {
+  if (int st = check_problem(0, H, W, K, true)) return st;
+  if (s_grid < 1 || s_grid > 64) return einval("sad_grid_expand: s_grid must be in [1, 64]");
+  if (!map_grid || !map_pixels) return einval("sad_grid_expand: null pointer");
+  if (!aligned16(map_grid) || !aligned16(map_pixels))
+    return einval("sad_grid_expand: pointers must be 16-byte aligned");
   const dim3 block(32, 8);
   const dim3 grid((W + 31) / 32, (H + 7) / 8);
-  const uint4* in = reinterpret_cast<const uint4*>(map_in);
-  uint4* out = reinterpret_cast<uint4*>(map_out);
   cudaStream_t st = as_stream(stream);
-  switch (K) {
-    case 4:
-      { TraceScope tr_(st, "k_topk_update"); k_topk_update<4><<<grid, block, 0, st>>>(p4, p4 + capacity, capacity, H, W, in, out,
-                                               step_code, n_inject, seed); }
-      break;
-    case 8:
-      { TraceScope tr_(st, "k_topk_update"); k_topk_update<8><<<grid, block, 0, st>>>(p4, p4 + capacity, capacity, H, W, in, out,
-                                               step_code, n_inject, seed); }
-      break;
-    default:
-      { TraceScope tr_(st, "k_topk_update"); k_topk_update<16><<<grid, block, 0, st>>>(p4, p4 + capacity, capacity, H, W, in, out,
-                                                step_code, n_inject, seed); }
-      break;
+  {
+    TraceScope tr_(st, "k_grid_expand");
+    k_grid_expand<<<grid, block, 0, st>>>(reinterpret_cast<const uint4*>(map_grid), H, W, s_grid, K / 4,
+                                         reinterpret_cast<uint4*>(map_pixels));
   }
-  return check_launch("k_topk_update");
+  return check_launch("k_grid_expand");
 }
 
 }  // extern "C"

@@ -99,7 +99,8 @@ __device__ __forceinline__ uint64_t cand_key(uint32_t id, SiteRange sr, float px
   return make_key(l, id);
 }
 
-// The K best keys of pixel (col, row) of an H x W image after one pass.
+// The K best keys of pixel (col, row) of an H x W image after one pass
+// (with a candidate grid: of cell (col, row) of an H x W grid).
 // map_in: K/4 planes of uint4 with plane stride P; the image's pixels start
 // at plane index pix_off.  q_local = row*W + col (injection counter).  Threads
 // outside the image pass inimg = false and get an empty list; the queue
@@ -110,14 +111,16 @@ __device__ __forceinline__ void pixel_update(uint64_t (&v)[K], bool inimg, int c
                                              const float4* __restrict__ met,
                                              const uint4* __restrict__ map_in, size_t P,
                                              size_t pix_off, uint32_t code, int J, uint64_t seed,
-                                             uint32_t (*s_q)[NT], int tid) {
+                                             uint32_t (*s_q)[NT], int tid, float cell = 1.f) {
   constexpr int NP = K / 4;
 #pragma unroll
   for (int k = 0; k < K; ++k) v[k] = 0ull;
   if (!inimg) return;
   const uint32_t q = static_cast<uint32_t>(row) * static_cast<uint32_t>(W) + col;
-  const float px = __fadd_rn(static_cast<float>(col), 0.5f);
-  const float py = __fadd_rn(static_cast<float>(row), 0.5f);
+  // the evaluation point: the pixel centre, or the cell centre of a
+  // candidate grid (col, row index cells of `cell` pixels)
+  const float px = __fmul_rn(__fadd_rn(static_cast<float>(col), 0.5f), cell);
+  const float py = __fmul_rn(__fadd_rn(static_cast<float>(row), 0.5f), cell);
 
   // A. own list
 #pragma unroll

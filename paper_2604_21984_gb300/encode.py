@@ -42,6 +42,7 @@ class EncodeConfig:
     cand_every: int = 1  # f_cand: refresh the candidate lists every this many iterations
     cand_passes: int = 1  # n_cand: propagation passes per refresh
     prepass: str = "propagate"   # warm-up: "propagate" (jump schedule) or "flood" (JFA 3x3 prepass)
+    s_grid: int = 1      # candidate grid cell size (> 1: lists per s x s cell; separate calls)
     keep_grads: bool = False   # fused: also write the step's gradients to Encoder.grads
     extra: dict = field(default_factory=dict)
 
@@ -126,6 +127,12 @@ class Encoder:
         self.it = 0
         self.n_active = self.n0
         self.history = []
+        if c.s_grid > 1:
+            # lists on the candidate grid; the per-pixel map is expanded from it
+            self.Hc, self.Wc = capi.grid_dims(H, W, c.s_grid)
+            self.gmaps = [torch.empty((K // 4, self.Hc * self.Wc, 4), dtype=torch.int32, device=self.dev)
+                          for _ in range(2)]
+            c.fused = False
         if c.fused:
             self.table = capi.batch_table([dict(H=H, W=W, site_offset=0, capacity=cap, pixel_offset=0,
                                                 seed=c.seed + 0x5AD)])
@@ -140,6 +147,14 @@ class Encoder:
 
     def _pass(self):
         c = self.cfg
+        if c.s_grid > 1:
+            capi.sad_grid_update(self.prep, self.cap, self.H, self.W, c.s_grid, c.K, self.gmaps[0],
+                                 self.gmaps[1], jump_code(self.t_pass, self.Hc, self.Wc), c.J,
+                                 c.seed + 0x5AD, self.stream)
+            self.gmaps.reverse()
+            capi.sad_grid_expand(self.gmaps[0], self.H, self.W, c.s_grid, c.K, self.maps[0], self.stream)
+            self.t_pass += 1
+            return
         capi.sad_update_topk(self.prep, self.cap, self.H, self.W, c.K, self.maps[0], self.maps[1],
                              jump_code(self.t_pass, self.H, self.W), c.J, c.seed + 0x5AD,
                              self.stream)
@@ -149,6 +164,17 @@ class Encoder:
     def init(self):
         """Gradient-weighted sites and the JFA warm-up of the field."""
         c = self.cfg
+        if c.s_grid > 1:
+            H, W = self.H, self.W
+            s = 1.0 / max(H, W)
+            log_tau0 = math.log(4.0 / (s * math.sqrt(H * W / self.n0)))
+            capi.sad_init_sites(self.target, self.n0, self.cap, c.lambda_init, c.seed, log_tau0,
+                                params=self.params, stream=self.stream)
+            capi.sad_prepare_sites(self.params, H, W, self.prep, self.stream)
+            capi.sad_grid_seed(self.prep, self.cap, H, W, c.s_grid, c.K, self.gmaps[0], self.stream)
+            for _ in range(max(1, math.ceil(math.log2(max(self.Hc, self.Wc, 2))))):
+                self._pass()
+            return
         a, b, self.t_pass = warm_start(self.target, self.n0, self.params, self.prep, self.maps[0],
                                        self.maps[1], c.K, c.J, c.lambda_init, c.seed, self.stream,
                                        prepass=c.prepass)
@@ -205,8 +231,11 @@ class Encoder:
         capi.sad_prepare_sites(self.params, self.H, self.W, self.prep, self.stream)
         capi.sad_site_stats(self.prep, self.cap, self.H, self.W, c.K, self.maps[0], self.target,
                             self.stats, self.ws, self.stream)
+        # on a candidate grid the children are found by the next passes (the
+        # per-pixel map is rebuilt from the grid), so they are not seeded
         self.n_active = capi.sad_densify_prune(self.params, self.m, self.v, self.H, self.W, c.K,
-                                               self.stats, self.target, self.maps[0], self.dp,
+                                               self.stats, self.target,
+                                               self.maps[0] if c.s_grid == 1 else None, self.dp,
                                                self.ws_dp, self.stream)
         if c.fused:   # the step expects the prepared table of the current sites
             capi.sad_prepare_sites(self.params, self.H, self.W, self.prep, self.stream)

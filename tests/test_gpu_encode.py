@@ -107,3 +107,21 @@ def test_full_size_fused_step_as_benchmarked(capi, oracle):
     assert abs(enc.loss.item() - L) <= 1e-5 * L
     grads = oracle.render_backward(p0, H, W, ids1, g)
     assert_grads_close(enc.grads.cpu().numpy().astype(np.float64), grads)
+
+
+def test_grid_encode_trains(capi):
+    """An encode on a 2x2 candidate grid trains, densifies and lands near the
+    per-pixel field's PSNR."""
+    from paper_2604_21984_gb300.encode import EncodeConfig, Encoder
+    H, W = 128, 192
+    img = dev(gen.image_noise_polygons_lines(H, W, seed=42, n_polygons=10, n_lines=6))
+    kw = dict(n_sites=1536, K=16, J=4, iters=300, densify_every=100, densify_start=100, densify_end=200, seed=3)
+    g = Encoder(img, EncodeConfig(s_grid=2, **kw))
+    g.init()
+    p0 = g.psnr()
+    g.run()
+    p_grid = g.psnr()
+    p_full = Encoder(img, EncodeConfig(**kw)).run().psnr()
+    print(f"PSNR grid2 {p0:.2f} -> {p_grid:.2f}, per-pixel {p_full:.2f}")
+    assert p_grid > p0 + 3.0
+    assert p_grid > p_full - 1.5

@@ -199,3 +199,37 @@ def test_maximum_image_side(capi, oracle):
     with pytest.raises(capi.SadError):
         capi.sad_update_topk(prep, p.shape[1], H + 1, W, K, capi.empty_map(H + 1, W, K),
                              capi.empty_map(H + 1, W, K), 1 << 16, J, 5)
+
+
+@pytest.mark.parametrize("cell", [1, 2, 3])
+def test_grid_passes_bit_exact(capi, oracle, cell):
+    """Candidate grid: seed + passes over the cells and the expansion to
+    pixels, step for step against the oracle; cell = 1 is the plain field."""
+    Hi, Wi, K, J = 45, 62, 8, 2
+    H, W = oracle.grid_dims(Hi, Wi, cell)
+    p = gen.sites_random_spd(Hi, Wi, 300, seed=90 + cell)
+    p = gen.deactivate_random(p, 0.1, seed=91)
+    _, prep = prepare(capi, p, Hi, Wi)
+    op = oracle.prepare_fp32(p, Hi, Wi)
+    a = capi.empty_map(H, W, K)
+    b = capi.empty_map(H, W, K)
+    capi.sad_grid_seed(prep, p.shape[1], Hi, Wi, cell, K, a)
+    ref = oracle.topk_seed_fp32(op, H, W, K, cell=cell, image=(Hi, Wi))
+    np.testing.assert_array_equal(capi.ids_from_map(a), ref)
+    for t in range(7):
+        code = oracle.step_code(t, H, W)
+        capi.sad_grid_update(prep, p.shape[1], Hi, Wi, cell, K, a, b, code, J, 17)
+        a, b = b, a
+        ref = oracle.topk_pass_fp32(op, ref, H, W, K, code, J, 17, cell=cell)
+        np.testing.assert_array_equal(capi.ids_from_map(a), ref)
+    px = capi.empty_map(Hi, Wi, K)
+    capi.sad_grid_expand(a, Hi, Wi, cell, K, px)
+    np.testing.assert_array_equal(capi.ids_from_map(px), oracle.expand_grid(ref, Hi, Wi, cell))
+    if cell == 1:
+        c = capi.empty_map(Hi, Wi, K)
+        capi.sad_topk_seed(prep, p.shape[1], Hi, Wi, K, c)
+        d = capi.empty_map(Hi, Wi, K)
+        capi.sad_update_topk(prep, p.shape[1], Hi, Wi, K, c, d, oracle.step_code(0, Hi, Wi), J, 17)
+        np.testing.assert_array_equal(capi.ids_from_map(d),
+                                      oracle.topk_pass_fp32(op, oracle.topk_seed_fp32(op, Hi, Wi, K), Hi, Wi, K,
+                                                            oracle.step_code(0, Hi, Wi), J, 17))
