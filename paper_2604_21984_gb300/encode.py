@@ -19,7 +19,7 @@ from dataclasses import dataclass, field
 
 import torch
 
-from . import capi
+from . import budget, capi
 
 
 @dataclass
@@ -43,6 +43,7 @@ class EncodeConfig:
     cand_passes: int = 1  # n_cand: propagation passes per refresh
     prepass: str = "propagate"   # warm-up: "propagate" (jump schedule) or "flood" (JFA 3x3 prepass)
     s_grid: int = 1      # candidate grid cell size (> 1: lists per s x s cell; separate calls)
+    target_bpp: float | None = None   # scale densify/prune percentiles to end near this bit rate
     keep_grads: bool = False   # fused: also write the step's gradients to Encoder.grads
     extra: dict = field(default_factory=dict)
 
@@ -109,6 +110,19 @@ class Encoder:
         H, W, K = self.H, self.W, c.K
         self.n0 = min(c.n_sites, H * W)
         self.cap = max(self.n0, int(math.ceil(c.capacity_factor * self.n0)))
+        self.pct_scale = 1.0
+        if c.target_bpp is not None:
+            # the schedule simulator of Sec. 4.5: one shared scale of both
+            # percentiles so that the expected final count meets the target
+            tgt = budget.target_sites(c.target_bpp, H, W)
+            big = max(8 * self.n0, 2 * tgt)
+            self.pct_scale, _ = budget.scale_for_target(
+                self.n0, tgt, c.iters, c.densify_every, c.densify_start, c.densify_end, c.densify_pct,
+                c.prune_pct, big)
+            trace, _ = budget.simulate_counts(self.n0, c.iters, c.densify_every, c.densify_start,
+                                              c.densify_end, c.densify_pct, c.prune_pct, big,
+                                              self.pct_scale)
+            self.cap = max(self.cap, max([n for _, n in trace], default=self.n0) + 1)
         cap = self.cap
         f32 = dict(dtype=torch.float32, device=self.dev)
         self.params = torch.empty((capi.N_PARAMS, cap), **f32)
@@ -122,7 +136,8 @@ class Encoder:
         self.ws = capi.backward_workspace(H, W, K, cap, device=self.dev)
         self.ws_dp = capi.densify_workspace(cap, H, W, self.dev)
         self.hp = capi.adam_hparams(lr=c.lr)
-        self.dp = capi.dp_params(densify_pct=c.densify_pct, prune_pct=c.prune_pct, alpha=c.alpha)
+        self.dp = capi.dp_params(densify_pct=c.densify_pct * self.pct_scale,
+                                 prune_pct=c.prune_pct * self.pct_scale, alpha=c.alpha)
         self.t_pass = 0
         self.it = 0
         self.n_active = self.n0
