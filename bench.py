@@ -488,7 +488,8 @@ def c3_leg(capi, dev, peak, peak_kind, args, iters=10):
 
 def c4_leg(capi, dev, peak, peak_kind, args, n_images=64, seed=4000):
     """64 uneven images: batched fused step (CUDA graph, autotuned K/J) vs the
-    plain loop (one image at a time, the separate calls), equal iterations."""
+    plain loop (one image at a time, the same fused kernels on a one-image
+    batch, no graph), equal iterations."""
     import torch
     from paper_2604_21984_gb300 import inputs as gen
     from paper_2604_21984_gb300.batch import BatchConfig, BatchTrainer, autotune
@@ -521,7 +522,8 @@ def c4_leg(capi, dev, peak, peak_kind, args, n_images=64, seed=4000):
     b_psnr = tr.psnr()
     del tr
     torch.cuda.empty_cache()
-    # plain loop: each image alone, K=16, J=4, the four separate calls per iteration
+    # plain loop: each image alone, K=16, J=4, the fused step on a one-image
+    # batch per iteration (no batching across images, no graph)
     p_psnr, p_train, p_init = [], 0.0, 0.0
     for i, img in enumerate(imgs):
         H, W = sizes[i]
@@ -529,7 +531,7 @@ def c4_leg(capi, dev, peak, peak_kind, args, n_images=64, seed=4000):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         enc = Encoder(img, EncodeConfig(n_sites=n, K=16, J=4, capacity_factor=1.0, seed=seeds[i],
-                                        densify_every=0, fused=False))
+                                        densify_every=0))
         enc.init()
         torch.cuda.synchronize()
         p_init += time.perf_counter() - t0

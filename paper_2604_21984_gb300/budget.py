@@ -10,10 +10,13 @@ Readings (the paper gives no more):
   * the simulator replays the encoder's event schedule: at every event
     t = every, 2 every, ... inside [start, end], first densify n += floor(lam
     d n) (capped by the capacity), then prune n -= floor(lam p n);
-  * the shared scale factor lam multiplies both base percentiles; it is
-    found by scanning lam over [0, lam_max] and refining the best interval
-    by bisection on |n_final - N*| (n_final is piecewise constant and need
-    not be monotone in lam).
+  * the shared scale factor lam multiplies both base percentiles, each
+    scaled percentile capped at 0.95 (Sec. 6.1); lam is found by scanning
+    [0, lam_max] and refining the best interval by ternary search on
+    |n_final - N*| (n_final is piecewise constant and need not be monotone
+    in lam).  With base percentiles that shrink the budget (densify < prune)
+    targets above the initial count are out of reach and lam = 0 is
+    returned (no events).
 """
 from __future__ import annotations
 
@@ -32,10 +35,11 @@ def simulate_counts(n0: int, iters: int, every: int, start: int, end: int, densi
     trace = []
     if every <= 0:
         return trace, n
+    d, p = min(0.95, lam * densify_pct), min(0.95, lam * prune_pct)
     for t in range(1, iters + 1):
         if start <= t <= end and t % every == 0:
-            n = min(capacity, n + int(math.floor(lam * densify_pct * n)))
-            n = max(0, n - int(math.floor(lam * prune_pct * n)))
+            n = min(capacity, n + int(math.floor(d * n)))
+            n = max(0, n - int(math.floor(p * n)))
             trace.append((t, n))
     return trace, n
 

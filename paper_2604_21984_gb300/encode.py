@@ -136,8 +136,8 @@ class Encoder:
         self.ws = capi.backward_workspace(H, W, K, cap, device=self.dev)
         self.ws_dp = capi.densify_workspace(cap, H, W, self.dev)
         self.hp = capi.adam_hparams(lr=c.lr)
-        self.dp = capi.dp_params(densify_pct=c.densify_pct * self.pct_scale,
-                                 prune_pct=c.prune_pct * self.pct_scale, alpha=c.alpha)
+        self.dp = capi.dp_params(densify_pct=min(0.95, c.densify_pct * self.pct_scale),
+                                 prune_pct=min(0.95, c.prune_pct * self.pct_scale), alpha=c.alpha)
         self.t_pass = 0
         self.it = 0
         self.n_active = self.n0

@@ -21,7 +21,7 @@ decode requests that have arrived are answered by one `sad_decode_batch`
 launch on their own stream.  Completion times are CUDA events.
 
 `PlainLoop` is the baseline: FIFO, one request at a time, each with the
-single-image calls.
+single-image calls (the same fused kernels, one image per launch).
 """
 from __future__ import annotations
 
@@ -499,8 +499,8 @@ class Server:
 
 class PlainLoop:
     """FIFO baseline: one request at a time with the single-image calls.
-    Encodes run `Encoder.step` with the separate calls per iteration
-    (prepare, propagation pass, fused forward/backward with its reduce, Adam;
+    Encodes run `Encoder.step`, the fused step on a one-image batch (the
+    same kernels as the served encodes, so both give bit-identical sites;
     no densify, no graph, nothing shared across images); decodes
     `sad_decode_points` on the resident set's own arrays."""
 
@@ -543,7 +543,7 @@ class PlainLoop:
                 enc = Encoder(req.image.contiguous(),
                               EncodeConfig(n_sites=n, K=c.K, J=c.J, capacity_factor=1.0,
                                            lambda_init=c.lambda_init, seed=req.seed, lr=c.lr,
-                                           densify_every=0, fused=False),
+                                           densify_every=0),
                               stream=self.stream)
                 enc.init()
                 for _ in range(req.iters):

@@ -128,16 +128,17 @@ def test_grid_encode_trains(capi):
 
 
 def test_target_bpp_schedule(capi):
-    """With a target bit rate the percentiles are scaled by the simulator;
-    the encode ends near the target site count (splits can fall short when
-    too few sites qualify, so within 15%)."""
+    """With a target bit rate the percentiles (the paper's base pair, which
+    shrinks the budget) are scaled by the simulator; the encode ends near
+    the target site count (splits can fall short when too few sites
+    qualify, so within 15%)."""
     from paper_2604_21984_gb300 import budget
     from paper_2604_21984_gb300.encode import EncodeConfig, Encoder
     H, W = 128, 192
     img = dev(gen.image_noise_polygons_lines(H, W, seed=45, n_polygons=10, n_lines=6))
-    for bpp in (4.0, 12.0):
+    for bpp in (2.5, 4.0):
         cfg = EncodeConfig(n_sites=1000, K=16, J=4, iters=400, densify_every=50, densify_start=50,
-                           densify_end=350, densify_pct=0.05, prune_pct=0.02, seed=4, target_bpp=bpp)
+                           densify_end=350, densify_pct=0.01, prune_pct=0.033, seed=4, target_bpp=bpp)
         enc = Encoder(img, cfg).run()
         tgt = budget.target_sites(bpp, H, W)
         print("bpp", bpp, "target", tgt, "scale", round(enc.pct_scale, 3), "active", enc.n_active)
