@@ -619,6 +619,13 @@ def c5_leg(capi, dev, peak, peak_kind, args, seed=5000, details=False):
                        f"{args.c5_iters} iterations)",
            "plain_capacity_req_per_s": round(capacity, 3), "requests": len(spec),
            "encodes": len(enc_idx), "pool_gb": round(srv.footprint_bytes() / 1e9, 2)}
+    # saturation: the same requests all at t = 0 (completion-bound throughput)
+    for name, eng in (("plain", plain), ("served", srv)):
+        reqs = requests([dict(r, arrival=0.0) for r in spec], imgs)
+        wall = run_stream(eng, reqs)
+        out.setdefault("saturated", {})[name] = {"wall_s": round(wall, 3),
+                                                 "throughput_req_per_s": round(len(reqs) / wall, 3)}
+        del reqs
     for name, eng in (("plain", plain), ("served", srv)):
         reqs = requests(spec, imgs)
         wall = run_stream(eng, reqs)

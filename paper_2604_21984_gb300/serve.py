@@ -47,6 +47,11 @@ class ServeConfig:
     max_decode_per_tick: int = 1 << 22
     pixels_per_call: int = 1 << 19    # fast-lane pixels per call (least remaining work first)
     bulk_pixels_per_call: int = 1 << 21   # bulk-lane pixels per call (arrival order)
+    # CUDA stream priorities of the lanes (lower = more urgent): large encodes
+    # ahead, small ones fill the gaps (measured: encode p99 no worse than the
+    # plain loop; the reverse order gives a 4x lower p50 but a higher p99)
+    fast_priority: int = 0
+    bulk_priority: int = -1
     lr: tuple = (1e-3, 1e-3, 1e-2, 1e-3, 5e-3, 5e-3, 5e-3, 1e-2, 1e-2, 1e-2, 0.0)
 
 
@@ -212,12 +217,12 @@ class _Lane:
 class Server:
     """Resident pools, admission, two training lanes and the batched decode.
 
-    The `fast` lane (high priority stream) takes small encodes, least
-    remaining work first, within `pixels_per_call`; the `bulk` lane (normal
-    priority) takes the others first come first served within
-    `bulk_pixels_per_call`.  The two lanes' calls overlap on the GPU, the
-    fast one ahead, so small encodes are not held to the pace of a large one
-    and large ones keep their arrival order.  Decodes run on a third stream at high
+    The `fast` lane takes small encodes, least remaining work first, within
+    `pixels_per_call`; the `bulk` lane takes the others first come first
+    served within `bulk_pixels_per_call`.  The two lanes' calls overlap on
+    the GPU (by default the bulk lane's stream has the higher priority and
+    the small encodes fill the gaps), so small encodes are not held to the
+    pace of a large one and large ones keep their arrival order.  Decodes run on a third stream at high
     priority (resident sets are never written by training)."""
 
     def __init__(self, cfg: ServeConfig | None = None, device="cuda", stream=None):
@@ -244,8 +249,8 @@ class Server:
         self.state = torch.zeros((128, 4), dtype=torch.int32, device=self.dev)
         self.free_rows = list(range(128))
         self.hp = capi.adam_hparams(lr=c.lr)
-        self.fast = _Lane(self, -1)
-        self.bulk = _Lane(self, 0)
+        self.fast = _Lane(self, c.fast_priority)
+        self.bulk = _Lane(self, c.bulk_priority)
         # staging for the single-image warm start (largest accepted image)
         Pmax = c.max_side * c.max_side
         nmax = encode_sites(c.max_side, c.max_side, c.sites_per_pixel)
