@@ -162,7 +162,7 @@ def gen_images(specs):
 NCU_COUNTERS = {
     "k_step_tile": {"sources": ["sad_step.cu", "sad_tile.cuh", "sad_topk.cuh", "sad_device.cuh",
                                 "sad_adam.cuh", "sad_blend.cuh"],
-                    "sha": "417c345137b568a9", "dram_bytes": 33945856, "warp_inst": 150208379},
+                    "sha": "a86d81782734f894", "dram_bytes": 33998336, "warp_inst": 150252466},
 }
 ISSUE_PEAK = 152 * 4 * 2.07e9   # warp instructions / s: 152 SMs x 4 schedulers x 1 issue/clk x 2070 MHz
 
