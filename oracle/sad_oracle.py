@@ -1038,3 +1038,31 @@ def unpack_eval(words, q, H, W):
     p[PX, ~act] = -1.0
     p[PY, ~act] = -1.0
     return p
+
+
+# ---------------------------------------------------------------------------
+# Part 6: tau diffusion (App. "Tau Diffusion")
+# ---------------------------------------------------------------------------
+
+def tau_diffusion(params, H, W, ids, lam, g_logtau):
+    """One Jacobi step that smooths the log tau gradients over each site's
+    candidate neighbourhood: g'_i = (1 - lam) g_i + lam * mean_{j in N(i)} g_j,
+    N(i) = the valid, active sites other than i listed at the pixel that
+    contains site i (position clamped into the image).  Inactive sites and
+    sites with an empty neighbourhood keep their gradient.  fp64; returns
+    float64[N]."""
+    p = np.asarray(params, dtype=np.float64)
+    g = np.asarray(g_logtau, dtype=np.float64)
+    ids = np.asarray(ids)
+    N = p.shape[1]
+    out = g.copy()
+    for i in range(N):
+        if not p[PX, i] >= 0:
+            continue
+        col = min(max(int(math.floor(p[PX, i])), 0), W - 1)
+        row = min(max(int(math.floor(p[PY, i])), 0), H - 1)
+        nb = [int(j) for j in ids[row * W + col]
+              if int(j) != INVALID and int(j) < N and int(j) != i and p[PX, int(j)] >= 0]
+        if nb:
+            out[i] = (1.0 - lam) * g[i] + lam * float(np.mean(g[nb]))
+    return out
