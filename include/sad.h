@@ -348,6 +348,19 @@ int sad_adam_step(float* params, const float* grads, float* m, float* v, int32_t
                   int32_t H, int32_t W, int32_t t, const sad_adam_hparams* hp, void* stream);
 
 /*
+ * sad_tau_diffusion -- one Jacobi smoothing step of the log tau gradients
+ * (App. "Tau Diffusion"): for every active site i, g_out[i] = (1 - lambda)
+ * g[i] + lambda * mean of g[j] over the entries j of the top-K list of the
+ * pixel containing site i (position clamped into the image) that are valid,
+ * active and not i; sites that are inactive or have no such neighbour keep
+ * g[i].  params: float32[11][capacity]; map: K/4 uint4 planes over H*W;
+ * g_logtau, g_out: float32[capacity], distinct; lambda in [0, 1].
+ */
+int sad_tau_diffusion(const float* params, int32_t capacity, int32_t H, int32_t W, int32_t K,
+                      const uint32_t* map, float lambda, const float* g_logtau, float* g_out,
+                      void* stream);
+
+/*
  * Batched training (many images, one launch per stage).  Each image owns a
  * contiguous range of site slots in the shared site arrays (ascending,
  * non-overlapping) and a contiguous range of pixels in the packed per-pixel

@@ -25,6 +25,7 @@ _lib = None
 N_PARAMS = 11
 INVALID = 0xFFFFFFFF
 STEP_KEEP_LISTS = 1   # batch-image flag (include/sad.h SAD_STEP_KEEP_LISTS)
+PLANE_LOGTAU = 2      # plane of log tau in the site parameter and gradient arrays
 
 
 class SadError(RuntimeError):
@@ -90,6 +91,9 @@ _SIGS = {
                                        ctypes.c_uint32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p]),
     "sad_grid_expand": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "sad_tau_diffusion": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int32, ctypes.c_void_p, ctypes.c_float, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p]),
     "sad_render": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                   ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_void_p]),
@@ -646,3 +650,13 @@ def sad_grid_expand(map_grid, H, W, s_grid, K, map_pixels, stream=None):
                                  _ptr(map_pixels, torch.int32, "map", H * W * K), _stream(stream)),
            "sad_grid_expand")
     return map_pixels
+
+
+def sad_tau_diffusion(params, H, W, K, map_in, lam, g_logtau, g_out, stream=None):
+    cap = params.shape[1]
+    _check(lib().sad_tau_diffusion(_ptr(params, torch.float32, "params", N_PARAMS * cap), cap, H, W, K,
+                                   _ptr(map_in, torch.int32, "map", H * W * K), float(lam),
+                                   _ptr(g_logtau, torch.float32, "g_logtau", cap),
+                                   _ptr(g_out, torch.float32, "g_out", cap), _stream(stream)),
+           "sad_tau_diffusion")
+    return g_out

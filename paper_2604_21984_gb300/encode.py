@@ -44,6 +44,7 @@ class EncodeConfig:
     prepass: str = "propagate"   # warm-up: "propagate" (jump schedule) or "flood" (JFA 3x3 prepass)
     s_grid: int = 1      # candidate grid cell size (> 1: lists per s x s cell; separate calls)
     target_bpp: float | None = None   # scale densify/prune percentiles to end near this bit rate
+    tau_diffusion: float = 0.0   # lambda of the log tau gradient smoothing (> 0: separate calls)
     keep_grads: bool = False   # fused: also write the step's gradients to Encoder.grads
     extra: dict = field(default_factory=dict)
 
@@ -142,6 +143,9 @@ class Encoder:
         self.it = 0
         self.n_active = self.n0
         self.history = []
+        if c.tau_diffusion > 0:
+            c.fused = False   # the smoothing sits between the gradient and Adam
+            self._g_tau = torch.empty(cap, dtype=torch.float32, device=self.dev)
         if c.s_grid > 1:
             # lists on the candidate grid; the per-pixel map is expanded from it
             self.Hc, self.Wc = capi.grid_dims(H, W, c.s_grid)
@@ -238,6 +242,10 @@ class Encoder:
                 self._pass()
         capi.sad_train_grads(self.params, self.prep, self.H, self.W, c.K, self.maps[0], self.target,
                              self.grads, self.loss, self.ws, stream=self.stream)
+        if c.tau_diffusion > 0:
+            capi.sad_tau_diffusion(self.params, self.H, self.W, c.K, self.maps[0], c.tau_diffusion,
+                                   self.grads[capi.PLANE_LOGTAU], self._g_tau, self.stream)
+            self.grads[capi.PLANE_LOGTAU].copy_(self._g_tau)
         capi.sad_adam_step(self.params, self.grads, self.m, self.v, self.H, self.W, self.it, self.hp,
                            self.stream)
 
