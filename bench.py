@@ -386,6 +386,10 @@ def encode_leg(capi, dev, peak, peak_kind, args, iters=2000):
                             "RTX 5090 implied"}
     res["cand_every_8"] = run(cand_every=8)
     res["s_grid_2"] = run(s_grid=2)   # lists on a 2x2-pixel candidate grid (separate calls)
+    # refresh passes scored from the half2 candidate table, against the same
+    # separate calls on the float32 table
+    res["separate_calls"] = run(fused=False)
+    res["cand_half2"] = run(cand_half2=True)
     return res
 
 
@@ -409,6 +413,28 @@ def c3_leg(capi, dev, peak, peak_kind, args, iters=10):
         a, b = b, a
     torch.cuda.synchronize()
     jfa_ms = (time.perf_counter() - t0) * 1e3
+    # one pass from the warm map, float32 table vs half2 candidate table, at
+    # jump 1 (a training refresh) and at jump 64
+    cand = torch.empty((N, 4), dtype=torch.int32, device=dev)
+    E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def timed(fn, n=10):
+        for _ in range(2):
+            fn()
+        ev = [E() for _ in range(n + 1)]
+        ev[0].record()
+        for i in range(n):
+            fn()
+            ev[i + 1].record()
+        torch.cuda.synchronize()
+        return statistics.mean(ev[i].elapsed_time(ev[i + 1]) for i in range(n))
+    pass_ms = {}
+    for s_j in (1, 64):
+        code = (s_j << 16) | 200
+        pass_ms[f"f32_jump{s_j}"] = timed(lambda: capi.sad_update_topk(prep, N, H, W, K, a, b, code, 2, 11))
+        pass_ms[f"half2_jump{s_j}"] = timed(lambda: capi.sad_update_topk_h2(cand, N, H, W, K, a, b, code, 2, 11))
+    pass_ms["pack_candidates"] = timed(lambda: capi.sad_pack_candidates(prep, N, cand))
+    del cand
     # the JFA 3x3 flood prepass (seed + 11 flood passes) + 4 propagation passes
     fa, fb = capi.empty_map(H, W, K, dev), capi.empty_map(H, W, K, dev)
     torch.cuda.synchronize()
@@ -427,7 +453,6 @@ def c3_leg(capi, dev, peak, peak_kind, args, iters=10):
     g = torch.from_numpy(gen.grad_image(H, W, seed=3002) / (H * W)).to(dev)
     grads = torch.empty((11, N), dtype=torch.float32, device=dev)
     ws = capi.backward_workspace(H, W, K, N, device=dev)
-    E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     for _ in range(3):
         capi.sad_render(prep, N, H, W, K, a, rgb)
         capi.sad_render_backward(pt, prep, H, W, K, a, g, grads, ws)
@@ -477,6 +502,7 @@ def c3_leg(capi, dev, peak, peak_kind, args, iters=10):
         "mpix_per_s_fwd_bwd": round(P / ((rb + bb) / 1e3) / 1e6, 1),
         "render_ms": round(rb, 4), "backward_ms": round(bb, 4), "jfa_16_passes_ms": round(jfa_ms, 3),
         "flood_prepass_11_plus_4_passes_ms": round(flood_ms, 3),
+        "one_pass_ms": {k: round(v, 4) for k, v in pass_ms.items()},
         "render_packed_16B_ms": round(statistics.mean(pk_ms), 4),
         "render_packed_max_abs_diff": round(float((rgb - rgb_p).abs().max().item()), 5),
         "records": used, "ws_status": st,

@@ -140,6 +140,27 @@ int sad_update_topk(const float* prep, int32_t capacity, int32_t H, int32_t W, i
                     int32_t n_inject, uint64_t seed, void* stream);
 
 /*
+ * Half2 candidate sites (App. "Data Layout and Packing", Packed candidate
+ * sites): a 16-byte per-site record that candidate passes read instead of
+ * the prepared table's two 16-byte scoring planes.
+ * sad_pack_candidates -- cand: uint32[capacity][4] (written), words
+ *   {x, y}, {tau s, r}, {G00, G01}, {G11, active} of the prepared table
+ *   `prep`, each word a half2 with the first value in the low 16 bits.
+ *   Each value is saturated to [-65504, 65504] (fminf/fmaxf semantics)
+ *   and rounded to the nearest half, ties to even.  Regenerate it whenever
+ *   the prepared table changes.
+ * sad_update_topk_h2 -- sad_update_topk with every candidate scored from
+ *   `cand` (the halves widened to float32 exactly, then the same float32
+ *   logit).  Lists are ordered by these logits; the render and the adjoint
+ *   still take the float32 table.
+ * cand must be 16-byte aligned; errors as sad_update_topk.
+ */
+int sad_pack_candidates(const float* prep, int32_t capacity, uint32_t* cand, void* stream);
+int sad_update_topk_h2(const uint32_t* cand, int32_t capacity, int32_t H, int32_t W, int32_t K,
+                       const uint32_t* map_in, uint32_t* map_out, uint32_t step_code,
+                       int32_t n_inject, uint64_t seed, void* stream);
+
+/*
  * Downscaled candidate grid (App. "Candidate Field and Jump Schedule",
  * Downscaled candidate grid): the lists live on a ceil(H/s) x ceil(W/s)
  * grid of s x s pixel cells, and a cell's candidates are scored at its

@@ -34,6 +34,9 @@ Part 3: gradient-weighted initialisation (Sec. 4.4).
 Part 4: adaptive budget: statistics, densify split, prune (Sec. 4.5).
 Part 5: packed 16-byte evaluation sites (App. "Data Layout and Packing",
   Packed storage for evaluation): pack_eval / unpack_eval.
+Part 6: tau diffusion (App. "Tau Diffusion").
+Part 7: half2 candidate sites (App. "Data Layout and Packing", Packed
+  candidate sites): candidate_halves / candidate_words / candidate_table_fp32.
 """
 from __future__ import annotations
 
@@ -1065,4 +1068,48 @@ def tau_diffusion(params, H, W, ids, lam, g_logtau):
               if int(j) != INVALID and int(j) < N and int(j) != i and p[PX, int(j)] >= 0]
         if nb:
             out[i] = (1.0 - lam) * g[i] + lam * float(np.mean(g[nb]))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Part 7: half2 candidate sites (App. "Data Layout and Packing", Packed
+# candidate sites)
+# ---------------------------------------------------------------------------
+
+HALF_MAX = 65504.0   # largest finite IEEE binary16 value
+_CAND_FIELDS = ("x", "y", "ts", "r", "G00", "G01", "G11", "active")
+
+
+def candidate_halves(prep):
+    """The 16-byte candidate record of every site as float16[N, 8]: the
+    scoring values x, y, tau s, r, G00, G01, G11 and the active flag (1 or 0)
+    of the float32 table, each saturated to [-HALF_MAX, HALF_MAX] (NaN-
+    ignoring min/max, like C's fminf/fmaxf) and rounded to the nearest
+    binary16 value, ties to even (IEEE 754 conversion)."""
+    cols = []
+    for f in _CAND_FIELDS:
+        v = prep[f].astype(F32)
+        v = np.fmin(np.fmax(v, F32(-HALF_MAX)), F32(HALF_MAX)).astype(F32)
+        cols.append(v.astype(np.float16))
+    return np.stack(cols, axis=1)
+
+
+def candidate_words(prep):
+    """candidate_halves as the record's four little-endian 32-bit words
+    (first value of each pair in the low 16 bits): uint32[N, 4]."""
+    h = np.ascontiguousarray(candidate_halves(prep))
+    bits = h.view(np.uint16).astype(np.uint32)
+    return bits[:, 0::2] | (bits[:, 1::2] << np.uint32(16))
+
+
+def candidate_table_fp32(prep):
+    """The table a half2 candidate pass scores from: prepare_fp32's dict with
+    the scoring values replaced by their binary16 records widened back to
+    float32 (exact), and active = record flag != 0.  Passing it to
+    topk_pass_fp32 is the candidate pass on half2 sites."""
+    h = candidate_halves(prep).astype(F32)
+    out = dict(prep)
+    for k, f in enumerate(_CAND_FIELDS[:-1]):
+        out[f] = h[:, k].copy()
+    out["active"] = h[:, 7] != F32(0)
     return out

@@ -81,6 +81,12 @@ _SIGS = {
                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int32,
                                        ctypes.c_uint64, ctypes.c_void_p]),
+    "sad_pack_candidates": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                           ctypes.c_void_p]),
+    "sad_update_topk_h2": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int32,
+                                          ctypes.c_uint64, ctypes.c_void_p]),
     "sad_jfa_flood": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                      ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
                                      ctypes.c_void_p]),
@@ -277,6 +283,23 @@ def sad_update_topk(prep, cap, H, W, K, map_in, map_out, step_code, n_inject, se
                                  _ptr(map_out, torch.int32, "map_out", H * W * K),
                                  step_code & 0xFFFFFFFF, n_inject, seed & ((1 << 64) - 1),
                                  _stream(stream)), "sad_update_topk")
+    return map_out
+
+
+def sad_pack_candidates(prep, cap, cand, stream=None):
+    """cand: int32 tensor of cap*4 words (the half2 candidate records)."""
+    _check(lib().sad_pack_candidates(_ptr(prep, torch.float32, "prep"), cap,
+                                     _ptr(cand, torch.int32, "cand", cap * 4), _stream(stream)),
+           "sad_pack_candidates")
+    return cand
+
+
+def sad_update_topk_h2(cand, cap, H, W, K, map_in, map_out, step_code, n_inject, seed, stream=None):
+    _check(lib().sad_update_topk_h2(_ptr(cand, torch.int32, "cand"), cap, H, W, K,
+                                    _ptr(map_in, torch.int32, "map_in", H * W * K),
+                                    _ptr(map_out, torch.int32, "map_out", H * W * K),
+                                    step_code & 0xFFFFFFFF, n_inject, seed & ((1 << 64) - 1),
+                                    _stream(stream)), "sad_update_topk_h2")
     return map_out
 
 

@@ -43,10 +43,8 @@ __global__ void k_seed(const float4* __restrict__ geo, const float4* __restrict_
 // ---------------------------------------------------------------------------
 constexpr int kUpdThreads = 256;
 
-template <int K>
-__global__ void __launch_bounds__(kUpdThreads) k_topk_update(const float4* __restrict__ geo,
-                                                             const float4* __restrict__ met, int cap,
-                                                             int H, int W,
+template <int K, class Sites>
+__global__ void __launch_bounds__(kUpdThreads) k_topk_update(Sites sites, int cap, int H, int W,
                                                              const uint4* __restrict__ map_in,
                                                              uint4* __restrict__ map_out,
                                                              uint32_t code, int J, uint64_t seed,
@@ -60,7 +58,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_topk_update(const float4* __res
   const size_t q = static_cast<size_t>(row) * W + col;
   uint64_t v[K];
   pixel_update<K, kUpdThreads>(v, true, col, row, H, W, SiteRange{0u, static_cast<uint32_t>(cap)},
-                               geo, met, map_in, P, 0, code, J, seed, s_q, tid, cell);
+                               sites, map_in, P, 0, code, J, seed, s_q, tid, cell);
 #pragma unroll
   for (int j = 0; j < K / 4; ++j)
     map_out[j * P + q] = make_uint4(key_id(v[4 * j]), key_id(v[4 * j + 1]), key_id(v[4 * j + 2]),
@@ -96,7 +94,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_jfa_flood(const float4* __restr
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       if (list_has<4>(v, id4[u])) continue;
-      const uint64_t c = cand_key(id4[u], sr, px, py, geo, met);
+      const uint64_t c = cand_key(id4[u], sr, px, py, F32Sites{geo, met});
       if (c > v[3]) list_insert<4>(v, c);
     }
   }
@@ -118,13 +116,44 @@ __global__ void k_grid_expand(const uint4* __restrict__ grid, int H, int W, int 
   for (int j = 0; j < NP; ++j) out[j * P + q] = ldg(&grid[j * Pc + qc]);
 }
 
+// Half2 candidate table from the prepared table (App. "Data Layout and
+// Packing", Packed candidate sites): each value rounded to the nearest
+// half (ties to even) after saturation to +-65504, the largest finite half.
+__device__ __forceinline__ uint32_t half2_bits(float lo, float hi) {
+  const float m = 65504.f;
+  const unsigned short a = __half_as_ushort(__float2half_rn(fminf(fmaxf(lo, -m), m)));
+  const unsigned short b = __half_as_ushort(__float2half_rn(fminf(fmaxf(hi, -m), m)));
+  return static_cast<uint32_t>(a) | (static_cast<uint32_t>(b) << 16);
+}
+
+__global__ void k_pack_candidates(const float4* __restrict__ geo, const float4* __restrict__ met,
+                                  int cap, uint4* __restrict__ cand) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cap) return;
+  const float4 g = ldg(&geo[i]), m = ldg(&met[i]);
+  cand[i] = make_uint4(half2_bits(g.x, g.y), half2_bits(g.z, g.w), half2_bits(m.x, m.y),
+                       half2_bits(m.z, m.w));
+}
+
+template <class Sites>
+static void launch_update(int K, dim3 grid, dim3 block, cudaStream_t st, Sites sites, int cap,
+                          int H, int W, const uint4* in, uint4* out, uint32_t code, int J,
+                          uint64_t seed, float cell) {
+  switch (K) {
+    case 4: k_topk_update<4><<<grid, block, 0, st>>>(sites, cap, H, W, in, out, code, J, seed, cell); break;
+    case 8: k_topk_update<8><<<grid, block, 0, st>>>(sites, cap, H, W, in, out, code, J, seed, cell); break;
+    default: k_topk_update<16><<<grid, block, 0, st>>>(sites, cap, H, W, in, out, code, J, seed, cell); break;
+  }
+}
+
 // One propagation pass over an H x W grid of lists whose entries are scored
-// at ((col + 0.5) cell, (row + 0.5) cell).
-static int run_update(const float* prep, int32_t capacity, int32_t H, int32_t W, int32_t K,
+// at ((col + 0.5) cell, (row + 0.5) cell), from the prepared fp32 table or,
+// with h2, from the half2 candidate table.
+static int run_update(const void* table, bool h2, int32_t capacity, int32_t H, int32_t W, int32_t K,
                       const uint32_t* map_in, uint32_t* map_out, uint32_t step_code,
                       int32_t n_inject, uint64_t seed, float cell, void* stream, const char* name) {
-  if (!map_in || !map_out || (!prep && capacity > 0)) return einval("%s: null pointer", name);
-  if (!aligned16(map_in) || !aligned16(map_out) || !aligned16(prep))
+  if (!map_in || !map_out || (!table && capacity > 0)) return einval("%s: null pointer", name);
+  if (!aligned16(map_in) || !aligned16(map_out) || !aligned16(table))
     return einval("%s: pointers must be 16-byte aligned", name);
   if (n_inject < 0 || n_inject > 16) return einval("%s: n_inject must be in [0,16]", name);
   const size_t P = static_cast<size_t>(H) * W;
@@ -134,19 +163,20 @@ static int run_update(const float* prep, int32_t capacity, int32_t H, int32_t W,
   const char* b = reinterpret_cast<const char*>(map_out);
   const size_t bytes = P * K * sizeof(uint32_t);
   if (a < b + bytes && b < a + bytes) return einval("%s: map_in and map_out overlap", name);
-  const float4* p4 = reinterpret_cast<const float4*>(prep);
   const dim3 block(32, 8);
   const dim3 grid((W + 31) / 32, (H + 7) / 8);
   const uint4* in = reinterpret_cast<const uint4*>(map_in);
   uint4* out = reinterpret_cast<uint4*>(map_out);
   cudaStream_t st = as_stream(stream);
-  {
+  if (!h2) {
+    const float4* p4 = reinterpret_cast<const float4*>(table);
     TraceScope tr_(st, "k_topk_update");
-    switch (K) {
-      case 4: k_topk_update<4><<<grid, block, 0, st>>>(p4, p4 + capacity, capacity, H, W, in, out, step_code, n_inject, seed, cell); break;
-      case 8: k_topk_update<8><<<grid, block, 0, st>>>(p4, p4 + capacity, capacity, H, W, in, out, step_code, n_inject, seed, cell); break;
-      default: k_topk_update<16><<<grid, block, 0, st>>>(p4, p4 + capacity, capacity, H, W, in, out, step_code, n_inject, seed, cell); break;
-    }
+    launch_update(K, grid, block, st, F32Sites{p4, p4 + capacity}, capacity, H, W, in, out,
+                  step_code, n_inject, seed, cell);
+  } else {
+    TraceScope tr_(st, "k_topk_update_h2");
+    launch_update(K, grid, block, st, H2Sites{reinterpret_cast<const uint4*>(table)}, capacity, H,
+                  W, in, out, step_code, n_inject, seed, cell);
   }
   return check_launch(name);
 }
@@ -223,8 +253,8 @@ int sad_update_topk(const float* prep, int32_t capacity, int32_t H, int32_t W, i
                     const uint32_t* map_in, uint32_t* map_out, uint32_t step_code,
                     int32_t n_inject, uint64_t seed, void* stream) {
   if (int st = check_problem(capacity, H, W, K, true)) return st;
-  return run_update(prep, capacity, H, W, K, map_in, map_out, step_code, n_inject, seed, 1.f, stream,
-                    "sad_update_topk");
+  return run_update(prep, false, capacity, H, W, K, map_in, map_out, step_code, n_inject, seed, 1.f,
+                    stream, "sad_update_topk");
 }
 
 int sad_grid_seed(const float* prep, int32_t capacity, int32_t H, int32_t W, int32_t s_grid,
@@ -255,9 +285,33 @@ int sad_grid_update(const float* prep, int32_t capacity, int32_t H, int32_t W, i
                     int32_t n_inject, uint64_t seed, void* stream) {
   if (int st = check_problem(capacity, H, W, K, true)) return st;
   if (s_grid < 1 || s_grid > 64) return einval("sad_grid_update: s_grid must be in [1, 64]");
-  return run_update(prep, capacity, (H + s_grid - 1) / s_grid, (W + s_grid - 1) / s_grid, K, map_in,
-                    map_out, step_code, n_inject, seed, static_cast<float>(s_grid), stream,
+  return run_update(prep, false, capacity, (H + s_grid - 1) / s_grid, (W + s_grid - 1) / s_grid, K,
+                    map_in, map_out, step_code, n_inject, seed, static_cast<float>(s_grid), stream,
                     "sad_grid_update");
+}
+
+int sad_pack_candidates(const float* prep, int32_t capacity, uint32_t* cand, void* stream) {
+  if (capacity < 0) return einval("sad_pack_candidates: capacity must be >= 0");
+  if (capacity == 0) return SAD_OK;
+  if (!prep || !cand) return einval("sad_pack_candidates: null pointer");
+  if (!aligned16(prep) || !aligned16(cand))
+    return einval("sad_pack_candidates: pointers must be 16-byte aligned");
+  const float4* p4 = reinterpret_cast<const float4*>(prep);
+  cudaStream_t st = as_stream(stream);
+  {
+    TraceScope tr_(st, "k_pack_candidates");
+    k_pack_candidates<<<(capacity + 255) / 256, 256, 0, st>>>(p4, p4 + capacity, capacity,
+                                                             reinterpret_cast<uint4*>(cand));
+  }
+  return check_launch("k_pack_candidates");
+}
+
+int sad_update_topk_h2(const uint32_t* cand, int32_t capacity, int32_t H, int32_t W, int32_t K,
+                       const uint32_t* map_in, uint32_t* map_out, uint32_t step_code,
+                       int32_t n_inject, uint64_t seed, void* stream) {
+  if (int st = check_problem(capacity, H, W, K, true)) return st;
+  return run_update(cand, true, capacity, H, W, K, map_in, map_out, step_code, n_inject, seed,
+                    1.f, stream, "sad_update_topk_h2");
 }
 
 int sad_grid_expand(const uint32_t* map_grid, int32_t H, int32_t W, int32_t s_grid, int32_t K,

@@ -20,6 +20,8 @@
 // candidates only, not for every candidate of every lane in the warp.
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include "sad_device.cuh"
 
 namespace sad {
@@ -87,14 +89,49 @@ struct SiteRange {
   __device__ __forceinline__ bool has(uint32_t id) const { return id - lo < n; }
 };
 
+// Where a pass reads a candidate's scoring record g = {x, y, tau s, r},
+// m = {G00, G01, G11, active}: the prepared fp32 table (two 16-byte gathers
+// per candidate) ...
+struct F32Sites {
+  const float4* geo;
+  const float4* met;
+  __device__ __forceinline__ void load(uint32_t id, float4& g, float4& m) const {
+    m = ldg(&met[id]);
+    g = ldg(&geo[id]);
+  }
+};
+
+__device__ __forceinline__ float2 half2_bits_to_float2(uint32_t u) {
+  __half2_raw r;
+  r.x = static_cast<unsigned short>(u & 0xffffu);
+  r.y = static_cast<unsigned short>(u >> 16);
+  return __half22float2(__half2(r));
+}
+
+// ... or the 16-byte half2 candidate table (App. "Data Layout and Packing",
+// Packed candidate sites): words {x, y}, {tau s, r}, {G00, G01},
+// {G11, active}, each a half2 with the first value in the low half (one
+// gather per candidate; halves widen to fp32 exactly).
+struct H2Sites {
+  const uint4* cand;
+  __device__ __forceinline__ void load(uint32_t id, float4& g, float4& m) const {
+    const uint4 w = ldg(&cand[id]);
+    const float2 a = half2_bits_to_float2(w.x), b = half2_bits_to_float2(w.y);
+    const float2 c = half2_bits_to_float2(w.z), d = half2_bits_to_float2(w.w);
+    g = make_float4(a.x, a.y, b.x, b.y);
+    m = make_float4(c.x, c.y, d.x, d.y);
+  }
+};
+
 // Logit key of candidate id at (px, py), or 0 if the id cannot enter.
+template <class Sites>
 __device__ __forceinline__ uint64_t cand_key(uint32_t id, SiteRange sr, float px, float py,
-                                             const float4* __restrict__ geo,
-                                             const float4* __restrict__ met) {
+                                             const Sites& sites) {
   if (!sr.has(id)) return 0ull;
-  const float4 m = ldg(&met[id]);
+  float4 g, m;
+  sites.load(id, g, m);
   if (m.w == 0.f) return 0ull;
-  const float l = score_exact(px, py, ldg(&geo[id]), m);
+  const float l = score_exact(px, py, g, m);
   if (l != l) return 0ull;
   return make_key(l, id);
 }
@@ -105,10 +142,9 @@ __device__ __forceinline__ uint64_t cand_key(uint32_t id, SiteRange sr, float px
 // at plane index pix_off.  q_local = row*W + col (injection counter).  Threads
 // outside the image pass inimg = false and get an empty list; the queue
 // column `tid` of s_q must be private to the thread.
-template <int K, int NT, int NG = 4>
+template <int K, int NT, int NG = 4, class Sites>
 __device__ __forceinline__ void pixel_update(uint64_t (&v)[K], bool inimg, int col, int row, int H,
-                                             int W, SiteRange sr, const float4* __restrict__ geo,
-                                             const float4* __restrict__ met,
+                                             int W, SiteRange sr, const Sites& sites,
                                              const uint4* __restrict__ map_in, size_t P,
                                              size_t pix_off, uint32_t code, int J, uint64_t seed,
                                              uint32_t (*s_q)[NT], int tid, float cell = 1.f) {
@@ -126,10 +162,10 @@ __device__ __forceinline__ void pixel_update(uint64_t (&v)[K], bool inimg, int c
 #pragma unroll
   for (int j = 0; j < NP; ++j) {
     const uint4 w = ldg(&map_in[j * P + pix_off + q]);
-    v[4 * j] = cand_key(w.x, sr, px, py, geo, met);
-    v[4 * j + 1] = cand_key(w.y, sr, px, py, geo, met);
-    v[4 * j + 2] = cand_key(w.z, sr, px, py, geo, met);
-    v[4 * j + 3] = cand_key(w.w, sr, px, py, geo, met);
+    v[4 * j] = cand_key(w.x, sr, px, py, sites);
+    v[4 * j + 1] = cand_key(w.y, sr, px, py, sites);
+    v[4 * j + 2] = cand_key(w.z, sr, px, py, sites);
+    v[4 * j + 3] = cand_key(w.w, sr, px, py, sites);
   }
   bitonic_sort_desc<K>(v);
   bool dup = false;
@@ -160,10 +196,7 @@ __device__ __forceinline__ void pixel_update(uint64_t (&v)[K], bool inimg, int c
 #pragma unroll
       for (int u = 0; u < NG; ++u) id[u] = s_q[i + u < qn ? i + u : i][tid];
 #pragma unroll
-      for (int u = 0; u < NG; ++u) {
-        m[u] = ldg(&met[id[u]]);
-        g[u] = ldg(&geo[id[u]]);
-      }
+      for (int u = 0; u < NG; ++u) sites.load(id[u], g[u], m[u]);
 #pragma unroll
       for (int u = 0; u < NG; ++u) {
         uint64_t c = 0ull;

@@ -45,6 +45,7 @@ class EncodeConfig:
     s_grid: int = 1      # candidate grid cell size (> 1: lists per s x s cell; separate calls)
     target_bpp: float | None = None   # scale densify/prune percentiles to end near this bit rate
     tau_diffusion: float = 0.0   # lambda of the log tau gradient smoothing (> 0: separate calls)
+    cand_half2: bool = False   # refresh passes score from the half2 candidate table (separate calls)
     keep_grads: bool = False   # fused: also write the step's gradients to Encoder.grads
     extra: dict = field(default_factory=dict)
 
@@ -152,6 +153,11 @@ class Encoder:
             self.gmaps = [torch.empty((K // 4, self.Hc * self.Wc, 4), dtype=torch.int32, device=self.dev)
                           for _ in range(2)]
             c.fused = False
+        if c.cand_half2:
+            if c.s_grid > 1:
+                raise ValueError("cand_half2 applies to per-pixel lists (s_grid = 1)")
+            self.cand = torch.empty((cap, 4), dtype=torch.int32, device=self.dev)
+            c.fused = False
         if c.fused:
             self.table = capi.batch_table([dict(H=H, W=W, site_offset=0, capacity=cap, pixel_offset=0,
                                                 seed=c.seed + 0x5AD)])
@@ -174,9 +180,14 @@ class Encoder:
             capi.sad_grid_expand(self.gmaps[0], self.H, self.W, c.s_grid, c.K, self.maps[0], self.stream)
             self.t_pass += 1
             return
-        capi.sad_update_topk(self.prep, self.cap, self.H, self.W, c.K, self.maps[0], self.maps[1],
-                             jump_code(self.t_pass, self.H, self.W), c.J, c.seed + 0x5AD,
-                             self.stream)
+        if c.cand_half2:
+            capi.sad_update_topk_h2(self.cand, self.cap, self.H, self.W, c.K, self.maps[0], self.maps[1],
+                                    jump_code(self.t_pass, self.H, self.W), c.J, c.seed + 0x5AD,
+                                    self.stream)
+        else:
+            capi.sad_update_topk(self.prep, self.cap, self.H, self.W, c.K, self.maps[0], self.maps[1],
+                                 jump_code(self.t_pass, self.H, self.W), c.J, c.seed + 0x5AD,
+                                 self.stream)
         self.maps.reverse()
         self.t_pass += 1
 
@@ -238,6 +249,8 @@ class Encoder:
             return
         capi.sad_prepare_sites(self.params, self.H, self.W, self.prep, self.stream)
         if refresh:
+            if c.cand_half2:   # the half2 table follows the sites (App. Packed candidate sites)
+                capi.sad_pack_candidates(self.prep, self.cap, self.cand, self.stream)
             for _ in range(c.cand_passes):
                 self._pass()
         capi.sad_train_grads(self.params, self.prep, self.H, self.W, c.K, self.maps[0], self.target,
