@@ -107,7 +107,7 @@ def test_h2_degenerate(capi, oracle):
     # capacity 0: every list empties
     m, m2 = capi.empty_map(6, 6, 8), capi.empty_map(6, 6, 8)
     capi.sad_topk_seed(capi.empty_prep(0), 0, 6, 6, 8, m)
-    cand = torch.empty((1, 4), dtype=torch.int32, device="cuda")
+    cand = torch.empty((0, 4), dtype=torch.int32, device="cuda")
     capi.sad_pack_candidates(capi.empty_prep(0), 0, cand)
     capi.sad_update_topk_h2(cand, 0, 6, 6, 8, m, m2, 0x10000, 2, 1)
     assert np.all(capi.ids_from_map(m2) == INV)
