@@ -162,7 +162,7 @@ def gen_images(specs):
 NCU_COUNTERS = {
     "k_step_tile": {"sources": ["sad_step.cu", "sad_tile.cuh", "sad_topk.cuh", "sad_device.cuh",
                                 "sad_adam.cuh", "sad_blend.cuh"],
-                    "sha": "d178fb6025757239", "dram_bytes": 33924864, "warp_inst": 150234238},
+                    "sha": "27a3a809a9a80410", "dram_bytes": 34088960, "warp_inst": 147492211},
 }
 ISSUE_PEAK = 152 * 4 * 2.07e9   # warp instructions / s: 152 SMs x 4 schedulers x 1 issue/clk x 2070 MHz
 
@@ -443,6 +443,19 @@ def c3_leg(capi, dev, peak, peak_kind, args, iters=10):
         pass_ms[f"half2_jump{s_j}"] = timed(lambda: capi.sad_update_topk_h2(cand, N, H, W, K, a, b, code, 2, 11))
     pass_ms["pack_candidates"] = timed(lambda: capi.sad_pack_candidates(prep, N, cand))
     del cand
+    # the same 16-pass warm-up with the passes at jump >= 4 on the half2 table
+    from paper_2604_21984_gb300.encode import propagate
+    ha, hb = capi.empty_map(H, W, K, dev), capi.empty_map(H, W, K, dev)
+    codes = [(max(1, 2048 >> (min(t, 10) + 1)) << 16) | t for t in range(16)]
+    for rep in range(2):
+        capi.sad_topk_seed(prep, N, H, W, K, ha)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ha, hb = propagate(prep, N, H, W, K, 2, 11, ha, hb, codes, half2_min_jump=4)
+        torch.cuda.synchronize()
+        jfa_h2_ms = (time.perf_counter() - t0) * 1e3
+    same_h2 = float((ha == a).all(dim=2).all(dim=0).float().mean().item())   # whole lists
+    del ha, hb
     # the JFA 3x3 flood prepass (seed + 11 flood passes) + 4 propagation passes
     fa, fb = capi.empty_map(H, W, K, dev), capi.empty_map(H, W, K, dev)
     torch.cuda.synchronize()
@@ -511,6 +524,8 @@ def c3_leg(capi, dev, peak, peak_kind, args, iters=10):
         "render_ms": round(rb, 4), "backward_ms": round(bb, 4), "jfa_16_passes_ms": round(jfa_ms, 3),
         "flood_prepass_11_plus_4_passes_ms": round(flood_ms, 3),
         "one_pass_ms": {k: round(v, 4) for k, v in pass_ms.items()},
+        "jfa_16_passes_half2_from_jump4_ms": round(jfa_h2_ms, 3),
+        "jfa_half2_lists_equal_frac": round(same_h2, 4),
         "render_packed_16B_ms": round(statistics.mean(pk_ms), 4),
         "render_packed_max_abs_diff": round(float((rgb - rgb_p).abs().max().item()), 5),
         "records": used, "ws_status": st,

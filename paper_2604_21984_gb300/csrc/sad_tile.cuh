@@ -5,8 +5,9 @@
 //     listed sites (nothing from the forward pass is stored), forms its
 //     upstream gradient g (given, or 2(c - I)/P for the fused MSE loss);
 //  2. the tile's distinct sites get slots in a shared hash table (the paper's
-//     multiplicative hash, linear probing); each warp ORs its lanes into its
-//     own word of a per-slot pixel mask (order independent);
+//     multiplicative hash, linear probing), one probe per group of lanes that
+//     list the same id at the same rank; each warp ORs its lanes into its own
+//     word of a per-slot pixel mask (order independent);
 //  3. the masks give each slot a stable, pixel-ordered pair list; one warp
 //     walks a slot's list 32 pairs at a time with the site's parameters in
 //     registers and a fixed-order recursive-halving reduction sums the lane
@@ -353,17 +354,27 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
       for (int w = 0; w < kWarps; ++w) s_mask[w][i] = 0u;
     }
     __syncthreads();
+    // Lanes holding the same id at list position k form a group (neighbouring
+    // pixels mostly list the same sites at the same ranks): its lowest lane
+    // probes the table once and ORs the whole group's bits into the warp's
+    // own mask word, so no two lanes of one instruction hit the same shared
+    // address.  OR is order independent, so the masks (and the pair lists
+    // built from them) are deterministic.
 #pragma unroll
     for (int k = 0; k < K; ++k) {
+      const bool want = (pending >> k & 1u) != 0u;
+      const uint32_t idk = want ? ids[k] : kInvalid;
+      const unsigned grp = __match_any_sync(0xffffffffu, idk);
+      const int leader = __ffs(grp) - 1;
       uint32_t sl = kNone;
-      if (pending >> k & 1u) {
-        sl = probe_slot(ids[k], s_keys);
-        if (sl != kNone) pending &= ~(1u << k);
+      if (want && lane == leader) {
+        sl = probe_slot(idk, s_keys);
+        if (sl != kNone) atomicOr(&s_mask[warp][sl], grp);
       }
+      sl = __shfl_sync(0xffffffffu, sl, leader);
+      if (!want) sl = kNone;
+      if (sl != kNone) pending &= ~(1u << k);
       slot[k] = sl;
-      // the warp's own mask word: OR is order independent, so the masks (and
-      // the pair lists built from them) are deterministic
-      if (sl != kNone) atomicOr(&s_mask[warp][sl], 1u << lane);
     }
     __syncthreads();
     uint64_t packed = 0;
@@ -411,7 +422,11 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
         const float dx = (x0 + static_cast<int>(p & (kTileSide - 1)) + 0.5f) - gs.x;
         const float dy = (y0 + static_cast<int>(p >> 4) + 0.5f) - gs.y;
         const float qq = ms.x * dx * dx + 2.f * ms.y * dx * dy + ms.z * dy * dy;
-        const float n = sqrtf(fmaxf(qq, 0.f));
+        // gradient mode: n and 1/n from one reciprocal square root (the
+        // adjoint's tolerance allows its few-ulp error; no division)
+        const float qc = fmaxf(qq, 0.f);
+        const float rq = rsqrtf(qc);
+        const float n = MODE == kModeStats ? sqrtf(qc) : (qc > 0.f ? qc * rq : 0.f);
         const float w = __expf(gs.z * (gs.w - n) - A.x) * A.y;
         if (MODE == kModeStats) {
           // A = {m, 1/Z, cbar.x, cbar.y}, B = {cbar.z, I}
@@ -446,7 +461,7 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
           acc[3] += d;
           acc[4] += d * n;
           if (n > 0.f) {
-            const float a = d / n;
+            const float a = d * rq;
             acc[5] += a * dx;
             acc[6] += a * dy;
             acc[7] += a * dx * dx;

@@ -46,6 +46,7 @@ class EncodeConfig:
     target_bpp: float | None = None   # scale densify/prune percentiles to end near this bit rate
     tau_diffusion: float = 0.0   # lambda of the log tau gradient smoothing (> 0: separate calls)
     cand_half2: bool = False   # refresh passes score from the half2 candidate table (separate calls)
+    warm_half2_jump: int = 0   # > 0: warm-up passes with at least this jump use the half2 table
     keep_grads: bool = False   # fused: also write the step's gradients to Encoder.grads
     extra: dict = field(default_factory=dict)
 
@@ -66,16 +67,19 @@ def psnr_from_loss(loss: float) -> float:
 
 
 def warm_start(target, n0, params, prep, map_a, map_b, K, J, lambda_init, seed, stream=None,
-               prepass="propagate", passes_after=4):
+               prepass="propagate", passes_after=4, half2_min_jump=0):
     """Gradient-weighted sites (Sec. 4.4) with tau s d0 = 4, d0 = sqrt(P/n0),
     then the top-K field's warm-up: seed + ceil(log2 max(H, W)) propagation
     passes at the jump schedule (Sec. 4.3), or with prepass="flood" the JFA
     prepass (seed + ceil(log2 max(H, W)) 3x3 flood passes, App. "Candidate
     Field and Jump Schedule") followed by `passes_after` propagation passes
-    at jump 1; injection seed `seed + 0x5AD`.  params: float32[11, cap]
-    (cap >= n0; slots from n0 on inactive); prep: the prepared table;
-    map_a/map_b: the two map buffers.  Returns (current map, other map,
-    propagation passes run)."""
+    at jump 1; injection seed `seed + 0x5AD`.  With half2_min_jump > 0 the
+    propagation passes whose jump is at least that score from the half2
+    candidate table (App. "Data Layout and Packing", Packed candidate
+    sites): their gathers scatter, and the 16-byte record halves them.
+    params: float32[11, cap] (cap >= n0; slots from n0 on inactive); prep:
+    the prepared table; map_a/map_b: the two map buffers.  Returns (current
+    map, other map, propagation passes run)."""
     H, W = int(target.shape[0]), int(target.shape[1])
     cap = params.shape[1]
     s = 1.0 / max(H, W)
@@ -93,10 +97,27 @@ def warm_start(target, n0, params, prep, map_a, map_b, K, J, lambda_init, seed, 
         codes = [(1 << 16) | t for t in range(passes_after)]
     else:
         codes = [jump_code(t, H, W) for t in range(lb)]
-    for code in codes:
-        capi.sad_update_topk(prep, cap, H, W, K, map_a, map_b, code, J, seed + 0x5AD, stream)
-        map_a, map_b = map_b, map_a
+    map_a, map_b = propagate(prep, cap, H, W, K, J, seed + 0x5AD, map_a, map_b, codes, stream,
+                             half2_min_jump)
     return map_a, map_b, len(codes)
+
+
+def propagate(prep, cap, H, W, K, J, seed, map_a, map_b, codes, stream=None, half2_min_jump=0):
+    """Propagation passes with the given step codes (Sec. 4.3), ping-ponging
+    map_a -> map_b; passes whose jump (code >> 16) is at least
+    half2_min_jump > 0 score from the half2 candidate table.  Returns
+    (current map, other map)."""
+    cand = None
+    if half2_min_jump > 0 and any((c >> 16) >= half2_min_jump for c in codes):
+        cand = torch.empty((max(cap, 1), 4), dtype=torch.int32, device=prep.device)
+        capi.sad_pack_candidates(prep, cap, cand, stream)
+    for code in codes:
+        if cand is not None and (code >> 16) >= half2_min_jump:
+            capi.sad_update_topk_h2(cand, cap, H, W, K, map_a, map_b, code, J, seed, stream)
+        else:
+            capi.sad_update_topk(prep, cap, H, W, K, map_a, map_b, code, J, seed, stream)
+        map_a, map_b = map_b, map_a
+    return map_a, map_b
 
 
 class Encoder:
@@ -207,7 +228,7 @@ class Encoder:
             return
         a, b, self.t_pass = warm_start(self.target, self.n0, self.params, self.prep, self.maps[0],
                                        self.maps[1], c.K, c.J, c.lambda_init, c.seed, self.stream,
-                                       prepass=c.prepass)
+                                       prepass=c.prepass, half2_min_jump=c.warm_half2_jump)
         self.maps = [a, b]
         if c.fused:
             # Adam step 1 next; pass indices continue after the warm-up's; the
