@@ -23,8 +23,8 @@ namespace sad {
 
 constexpr int kTileSide = 16;
 constexpr int kTileThreads = kTileSide * kTileSide;
-constexpr int kSlots = 128;  // shared hash table size per round (power of 2)
-constexpr int kLog2Slots = 7;
+constexpr int kSlots = 256;  // shared hash table size per round (power of 2)
+constexpr int kLog2Slots = 8;
 constexpr uint32_t kNone = 0xffffffffu;
 constexpr int kModeGrad = 0;
 constexpr int kModeStats = 1;
@@ -406,88 +406,100 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
     }
     __syncthreads();
     // one warp per slot: lanes walk the slot's pixel-ordered pairs, then a
-    // fixed butterfly sums the 32 lane partials (deterministic order)
-    for (int sl = warp; sl < kSlots; sl += kWarps) {
-      const uint32_t cnt = s_cnt[sl];
-      if (cnt == 0) continue;
-      const uint32_t id = s_keys[sl];
-      const uint32_t off = s_off[sl];
-      const float4 gs = ldg(&geo[id]), ms = ldg(&met[id]), cs = ldg(&col[id]);
-      float acc[10];
+    // fixed-order reduction sums the 32 lane partials.  Warps take balanced
+    // slot ranges: a slot's work is its pairs plus one reduction (counted as
+    // 32 pairs), and warp w takes the slots whose work prefix falls in
+    // [w T / 8, (w + 1) T / 8) of the tile's total T.
+    const uint32_t tw = static_cast<uint32_t>(total & 0xffffffffu) + 32u * static_cast<uint32_t>(total >> 32);
+    const uint32_t wlo = static_cast<uint32_t>((static_cast<uint64_t>(tw) * warp) / kWarps);
+    const uint32_t whi = static_cast<uint32_t>((static_cast<uint64_t>(tw) * (warp + 1)) / kWarps);
+    for (int g = 0; g < kSlots / 32; ++g) {
+      const int mine = g * 32 + lane;
+      const uint32_t wpre = s_off[mine] + 32u * s_rix[mine];
+      unsigned todo = __ballot_sync(0xffffffffu, s_cnt[mine] != 0u && wpre >= wlo && wpre < whi);
+      while (todo) {
+        const int sl = g * 32 + __ffs(todo) - 1;
+        todo &= todo - 1;
+        const uint32_t cnt = s_cnt[sl];
+        const uint32_t id = s_keys[sl];
+        const uint32_t off = s_off[sl];
+        const float4 gs = ldg(&geo[id]), ms = ldg(&met[id]), cs = ldg(&col[id]);
+        float acc[10];
 #pragma unroll
-      for (int j = 0; j < 10; ++j) acc[j] = 0.f;
-      for (uint32_t i = lane; i < cnt; i += 32) {
-        const uint32_t p = s_list[off + i];
-        const float4 A = s_pa[p];
-        const float dx = (x0 + static_cast<int>(p & (kTileSide - 1)) + 0.5f) - gs.x;
-        const float dy = (y0 + static_cast<int>(p >> 4) + 0.5f) - gs.y;
-        const float qq = ms.x * dx * dx + 2.f * ms.y * dx * dy + ms.z * dy * dy;
-        // gradient mode: n and 1/n from one reciprocal square root (the
-        // adjoint's tolerance allows its few-ulp error; no division)
-        const float qc = fmaxf(qq, 0.f);
-        const float rq = rsqrtf(qc);
-        const float n = MODE == kModeStats ? sqrtf(qc) : (qc > 0.f ? qc * rq : 0.f);
-        const float w = __expf(gs.z * (gs.w - n) - A.x) * A.y;
-        if (MODE == kModeStats) {
-          // A = {m, 1/Z, cbar.x, cbar.y}, B = {cbar.z, I}
-          const float4 B = s_pb[p];
-          const float ex = A.z - B.y, ey = A.w - B.z, ez = B.x - B.w;
-          const float e = ex * ex + ey * ey + ez * ez;
-          const float om = w * e;
-          acc[0] += w;
-          acc[1] += om;
-          acc[2] += om * dx;
-          acc[3] += om * dy;
-          acc[4] += om * dx * dx;
-          acc[5] += om * dx * dy;
-          acc[6] += om * dy * dy;
-          float3 cp;
-          const float4 C = s_pc[p];
-          if (__float_as_uint(C.w) == id) {
-            cp = make_float3(C.x, C.y, C.z);
+        for (int j = 0; j < 10; ++j) acc[j] = 0.f;
+        for (uint32_t i = lane; i < cnt; i += 32) {
+          const uint32_t p = s_list[off + i];
+          const float4 A = s_pa[p];
+          const float dx = (x0 + static_cast<int>(p & (kTileSide - 1)) + 0.5f) - gs.x;
+          const float dy = (y0 + static_cast<int>(p >> 4) + 0.5f) - gs.y;
+          const float qq = ms.x * dx * dx + 2.f * ms.y * dx * dy + ms.z * dy * dy;
+          // gradient mode: n and 1/n from one reciprocal square root (the
+          // adjoint's tolerance allows its few-ulp error; no division)
+          const float qc = fmaxf(qq, 0.f);
+          const float rq = rsqrtf(qc);
+          const float n = MODE == kModeStats ? sqrtf(qc) : (qc > 0.f ? qc * rq : 0.f);
+          const float w = __expf(gs.z * (gs.w - n) - A.x) * A.y;
+          if (MODE == kModeStats) {
+            // A = {m, 1/Z, cbar.x, cbar.y}, B = {cbar.z, I}
+            const float4 B = s_pb[p];
+            const float ex = A.z - B.y, ey = A.w - B.z, ez = B.x - B.w;
+            const float e = ex * ex + ey * ey + ez * ez;
+            const float om = w * e;
+            acc[0] += w;
+            acc[1] += om;
+            acc[2] += om * dx;
+            acc[3] += om * dy;
+            acc[4] += om * dx * dx;
+            acc[5] += om * dx * dy;
+            acc[6] += om * dy * dy;
+            float3 cp;
+            const float4 C = s_pc[p];
+            if (__float_as_uint(C.w) == id) {
+              cp = make_float3(C.x, C.y, C.z);
+            } else {
+              const float inv = 1.f / (1.f - w);
+              cp = make_float3((A.z - w * cs.x) * inv, (A.w - w * cs.y) * inv, (B.x - w * cs.z) * inv);
+            }
+            const float fx = cp.x - B.y, fy = cp.y - B.z, fz = cp.z - B.w;
+            acc[7] += fx * fx + fy * fy + fz * fz - e;
           } else {
-            const float inv = 1.f / (1.f - w);
-            cp = make_float3((A.z - w * cs.x) * inv, (A.w - w * cs.y) * inv, (B.x - w * cs.z) * inv);
-          }
-          const float fx = cp.x - B.y, fy = cp.y - B.z, fz = cp.z - B.w;
-          acc[7] += fx * fx + fy * fy + fz * fz - e;
-        } else {
-          // A = {m, 1/Z, g.cbar, gx}, B = {gy, gz}
-          const float2 B = s_pg[p];
-          const float d = w * (A.w * cs.x + B.x * cs.y + B.y * cs.z - A.z);
-          acc[0] += w * A.w;
-          acc[1] += w * B.x;
-          acc[2] += w * B.y;
-          acc[3] += d;
-          acc[4] += d * n;
-          if (n > 0.f) {
-            const float a = d * rq;
-            acc[5] += a * dx;
-            acc[6] += a * dy;
-            acc[7] += a * dx * dx;
-            acc[8] += a * dx * dy;
-            acc[9] += a * dy * dy;
+            // A = {m, 1/Z, g.cbar, gx}, B = {gy, gz}
+            const float2 B = s_pg[p];
+            const float d = w * (A.w * cs.x + B.x * cs.y + B.y * cs.z - A.z);
+            acc[0] += w * A.w;
+            acc[1] += w * B.x;
+            acc[2] += w * B.y;
+            acc[3] += d;
+            acc[4] += d * n;
+            if (n > 0.f) {
+              const float a = d * rq;
+              acc[5] += a * dx;
+              acc[6] += a * dy;
+              acc[7] += a * dx * dx;
+              acc[8] += a * dx * dy;
+              acc[9] += a * dy * dy;
+            }
           }
         }
-      }
-      // sum the 10 lane partials over the warp by recursive halving (fixed
-      // order): afterwards lanes 2i and 2i+1 hold the total of statistic i
-      const float tot = warp_sum10_halving(acc, lane);
-      const uint32_t ridx = s_base + s_rix[sl];
-      const int stat = lane >> 1;
-      if (ridx < max_records) {
-        float* dst = reinterpret_cast<float*>(&records[ridx]);
-        if (lane == 0) {
-          dst[0] = __uint_as_float(id);
-          dst[1] = __uint_as_float(c.img);
+        // sum the 10 lane partials over the warp by recursive halving (fixed
+        // order): afterwards lanes 2i and 2i+1 hold the total of statistic i
+        const float tot = warp_sum10_halving(acc, lane);
+        const uint32_t ridx = s_base + s_rix[sl];
+        const int stat = lane >> 1;
+        if (ridx < max_records) {
+          float* dst = reinterpret_cast<float*>(&records[ridx]);
+          if (lane == 0) {
+            dst[0] = __uint_as_float(id);
+            dst[1] = __uint_as_float(c.img);
+          }
+          if ((lane & 1) == 0 && stat < 10) {
+            const float v = isfinite(tot) ? tot : 0.f;  // non-finite contributions are dropped
+            dst[2 + stat] = v;
+            if (v != 0.f) atomicMax(&s_pmax[stat], __float_as_uint(fabsf(v)));
+          }
+        } else if (lane == 0) {
+          hdr->overflow = 1u;
         }
-        if ((lane & 1) == 0 && stat < 10) {
-          const float v = isfinite(tot) ? tot : 0.f;  // non-finite contributions are dropped
-          dst[2 + stat] = v;
-          if (v != 0.f) atomicMax(&s_pmax[stat], __float_as_uint(fabsf(v)));
-        }
-      } else if (lane == 0) {
-        hdr->overflow = 1u;
       }
     }
     if (!__syncthreads_or(pending != 0u)) break;
