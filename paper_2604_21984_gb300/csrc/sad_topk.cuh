@@ -178,12 +178,13 @@ __device__ __forceinline__ void pixel_update(uint64_t (&v)[K], bool inimg, int c
     bitonic_sort_desc<K>(v);
   }
 
-  // B + C. Novel ids (valid, not in the list, not yet queued) go to the
-  // thread's queue column.  A queued id cannot be in the list when it is
-  // scored: the list only gains queued ids, and the queue holds distinct ids.
-  // So the queue is scored in groups of NG (2 NG independent gathers in
-  // flight) and merged; the result is the top K of the union, whatever the
-  // order.  The drain and offer bodies each appear at a handful of call sites
+  // B + C. Novel ids (valid, not in the list) go to the thread's queue
+  // column without a scan of the queue: an id that two neighbours offer is
+  // queued twice and scored twice, and the insertion test drops the second
+  // copy.  (Scanning the queue for every offer was a chain of dependent
+  // shared loads, the slowest part of the pass at long jumps.)  The queue
+  // is scored in groups of NG (2 NG independent gathers in flight) and
+  // merged; the result is the top K of the union, whatever the order.  The drain and offer bodies each appear at a handful of call sites
   // only: fully unrolling them over all candidates made the kernel too large
   // for the instruction cache when most candidates are novel (the long jumps
   // of the warm-up).
@@ -204,15 +205,16 @@ __device__ __forceinline__ void pixel_update(uint64_t (&v)[K], bool inimg, int c
           const float l = score_exact(px, py, g[u], m[u]);
           if (l == l) c = make_key(l, id[u]);
         }
-        if (c > v[K - 1]) list_insert<K>(v, c);
+        // an id queued twice (offered by two neighbours) finds itself in
+        // the list the second time; only candidates that beat the list's
+        // last key pay for that test
+        if (c > v[K - 1] && !list_has<K>(v, id[u])) list_insert<K>(v, c);
       }
     }
     qn = 0;
   };
   auto offer = [&](uint32_t id) {
     if (!sr.has(id) || list_has<K>(v, id)) return;
-    for (int i = 0; i < qn; ++i)
-      if (s_q[i][tid] == id) return;
     s_q[qn++][tid] = id;
   };
   static_assert(kQueue >= K, "queue must hold one neighbour list");
