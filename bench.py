@@ -424,6 +424,7 @@ def c3_leg(capi, dev, peak, peak_kind, args, iters=10):
     # one pass from the warm map, float32 table vs half2 candidate table, at
     # jump 1 (a training refresh) and at the warm-up's longer jumps
     cand = torch.empty((N, 4), dtype=torch.int32, device=dev)
+    capi.sad_pack_candidates(prep, N, cand)
     E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
     def timed(fn, n=10):

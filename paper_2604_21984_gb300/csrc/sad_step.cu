@@ -180,7 +180,23 @@ __global__ void k_site_step(const BatchDesc d, float* __restrict__ params, float
                             unsigned long long* __restrict__ accq, AdamArgs A,
                             const int32_t* __restrict__ state, float* __restrict__ grads_out,
                             bool adam) {
+  // Adam's bias corrections 1 - beta^t in double: once per block for the
+  // image of its first slot (a double-precision pow per site thread cost
+  // more than the rest of the kernel); threads of another image compute
+  // their own.
+  __shared__ int s_b;
+  __shared__ float s_bc[2];
   const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (adam) {
+    if (threadIdx.x == 0) {
+      const int b0 = image_of_slot(d, blockIdx.x * blockDim.x);
+      const int t0 = state[kStateWords * d.img[b0].state];
+      s_b = b0;
+      s_bc[0] = static_cast<float>(1.0 - pow(static_cast<double>(A.beta1), t0));
+      s_bc[1] = static_cast<float>(1.0 - pow(static_cast<double>(A.beta2), t0));
+    }
+    __syncthreads();  // adam is the same for the whole grid
+  }
   if (j >= d.n_sites) return;
   const int b = image_of_slot(d, j);
   const BatchImg im = d.img[b];
@@ -241,9 +257,12 @@ __global__ void k_site_step(const BatchDesc d, float* __restrict__ params, float
       for (int k = 0; k < kNParams; ++k) grads_out[k * c + i] = g[k];
     }
     if (p[PX] >= 0.f) {
-      const int t = state[kStateWords * im.state];
-      const float bc1 = static_cast<float>(1.0 - pow(static_cast<double>(A.beta1), t));
-      const float bc2 = static_cast<float>(1.0 - pow(static_cast<double>(A.beta2), t));
+      float bc1 = s_bc[0], bc2 = s_bc[1];
+      if (b != s_b) {
+        const int t = state[kStateWords * im.state];
+        bc1 = static_cast<float>(1.0 - pow(static_cast<double>(A.beta1), t));
+        bc2 = static_cast<float>(1.0 - pow(static_cast<double>(A.beta2), t));
+      }
       adam_site(p, g, m, v, c, i, A, bc1, bc2, im.H, im.W);
 #pragma unroll
       for (int k = 0; k < kNParams; ++k) params[k * c + i] = p[k];
