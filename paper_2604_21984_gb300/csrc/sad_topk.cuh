@@ -217,35 +217,42 @@ __device__ __forceinline__ void pixel_update(uint64_t (&v)[K], bool inimg, int c
     if (!sr.has(id) || list_has<K>(v, id)) return;
     s_q[qn++][tid] = id;
   };
-  static_assert(kQueue >= K, "queue must hold one neighbour list");
+  // One drain call site (the drain body is large; more copies cost
+  // instruction-cache misses): stages 0..3 offer the four neighbours'
+  // lists, stage 4 the injected ids.  After a stage the queue is drained
+  // unless it has room for the next one: K ids before a neighbour, J
+  // (at most 16, checked by every entry point) before the injections.
+  static_assert(kQueue >= K && kQueue >= 16, "queue must hold a neighbour list or the injections");
   const int s = static_cast<int>(code >> 16);
-#pragma unroll 1
-  for (int d = 0; d < 4; ++d) {
-    const int nc = d == 0 ? col - s : (d == 1 ? col + s : col);
-    const int nr = d == 2 ? row - s : (d == 3 ? row + s : row);
-    if (nc < 0 || nc >= W || nr < 0 || nr >= H) continue;
-    const size_t nq = pix_off + static_cast<size_t>(nr) * W + nc;
-    uint4 w[NP];
-#pragma unroll
-    for (int j = 0; j < NP; ++j) w[j] = ldg(&map_in[j * P + nq]);
-#pragma unroll
-    for (int j = 0; j < NP; ++j) {
-      offer(w[j].x);
-      offer(w[j].y);
-      offer(w[j].z);
-      offer(w[j].w);
-    }
-    if (qn > kQueue - K) drain();  // room for the next neighbour's K ids
-  }
   const uint64_t base = (static_cast<uint64_t>(code) << 32);
 #pragma unroll 1
-  for (int j = 0; j < J; ++j) {
-    const uint64_t ctr = base | static_cast<uint32_t>(q * static_cast<uint32_t>(J) + j);
-    const uint64_t h = splitmix64_at(seed, ctr);
-    offer(sr.lo + static_cast<uint32_t>(((h >> 32) * static_cast<uint64_t>(sr.n)) >> 32));
-    if (qn == kQueue) drain();
+  for (int d = 0; d < 5; ++d) {
+    if (d < 4) {
+      const int nc = d == 0 ? col - s : (d == 1 ? col + s : col);
+      const int nr = d == 2 ? row - s : (d == 3 ? row + s : row);
+      if (nc >= 0 && nc < W && nr >= 0 && nr < H) {
+        const size_t nq = pix_off + static_cast<size_t>(nr) * W + nc;
+        uint4 w[NP];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) w[j] = ldg(&map_in[j * P + nq]);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+          offer(w[j].x);
+          offer(w[j].y);
+          offer(w[j].z);
+          offer(w[j].w);
+        }
+      }
+    } else {
+#pragma unroll 1
+      for (int j = 0; j < J; ++j) {
+        const uint64_t ctr = base | static_cast<uint32_t>(q * static_cast<uint32_t>(J) + j);
+        const uint64_t h = splitmix64_at(seed, ctr);
+        offer(sr.lo + static_cast<uint32_t>(((h >> 32) * static_cast<uint64_t>(sr.n)) >> 32));
+      }
+    }
+    if (d == 4 || qn > kQueue - (d == 3 ? (J > K ? J : K) : K)) drain();
   }
-  drain();
 }
 
 }  // namespace sad
