@@ -11,16 +11,24 @@ namespace sad {
 // with an online max-subtracted softmax: m = running max of the logits,
 // z = sum exp(l - m), c = sum exp(l - m) c_i, rescaled by exp(m_old - m_new)
 // when the max grows (the same w_i = exp(l_i - m)/z in exact arithmetic, no
-// per-entry state kept).  Black if no listed site is valid.
+// per-entry state kept).  Lists are sorted by logit, so the rescale is a
+// rare branch rather than a second exponential per entry.  Black if no
+// listed site is valid.
 __device__ __forceinline__ void blend_step(float l, bool ok, float4 ck, float& m, float& z, float3& c) {
-  const float mn = ok ? fmaxf(m, l) : m;
-  const float a = m == mn ? 1.f : __expf(m - mn);   // unchanged max (or still -inf): 1
-  const float b = ok ? (l == mn ? 1.f : __expf(l - mn)) : 0.f;
-  z = z * a + b;
-  c.x = c.x * a + b * ck.x;
-  c.y = c.y * a + b * ck.y;
-  c.z = c.z * a + b * ck.z;
-  m = mn;
+  if (!ok) return;
+  if (l > m) {  // a new maximum: rare after the first entry (lists are sorted by logit)
+    const float a = __expf(m - l);
+    z *= a;
+    c.x *= a;
+    c.y *= a;
+    c.z *= a;
+    m = l;
+  }
+  const float b = l == m ? 1.f : __expf(l - m);
+  z += b;
+  c.x += b * ck.x;
+  c.y += b * ck.y;
+  c.z += b * ck.z;
 }
 
 template <int NP>

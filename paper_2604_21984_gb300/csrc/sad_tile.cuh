@@ -238,6 +238,8 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
     }
   } else {
     // online max-subtracted softmax over the list, kB entries at a time
+    // (a new maximum is rare: lists are sorted by logit, so the rescale
+    // is a branch, not a second exponential per entry)
     constexpr int kB = 1;
 #pragma unroll
     for (int k0 = 0; k0 < K; k0 += kB) {
@@ -254,14 +256,21 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
         const bool ok = ids[k0 + u] != kInvalid && mt[u].w != 0.f;
         vm |= ok ? (1u << (k0 + u)) : 0u;
         const float lk = score_fast(px, py, g[u], mt[u]).l;
-        const float mn = ok ? fmaxf(m, lk) : m;
-        const float a = m == mn ? 1.f : __expf(m - mn);   // unchanged max (or still -inf): 1
-        const float b = ok ? (lk == mn ? 1.f : __expf(lk - mn)) : 0.f;
-        z = z * a + b;
-        cb.x = cb.x * a + b * ck[u].x;
-        cb.y = cb.y * a + b * ck[u].y;
-        cb.z = cb.z * a + b * ck[u].z;
-        m = mn;
+        if (ok) {
+          if (lk > m) {  // a new maximum: rare after the first entry (lists are sorted by logit)
+            const float a = __expf(m - lk);
+            z *= a;
+            cb.x *= a;
+            cb.y *= a;
+            cb.z *= a;
+            m = lk;
+          }
+          const float b = lk == m ? 1.f : __expf(lk - m);
+          z += b;
+          cb.x += b * ck[u].x;
+          cb.y += b * ck[u].y;
+          cb.z += b * ck[u].z;
+        }
       }
     }
   }
