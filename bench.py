@@ -537,7 +537,7 @@ def c3_leg(capi, dev, peak, peak_kind, args, iters=10):
 
 
 def c4_leg(capi, dev, peak, peak_kind, args, n_images=64, seed=4000):
-    """64 uneven images: batched fused step (CUDA graph, autotuned K/J) vs the
+    """64 uneven images: batched fused step (CUDA graph, autotuned K/J/tile shape) vs the
     plain loop (one image at a time, the same fused kernels on a one-image
     batch, no graph), equal iterations."""
     import torch
@@ -552,13 +552,13 @@ def c4_leg(capi, dev, peak, peak_kind, args, n_images=64, seed=4000):
     imgs = [torch.from_numpy(a).to(dev) for a in imgs_np]
     del imgs_np
     P = sum(H * W for H, W in sizes)
-    (K, J), table = autotune(imgs[:8], iters=iters, seed=seed)
+    (K, J, TW), table = autotune(imgs[:8], iters=iters, seed=seed)
     E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     # batched
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     seeds = [seed + 1 + i for i in range(n_images)]
-    tr = BatchTrainer(imgs, BatchConfig(K=K, J=J), seeds=seeds)
+    tr = BatchTrainer(imgs, BatchConfig(K=K, J=J, tile_w=TW), seeds=seeds)
     torch.cuda.synchronize()
     b_init = time.perf_counter() - t0
     tr.run(2)                              # graph capture outside the timed region
@@ -598,9 +598,9 @@ def c4_leg(capi, dev, peak, peak_kind, args, n_images=64, seed=4000):
     return {
         "workload": f"{n_images} images, long side log-uniform 256..2048, aspect 1..1.5, "
                     f"{P / 1e6:.1f} MP total, 0.06 sites/px, {iters} iterations",
-        "autotune": {"picked": {"K": K, "J": J},
-                     "candidates": [{"K": k, "J": j, "ms_per_iter": round(ms, 3), "psnr_db": round(ps, 3)}
-                                    for k, j, ms, ps in table]},
+        "autotune": {"picked": {"K": K, "J": J, "tile": f"{TW}x{256 // TW}"},
+                     "candidates": [{"K": k, "J": j, "tile": f"{tw}x{256 // tw}", "ms_per_iter": round(ms, 3),
+                                     "psnr_db": round(ps, 3)} for k, j, tw, ms, ps in table]},
         "batched": {"train_s": round(b_train, 4), "init_s": round(b_init, 3),
                     "images_per_s": round(n_images / (b_train + b_init), 3),
                     "train_mpix_per_s": round(P * iters / b_train / 1e6, 1),

@@ -412,7 +412,7 @@ typedef struct sad_batch_image {
  * so one workspace serves any sequence of tables over the same arrays.  A
  * call that returned an error may leave them dirty: zero the workspace again. */
 size_t sad_step_workspace_bytes(const sad_batch_image* images, int32_t B, int32_t K,
-                                int32_t total_capacity, int64_t total_pixels,
+                                int32_t tile_w, int32_t total_capacity, int64_t total_pixels,
                                 int64_t max_records);
 
 /* sad_prepare_sites for every image of a batch (each with its own s); only
@@ -422,7 +422,10 @@ int sad_prepare_batch(const sad_batch_image* images, int32_t B, const float* par
 
 /*
  * sad_train_step -- one fused training iteration of every image of a batch
- * (Sec. 5: no host work inside an iteration).  Per 16x16 tile: one
+ * (Sec. 5: no host work inside an iteration).  tile_w: 16 (16x16 pixel
+ * tiles) or 32 (32x8 tiles), the tile shape of the adjoint's per-tile
+ * reduction (an autotuning choice; the lists do not depend on it, the
+ * gradients only by rounding).  Per tile: one
  * propagation pass at jump 1 (sad_update_topk semantics with the image's own
  * site range and seed) writing the image's next map, then, on those lists,
  * the fused render + MSE + adjoint of sad_train_grads; per site: the
@@ -448,8 +451,8 @@ int sad_prepare_batch(const sad_batch_image* images, int32_t B, const float* par
  * join or leave between calls (continuous batching); images must not share
  * pixels (SAD_EINVAL).
  */
-int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t J, float* params,
-                   float* m, float* v, float* prep, int32_t total_capacity,
+int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t J, int32_t tile_w,
+                   float* params, float* m, float* v, float* prep, int32_t total_capacity,
                    uint32_t* map_in, uint32_t* map_out, int64_t total_pixels,
                    const float* targets, float* loss, const sad_adam_hparams* hp,
                    int32_t* image_state, int32_t n_states, float* grads_out, void* workspace,
@@ -461,7 +464,8 @@ int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t 
  * current map from its state row) for every image of the table, advancing
  * each row's pass index and parity (t unchanged): the extra passes of a
  * candidate update with n_cand > 1 (App. "Candidate Field and Jump
- * Schedule", Candidate update frequency).  Arguments as sad_train_step.
+ * Schedule", Candidate update frequency).  Arguments as sad_train_step
+ * (the pass does not depend on a tile shape).
  */
 int sad_batch_update(const sad_batch_image* images, int32_t B, int32_t K, int32_t J,
                      const float* prep, int32_t total_capacity, uint32_t* map_in, uint32_t* map_out,

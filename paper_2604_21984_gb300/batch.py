@@ -16,7 +16,9 @@ encoder's (same seeds, same pass numbering).
 """
 from __future__ import annotations
 
+import json
 import math
+import os
 import time
 from dataclasses import dataclass
 
@@ -36,6 +38,7 @@ class BatchConfig:
     lr: tuple = (1e-3, 1e-3, 1e-2, 1e-3, 5e-3, 5e-3, 5e-3, 1e-2, 1e-2, 1e-2, 0.0)
     graph: bool = True
     cand_every: int = 1   # f_cand: candidate refresh every this many iterations
+    tile_w: int = 16      # adjoint tiles: 16 (16x16) or 32 (32x8)
 
 
 class BatchTrainer:
@@ -72,18 +75,18 @@ class BatchTrainer:
         self.loss = torch.zeros(len(targets), **f32)
         self.state = torch.zeros((len(targets), 4), dtype=torch.int32, device=self.dev)
         self.hp = capi.adam_hparams(lr=c.lr)
-        self.ws = capi.step_workspace(self.table, K, site, pix, device=self.dev)
+        self.ws = capi.step_workspace(self.table, K, site, pix, device=self.dev, tile_w=c.tile_w)
         self.graph = None
         self.steps = 0
         self.refreshes = 0
         self._init(targets)
         self._call = capi.TrainStepCall(self.table, c.K, c.J, self.params, self.m, self.v, self.prep,
                                         self.bufs[0], self.bufs[1], self.total_pixels, self.targets,
-                                        self.loss, self.hp, self.state, self.ws)
+                                        self.loss, self.hp, self.state, self.ws, tile_w=c.tile_w)
         keep = capi.batch_table([dict(im, flags=capi.STEP_KEEP_LISTS) for im in self.images])
         self._call_keep = capi.TrainStepCall(keep, c.K, c.J, self.params, self.m, self.v, self.prep,
                                              self.bufs[0], self.bufs[1], self.total_pixels, self.targets,
-                                             self.loss, self.hp, self.state, self.ws)
+                                             self.loss, self.hp, self.state, self.ws, tile_w=c.tile_w)
 
     @property
     def maps(self):
@@ -173,16 +176,63 @@ class BatchTrainer:
         return [float("inf") if l <= 0 else 10 * math.log10(3.0 / l) for l in self.loss.tolist()]
 
 
-def autotune(targets, iters: int = 100, candidates=((16, 4), (16, 2), (8, 4), (8, 2)),
-             psnr_tol: float = 0.05, seed: int = 0):
-    """Pick (K, J) for a batch: each candidate trains `targets` (a sample of
-    the batch) for `iters` iterations, the intended budget, so that the PSNR
-    compared is the one the job will reach; the pick is the fastest candidate
-    whose mean PSNR is within psnr_tol dB of the best.  Returns (best (K, J),
-    table of (K, J, ms per iteration, mean PSNR))."""
+def tune_key(image_sizes, iters, candidates, psnr_tol, sites_per_pixel, device_name):
+    """Cache key of an autotuner decision: the batch's image sizes (sorted),
+    the iteration budget, the candidates, the PSNR tolerance, the site
+    density and the GPU."""
+    return json.dumps({"images": sorted([int(h), int(w)] for h, w in image_sizes), "iters": int(iters),
+                       "candidates": [list(map(int, c)) for c in candidates], "psnr_tol": float(psnr_tol),
+                       "sites_per_pixel": float(sites_per_pixel), "gpu": str(device_name)}, sort_keys=True)
+
+
+def cache_load(path, key):
+    """The cached decision for key, or None (a missing or unreadable file is
+    an empty cache)."""
+    try:
+        with open(path) as f:
+            return json.load(f).get(key)
+    except (OSError, ValueError):
+        return None
+
+
+def cache_store(path, key, value):
+    """Add key -> value to the JSON cache file (written whole, then renamed)."""
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except (OSError, ValueError):
+        data = {}
+    data[key] = value
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+TUNE_CANDIDATES = ((16, 4, 16), (16, 4, 32), (16, 2, 16), (8, 4, 16), (8, 4, 32), (8, 2, 16))
+
+
+def autotune(targets, iters: int = 100, candidates=TUNE_CANDIDATES, psnr_tol: float = 0.05,
+             seed: int = 0, cache_path: str | None = None):
+    """Pick (K, J, tile width) for a batch: each candidate (a (K, J) pair
+    means tile width 16) trains `targets` (a sample of the batch) for
+    `iters` iterations, the intended budget, so that the PSNR compared is
+    the one the job will reach; the pick is the fastest candidate whose
+    (K, J) reaches a mean PSNR (over its tile shapes) within psnr_tol dB of
+    the best (K, J).  With cache_path, the decision
+    is read from / written to a JSON cache keyed by tune_key.  Returns (best
+    (K, J, tile_w), table of (K, J, tile_w, ms per iteration, mean PSNR))."""
+    candidates = tuple(tuple(c) if len(c) == 3 else (c[0], c[1], 16) for c in candidates)
+    key = None
+    if cache_path is not None:
+        key = tune_key([t.shape[:2] for t in targets], iters, candidates, psnr_tol,
+                       BatchConfig().sites_per_pixel, torch.cuda.get_device_name(targets[0].device))
+        hit = cache_load(cache_path, key)
+        if hit is not None:
+            return tuple(hit["pick"]), [tuple(r) for r in hit["table"]]
     rows = []
-    for K, J in candidates:
-        tr = BatchTrainer(targets, BatchConfig(K=K, J=J, seed=seed))
+    for K, J, TW in candidates:
+        tr = BatchTrainer(targets, BatchConfig(K=K, J=J, seed=seed, tile_w=TW))
         n_t = min(10, max(1, iters // 4))
         tr.run(iters - n_t)
         torch.cuda.synchronize()
@@ -191,9 +241,19 @@ def autotune(targets, iters: int = 100, candidates=((16, 4), (16, 2), (8, 4), (8
         torch.cuda.synchronize()
         ms = (time.perf_counter() - t0) * 1e3 / n_t
         p = sum(tr.psnr()) / len(targets)
-        rows.append((K, J, ms, p))
+        rows.append((K, J, TW, ms, p))
         del tr
-    best_p = max(r[3] for r in rows)
-    ok = [r for r in rows if r[3] >= best_p - psnr_tol]
-    best = min(ok, key=lambda r: r[2])
-    return (best[0], best[1]), rows
+    # the tile shape changes the computation only by rounding, so the
+    # quality of a candidate is that of its (K, J): the mean PSNR over its
+    # tile shapes (one trajectory's PSNR moves by a few hundredths of a dB
+    # under any change of rounding)
+    groups = {}
+    for r in rows:
+        groups.setdefault((r[0], r[1]), []).append(r[4])
+    quality = {kj: sum(v) / len(v) for kj, v in groups.items()}
+    best_q = max(quality.values())
+    ok = [r for r in rows if quality[(r[0], r[1])] >= best_q - psnr_tol]
+    best = min(ok, key=lambda r: r[3])
+    if key is not None:
+        cache_store(cache_path, key, {"pick": list(best[:3]), "table": [list(r) for r in rows]})
+    return tuple(best[:3]), rows

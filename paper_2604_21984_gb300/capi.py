@@ -140,11 +140,12 @@ _SIGS = {
                                          ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p, ctypes.c_size_t,
                                          ctypes.c_void_p]),
     "sad_step_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
-                                                   ctypes.c_int32, ctypes.c_int64, ctypes.c_int64]),
+                                                   ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                                   ctypes.c_int64]),
     "sad_prepare_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p]),
     "sad_train_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
-                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(AdamHparams),
                                       ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
@@ -475,9 +476,9 @@ def batch_table(images):
     return arr
 
 
-def step_workspace(table, K, total_cap, total_pixels, max_records=0, device="cuda"):
-    n = lib().sad_step_workspace_bytes(ctypes.cast(table, ctypes.c_void_p), len(table), K, total_cap,
-                                       total_pixels, max_records)
+def step_workspace(table, K, total_cap, total_pixels, max_records=0, device="cuda", tile_w=16):
+    n = lib().sad_step_workspace_bytes(ctypes.cast(table, ctypes.c_void_p), len(table), K, tile_w,
+                                       total_cap, total_pixels, max_records)
     if n == 0:
         raise ValueError("invalid batch table for sad_step_workspace_bytes")
     # zeroed once: the per-site accumulators must start at zero (each call
@@ -494,11 +495,12 @@ def sad_prepare_batch(table, params, prep, total_pixels, stream=None):
 
 
 def sad_train_step(table, K, J, params, m, v, prep, map_in, map_out, total_pixels, targets, loss,
-                   hp, state, ws, grads_out=None, stream=None):
-    """state: device int32[n_states, 4] per-image rows {t, pass, parity, 0}."""
+                   hp, state, ws, grads_out=None, stream=None, tile_w=16):
+    """state: device int32[n_states, 4] per-image rows {t, pass, parity, 0};
+    tile_w: 16 (16x16 tiles) or 32 (32x8 tiles)."""
     cap = params.shape[1]
     n = N_PARAMS * cap
-    _check(lib().sad_train_step(ctypes.cast(table, ctypes.c_void_p), len(table), K, J,
+    _check(lib().sad_train_step(ctypes.cast(table, ctypes.c_void_p), len(table), K, J, tile_w,
                                 _ptr(params, torch.float32, "params", n), _ptr(m, torch.float32, "m", n),
                                 _ptr(v, torch.float32, "v", n), _ptr(prep, torch.float32, "prep"), cap,
                                 _ptr(map_in, torch.int32, "map_in", total_pixels * K),
@@ -517,13 +519,13 @@ class TrainStepCall:
     call (eager or while being captured into a graph) is one ctypes call."""
 
     def __init__(self, table, K, J, params, m, v, prep, map_in, map_out, total_pixels, targets, loss,
-                 hp, state, ws, grads_out=None):
+                 hp, state, ws, grads_out=None, tile_w=16):
         cap = params.shape[1]
         n = N_PARAMS * cap
         self.table = table
         self.hp = hp
         self.keep = (params, m, v, prep, map_in, map_out, targets, loss, state, ws, grads_out)
-        self.args = [ctypes.cast(table, ctypes.c_void_p), len(table), K, J,
+        self.args = [ctypes.cast(table, ctypes.c_void_p), len(table), K, J, tile_w,
                      _ptr(params, torch.float32, "params", n), _ptr(m, torch.float32, "m", n),
                      _ptr(v, torch.float32, "v", n), _ptr(prep, torch.float32, "prep"), cap,
                      _ptr(map_in, torch.int32, "map_in", total_pixels * K),

@@ -46,6 +46,7 @@ constexpr int kStateWords = 4;  // per image: {Adam step t, pass index, map pari
 
 struct BatchDesc {
   int32_t B;
+  int32_t tw;  // tile width: 16 (16x16 tiles) or 32 (32x8 tiles)
   uint32_t n_tiles;
   uint32_t n_sites;  // sites of all images
   BatchImg img[kMaxImages];
@@ -79,8 +80,8 @@ __device__ __forceinline__ TileCtx tile_ctx(const BatchDesc& d, int b, uint32_t 
   TileCtx c;
   c.H = im.H;
   c.W = im.W;
-  c.x0 = static_cast<int>(lt % im.tiles_x) * kTileSide;
-  c.y0 = static_cast<int>(lt / im.tiles_x) * kTileSide;
+  c.x0 = static_cast<int>(lt % im.tiles_x) * d.tw;
+  c.y0 = static_cast<int>(lt / im.tiles_x) * (kTileThreads / d.tw);
   c.pix_off = im.pix_off;
   c.sr = SiteRange{im.site_lo, im.site_n};
   c.tile = tile;
@@ -93,7 +94,7 @@ constexpr int kKeepLists = SAD_STEP_KEEP_LISTS;
 
 // Propagation pass + adjoint of the tiles of images that refresh their lists
 // this call (UPDATE_ONLY: the pass alone, for extra passes between steps).
-template <int K, bool UPDATE_ONLY>
+template <int K, bool UPDATE_ONLY, int TW>
 __global__ void __launch_bounds__(kTileThreads, 3)
     k_step_tile(const BatchDesc d, TileIO io, uint4* map_a, uint4* map_b, size_t Ptot, int J,
                 const int32_t* __restrict__ state) {
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(kTileThreads, 3)
   uint4* map_out = swap ? map_a : map_b;
   const TileCtx c = tile_ctx(d, b, blockIdx.x);
   const int t = threadIdx.x;
-  const int x = c.x0 + (t & (kTileSide - 1)), y = c.y0 + (t >> 4);
+  const int x = c.x0 + (t & (TW - 1)), y = c.y0 + t / TW;
   const bool inimg = x < c.W && y < c.H;
   const uint32_t code = (1u << 16) | (static_cast<uint32_t>(st[1]) & 0xffffu);
   uint64_t v[K];
@@ -126,12 +127,12 @@ __global__ void __launch_bounds__(kTileThreads, 3)
     for (int j = 0; j < K / 4; ++j)
       map_out[j * Ptot + q] = make_uint4(ids[4 * j], ids[4 * j + 1], ids[4 * j + 2], ids[4 * j + 3]);
   }
-  if (!UPDATE_ONLY) tile_body<K, kModeGrad, true>(c, io, ids, lk);
+  if (!UPDATE_ONLY) tile_body<K, kModeGrad, true, TW>(c, io, ids, lk);
 }
 
 // Adjoint of the tiles of images that keep their lists this call: the lists
 // are read from the image's current map (candidate update period > 1).
-template <int K>
+template <int K, int TW>
 __global__ void __launch_bounds__(kTileThreads, 3)
     k_keep_tile(const BatchDesc d, TileIO io, const uint4* map_a, const uint4* map_b, size_t Ptot,
                 const int32_t* __restrict__ state) {
@@ -142,7 +143,7 @@ __global__ void __launch_bounds__(kTileThreads, 3)
   const uint4* map = (st[2] & 1) ? map_b : map_a;
   const TileCtx c = tile_ctx(d, b, blockIdx.x);
   const int t = threadIdx.x;
-  const int x = c.x0 + (t & (kTileSide - 1)), y = c.y0 + (t >> 4);
+  const int x = c.x0 + (t & (TW - 1)), y = c.y0 + t / TW;
   uint32_t ids[K];
 #pragma unroll
   for (int j = 0; j < K / 4; ++j) {
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(kTileThreads, 3)
   float lk[K];  // unused without HAVE_L
 #pragma unroll
   for (int k = 0; k < K; ++k) lk[k] = 0.f;
-  tile_body<K, kModeGrad>(c, io, ids, lk);
+  tile_body<K, kModeGrad, false, TW>(c, io, ids, lk);
 }
 
 // After a propagation-only pass: every image's pass index and map parity advance.
@@ -391,10 +392,14 @@ static StepLayout step_layout(uint32_t n_tiles, uint64_t total_pixels, int K, in
 
 // Validates the host image table and fills the device descriptor.
 static int make_desc(const sad_batch_image* images, int32_t B, int32_t total_cap,
-                     int64_t total_pixels, BatchDesc& d, const char* name, int32_t n_states = -1) {
+                     int64_t total_pixels, BatchDesc& d, const char* name, int32_t n_states = -1,
+                     int32_t tile_w = kTileSide) {
   if (!images || B < 1 || B > kMaxImages)
     return einval("%s: need 1 <= B <= %d images", name, kMaxImages);
+  if (tile_w != 16 && tile_w != 32) return einval("%s: tile_w must be 16 or 32", name);
+  const int32_t tile_h = kTileThreads / tile_w;
   d.B = B;
+  d.tw = tile_w;
   uint32_t tiles = 0, sites = 0;
   for (int b = 0; b < B; ++b) {
     const sad_batch_image& im = images[b];
@@ -412,7 +417,7 @@ static int make_desc(const sad_batch_image* images, int32_t B, int32_t total_cap
     o.site_lo = static_cast<uint32_t>(im.site_offset);
     o.site_n = static_cast<uint32_t>(im.capacity);
     o.pix_off = static_cast<uint64_t>(im.pixel_offset);
-    o.tiles_x = static_cast<uint32_t>((im.W + kTileSide - 1) / kTileSide);
+    o.tiles_x = static_cast<uint32_t>((im.W + tile_w - 1) / tile_w);
     o.tile_off = tiles;
     o.seed = im.seed;
     o.s = 1.0f / static_cast<float>(im.H > im.W ? im.H : im.W);
@@ -427,7 +432,7 @@ static int make_desc(const sad_batch_image* images, int32_t B, int32_t total_cap
     o.flags = im.flags;
     o.site_cum = sites;
     sites += o.site_n;
-    tiles += o.tiles_x * static_cast<uint32_t>((im.H + kTileSide - 1) / kTileSide);
+    tiles += o.tiles_x * static_cast<uint32_t>((im.H + tile_h - 1) / tile_h);
   }
   for (int b = 0; b < B; ++b)
     for (int c = 0; c < b; ++c) {
@@ -447,11 +452,12 @@ using namespace sad;
 extern "C" {
 
 size_t sad_step_workspace_bytes(const sad_batch_image* images, int32_t B, int32_t K,
-                                int32_t total_capacity, int64_t total_pixels,
+                                int32_t tile_w, int32_t total_capacity, int64_t total_pixels,
                                 int64_t max_records) {
   BatchDesc d;
   if (K != 4 && K != 8 && K != 16) return 0;
-  if (make_desc(images, B, total_capacity, total_pixels, d, "sad_step_workspace_bytes") != SAD_OK)
+  if (make_desc(images, B, total_capacity, total_pixels, d, "sad_step_workspace_bytes", -1,
+                tile_w) != SAD_OK)
     return 0;
   return step_layout(d.n_tiles, static_cast<uint64_t>(total_pixels), K, total_capacity, max_records)
       .total;
@@ -472,14 +478,15 @@ int sad_prepare_batch(const sad_batch_image* images, int32_t B, const float* par
   return check_launch("sad_prepare_batch");
 }
 
-int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t J, float* params,
-                   float* m, float* v, float* prep, int32_t total_capacity,
+int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t J, int32_t tile_w,
+                   float* params, float* m, float* v, float* prep, int32_t total_capacity,
                    uint32_t* map_in, uint32_t* map_out, int64_t total_pixels,
                    const float* targets, float* loss, const sad_adam_hparams* hp,
                    int32_t* image_state, int32_t n_states, float* grads_out, void* workspace,
                    size_t workspace_bytes, void* stream) {
   BatchDesc d;
-  if (int e = make_desc(images, B, total_capacity, total_pixels, d, "sad_train_step", n_states))
+  if (int e = make_desc(images, B, total_capacity, total_pixels, d, "sad_train_step", n_states,
+                        tile_w))
     return e;
   if (K != 4 && K != 8 && K != 16) return einval("sad_train_step: K must be 4, 8 or 16");
   if (J < 0 || J > 16) return einval("sad_train_step: J must be in [0,16]");
@@ -547,21 +554,32 @@ int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t 
     any_keep |= (images[b].flags & SAD_STEP_KEEP_LISTS) != 0;
     any_refresh |= (images[b].flags & SAD_STEP_KEEP_LISTS) == 0;
   }
+  const int kt = K * 100 + tile_w;  // (K, tile width)
   if (any_refresh) {
     TraceScope tr_(st, "k_step_tile");
-    switch (K) {
-      case 4: k_step_tile<4, false><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, image_state); break;
-      case 8: k_step_tile<8, false><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, image_state); break;
-      default: k_step_tile<16, false><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, image_state); break;
+#define SAD_STEP(KK, TT) k_step_tile<KK, false, TT><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, image_state)
+    switch (kt) {
+      case 416: SAD_STEP(4, 16); break;
+      case 432: SAD_STEP(4, 32); break;
+      case 816: SAD_STEP(8, 16); break;
+      case 832: SAD_STEP(8, 32); break;
+      case 1632: SAD_STEP(16, 32); break;
+      default: SAD_STEP(16, 16); break;
     }
+#undef SAD_STEP
   }
   if (any_keep) {
     TraceScope tr_(st, "k_keep_tile");
-    switch (K) {
-      case 4: k_keep_tile<4><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, image_state); break;
-      case 8: k_keep_tile<8><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, image_state); break;
-      default: k_keep_tile<16><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, image_state); break;
+#define SAD_KEEP(KK, TT) k_keep_tile<KK, TT><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, image_state)
+    switch (kt) {
+      case 416: SAD_KEEP(4, 16); break;
+      case 432: SAD_KEEP(4, 32); break;
+      case 816: SAD_KEEP(8, 16); break;
+      case 832: SAD_KEEP(8, 32); break;
+      case 1632: SAD_KEEP(16, 32); break;
+      default: SAD_KEEP(16, 16); break;
     }
+#undef SAD_KEEP
   }
   if (int r = check_launch("k_step_tile / k_keep_tile")) return r;
   { TraceScope tr_(st, "k_seg_accum"); k_seg_accum<10><<<152 * 8, 256, 0, st>>>(rec, hdr, L.max_records, total_capacity, accq); }
@@ -605,9 +623,9 @@ int sad_batch_update(const sad_batch_image* images, int32_t B, int32_t K, int32_
   {
     TraceScope tr_(st, "k_update_tile");
     switch (K) {
-      case 4: k_step_tile<4, true><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, image_state); break;
-      case 8: k_step_tile<8, true><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, image_state); break;
-      default: k_step_tile<16, true><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, image_state); break;
+      case 4: k_step_tile<4, true, 16><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, image_state); break;
+      case 8: k_step_tile<8, true, 16><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, image_state); break;
+      default: k_step_tile<16, true, 16><<<d.n_tiles, kTileThreads, 0, st>>>(d, io, mi, mo, Ptot, J, image_state); break;
     }
   }
   if (int r = check_launch("k_update_tile")) return r;

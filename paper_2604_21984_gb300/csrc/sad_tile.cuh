@@ -1,6 +1,7 @@
 // Per-tile adjoint / statistics of the SAD blend (App. "Gradient Computation
 // and Reduction"), shared by the stand-alone backward and the fused training
-// step.  Per 16x16 pixel tile (one 256-thread block, one pixel per thread):
+// step.  Per pixel tile of 256 pixels (16x16, or 32x8 in the batched step;
+// one 256-thread block, one pixel per thread):
 //  1. forward: every pixel recomputes its max-subtracted softmax over its K
 //     listed sites (nothing from the forward pass is stored), forms its
 //     upstream gradient g (given, or 2(c - I)/P for the fused MSE loss);
@@ -114,7 +115,7 @@ __device__ __forceinline__ float warp_sum10_halving(const float (&in)[10], int l
 // ---------------------------------------------------------------------------
 // per-tile kernel
 // ---------------------------------------------------------------------------
-// Geometry of one 16x16 tile of one image of a (possibly single-image) batch.
+// Geometry of one tile of one image of a (possibly single-image) batch.
 struct TileCtx {
   int H, W;          // image size
   int x0, y0;        // tile origin inside the image
@@ -137,13 +138,14 @@ struct TileIO {
 };
 
 // Adjoint (MODE = kModeGrad) or budget statistics (kModeStats) of one tile
-// whose pixels' lists are ids[] (thread t = pixel (t%16, t/16) of the tile).
+// of TW x (256 / TW) pixels whose pixels' lists are ids[] (thread t = pixel
+// (t % TW, t / TW) of the tile).
 // With HAVE_L (gradient mode), lk[] holds the logits of the listed sites in
 // descending order (the propagation pass just computed them exactly; invalid
 // entries are the empty tail), so the forward takes them instead of
 // re-gathering and re-scoring, and the first entry is the maximum.
 // Every thread of the 256-thread block must call it.
-template <int K, int MODE, bool HAVE_L = false>
+template <int K, int MODE, bool HAVE_L = false, int TW = kTileSide>
 __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, uint32_t (&ids)[K],
                                           const float (&lk)[K]) {
   const float4* __restrict__ geo = io.geo;
@@ -181,8 +183,10 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
   const int lane = t & 31, warp = t >> 5;
   const int H = c.H, W = c.W, x0 = c.x0, y0 = c.y0;
   const uint32_t tile = c.tile;
-  const int x = x0 + (t & (kTileSide - 1));
-  const int y = y0 + (t >> 4);
+  static_assert(TW == 16 || TW == 32, "tile width 16 (16x16 tiles) or 32 (32x8 tiles)");
+  constexpr int kLog2TW = TW == 16 ? 4 : 5;
+  const int x = x0 + (t & (TW - 1));
+  const int y = y0 + (t >> kLog2TW);
   const bool inimg = x < W && y < H;
   const size_t q = inimg ? c.pix_off + static_cast<size_t>(y) * W + x : 0;
   const SiteRange sr = c.sr;
@@ -439,8 +443,8 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
         for (uint32_t i = lane; i < cnt; i += 32) {
           const uint32_t p = s_list[off + i];
           const float4 A = s_pa[p];
-          const float dx = (x0 + static_cast<int>(p & (kTileSide - 1)) + 0.5f) - gs.x;
-          const float dy = (y0 + static_cast<int>(p >> 4) + 0.5f) - gs.y;
+          const float dx = (x0 + static_cast<int>(p & (TW - 1)) + 0.5f) - gs.x;
+          const float dy = (y0 + static_cast<int>(p >> kLog2TW) + 0.5f) - gs.y;
           const float qq = ms.x * dx * dx + 2.f * ms.y * dx * dy + ms.z * dy * dy;
           // gradient mode: n and 1/n from one reciprocal square root (the
           // adjoint's tolerance allows its few-ulp error; no division)

@@ -184,10 +184,10 @@ __device__ __forceinline__ void pixel_update(uint64_t (&v)[K], bool inimg, int c
   // copy.  (Scanning the queue for every offer was a chain of dependent
   // shared loads, the slowest part of the pass at long jumps.)  The queue
   // is scored in groups of NG (2 NG independent gathers in flight) and
-  // merged; the result is the top K of the union, whatever the order.  The drain and offer bodies each appear at a handful of call sites
-  // only: fully unrolling them over all candidates made the kernel too large
-  // for the instruction cache when most candidates are novel (the long jumps
-  // of the warm-up).
+  // merged; the result is the top K of the union, whatever the order.  The
+  // drain body has one call site and the offer body a few: fully unrolling
+  // them over all candidates made the kernel too large for the instruction
+  // cache.
   int qn = 0;
   auto drain = [&]() {
 #pragma unroll 1

@@ -48,6 +48,7 @@ class EncodeConfig:
     cand_half2: bool = False   # refresh passes score from the half2 candidate table (separate calls)
     warm_half2_jump: int = 0   # > 0: warm-up passes with at least this jump use the half2 table
     keep_grads: bool = False   # fused: also write the step's gradients to Encoder.grads
+    tile_w: int = 16           # fused: adjoint tiles 16x16 (16) or 32x8 (32)
     extra: dict = field(default_factory=dict)
 
 
@@ -182,7 +183,7 @@ class Encoder:
         if c.fused:
             self.table = capi.batch_table([dict(H=H, W=W, site_offset=0, capacity=cap, pixel_offset=0,
                                                 seed=c.seed + 0x5AD)])
-            self.ws_step = capi.step_workspace(self.table, K, cap, H * W, device=self.dev)
+            self.ws_step = capi.step_workspace(self.table, K, cap, H * W, device=self.dev, tile_w=c.tile_w)
             self.state = torch.zeros((1, 4), dtype=torch.int32, device=self.dev)
             self.target_flat = self.target.reshape(-1, 3)
             self._call = None
@@ -239,14 +240,15 @@ class Encoder:
             self._call = capi.TrainStepCall(self.table, c.K, c.J, self.params, self.m, self.v, self.prep,
                                             self.bufs[0], self.bufs[1], self.H * self.W, self.target_flat,
                                             self.loss, self.hp, self.state, self.ws_step,
-                                            grads_out=self.grads if c.keep_grads else None)
+                                            grads_out=self.grads if c.keep_grads else None, tile_w=c.tile_w)
             e = dict(H=self.H, W=self.W, site_offset=0, capacity=self.cap, pixel_offset=0,
                      seed=c.seed + 0x5AD, flags=capi.STEP_KEEP_LISTS)
             self._call_keep = capi.TrainStepCall(capi.batch_table([e]), c.K, c.J, self.params, self.m,
                                                  self.v, self.prep, self.bufs[0], self.bufs[1],
                                                  self.H * self.W, self.target_flat, self.loss, self.hp,
                                                  self.state, self.ws_step,
-                                                 grads_out=self.grads if c.keep_grads else None)
+                                                 grads_out=self.grads if c.keep_grads else None,
+                                                 tile_w=c.tile_w)
 
     def step(self):
         """One training iteration: a candidate refresh (cand_passes passes)

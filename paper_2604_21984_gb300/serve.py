@@ -281,7 +281,7 @@ class Server:
         side = 16 * int(math.isqrt(tiles)) + 16
         entry = [dict(H=side, W=side, site_offset=0, capacity=0, pixel_offset=0, seed=0)]
         n = capi.lib().sad_step_workspace_bytes(
-            capi.ctypes.cast(capi.batch_table(entry), capi.ctypes.c_void_p), 1, c.K, c.site_pool,
+            capi.ctypes.cast(capi.batch_table(entry), capi.ctypes.c_void_p), 1, c.K, 16, c.site_pool,
             side * side, Pp * c.K // 8)
         if n == 0:
             raise ValueError("pool too large for one step workspace")

@@ -243,3 +243,61 @@ def test_candidate_period_graph_equals_eager(capi):
     assert torch.equal(a.params, b.params)
     assert torch.equal(a.maps[0], b.maps[0])
     assert a.refreshes == b.refreshes == 4
+
+
+def test_autotune_picks_fastest_within_tolerance_and_caches(capi, tmp_path):
+    """The autotuner trains each candidate for the budget, picks the fastest
+    whose mean PSNR is within the tolerance of the best, and a second call
+    with the same key is served from its JSON cache without training."""
+    import json
+    import time
+    from paper_2604_21984_gb300.batch import autotune
+    imgs = _images([(64, 80), (48, 48), (96, 64)], 21)
+    cands = ((16, 4, 16), (16, 4, 32), (8, 2))
+    path = str(tmp_path / "tune.json")
+    t0 = time.perf_counter()
+    pick, rows = autotune(imgs, iters=20, candidates=cands, cache_path=path)
+    t_first = time.perf_counter() - t0
+    assert pick in ((16, 4, 16), (16, 4, 32), (8, 2, 16)) and len(rows) == 3
+    assert all(np.isfinite(r[4]) and r[3] > 0 for r in rows)
+    q = {}
+    for r in rows:
+        q.setdefault(r[:2], []).append(r[4])
+    q = {kj: float(np.mean(v)) for kj, v in q.items()}
+    ok = [r for r in rows if q[r[:2]] >= max(q.values()) - 0.05]
+    assert pick == tuple(min(ok, key=lambda r: r[3])[:3])
+    t0 = time.perf_counter()
+    pick2, rows2 = autotune(imgs, iters=20, candidates=cands, cache_path=path)
+    assert pick2 == pick and [tuple(r) for r in rows2] == [tuple(r) for r in rows]
+    assert time.perf_counter() - t0 < 0.2 * t_first
+    with open(path) as f:
+        assert len(json.load(f)) == 1
+
+
+def test_tile_shapes_agree(capi):
+    """The batched step with 32x8 adjoint tiles equals the 16x16 step: the
+    same new maps, losses and gradients up to the rounding of the per-tile
+    partial sums, on uneven images with ragged tiles."""
+    torch = pytest.importorskip("torch")
+    from paper_2604_21984_gb300.batch import BatchConfig, BatchTrainer
+    imgs = _images([(40, 56), (73, 29), (64, 96)], 31)
+    out = {}
+    for tw in (16, 32):
+        tr = BatchTrainer(imgs, BatchConfig(K=16, J=4, seed=9, graph=False, tile_w=tw))
+        grads = torch.empty_like(tr.params)
+        capi.sad_train_step(tr.table, 16, 4, tr.params, tr.m, tr.v, tr.prep, tr.bufs[0], tr.bufs[1],
+                            tr.total_pixels, tr.targets, tr.loss, tr.hp, tr.state, tr.ws, grads_out=grads,
+                            tile_w=tw)
+        torch.cuda.synchronize()
+        out[tw] = (capi.ids_from_map(tr.bufs[1]), tr.loss.cpu().numpy().copy(), grads.cpu().numpy())
+    assert np.array_equal(out[16][0], out[32][0])
+    np.testing.assert_allclose(out[32][1], out[16][1], rtol=1e-5)
+    g16, g32 = out[16][2].astype(np.float64), out[32][2].astype(np.float64)
+    for j in range(11):
+        scale = np.abs(g16[j]).max()
+        if scale > 0:
+            assert np.abs(g32[j] - g16[j]).max() <= 1e-5 * scale, j
+    # a bad tile width is refused on the host
+    with pytest.raises(capi.SadError):
+        capi.sad_train_step(tr.table, 16, 4, tr.params, tr.m, tr.v, tr.prep, tr.bufs[0], tr.bufs[1],
+                            tr.total_pixels, tr.targets, tr.loss, tr.hp, tr.state, tr.ws, tile_w=24)

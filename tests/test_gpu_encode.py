@@ -14,16 +14,17 @@ def capi():
     return require_gpu()
 
 
-@pytest.mark.parametrize("fused", [False, True])
-def test_one_iteration_matches_oracle(capi, oracle, fused):
+@pytest.mark.parametrize("fused,tile_w,H,W", [(False, 16, 48, 64), (True, 16, 48, 64), (True, 32, 48, 64),
+                                              (True, 32, 37, 75)])
+def test_one_iteration_matches_oracle(capi, oracle, fused, tile_w, H, W):
     """prepare -> pass (jump 1) -> MSE gradient -> Adam, GPU vs oracle, as
-    separate calls and as the fused step."""
+    separate calls and as the fused step with 16x16 and 32x8 adjoint tiles
+    (the last case with ragged tiles in both directions)."""
     torch = pytest.importorskip("torch")
     from paper_2604_21984_gb300.encode import EncodeConfig, Encoder, jump_code
-    H, W = 48, 64
     img = gen.image_noise_polygons_lines(H, W, seed=41, n_polygons=5, n_lines=3)
     enc = Encoder(dev(img), EncodeConfig(n_sites=300, K=8, J=2, iters=1, seed=5, fused=fused,
-                                         keep_grads=True))
+                                         keep_grads=True, tile_w=tile_w))
     enc.init()
     p0 = enc.params.cpu().numpy().copy()
     ids0 = capi.ids_from_map(enc.maps[0])
