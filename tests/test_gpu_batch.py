@@ -301,3 +301,19 @@ def test_tile_shapes_agree(capi):
     with pytest.raises(capi.SadError):
         capi.sad_train_step(tr.table, 16, 4, tr.params, tr.m, tr.v, tr.prep, tr.bufs[0], tr.bufs[1],
                             tr.total_pixels, tr.targets, tr.loss, tr.hp, tr.state, tr.ws, tile_w=24)
+
+
+def test_tile_shapes_agree_with_kept_lists(capi):
+    """Candidate refresh every 2 iterations (the keep-lists tile kernel on
+    the other iterations): 32x8 and 16x16 adjoint tiles train alike over a
+    few iterations."""
+    torch = pytest.importorskip("torch")
+    from paper_2604_21984_gb300.batch import BatchConfig, BatchTrainer
+    imgs = _images([(40, 56), (73, 29)], 41)
+    losses = {}
+    for tw in (16, 32):
+        tr = BatchTrainer(imgs, BatchConfig(K=8, J=2, seed=4, graph=False, cand_every=2, tile_w=tw))
+        tr.run(4)
+        torch.cuda.synchronize()
+        losses[tw] = tr.loss.cpu().numpy().copy()
+    np.testing.assert_allclose(losses[32], losses[16], rtol=1e-3)
