@@ -92,6 +92,17 @@ __device__ __forceinline__ TileCtx tile_ctx(const BatchDesc& d, int b, uint32_t 
 
 constexpr int kKeepLists = SAD_STEP_KEEP_LISTS;
 
+// Adam's bias corrections 1 - beta^t of every image of the step, in double,
+// by the first threads of block 0 of the tile kernel (the site step, two
+// launches later, reads them instead of taking two double-precision powers
+// per site).
+__device__ __forceinline__ void write_bias(const BatchDesc& d, const int32_t* state, const TileIO& io) {
+  if (io.bias == nullptr || blockIdx.x != 0 || static_cast<int>(threadIdx.x) >= d.B) return;
+  const int t = state[kStateWords * d.img[threadIdx.x].state];
+  io.bias[threadIdx.x] = make_float2(static_cast<float>(1.0 - pow(static_cast<double>(io.beta1), t)),
+                                     static_cast<float>(1.0 - pow(static_cast<double>(io.beta2), t)));
+}
+
 // Propagation pass + adjoint of the tiles of images that refresh their lists
 // this call (UPDATE_ONLY: the pass alone, for extra passes between steps).
 template <int K, bool UPDATE_ONLY, int TW>
@@ -99,6 +110,7 @@ __global__ void __launch_bounds__(kTileThreads, 3)
     k_step_tile(const BatchDesc d, TileIO io, uint4* map_a, uint4* map_b, size_t Ptot, int J,
                 const int32_t* __restrict__ state) {
   __shared__ uint32_t s_q[kQueue][kTileThreads];
+  if (!UPDATE_ONLY) write_bias(d, state, io);
   const int b = image_of_tile(d, blockIdx.x);
   const BatchImg im = d.img[b];
   if (!UPDATE_ONLY && (im.flags & kKeepLists)) return;  // whole block: handled by k_keep_tile
@@ -136,6 +148,7 @@ template <int K, int TW>
 __global__ void __launch_bounds__(kTileThreads, 3)
     k_keep_tile(const BatchDesc d, TileIO io, const uint4* map_a, const uint4* map_b, size_t Ptot,
                 const int32_t* __restrict__ state) {
+  write_bias(d, state, io);
   const int b = image_of_tile(d, blockIdx.x);
   const BatchImg im = d.img[b];
   if (!(im.flags & kKeepLists)) return;
@@ -179,25 +192,9 @@ __global__ void k_site_step(const BatchDesc d, float* __restrict__ params, float
                             float4* __restrict__ met, float4* __restrict__ col, int cap,
                             const WsHeader* __restrict__ hdr,
                             unsigned long long* __restrict__ accq, AdamArgs A,
-                            const int32_t* __restrict__ state, float* __restrict__ grads_out,
+                            const float2* __restrict__ bias, float* __restrict__ grads_out,
                             bool adam) {
-  // Adam's bias corrections 1 - beta^t in double: once per block for the
-  // image of its first slot (a double-precision pow per site thread cost
-  // more than the rest of the kernel); threads of another image compute
-  // their own.
-  __shared__ int s_b;
-  __shared__ float s_bc[2];
   const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (adam) {
-    if (threadIdx.x == 0) {
-      const int b0 = image_of_slot(d, blockIdx.x * blockDim.x);
-      const int t0 = state[kStateWords * d.img[b0].state];
-      s_b = b0;
-      s_bc[0] = static_cast<float>(1.0 - pow(static_cast<double>(A.beta1), t0));
-      s_bc[1] = static_cast<float>(1.0 - pow(static_cast<double>(A.beta2), t0));
-    }
-    __syncthreads();  // adam is the same for the whole grid
-  }
   if (j >= d.n_sites) return;
   const int b = image_of_slot(d, j);
   const BatchImg im = d.img[b];
@@ -258,13 +255,8 @@ __global__ void k_site_step(const BatchDesc d, float* __restrict__ params, float
       for (int k = 0; k < kNParams; ++k) grads_out[k * c + i] = g[k];
     }
     if (p[PX] >= 0.f) {
-      float bc1 = s_bc[0], bc2 = s_bc[1];
-      if (b != s_b) {
-        const int t = state[kStateWords * im.state];
-        bc1 = static_cast<float>(1.0 - pow(static_cast<double>(A.beta1), t));
-        bc2 = static_cast<float>(1.0 - pow(static_cast<double>(A.beta2), t));
-      }
-      adam_site(p, g, m, v, c, i, A, bc1, bc2, im.H, im.W);
+      const float2 bc = bias[b];  // written by the tile kernel of this step
+      adam_site(p, g, m, v, c, i, A, bc.x, bc.y, im.H, im.W);
 #pragma unroll
       for (int k = 0; k < kNParams; ++k) params[k * c + i] = p[k];
     }
@@ -366,7 +358,7 @@ __global__ void k_insert_pixels(const uint4* __restrict__ src_map, const float* 
 }
 
 struct StepLayout {
-  size_t hdr, tile_loss, acc, records, total;
+  size_t hdr, tile_loss, acc, bias, records, total;
   uint32_t max_records;
 };
 
@@ -385,6 +377,7 @@ static StepLayout step_layout(uint32_t n_tiles, uint64_t total_pixels, int K, in
   L.hdr = o;       o = al256(o + sizeof(WsHeader));
   L.acc = o;       o = al256(o + sizeof(unsigned long long) * 10 * static_cast<size_t>(total_cap));
   L.tile_loss = o; o = al256(o + sizeof(float) * n_tiles);
+  L.bias = o;      o = al256(o + sizeof(float2) * kMaxImages);
   L.records = o;   o = al256(o + sizeof(Record) * L.max_records);
   L.total = o;
   return L;
@@ -546,6 +539,10 @@ int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t 
   io.records = rec;
   io.max_records = L.max_records;
   io.hdr = hdr;
+  float2* bias = reinterpret_cast<float2*>(base + L.bias);
+  io.bias = bias;
+  io.beta1 = hp->beta1;
+  io.beta2 = hp->beta2;
   uint4* mi = reinterpret_cast<uint4*>(map_in);
   uint4* mo = reinterpret_cast<uint4*>(map_out);
   const size_t Ptot = static_cast<size_t>(total_pixels);
@@ -588,7 +585,7 @@ int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t 
   if (d.n_sites > 0)
     { TraceScope tr_(st, "k_site_step"); k_site_step<<<(d.n_sites + 255) / 256, 256, 0, st>>>(
       d, params, m, v, p4, p4 + total_capacity, p4 + 2 * static_cast<size_t>(total_capacity),
-      total_capacity, hdr, accq, A, image_state, grads_out, true); }
+      total_capacity, hdr, accq, A, bias, grads_out, true); }
   if (int r = check_launch("k_site_step")) return r;
   { TraceScope tr_(st, "k_step_finish"); k_step_finish<<<B, 256, 0, st>>>(d, tile_loss, loss, image_state); }
   return check_launch("k_step_finish");

@@ -135,6 +135,8 @@ struct TileIO {
   Record* records;
   uint32_t max_records;
   WsHeader* hdr;
+  float2* bias = nullptr;  // training step: per image {1 - beta1^t, 1 - beta2^t} for the site step
+  float beta1 = 0.f, beta2 = 0.f;
 };
 
 // Adjoint (MODE = kModeGrad) or budget statistics (kModeStats) of one tile
