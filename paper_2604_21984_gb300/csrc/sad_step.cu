@@ -1,12 +1,12 @@
 // Fused, batched training step (the paper's GPU-resident iteration, Sec. 5;
 // Sec. 6.3 epoch = one pass over all pixels) over up to kMaxImages images.
 //
-// One iteration is four kernels and one small memset, all on one stream.  Each
+// One iteration is three kernels and one small memset, all on one stream.  Each
 // image's counters (Adam step, pass index, which map buffer is current) live
 // in a device state row that the step itself advances, so a fixed set of
 // images always makes the same call, which is captured once in a CUDA graph
 // and replayed:
-//  1. k_step_tile, one block per 16x16 tile of any image: the tile's pixels
+//  1. k_step_tile, one block per tile (16x16 or 32x8) of any image: the tile's pixels
 //     run one propagation pass at jump 1 (Sec. 4.3; reads the neighbours' old
 //     lists, writes the new ones), then - on the lists just computed, still in
 //     registers - the fused render + MSE + adjoint of the tile (per-tile
@@ -14,9 +14,9 @@
 //  2. k_seg_accum: exact fixed-point per-site sums of the records;
 //  3. k_site_step, one thread per site: the chain rule to the 11 gradients,
 //     Adam with the paper's clamps (Sec. 6.1), and the prepared table of the
-//     updated site for the next iteration;
-//  4. k_step_finish: the per-image mean loss (fixed-order sums) and each
-//     image's state row advances.
+//     updated site for the next iteration; its blocks also take the
+//     per-image mean loss (fixed-order sums) and advance each image's state
+//     row.
 // Each image uses its own site range, pixel range, injection seed and
 // fixed-point scale, so an image's result does not depend on the rest of the
 // batch.
@@ -187,15 +187,14 @@ __global__ void k_state_pass(const BatchDesc d, int32_t* __restrict__ state) {
 // site of the table (slot ranges of the images only), and the accumulators
 // are cleared once read, so the next call finds them zero without a memset
 // over the whole site array.
-__global__ void k_site_step(const BatchDesc d, float* __restrict__ params, float* __restrict__ m,
-                            float* __restrict__ v, float4* __restrict__ geo,
-                            float4* __restrict__ met, float4* __restrict__ col, int cap,
-                            const WsHeader* __restrict__ hdr,
-                            unsigned long long* __restrict__ accq, AdamArgs A,
-                            const float2* __restrict__ bias, float* __restrict__ grads_out,
-                            bool adam) {
-  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= d.n_sites) return;
+__device__ __forceinline__ void site_work(const BatchDesc& d, uint32_t j, float* __restrict__ params,
+                                          float* __restrict__ m, float* __restrict__ v,
+                                          float4* __restrict__ geo, float4* __restrict__ met,
+                                          float4* __restrict__ col, int cap,
+                                          const WsHeader* __restrict__ hdr,
+                                          unsigned long long* __restrict__ accq, const AdamArgs& A,
+                                          const float2* __restrict__ bias,
+                                          float* __restrict__ grads_out, bool adam) {
   const int b = image_of_slot(d, j);
   const BatchImg im = d.img[b];
   const uint32_t i = im.site_lo + (j - im.site_cum);
@@ -265,11 +264,12 @@ __global__ void k_site_step(const BatchDesc d, float* __restrict__ params, float
                p[PB], im.s, geo[i], met[i], col[i]);
 }
 
-__global__ void k_step_finish(const BatchDesc d, const float* __restrict__ tile_loss,
-                              float* __restrict__ loss, int32_t* __restrict__ state) {
-  __shared__ float s_w[8];
-  const int b = blockIdx.x;
-  const BatchImg im = d.img[b];
+// The step's finish for image b: its mean loss from the tile losses (fixed
+// order) and its state row advanced.  Every thread of the block calls it.
+__device__ __forceinline__ void finish_image(const BatchDesc& d, int b, const float* __restrict__ tile_loss,
+                                             float* __restrict__ loss, int32_t* __restrict__ state,
+                                             float* s_w) {
+  const BatchImg& im = d.img[b];
   const uint32_t n = (b + 1 < d.B ? d.img[b + 1].tile_off : d.n_tiles) - im.tile_off;
   float v = 0.f;
   for (uint32_t i = threadIdx.x; i < n; i += 256) v += tile_loss[im.tile_off + i];
@@ -288,6 +288,25 @@ __global__ void k_step_finish(const BatchDesc d, const float* __restrict__ tile_
       st[2] ^= 1;
     }
   }
+  __syncthreads();  // s_w is reused by the next image
+}
+
+// Per site: gradient -> Adam -> prepared table; with tile_loss, the blocks
+// also do the step's per-image finish (no site step reads a state row, so
+// advancing them here is safe).  256 threads per block.
+__global__ void k_site_step(const BatchDesc d, float* __restrict__ params, float* __restrict__ m,
+                            float* __restrict__ v, float4* __restrict__ geo,
+                            float4* __restrict__ met, float4* __restrict__ col, int cap,
+                            const WsHeader* __restrict__ hdr,
+                            unsigned long long* __restrict__ accq, AdamArgs A,
+                            const float2* __restrict__ bias, float* __restrict__ grads_out,
+                            bool adam, const float* __restrict__ tile_loss, float* __restrict__ loss,
+                            int32_t* __restrict__ state) {
+  __shared__ float s_w[8];
+  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < d.n_sites) site_work(d, j, params, m, v, geo, met, col, cap, hdr, accq, A, bias, grads_out, adam);
+  if (tile_loss != nullptr)
+    for (int b = blockIdx.x; b < d.B; b += gridDim.x) finish_image(d, b, tile_loss, loss, state, s_w);
 }
 
 __global__ void __launch_bounds__(256) k_decode_batch(const BatchDesc d, const float4* __restrict__ geo,
@@ -467,7 +486,7 @@ int sad_prepare_batch(const sad_batch_image* images, int32_t B, const float* par
   { TraceScope tr_(as_stream(stream), "k_site_step"); k_site_step<<<(d.n_sites + 255) / 256, 256, 0, as_stream(stream)>>>(
       d, const_cast<float*>(params), nullptr, nullptr, p4, p4 + total_capacity,
       p4 + 2 * static_cast<size_t>(total_capacity), total_capacity, nullptr, nullptr, A, nullptr,
-      nullptr, false); }
+      nullptr, false, nullptr, nullptr, nullptr); }
   return check_launch("sad_prepare_batch");
 }
 
@@ -582,13 +601,15 @@ int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t 
   { TraceScope tr_(st, "k_seg_accum"); k_seg_accum<10><<<152 * 8, 256, 0, st>>>(rec, hdr, L.max_records, total_capacity, accq); }
   if (int r = check_launch("k_seg_accum")) return r;
   const AdamArgs A = adam_args(hp);
-  if (d.n_sites > 0)
-    { TraceScope tr_(st, "k_site_step"); k_site_step<<<(d.n_sites + 255) / 256, 256, 0, st>>>(
-      d, params, m, v, p4, p4 + total_capacity, p4 + 2 * static_cast<size_t>(total_capacity),
-      total_capacity, hdr, accq, A, bias, grads_out, true); }
-  if (int r = check_launch("k_site_step")) return r;
-  { TraceScope tr_(st, "k_step_finish"); k_step_finish<<<B, 256, 0, st>>>(d, tile_loss, loss, image_state); }
-  return check_launch("k_step_finish");
+  {
+    // the site step also finishes the step (per-image loss, state rows)
+    const unsigned grid = d.n_sites > 0 ? (d.n_sites + 255) / 256 : 1;
+    TraceScope tr_(st, "k_site_step");
+    k_site_step<<<grid, 256, 0, st>>>(d, params, m, v, p4, p4 + total_capacity,
+                                      p4 + 2 * static_cast<size_t>(total_capacity), total_capacity,
+                                      hdr, accq, A, bias, grads_out, true, tile_loss, loss, image_state);
+  }
+  return check_launch("k_site_step");
 }
 
 int sad_batch_update(const sad_batch_image* images, int32_t B, int32_t K, int32_t J,
