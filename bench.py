@@ -495,6 +495,25 @@ def c3_leg(capi, dev, peak, peak_kind, args, iters=10):
         b_ms.append(e1.elapsed_time(e2))
     capi.sad_trace_enable(False)
     trace = capi.sad_trace_collect()
+    # the autograd pair: render keeping {max logit, 1/Z} per pixel, then the
+    # adjoint from that state (no recomputed normaliser)
+    fwd = torch.empty((2, H * W), dtype=torch.float32, device=dev)
+    rgb_s = torch.empty_like(rgb)
+    for _ in range(3):
+        capi.sad_render_save(prep, N, H, W, K, a, rgb_s, fwd)
+        capi.sad_render_backward_saved(pt, prep, H, W, K, a, g, rgb_s, fwd, grads, ws)
+    rs_ms, bs_ms = [], []
+    for _ in range(iters):
+        e0, e1, e2 = E(), E(), E()
+        e0.record()
+        capi.sad_render_save(prep, N, H, W, K, a, rgb_s, fwd)
+        e1.record()
+        capi.sad_render_backward_saved(pt, prep, H, W, K, a, g, rgb_s, fwd, grads, ws)
+        e2.record()
+        torch.cuda.synchronize()
+        rs_ms.append(e0.elapsed_time(e1))
+        bs_ms.append(e1.elapsed_time(e2))
+    del fwd, rgb_s
     # the paper's evaluation render from the packed 16-byte records
     words, q = capi.sad_pack_sites(pt, H, W)
     qh = q.cpu()
@@ -522,6 +541,9 @@ def c3_leg(capi, dev, peak, peak_kind, args, iters=10):
     return {
         "workload": "2048x2048, 262144 random anisotropic sites, K=16, map from seed + 16 passes",
         "mpix_per_s_fwd_bwd": round(P / ((rb + bb) / 1e3) / 1e6, 1),
+        "saved_forward": {"render_save_ms": round(statistics.mean(rs_ms), 4),
+                          "backward_saved_ms": round(statistics.mean(bs_ms), 4),
+                          "mpix_per_s_fwd_bwd": round(P / ((statistics.mean(rs_ms) + statistics.mean(bs_ms)) / 1e3) / 1e6, 1)},
         "render_ms": round(rb, 4), "backward_ms": round(bb, 4), "jfa_16_passes_ms": round(jfa_ms, 3),
         "flood_prepass_11_plus_4_passes_ms": round(flood_ms, 3),
         "one_pass_ms": {k: round(v, 4) for k, v in pass_ms.items()},

@@ -192,6 +192,17 @@ int sad_render(const float* prep, int32_t capacity, int32_t H, int32_t W, int32_
                const uint32_t* map, float* rgb, void* stream);
 
 /*
+ * sad_render_save -- sad_render that also keeps, per pixel, what the adjoint
+ * needs of the forward: fwd = float32[2][H*W] planes {max listed logit m,
+ * 1/Z} with Z = sum_i exp(l_i - m) (both 0 for a black pixel).  Together
+ * with rgb (the blend) they let sad_render_backward_saved skip recomputing
+ * each pixel's softmax normaliser; no per-(pixel, site) weight is stored.
+ * rgb is the same as sad_render's, bit for bit.
+ */
+int sad_render_save(const float* prep, int32_t capacity, int32_t H, int32_t W, int32_t K,
+                    const uint32_t* map, float* rgb, float* fwd, void* stream);
+
+/*
  * sad_decode_points -- random-access decode at float coordinates (the
  * render-only path with cached top-K lists, Sec. 6.6).  Query (x,y) uses the
  * list of pixel (clamp(floor x), clamp(floor y)) and evaluates the blend of
@@ -227,6 +238,19 @@ size_t sad_backward_workspace_bytes(int32_t H, int32_t W, int32_t K, int32_t cap
 int sad_render_backward(const float* params, const float* prep, int32_t capacity, int32_t H,
                         int32_t W, int32_t K, const uint32_t* map, const float* grad_rgb,
                         float* grads, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * sad_render_backward_saved -- sad_render_backward from the forward that
+ * sad_render_save kept: rgb (its output) and fwd (its {m, 1/Z} planes), for
+ * the same prep and map.  Each (pixel, site) weight is recomputed from its
+ * logit and the pixel's m and 1/Z; the per-tile reduction, the exact sums and
+ * the result are as in sad_render_backward (equal up to float rounding).
+ * Listed inactive sites get zero weight.
+ */
+int sad_render_backward_saved(const float* params, const float* prep, int32_t capacity, int32_t H,
+                              int32_t W, int32_t K, const uint32_t* map, const float* grad_rgb,
+                              const float* rgb, const float* fwd, float* grads, void* workspace,
+                              size_t workspace_bytes, void* stream);
 
 /*
  * sad_train_grads -- fused training gradient (Sec. 6.1): renders, forms the

@@ -2,10 +2,11 @@
 
 ``sad_render_fn(params, topk_map, H, W)`` returns the rendered image
 float32[H, W, 3] and is differentiable in ``params`` (float32[11, N]).  The
-top-K map is a frozen, non-differentiable index set.  Only the inputs are
-saved for backward; the backward call recomputes every pixel's softmax inside
-the CUDA adjoint instead of storing the N x K weights.  All work runs in
-libsad.so through the C-ABI binding.
+top-K map is a frozen, non-differentiable index set.  The forward keeps the
+inputs, its output and two floats per pixel (the max logit and 1/Z of the
+softmax); the backward recomputes every (pixel, site) weight from its logit
+inside the CUDA adjoint instead of storing the N x K weights.  All work runs
+in libsad.so through the C-ABI binding.
 """
 from __future__ import annotations
 
@@ -43,20 +44,21 @@ class SADRender(torch.autograd.Function):
         prep = capi.empty_prep(cap, params.device)
         capi.sad_prepare_sites(params, H, W, prep)
         rgb = torch.empty((H, W, 3), dtype=torch.float32, device=params.device)
-        capi.sad_render(prep, cap, H, W, K, topk_map, rgb)
-        ctx.save_for_backward(params, topk_map, prep)
+        fwd = torch.empty((2, H * W), dtype=torch.float32, device=params.device)
+        capi.sad_render_save(prep, cap, H, W, K, topk_map, rgb, fwd)
+        ctx.save_for_backward(params, topk_map, prep, rgb, fwd)
         ctx.H, ctx.W, ctx.K = H, W, K
         return rgb
 
     @staticmethod
     def backward(ctx, grad_rgb):
-        params, topk_map, prep = ctx.saved_tensors
+        params, topk_map, prep, rgb, fwd = ctx.saved_tensors
         H, W, K = ctx.H, ctx.W, ctx.K
         cap = params.shape[1]
         grads = torch.empty_like(params)
         ws = _WS.get(params.device, H, W, K, cap)
-        capi.sad_render_backward(params, prep, H, W, K, topk_map,
-                                 grad_rgb.contiguous().to(torch.float32), grads, ws)
+        capi.sad_render_backward_saved(params, prep, H, W, K, topk_map,
+                                       grad_rgb.contiguous().to(torch.float32), rgb, fwd, grads, ws)
         return grads, None, None, None
 
 

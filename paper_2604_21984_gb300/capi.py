@@ -103,6 +103,14 @@ _SIGS = {
     "sad_render": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                   ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_void_p]),
+    "sad_render_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "sad_render_backward_saved": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                                 ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_size_t, ctypes.c_void_p]),
     "sad_decode_points": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
@@ -312,6 +320,16 @@ def sad_render(prep, cap, H, W, K, map_in, rgb, stream=None):
     return rgb
 
 
+def sad_render_save(prep, cap, H, W, K, map_in, rgb, fwd, stream=None):
+    """sad_render that also writes fwd = float32[2, H*W] {max logit, 1/Z}."""
+    _check(lib().sad_render_save(_ptr(prep, torch.float32, "prep"), cap, H, W, K,
+                                 _ptr(map_in, torch.int32, "map", H * W * K),
+                                 _ptr(rgb, torch.float32, "rgb", H * W * 3),
+                                 _ptr(fwd, torch.float32, "fwd", 2 * H * W), _stream(stream)),
+           "sad_render_save")
+    return rgb
+
+
 def sad_decode_points(prep, cap, H, W, K, map_in, xy, rgb, stream=None):
     n = xy.shape[0]
     _check(lib().sad_decode_points(_ptr(prep, torch.float32, "prep"), cap, H, W, K,
@@ -331,6 +349,22 @@ def sad_render_backward(params, prep, H, W, K, map_in, grad_rgb, grads, ws, stre
                                      _ptr(grads, torch.float32, "grads", N_PARAMS * cap),
                                      _ptr(ws, torch.uint8, "workspace"), ws.numel(),
                                      _stream(stream)), "sad_render_backward")
+    return grads
+
+
+def sad_render_backward_saved(params, prep, H, W, K, map_in, grad_rgb, rgb, fwd, grads, ws,
+                              stream=None):
+    """sad_render_backward from sad_render_save's rgb and fwd."""
+    cap = params.shape[1]
+    _check(lib().sad_render_backward_saved(_ptr(params, torch.float32, "params", N_PARAMS * cap),
+                                           _ptr(prep, torch.float32, "prep"), cap, H, W, K,
+                                           _ptr(map_in, torch.int32, "map", H * W * K),
+                                           _ptr(grad_rgb, torch.float32, "grad_rgb", H * W * 3),
+                                           _ptr(rgb, torch.float32, "rgb", H * W * 3),
+                                           _ptr(fwd, torch.float32, "fwd", 2 * H * W),
+                                           _ptr(grads, torch.float32, "grads", N_PARAMS * cap),
+                                           _ptr(ws, torch.uint8, "workspace"), ws.numel(),
+                                           _stream(stream)), "sad_render_backward_saved")
     return grads
 
 

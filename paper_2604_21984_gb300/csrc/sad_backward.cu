@@ -65,7 +65,7 @@ static WsLayout ws_layout(int H, int W, int K, int cap, int64_t max_records) {
 // ---------------------------------------------------------------------------
 // stand-alone per-tile kernel: the tile's lists come from the map
 // ---------------------------------------------------------------------------
-template <int K, int MODE>
+template <int K, int MODE, bool SAVED = false>
 __global__ void __launch_bounds__(kTileThreads, MODE == kModeStats ? 2 : 4)
     k_bwd_tile(TileIO io, int cap, int H, int W, const uint4* __restrict__ map) {
   const uint32_t tiles_x = (W + kTileSide - 1) / kTileSide;
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kTileThreads, MODE == kModeStats ? 2 : 4)
   float lk[K];  // unused without HAVE_L
 #pragma unroll
   for (int k = 0; k < K; ++k) lk[k] = 0.f;
-  tile_body<K, MODE>(c, io, ids, lk);
+  tile_body<K, MODE, false, kTileSide, SAVED>(c, io, ids, lk);
 }
 
 // ---------------------------------------------------------------------------
@@ -206,7 +206,8 @@ __global__ void k_loss_final(const float* __restrict__ tile_loss, uint32_t n_til
 static int run_backward(const float* params, const float* prep, int cap, int H, int W, int K,
                         const uint32_t* map, const float* grad_rgb, const float* target,
                         float* grads, float* loss, float* rgb_out, void* ws, size_t ws_bytes,
-                        cudaStream_t st, const char* name, float* stats = nullptr) {
+                        cudaStream_t st, const char* name, float* stats = nullptr,
+                        const float* fwd = nullptr, const float* rgb_in = nullptr) {
   if (int e = check_problem(cap, H, W, K, true)) return e;
   const bool stats_mode = stats != nullptr;
   if (!map || (!grads && !stats_mode) || !ws || (!prep && cap > 0) ||
@@ -262,11 +263,21 @@ static int run_backward(const float* params, const float* prep, int cap, int H, 
   io.records = rec;
   io.max_records = LL.max_records;
   io.hdr = hdr;
+  io.fwd = fwd;
+  io.rgb_in = rgb_in;
 #define SAD_TILE_LAUNCH(KK, MM) \
   k_bwd_tile<KK, MM><<<LL.n_tiles, kTileThreads, 0, st>>>(io, cap, H, W, m4)
+#define SAD_TILE_SAVED(KK) \
+  k_bwd_tile<KK, kModeGrad, true><<<LL.n_tiles, kTileThreads, 0, st>>>(io, cap, H, W, m4)
   {
     TraceScope tr_(st, "k_bwd_tile");
-    if (stats_mode) {
+    if (fwd) {
+      switch (K) {
+        case 4: SAD_TILE_SAVED(4); break;
+        case 8: SAD_TILE_SAVED(8); break;
+        default: SAD_TILE_SAVED(16); break;
+      }
+    } else if (stats_mode) {
       switch (K) {
         case 4: SAD_TILE_LAUNCH(4, kModeStats); break;
         case 8: SAD_TILE_LAUNCH(8, kModeStats); break;
@@ -281,6 +292,7 @@ static int run_backward(const float* params, const float* prep, int cap, int H, 
     }
   }
 #undef SAD_TILE_LAUNCH
+#undef SAD_TILE_SAVED
   if (int r = check_launch("k_bwd_tile")) return r;
   if (target && loss) {
     { TraceScope tr_(st, "k_loss_final"); k_loss_final<<<1, 256, 0, st>>>(tile_loss, LL.n_tiles, 1.0f / static_cast<float>(static_cast<double>(H) * W), loss); }
@@ -318,6 +330,16 @@ int sad_render_backward(const float* params, const float* prep, int32_t capacity
   if (!grad_rgb) return einval("sad_render_backward: null grad_rgb");
   return run_backward(params, prep, capacity, H, W, K, map, grad_rgb, nullptr, grads, nullptr,
                       nullptr, workspace, workspace_bytes, as_stream(stream), "sad_render_backward");
+}
+
+int sad_render_backward_saved(const float* params, const float* prep, int32_t capacity, int32_t H,
+                              int32_t W, int32_t K, const uint32_t* map, const float* grad_rgb,
+                              const float* rgb, const float* fwd, float* grads, void* workspace,
+                              size_t workspace_bytes, void* stream) {
+  if (!grad_rgb || !rgb || !fwd) return einval("sad_render_backward_saved: null grad_rgb, rgb or fwd");
+  return run_backward(params, prep, capacity, H, W, K, map, grad_rgb, nullptr, grads, nullptr,
+                      nullptr, workspace, workspace_bytes, as_stream(stream),
+                      "sad_render_backward_saved", nullptr, fwd, rgb);
 }
 
 int sad_train_grads(const float* params, const float* prep, int32_t capacity, int32_t H,

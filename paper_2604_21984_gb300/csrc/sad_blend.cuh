@@ -31,12 +31,15 @@ __device__ __forceinline__ void blend_step(float l, bool ok, float4 ck, float& m
   c.z += b * ck.z;
 }
 
+// m_out / iz_out (optional): the max logit and 1/Z of the blend (0 if no
+// listed site is valid), the per-pixel state the saved-forward adjoint reads.
 template <int NP>
 __device__ __forceinline__ float3 blend_planes(const uint4* __restrict__ map, size_t P, size_t q,
                                                float px, float py, SiteRange sr,
                                                const float4* __restrict__ geo,
                                                const float4* __restrict__ met,
-                                               const float4* __restrict__ col) {
+                                               const float4* __restrict__ col,
+                                               float* m_out = nullptr, float* iz_out = nullptr) {
   float m = -INFINITY, z = 0.f;
   float3 c = make_float3(0.f, 0.f, 0.f);
 #pragma unroll
@@ -60,12 +63,15 @@ __device__ __forceinline__ float3 blend_planes(const uint4* __restrict__ map, si
       }
     }
   }
+  float iz = 0.f;
   if (z > 0.f) {
-    const float iz = 1.f / z;
+    iz = 1.f / z;
     c.x *= iz;
     c.y *= iz;
     c.z *= iz;
   }
+  if (m_out) *m_out = z > 0.f ? m : 0.f;
+  if (iz_out) *iz_out = iz;
   return c;
 }
 

@@ -137,6 +137,8 @@ struct TileIO {
   WsHeader* hdr;
   float2* bias = nullptr;  // training step: per image {1 - beta1^t, 1 - beta2^t} for the site step
   float beta1 = 0.f, beta2 = 0.f;
+  const float* fwd = nullptr;     // saved forward: float32[2][P] {max logit, 1/Z} per pixel
+  const float* rgb_in = nullptr;  // saved forward: the blend c per pixel, float32[P][3]
 };
 
 // Adjoint (MODE = kModeGrad) or budget statistics (kModeStats) of one tile
@@ -147,7 +149,7 @@ struct TileIO {
 // entries are the empty tail), so the forward takes them instead of
 // re-gathering and re-scoring, and the first entry is the maximum.
 // Every thread of the 256-thread block must call it.
-template <int K, int MODE, bool HAVE_L = false, int TW = kTileSide>
+template <int K, int MODE, bool HAVE_L = false, int TW = kTileSide, bool SAVED = false>
 __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, uint32_t (&ids)[K],
                                           const float (&lk)[K]) {
   const float4* __restrict__ geo = io.geo;
@@ -203,7 +205,18 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
   float3 cb = make_float3(0.f, 0.f, 0.f);
   uint32_t vm = 0;
   float l[MODE == kModeStats ? K : 1];
-  if (MODE == kModeStats) {
+  if (SAVED) {
+    // the render's max logit, 1/Z and blend (io.fwd, io.rgb_in): no
+    // gathers; listed inactive sites contribute zero in the pair loop
+#pragma unroll
+    for (int k = 0; k < K; ++k) vm |= ids[k] != kInvalid ? (1u << k) : 0u;
+    if (inimg) {
+      const size_t P = static_cast<size_t>(c.H) * c.W;  // stand-alone: one image
+      m = io.fwd[q];
+      z = io.fwd[P + q];  // holds 1/Z here
+      cb = make_float3(io.rgb_in[3 * q], io.rgb_in[3 * q + 1], io.rgb_in[3 * q + 2]);
+    }
+  } else if (MODE == kModeStats) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       l[k] = -INFINITY;
@@ -280,10 +293,12 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
       }
     }
   }
-  const float iz = vm ? 1.f / z : 0.f;
-  cb.x *= iz;
-  cb.y *= iz;
-  cb.z *= iz;
+  const float iz = SAVED ? z : (vm ? 1.f / z : 0.f);
+  if (!SAVED) {
+    cb.x *= iz;
+    cb.y *= iz;
+    cb.z *= iz;
+  }
   float3 g = make_float3(0.f, 0.f, 0.f);
   float lpx = 0.f;
   float3 I = make_float3(0.f, 0.f, 0.f);
@@ -453,7 +468,8 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
           const float qc = fmaxf(qq, 0.f);
           const float rq = rsqrtf(qc);
           const float n = MODE == kModeStats ? sqrtf(qc) : (qc > 0.f ? qc * rq : 0.f);
-          const float w = __expf(gs.z * (gs.w - n) - A.x) * A.y;
+          // (ms.w = 0 only for a listed inactive site in the saved-forward mode)
+        const float w = __expf(gs.z * (gs.w - n) - A.x) * A.y * (SAVED ? ms.w : 1.f);
           if (MODE == kModeStats) {
             // A = {m, 1/Z, cbar.x, cbar.y}, B = {cbar.z, I}
             const float4 B = s_pb[p];

@@ -16,36 +16,46 @@ def capi():
     return require_gpu()
 
 
-def _backward(capi, p, H, W, ids, g, max_records=0):
+def _backward(capi, p, H, W, ids, g, max_records=0, saved=False):
+    """The adjoint by sad_render_backward, or (saved) by sad_render_save then
+    sad_render_backward_saved."""
     torch = pytest.importorskip("torch")
     K = ids.shape[1]
     cap = p.shape[1]
     pt, prep = prepare(capi, p, H, W)
     grads = torch.empty((11, cap), dtype=torch.float32, device="cuda")
     ws = capi.backward_workspace(H, W, K, cap, max_records)
-    capi.sad_render_backward(pt, prep, H, W, K, capi.map_from_ids(ids), dev(g.astype(np.float32)),
-                             grads, ws)
+    m = capi.map_from_ids(ids)
+    if saved:
+        rgb = torch.empty((H, W, 3), dtype=torch.float32, device="cuda")
+        fwd = torch.empty((2, H * W), dtype=torch.float32, device="cuda")
+        capi.sad_render_save(prep, cap, H, W, K, m, rgb, fwd)
+        capi.sad_render_backward_saved(pt, prep, H, W, K, m, dev(g.astype(np.float32)), rgb, fwd, grads, ws)
+    else:
+        capi.sad_render_backward(pt, prep, H, W, K, m, dev(g.astype(np.float32)), grads, ws)
     st, used = capi.sad_workspace_status(ws)
     assert st == 0, used
     return grads.cpu().numpy().astype(np.float64), used
 
 
-def test_config1_backward(capi, oracle):
+@pytest.mark.parametrize("saved", [False, True])
+def test_config1_backward(capi, oracle, saved):
     H = W = 64
     img = gen.image_sinusoid_polygons(H, W, seed=1000)
     p = gen.sites_isotropic(img, 256, seed=1001)
     p[0] += 0.01                                           # keep sites off pixel centres
     ids = oracle.propagate_fp32(p, H, W, 8, passes=6, J=2, seed=77)
     g = gen.grad_image(H, W, seed=1002) / (H * W)
-    got, used = _backward(capi, p, H, W, ids, g)
+    got, used = _backward(capi, p, H, W, ids, g, saved=saved)
     ref = oracle.render_backward(p, H, W, ids, g)
     assert_grads_close(got, ref)
     assert used > 0
 
 
+@pytest.mark.parametrize("saved", [False, True])
 @pytest.mark.parametrize("K", [4, 8, 16])
 @pytest.mark.parametrize("H,W", [(40, 56), (17, 33), (1, 1)])
-def test_backward_edge_cases(capi, oracle, K, H, W):
+def test_backward_edge_cases(capi, oracle, K, H, W, saved):
     n = max(K + 4, 60)
     p = gen.sites_random_spd(H, W, n, seed=H * 7 + W + K, capacity=n + 5)
     p[2] += 2.0
@@ -53,19 +63,20 @@ def test_backward_edge_cases(capi, oracle, K, H, W):
     ids = gen.knn_map(p, H, W, K, seed=4, truncate_frac=0.3, shuffle=True, include_inactive_frac=0.2)
     ids[0, :] = INV
     g = gen.grad_image(H, W, seed=5)
-    got, _ = _backward(capi, p, H, W, ids, g)
+    got, _ = _backward(capi, p, H, W, ids, g, saved=saved)
     ref = oracle.render_backward(p, H, W, ids, g)
     assert_grads_close(got, ref)
 
 
-def test_incoherent_map_uses_extra_rounds(capi, oracle):
+@pytest.mark.parametrize("saved", [False, True])
+def test_incoherent_map_uses_extra_rounds(capi, oracle, saved):
     """Random, spatially incoherent lists: far more distinct sites per tile
     than the per-round table holds, so the multi-round path runs."""
     H, W, K = 32, 48, 16
     p = gen.sites_random_spd(H, W, 3000, seed=51)
     ids = gen.random_map(H * W, K, 3000, seed=52, invalid_frac=0.05)
     g = gen.grad_image(H, W, seed=53)
-    got, used = _backward(capi, p, H, W, ids, g, max_records=H * W * K)
+    got, used = _backward(capi, p, H, W, ids, g, max_records=H * W * K, saved=saved)
     ref = oracle.render_backward(p, H, W, ids, g)
     assert_grads_close(got, ref)
     assert used > 128 * ((H + 15) // 16) * ((W + 15) // 16)
@@ -129,3 +140,37 @@ def test_full_size_sampled_sites(capi, oracle):
     r, c = np.divmod(rows, W)
     ref = oracle.render_backward(p, H, W, ids[rows], g.reshape(-1, 3)[rows], c + 0.5, r + 0.5)
     assert_grads_close(got[:, sites], ref[:, sites])
+
+
+def test_render_save_state(capi, oracle):
+    """sad_render_save: the same image as sad_render bit for bit, and per
+    pixel the max listed logit and 1/Z of the oracle's softmax (a black pixel
+    with no valid site: both 0)."""
+    torch = pytest.importorskip("torch")
+    H, W, K = 37, 53, 16
+    p = gen.sites_random_spd(H, W, 400, seed=61)
+    p = gen.deactivate_random(p, 0.15, seed=62)
+    ids = gen.knn_map(p, H, W, K, seed=63, truncate_frac=0.3, shuffle=True, include_inactive_frac=0.2)
+    ids[5, :] = INV
+    cap = p.shape[1]
+    _, prep = prepare(capi, p, H, W)
+    m = capi.map_from_ids(ids)
+    a = torch.empty((H, W, 3), dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    fwd = torch.empty((2, H * W), dtype=torch.float32, device="cuda")
+    capi.sad_render(prep, cap, H, W, K, m, a)
+    capi.sad_render_save(prep, cap, H, W, K, m, b, fwd)
+    assert torch.equal(a, b)
+    f = fwd.cpu().numpy().astype(np.float64)
+    valid, safe = oracle._valid_entries(p, ids)
+    px, py = oracle.pixel_centres(H, W)
+    l = oracle.logits(p, H, W, safe, px, py)
+    lm = np.where(valid, l, -np.inf)
+    mx = lm.max(axis=1)
+    has = valid.any(axis=1)
+    mx_safe = np.where(has, mx, 0.0)
+    z = np.where(valid, np.exp(np.where(valid, l, 0.0) - mx_safe[:, None]), 0.0).sum(axis=1)
+    np.testing.assert_allclose(f[0][has], mx[has], rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(f[1][has], 1.0 / z[has], rtol=1e-5)
+    assert np.all(f[:, ~has] == 0.0) and (~has).any()
+
