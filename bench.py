@@ -402,7 +402,9 @@ def encode_leg(capi, dev, peak, peak_kind, args, iters=2000):
 
 
 def c3_leg(capi, dev, peak, peak_kind, args, iters=10):
-    """render + render_backward at 2048^2, 262144 random anisotropic sites, K=16."""
+    """render + render_backward at 2048^2, 262144 random anisotropic sites, K=16: the
+    autograd pair (sad_render_save + sad_render_backward_saved) and the
+    recomputing pair (sad_render + sad_render_backward)."""
     import torch
     from paper_2604_21984_gb300 import inputs as gen
     H = W = 2048
@@ -514,6 +516,7 @@ def c3_leg(capi, dev, peak, peak_kind, args, iters=10):
         rs_ms.append(e0.elapsed_time(e1))
         bs_ms.append(e1.elapsed_time(e2))
     del fwd, rgb_s
+    rs, bs = statistics.mean(rs_ms), statistics.mean(bs_ms)
     # the paper's evaluation render from the packed 16-byte records
     words, q = capi.sad_pack_sites(pt, H, W)
     qh = q.cpu()
@@ -540,11 +543,14 @@ def c3_leg(capi, dev, peak, peak_kind, args, iters=10):
                 "frac": round(a / peak, 4), "peak_kind": peak_kind}
     return {
         "workload": "2048x2048, 262144 random anisotropic sites, K=16, map from seed + 16 passes",
-        "mpix_per_s_fwd_bwd": round(P / ((rb + bb) / 1e3) / 1e6, 1),
-        "saved_forward": {"render_save_ms": round(statistics.mean(rs_ms), 4),
-                          "backward_saved_ms": round(statistics.mean(bs_ms), 4),
-                          "mpix_per_s_fwd_bwd": round(P / ((statistics.mean(rs_ms) + statistics.mean(bs_ms)) / 1e3) / 1e6, 1)},
-        "render_ms": round(rb, 4), "backward_ms": round(bb, 4), "jfa_16_passes_ms": round(jfa_ms, 3),
+        # the autograd pair (render keeping {max logit, 1/Z}, adjoint from it)
+        "mpix_per_s_fwd_bwd": round(P / ((rs + bs) / 1e3) / 1e6, 1),
+        "render_save_ms": round(rs, 4), "backward_saved_ms": round(bs, 4),
+        # sad_render + sad_render_backward, nothing kept between them
+        "recompute": {"render_ms": round(rb, 4), "backward_ms": round(bb, 4),
+                      "mpix_per_s_fwd_bwd": round(P / ((rb + bb) / 1e3) / 1e6, 1),
+                      "roofline_fwd_bwd": roof(render_bytes + bwd_bytes, rb + bb)},
+        "jfa_16_passes_ms": round(jfa_ms, 3),
         "flood_prepass_11_plus_4_passes_ms": round(flood_ms, 3),
         "one_pass_ms": {k: round(v, 4) for k, v in pass_ms.items()},
         "jfa_16_passes_half2_from_jump4_ms": round(jfa_h2_ms, 3),
@@ -554,7 +560,7 @@ def c3_leg(capi, dev, peak, peak_kind, args, iters=10):
         "records": used, "ws_status": st,
         "kernels_ms": {k: round(ms / max(n, 1), 5) for k, (n, ms) in sorted(trace.items())},
         "roofline_render": roof(render_bytes, rb),
-        "roofline_fwd_bwd": roof(render_bytes + bwd_bytes, rb + bb),
+        "roofline_fwd_bwd": roof(render_bytes + bwd_bytes, rs + bs),
     }
 
 
