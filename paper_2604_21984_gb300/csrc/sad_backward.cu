@@ -95,7 +95,8 @@ __global__ void __launch_bounds__(kTileThreads, MODE == kModeStats ? 2 : 4)
   float lk[K];  // unused without HAVE_L
 #pragma unroll
   for (int k = 0; k < K; ++k) lk[k] = 0.f;
-  tile_body<K, MODE, false, kTileSide, SAVED>(c, io, ids, lk);
+  __shared__ TileShared<K, MODE> sm;
+  tile_body<K, MODE, false, kTileSide, SAVED>(c, io, ids, lk, sm);
 }
 
 // ---------------------------------------------------------------------------

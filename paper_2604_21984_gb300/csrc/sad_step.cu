@@ -106,10 +106,16 @@ __device__ __forceinline__ void write_bias(const BatchDesc& d, const int32_t* st
 // Propagation pass + adjoint of the tiles of images that refresh their lists
 // this call (UPDATE_ONLY: the pass alone, for extra passes between steps).
 template <int K, bool UPDATE_ONLY, int TW>
-__global__ void __launch_bounds__(kTileThreads, 3)
+__global__ void __launch_bounds__(kTileThreads, UPDATE_ONLY ? 3 : 4)
     k_step_tile(const BatchDesc d, TileIO io, uint4* map_a, uint4* map_b, size_t Ptot, int J,
                 const int32_t* __restrict__ state) {
-  __shared__ uint32_t s_q[kQueue][kTileThreads];
+  // the propagation's candidate queue and the tile body's tables are never
+  // live together: one shared region
+  __shared__ union Smem {
+    uint32_t q[kQueue][kTileThreads];
+    TileShared<K, kModeGrad> t;
+  } sm;
+  auto& s_q = sm.q;
   if (!UPDATE_ONLY) write_bias(d, state, io);
   const int b = image_of_tile(d, blockIdx.x);
   const BatchImg im = d.img[b];
@@ -139,7 +145,10 @@ __global__ void __launch_bounds__(kTileThreads, 3)
     for (int j = 0; j < K / 4; ++j)
       map_out[j * Ptot + q] = make_uint4(ids[4 * j], ids[4 * j + 1], ids[4 * j + 2], ids[4 * j + 3]);
   }
-  if (!UPDATE_ONLY) tile_body<K, kModeGrad, true, TW>(c, io, ids, lk);
+  if (!UPDATE_ONLY) {
+    __syncthreads();  // every thread's queue is drained before the tables overwrite it
+    tile_body<K, kModeGrad, true, TW>(c, io, ids, lk, sm.t);
+  }
 }
 
 // Adjoint of the tiles of images that keep their lists this call: the lists
@@ -170,7 +179,8 @@ __global__ void __launch_bounds__(kTileThreads, 3)
   float lk[K];  // unused without HAVE_L
 #pragma unroll
   for (int k = 0; k < K; ++k) lk[k] = 0.f;
-  tile_body<K, kModeGrad, false, TW>(c, io, ids, lk);
+  __shared__ TileShared<K, kModeGrad> sm;
+  tile_body<K, kModeGrad, false, TW>(c, io, ids, lk, sm);
 }
 
 // After a propagation-only pass: every image's pass index and map parity advance.

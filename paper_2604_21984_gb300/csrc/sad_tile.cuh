@@ -149,9 +149,35 @@ struct TileIO {
 // entries are the empty tail), so the forward takes them instead of
 // re-gathering and re-scoring, and the first entry is the maximum.
 // Every thread of the 256-thread block must call it.
+// The tile body's shared memory, as one object so that a kernel can overlay
+// it on other shared data it no longer needs (the fused step: the
+// propagation's candidate queue).
+template <int K, int MODE>
+struct TileShared {
+  static constexpr int kW = kTileThreads / 32;
+  uint32_t keys[kSlots];
+  uint32_t mask[kW][kSlots];  // [warp word][slot]: conflict-free per-slot reads
+  uint16_t wpre[kW][kSlots];
+  uint32_t cnt[kSlots];
+  uint32_t off[kSlots];
+  uint32_t rix[kSlots];
+  uint8_t list[kTileThreads * K];
+  // per pixel.  gradient mode: {m, 1/Z, g.cbar, gx}, {gy, gz, -, -};
+  // statistics mode: {m, 1/Z, cbar.x, cbar.y}, {cbar.z, I}, {c' of the
+  // dominant site (blend without it), dominant id}
+  float4 pa[kTileThreads];
+  float2 pg[MODE == kModeStats ? 1 : kTileThreads];
+  float4 pb[MODE == kModeStats ? kTileThreads : 1];
+  float4 pc[MODE == kModeStats ? kTileThreads : 1];
+  uint64_t scan[kW];
+  float red[kW];
+  uint32_t base;
+  uint32_t pmax[10];
+};
+
 template <int K, int MODE, bool HAVE_L = false, int TW = kTileSide, bool SAVED = false>
 __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, uint32_t (&ids)[K],
-                                          const float (&lk)[K]) {
+                                          const float (&lk)[K], TileShared<K, MODE>& sm) {
   const float4* __restrict__ geo = io.geo;
   const float4* __restrict__ met = io.met;
   const float4* __restrict__ col = io.col;
@@ -164,24 +190,21 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
   WsHeader* __restrict__ hdr = io.hdr;
   const float two_over_P = c.two_over_P;
   constexpr int kWarps = kTileThreads / 32;
-  __shared__ uint32_t s_keys[kSlots];
-  __shared__ uint32_t s_mask[kWarps][kSlots];   // [warp word][slot]: conflict-free per-slot reads
-  __shared__ uint16_t s_wpre[kWarps][kSlots];
-  __shared__ uint32_t s_cnt[kSlots];
-  __shared__ uint32_t s_off[kSlots];
-  __shared__ uint32_t s_rix[kSlots];
-  __shared__ uint8_t s_list[kTileThreads * K];
-  // per pixel.  gradient mode: {m, 1/Z, g.cbar, gx}, {gy, gz, -, -};
-  // statistics mode: {m, 1/Z, cbar.x, cbar.y}, {cbar.z, I}, {c' of the
-  // dominant site (blend without it), dominant id}
-  __shared__ float4 s_pa[kTileThreads];
-  __shared__ float2 s_pg[MODE == kModeStats ? 1 : kTileThreads];
-  __shared__ float4 s_pb[MODE == kModeStats ? kTileThreads : 1];
-  __shared__ float4 s_pc[MODE == kModeStats ? kTileThreads : 1];
-  __shared__ uint64_t s_scan[kWarps];
-  __shared__ float s_red[kWarps];
-  __shared__ uint32_t s_base;
-  __shared__ uint32_t s_pmax[10];
+  auto& s_keys = sm.keys;
+  auto& s_mask = sm.mask;
+  auto& s_wpre = sm.wpre;
+  auto& s_cnt = sm.cnt;
+  auto& s_off = sm.off;
+  auto& s_rix = sm.rix;
+  auto& s_list = sm.list;
+  auto& s_pa = sm.pa;
+  auto& s_pg = sm.pg;
+  auto& s_pb = sm.pb;
+  auto& s_pc = sm.pc;
+  auto& s_scan = sm.scan;
+  auto& s_red = sm.red;
+  auto& s_base = sm.base;
+  auto& s_pmax = sm.pmax;
 
   const int t = threadIdx.x;
   const int lane = t & 31, warp = t >> 5;
