@@ -209,7 +209,7 @@ class _Lane:
                     a["req"].done_event = fin
                     srv._retire(a, fin)
         self.ticks_same += 1
-        srv.launches += 4 * T
+        srv.launches += 3 * T   # per iteration: tile pass + adjoint, exact sums, site step
         self.inflight.append(ev)
         return T
 
@@ -555,7 +555,7 @@ class PlainLoop:
                     enc.step()
                 req.result = enc.params[:, :n].clone()
                 req.loss = enc.loss.clone()
-                self.launches += 7 + enc.t_pass + 4 * req.iters
+                self.launches += 7 + enc.t_pass + 3 * req.iters
             else:
                 r = self.residents[req.resident]
                 n = req.xy.shape[0]
