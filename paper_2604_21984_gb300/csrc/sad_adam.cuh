@@ -12,6 +12,12 @@ struct AdamArgs {
   float log_tau_min, log_tau_max, r_min, r_max, a_min, a_max, b_min, b_max;
 };
 
+__device__ __forceinline__ void adam_site_mv(float (&p)[kNParams], const float (&g)[kNParams],
+                                             const float (&m0)[kNParams], const float (&v0)[kNParams],
+                                             float* __restrict__ m, float* __restrict__ v, size_t c,
+                                             size_t i, const AdamArgs& A, float bc1, float bc2,
+                                             int H, int W);
+
 // Bias-corrected Adam on the 11 planes of site i (planes of stride c) with
 // gradient g: x, y and r step in normalised units (gradient / s, step * 1/s);
 // then positions clamp to [0,W]x[0,H], log_tau/r/a/b to their ranges, colours
@@ -21,14 +27,30 @@ __device__ __forceinline__ void adam_site(float (&p)[kNParams], const float (&g)
                                           float* __restrict__ m, float* __restrict__ v, size_t c,
                                           size_t i, const AdamArgs& A, float bc1, float bc2,
                                           int H, int W) {
+  float m0[kNParams], v0[kNParams];
+#pragma unroll
+  for (int j = 0; j < kNParams; ++j) {
+    m0[j] = m[j * c + i];
+    v0[j] = v[j * c + i];
+  }
+  adam_site_mv(p, g, m0, v0, m, v, c, i, A, bc1, bc2, H, W);
+}
+
+// adam_site with the site's m and v already loaded (m0, v0), so that a
+// caller can issue those loads early.
+__device__ __forceinline__ void adam_site_mv(float (&p)[kNParams], const float (&g)[kNParams],
+                                             const float (&m0)[kNParams], const float (&v0)[kNParams],
+                                             float* __restrict__ m, float* __restrict__ v, size_t c,
+                                             size_t i, const AdamArgs& A, float bc1, float bc2,
+                                             int H, int W) {
   const float inv_s = static_cast<float>(H > W ? H : W);
 #pragma unroll
   for (int j = 0; j < kNParams; ++j) {
     const size_t o = j * c + i;
     const bool norm_units = (j == PX || j == PY || j == PR);
     const float gj = norm_units ? g[j] * inv_s : g[j];
-    const float mj = A.beta1 * m[o] + (1.f - A.beta1) * gj;
-    const float vj = A.beta2 * v[o] + (1.f - A.beta2) * gj * gj;
+    const float mj = A.beta1 * m0[j] + (1.f - A.beta1) * gj;
+    const float vj = A.beta2 * v0[j] + (1.f - A.beta2) * gj * gj;
     m[o] = mj;
     v[o] = vj;
     const float mhat = mj / bc1, vhat = vj / bc2;

@@ -212,6 +212,14 @@ __device__ __forceinline__ void site_work(const BatchDesc& d, uint32_t j, float*
   float p[kNParams];
 #pragma unroll
   for (int k = 0; k < kNParams; ++k) p[k] = params[k * c + i];
+  float m0[kNParams], v0[kNParams];  // issued with the other loads, used by Adam at the end
+  if (adam) {
+#pragma unroll
+    for (int k = 0; k < kNParams; ++k) {
+      m0[k] = m[k * c + i];
+      v0[k] = v[k * c + i];
+    }
+  }
   if (adam) {
     float acc[10];
     bool any = false;
@@ -265,7 +273,7 @@ __device__ __forceinline__ void site_work(const BatchDesc& d, uint32_t j, float*
     }
     if (p[PX] >= 0.f) {
       const float2 bc = bias[b];  // written by the tile kernel of this step
-      adam_site(p, g, m, v, c, i, A, bc.x, bc.y, im.H, im.W);
+      adam_site_mv(p, g, m0, v0, m, v, c, i, A, bc.x, bc.y, im.H, im.W);
 #pragma unroll
       for (int k = 0; k < kNParams; ++k) params[k * c + i] = p[k];
     }
