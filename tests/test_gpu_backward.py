@@ -125,15 +125,17 @@ def test_train_grads_and_loss(capi, oracle):
     assert_grads_close(grads.cpu().numpy().astype(np.float64), oracle.render_backward(p, H, W, ids, g))
 
 
-def test_full_size_sampled_sites(capi, oracle):
-    """2048^2, 262144 sites, K=16: 64 sampled sites' gradients, each from every
-    pixel that lists it (oracle restricted to those pixels)."""
+@pytest.mark.parametrize("saved", [False, True])
+def test_full_size_sampled_sites(capi, oracle, saved):
+    """2048^2, 262144 sites, K=16 (config 3, both adjoint forms): 64 sampled
+    sites' gradients, each from every pixel that lists it (oracle restricted
+    to those pixels)."""
     H = W = 2048
     K = 16
     p = gen.sites_random_spd(H, W, 262144, seed=3000)
     ids = gen.knn_map(p, H, W, K, seed=3001)
     g = gen.grad_image(H, W, seed=3002) / (H * W)
-    got, _ = _backward(capi, p, H, W, ids, g)
+    got, _ = _backward(capi, p, H, W, ids, g, saved=saved)
     rng = np.random.default_rng(3)
     sites = rng.choice(262144, 64, replace=False)
     rows = np.nonzero(np.isin(ids, sites.astype(np.uint32)).any(axis=1))[0]

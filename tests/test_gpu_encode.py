@@ -79,17 +79,20 @@ def test_candidate_period_fused_matches_separate_calls(capi):
     assert same > 0.95
 
 
-def test_full_size_fused_step_as_benchmarked(capi, oracle):
+@pytest.mark.parametrize("tile_w", [16, 32])
+def test_full_size_fused_step_as_benchmarked(capi, oracle, tile_w):
     """The benchmark's configuration: 768x512, 32768 gradient-weighted sites
-    (capacity 65536), K=16, J=4, one fused step after three.  The new map on
-    4096 sampled pixels equals the oracle's pass bit for bit; the loss and
-    every site's gradient match the oracle's fp64 render and adjoint on the
-    new lists over the whole image."""
+    (capacity 65536), K=16, J=4, one fused step after three, with 16x16 and
+    32x8 adjoint tiles.  The new map on 4096 sampled pixels equals the
+    oracle's pass bit for bit; the loss and every site's gradient match the
+    oracle's fp64 render and adjoint on the new lists over the whole
+    image."""
     torch = pytest.importorskip("torch")
     from paper_2604_21984_gb300.encode import EncodeConfig, Encoder
     H, W = 512, 768
     img = gen.image_noise_polygons_lines(H, W, seed=2000)
-    enc = Encoder(dev(img), EncodeConfig(n_sites=32768, K=16, J=4, seed=0, densify_every=0, keep_grads=True))
+    enc = Encoder(dev(img), EncodeConfig(n_sites=32768, K=16, J=4, seed=0, densify_every=0, keep_grads=True,
+                                         tile_w=tile_w))
     enc.init()
     for _ in range(3):
         enc.step()
