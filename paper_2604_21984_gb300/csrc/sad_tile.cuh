@@ -266,16 +266,25 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
   } else if (HAVE_L) {
     // sorted logits: the first valid entry is the maximum
     m = ids[0] != kInvalid ? lk[0] : -INFINITY;
+    // entries whose weight is below 1e-7 of the running sum are left out of
+    // the blend and of the pair lists (the rest of the list is smaller
+    // still: it is sorted): at most 16e-7 of the pixel's weight, far
+    // inside the loss and gradient tolerances, and no colour gathers or
+    // pairs for them once the field has sharpened
+    bool cut = false;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      if (ids[k] != kInvalid) {
-        vm |= 1u << k;
+      if (ids[k] != kInvalid && !cut) {
         const float e = __expf(lk[k] - m);
-        const float4 ck = ldg(&col[ids[k]]);
-        z += e;
-        cb.x += e * ck.x;
-        cb.y += e * ck.y;
-        cb.z += e * ck.z;
+        cut = e < 1e-7f * z;
+        if (!cut) {
+          vm |= 1u << k;
+          const float4 ck = ldg(&col[ids[k]]);
+          z += e;
+          cb.x += e * ck.x;
+          cb.y += e * ck.y;
+          cb.z += e * ck.z;
+        }
       }
     }
   } else {
