@@ -452,7 +452,10 @@ int sad_prepare_batch(const sad_batch_image* images, int32_t B, const float* par
  * gradients only by rounding).  Per tile: one
  * propagation pass at jump 1 (sad_update_topk semantics with the image's own
  * site range and seed) writing the image's next map, then, on those lists,
- * the fused render + MSE + adjoint of sad_train_grads; per site: the
+ * the fused render + MSE + adjoint of sad_train_grads (one difference: a
+ * pixel's list ends at the first entry whose softmax weight is below 1e-7
+ * of the running sum, the list being sorted by the pass's logits, so at
+ * most 1.6e-6 of the pixel's weight is left out); per site: the
  * gradient, an Adam step (sad_adam_step semantics with the image's H, W) and
  * the prepared table of the new parameters, so `prep` must hold the
  * prepared table of `params` on entry (sad_prepare_batch) and holds it again

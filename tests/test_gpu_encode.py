@@ -86,7 +86,9 @@ def test_full_size_fused_step_as_benchmarked(capi, oracle, tile_w):
     32x8 adjoint tiles.  The new map on 4096 sampled pixels equals the
     oracle's pass bit for bit; the loss and every site's gradient match the
     oracle's fp64 render and adjoint on the new lists over the whole
-    image."""
+    image.  Many listed entries carry a weight below 1e-7 here, so the
+    step's cut of negligible entries is exercised against the full
+    softmax."""
     torch = pytest.importorskip("torch")
     from paper_2604_21984_gb300.encode import EncodeConfig, Encoder
     H, W = 512, 768
@@ -106,6 +108,8 @@ def test_full_size_fused_step_as_benchmarked(capi, oracle, tile_w):
     sample = np.random.default_rng(11).choice(H * W, 4096, replace=False)
     ref = oracle.topk_pass_fp32(oracle.prepare_fp32(p0, H, W), ids0, H, W, 16, code, 4, 0x5AD, sample)
     assert np.array_equal(ids1[sample], ref)
+    w, _, valid, _ = oracle.weights(p0, H, W, ids1)
+    assert (w[valid] < 1e-7).mean() > 0.2
     rgb = oracle.render(p0, H, W, ids1)
     L, g = oracle.mse_loss_and_grad_rgb(rgb, img)
     assert abs(enc.loss.item() - L) <= 1e-5 * L
