@@ -65,8 +65,11 @@ static WsLayout ws_layout(int H, int W, int K, int cap, int64_t max_records) {
 // ---------------------------------------------------------------------------
 // stand-alone per-tile kernel: the tile's lists come from the map
 // ---------------------------------------------------------------------------
+// The saved-forward form keeps no per-entry forward state, so it fits 5
+// blocks per SM (48 registers, a few spilled) and the extra resident warps
+// hide its barrier waits; the recomputing form stays at 4 (64 registers).
 template <int K, int MODE, bool SAVED = false>
-__global__ void __launch_bounds__(kTileThreads, MODE == kModeStats ? 2 : 4)
+__global__ void __launch_bounds__(kTileThreads, MODE == kModeStats ? 2 : (SAVED ? 5 : 4))
     k_bwd_tile(TileIO io, int cap, int H, int W, const uint4* __restrict__ map) {
   const uint32_t tiles_x = (W + kTileSide - 1) / kTileSide;
   TileCtx c;
