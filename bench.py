@@ -162,7 +162,7 @@ def gen_images(specs):
 NCU_COUNTERS = {
     "k_step_tile": {"sources": ["sad_step.cu", "sad_tile.cuh", "sad_topk.cuh", "sad_device.cuh",
                                 "sad_adam.cuh", "sad_blend.cuh"],
-                    "sha": "18552346185120a7", "dram_bytes": 33728768, "warp_inst": 153631217},
+                    "sha": "48e389fda0039ac8", "dram_bytes": 33728768, "warp_inst": 153631217},
 }
 ISSUE_PEAK = 152 * 4 * 2.07e9   # warp instructions / s: 152 SMs x 4 schedulers x 1 issue/clk x 2070 MHz
 

@@ -2,9 +2,13 @@
 // and Reduction"), shared by the stand-alone backward and the fused training
 // step.  Per pixel tile of 256 pixels (16x16, or 32x8 in the batched step;
 // one 256-thread block, one pixel per thread):
-//  1. forward: every pixel recomputes its max-subtracted softmax over its K
-//     listed sites (nothing from the forward pass is stored), forms its
-//     upstream gradient g (given, or 2(c - I)/P for the fused MSE loss);
+//  1. forward: every pixel forms its max-subtracted softmax over its K
+//     listed sites (no per-entry weights are stored): recomputed from the
+//     site table; or, in the fused step, from the exact sorted logits its
+//     propagation pass just produced, its list ending at the first entry
+//     below 1e-7 of the running sum; or, in the saved-forward form, from
+//     the render's max logit, 1/Z and blend.  It then forms its upstream
+//     gradient g (given, or 2(c - I)/P for the fused MSE loss);
 //  2. the tile's distinct sites get slots in a shared hash table (the paper's
 //     multiplicative hash, linear probing), one probe per group of lanes that
 //     list the same id at the same rank; each warp ORs its lanes into its own
