@@ -67,3 +67,23 @@ def test_reference_arm_line(tmp_path):
     assert d["impl"] == "reference" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_ncu_counters_only_for_the_sources_they_were_taken_on(monkeypatch):
+    """The roofline's `traffic` comes from a stored ncu capture; it is
+    reported only while the kernel's sources hash to the capture's value,
+    and dropped (null) as soon as any of them changes."""
+    import hashlib
+    sys.path.insert(0, ROOT)
+    import bench
+    entry = bench.NCU_COUNTERS["k_step_tile"]
+    h = hashlib.sha256()
+    for f in entry["sources"]:
+        with open(os.path.join(ROOT, "paper_2604_21984_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    current = dict(entry, sha=h.hexdigest()[:16])
+    monkeypatch.setitem(bench.NCU_COUNTERS, "k_step_tile", current)
+    assert bench.ncu_counters("k_step_tile") == current
+    monkeypatch.setitem(bench.NCU_COUNTERS, "k_step_tile", dict(entry, sha="0" * 16))
+    assert bench.ncu_counters("k_step_tile") is None
+    assert bench.ncu_counters("no_such_kernel") is None
