@@ -140,6 +140,22 @@ int sad_update_topk(const float* prep, int32_t capacity, int32_t H, int32_t W, i
                     int32_t n_inject, uint64_t seed, void* stream);
 
 /*
+ * sad_exact_topk -- the exact top-K of sampled pixels by brute force over
+ * every site: the set that the propagation of Sec. 4.3 approximates, for
+ * measuring the recall and exact-match fraction of a propagated map (Sec. 6.5,
+ * Table "Top-K propagation convergence").  Each pixel scores all `capacity`
+ * sites with the fp32 score of sad_update_topk (same operation order, inactive
+ * and NaN-scored sites dropped) and keeps the K best by (logit descending, id
+ * ascending), so a propagated list that has converged equals it bit for bit.
+ * pixels: int64[n] pixel indices (row * W + col, each in [0, H*W)), 8-byte
+ * aligned; ids_out: uint32[n][K] (sentinel 0xffffffff past the active count).
+ * One 256-thread block per pixel: O(n * capacity) work, a measurement tool,
+ * not a hot-path call.  Requires 0 <= n < 2^31.
+ */
+int sad_exact_topk(const float* prep, int32_t capacity, int32_t H, int32_t W, int32_t K,
+                   const int64_t* pixels, int64_t n, uint32_t* ids_out, void* stream);
+
+/*
  * Half2 candidate sites (App. "Data Layout and Packing", Packed candidate
  * sites): a 16-byte per-site record that candidate passes read instead of
  * the prepared table's two 16-byte scoring planes.
@@ -269,16 +285,22 @@ int sad_train_grads(const float* params, const float* prep, int32_t capacity, in
  * for callers that cannot allocate device memory for a workspace (they only
  * hold device pointers handed to them, or run where an allocation is not
  * allowed).  The paper has no counterpart; it is a deployment convenience.
- * Scratch is one 64 MiB buffer inside the library (allocated on every device
- * that loads the library, kept until exit).  Limits: H*W <= 4194304 and
- * capacity <= 262144, else SAD_EINVAL; within them about 0.9 million
- * per-tile records fit.  The first call on a device looks up the buffer's
- * device address (make it before any stream capture).  All calls share the
- * buffer: calls that overlap on the GPU race and must be serialised by the
- * caller.  status_out (device int32, may be NULL) receives SAD_OK, or
- * SAD_EWORKSPACE if the records did not fit (gradients then incomplete).
+ * Scratch is one SAD_NOALLOC_SCRATCH_BYTES buffer inside the library
+ * (allocated on every device that loads the library, kept until exit).
+ * Limits: H*W <= 4194304 and capacity <= 262144, else SAD_EINVAL; within them
+ * about 0.9 million per-tile records fit (a 2048 x 2048 render of 262144
+ * random sites at K = 16 makes about 0.83 million; spatially incoherent lists
+ * make many more and overflow).  The first call on a device looks up the
+ * buffer's device address and keeps it for the life of the process (make that
+ * call before any stream capture; a device reset while the library is loaded
+ * is not supported).  All calls share the buffer: calls that overlap on the
+ * GPU race and must be serialised by the caller.  status_out (device int32)
+ * receives SAD_OK, or SAD_EWORKSPACE if the records did not fit (gradients
+ * then incomplete).  status_out may be NULL, but then an overflow is not
+ * reported anywhere: pass it unless the problem is known to fit.
  * Allocates nothing.
  */
+#define SAD_NOALLOC_SCRATCH_BYTES (64ull << 20)
 int sad_render_backward_noalloc(const float* params, const float* prep, int32_t capacity,
                                 int32_t H, int32_t W, int32_t K, const uint32_t* map,
                                 const float* grad_rgb, float* grads, int32_t* status_out,
@@ -368,6 +390,19 @@ int sad_densify_prune(float* params, float* m, float* v, int32_t capacity, int32
                       int32_t K, const float* stats, const float* target, uint32_t* map,
                       const sad_dp_params* dp, int32_t* n_active_out, void* workspace,
                       size_t workspace_bytes, void* stream);
+
+/*
+ * sad_densify_prune_async -- the same event entirely on the stream: nothing
+ * synchronises and no host memory is touched, so a training loop with
+ * budget events runs without a host round trip and the call can be captured
+ * in a CUDA graph (Sec. 5: the whole iteration stays on the GPU).
+ * n_active_dev (DEVICE int32, 4-byte aligned) receives the active count
+ * after the event, in stream order.  Other arguments as sad_densify_prune.
+ */
+int sad_densify_prune_async(float* params, float* m, float* v, int32_t capacity, int32_t H,
+                            int32_t W, int32_t K, const float* stats, const float* target,
+                            uint32_t* map, const sad_dp_params* dp, int32_t* n_active_dev,
+                            void* workspace, size_t workspace_bytes, void* stream);
 
 /* Adam hyper-parameters (Sec. 6.1; betas/eps after Kingma & Ba 2015). */
 typedef struct sad_adam_hparams {

@@ -7,6 +7,14 @@ inputs, its output and two floats per pixel (the max logit and 1/Z of the
 softmax); the backward recomputes every (pixel, site) weight from its logit
 inside the CUDA adjoint instead of storing the N x K weights.  All work runs
 in libsad.so through the C-ABI binding.
+
+The adjoint writes one partial record per (site, tile) into a workspace sized
+for H*W*K/8 records, ten times what a propagated top-K map of random sites
+needs; a spatially incoherent map can need more.  ``CHECK_OVERFLOW`` (on by
+default) reads the workspace's record count after every backward (a stream
+synchronisation): on an overflow the workspace grows to the count reported
+and the backward runs again, so the gradients are always complete.  A caller
+that knows its maps fit may turn the check off.
 """
 from __future__ import annotations
 
@@ -15,18 +23,21 @@ import torch
 from . import capi
 
 
+CHECK_OVERFLOW = True
+
+
 class _Workspaces:
     """Per-(device, problem) cache of the backward workspace."""
 
     def __init__(self):
         self._ws = {}
 
-    def get(self, device, H, W, K, cap):
+    def get(self, device, H, W, K, cap, min_records=0):
         key = (str(device), H, W, K, cap)
-        ws = self._ws.get(key)
-        if ws is None:
-            ws = capi.backward_workspace(H, W, K, cap, device=device)
-            self._ws = {key: ws}          # keep only the latest problem
+        ws, n = self._ws.get(key, (None, 0))
+        if ws is None or n < min_records:
+            ws = capi.backward_workspace(H, W, K, cap, max_records=min_records, device=device)
+            self._ws = {key: (ws, min_records)}   # keep only the latest problem
         return ws
 
 
@@ -56,9 +67,19 @@ class SADRender(torch.autograd.Function):
         H, W, K = ctx.H, ctx.W, ctx.K
         cap = params.shape[1]
         grads = torch.empty_like(params)
+        g = grad_rgb.contiguous().to(torch.float32)
         ws = _WS.get(params.device, H, W, K, cap)
-        capi.sad_render_backward_saved(params, prep, H, W, K, topk_map,
-                                       grad_rgb.contiguous().to(torch.float32), rgb, fwd, grads, ws)
+        capi.sad_render_backward_saved(params, prep, H, W, K, topk_map, g, rgb, fwd, grads, ws)
+        if CHECK_OVERFLOW:
+            st, used = capi.sad_workspace_status(ws)
+            if st == capi.SAD_EWORKSPACE:
+                # the record count is a property of the map alone: a workspace
+                # of that many records holds them all on the second run
+                ws = _WS.get(params.device, H, W, K, cap, min_records=used)
+                capi.sad_render_backward_saved(params, prep, H, W, K, topk_map, g, rgb, fwd, grads, ws)
+                st, used = capi.sad_workspace_status(ws)
+            if st != 0:
+                raise capi.SadError(st, f"render backward: {used} partial records did not fit")
         return grads, None, None, None
 
 

@@ -26,6 +26,8 @@ N_PARAMS = 11
 INVALID = 0xFFFFFFFF
 STEP_KEEP_LISTS = 1   # batch-image flag (include/sad.h SAD_STEP_KEEP_LISTS)
 PLANE_LOGTAU = 2      # plane of log tau in the site parameter and gradient arrays
+SAD_EWORKSPACE = 3    # status: per-tile records did not fit the workspace
+NOALLOC_SCRATCH_BYTES = 64 << 20   # include/sad.h SAD_NOALLOC_SCRATCH_BYTES: held on every device
 
 
 class SadError(RuntimeError):
@@ -81,6 +83,9 @@ _SIGS = {
                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int32,
                                        ctypes.c_uint64, ctypes.c_void_p]),
+    "sad_exact_topk": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                      ctypes.c_void_p]),
     "sad_pack_candidates": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                            ctypes.c_void_p]),
     "sad_update_topk_h2": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
@@ -147,6 +152,11 @@ _SIGS = {
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(DpParams),
                                          ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p, ctypes.c_size_t,
                                          ctypes.c_void_p]),
+    "sad_densify_prune_async": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.POINTER(DpParams), ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_size_t, ctypes.c_void_p]),
     "sad_step_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                                    ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
                                                    ctypes.c_int64]),
@@ -295,6 +305,19 @@ def sad_update_topk(prep, cap, H, W, K, map_in, map_out, step_code, n_inject, se
     return map_out
 
 
+def sad_exact_topk(prep, cap, H, W, K, pixels, ids_out=None, stream=None):
+    """Exact top-K ids of the pixels (int64[n] device indices) by brute force
+    over every site: uint32 values in an int32[n, K] device tensor."""
+    n = pixels.numel()
+    if ids_out is None:
+        ids_out = torch.empty((n, K), dtype=torch.int32, device=pixels.device)
+    _check(lib().sad_exact_topk(_ptr(prep, torch.float32, "prep"), cap, H, W, K,
+                                _ptr(pixels, torch.int64, "pixels", n), n,
+                                _ptr(ids_out, torch.int32, "ids_out", n * K), _stream(stream)),
+           "sad_exact_topk")
+    return ids_out
+
+
 def sad_pack_candidates(prep, cap, cand, stream=None):
     """cand: int32 tensor of cap*4 words (the half2 candidate records)."""
     _check(lib().sad_pack_candidates(_ptr(prep, torch.float32, "prep"), cap,
@@ -373,8 +396,8 @@ def sad_render_backward_noalloc(params, prep, H, W, K, map_in, grad_rgb, grads, 
     """sad_render_backward for callers that cannot allocate a workspace: the
     library's own fixed scratch buffer is used instead (see include/sad.h for
     its limits; concurrent calls on different streams race on it).  `status`
-    is an optional device int32[1] that receives 0, or 3 if the per-tile
-    records did not fit."""
+    is an optional device int32[1] that receives 0, or SAD_EWORKSPACE if the
+    per-tile records did not fit; without it an overflow goes unreported."""
     cap = params.shape[1]
     _check(lib().sad_render_backward_noalloc(
         _ptr(params, torch.float32, "params", N_PARAMS * cap), _ptr(prep, torch.float32, "prep"),
@@ -464,6 +487,23 @@ def sad_densify_prune(params, m, v, H, W, K, stats, target, map_inout, dp, ws, s
                                    _ptr(ws, torch.uint8, "workspace"), ws.numel(), _stream(stream)),
            "sad_densify_prune")
     return int(n.value)
+
+
+def sad_densify_prune_async(params, m, v, H, W, K, stats, target, map_inout, dp, n_active, ws,
+                            stream=None):
+    """The same event entirely in stream order: no synchronisation; the
+    active count afterwards goes to `n_active` (device int32[1])."""
+    cap = params.shape[1]
+    _check(lib().sad_densify_prune_async(_ptr(params, torch.float32, "params", N_PARAMS * cap),
+                                         _ptr(m, torch.float32, "m", N_PARAMS * cap),
+                                         _ptr(v, torch.float32, "v", N_PARAMS * cap), cap, H, W, K,
+                                         _ptr(stats, torch.float32, "stats", 8 * cap),
+                                         _ptr(target, torch.float32, "target", H * W * 3),
+                                         _ptr(map_inout, torch.int32, "map", H * W * K),
+                                         ctypes.byref(dp), _ptr(n_active, torch.int32, "n_active", 1),
+                                         _ptr(ws, torch.uint8, "workspace"), ws.numel(), _stream(stream)),
+           "sad_densify_prune_async")
+    return n_active
 
 
 def adam_hparams(lr=None, beta1=0.9, beta2=0.999, eps=1e-8, log_tau_range=(2.0, 20.0),

@@ -398,14 +398,16 @@ int sad_workspace_status(const void* workspace, int64_t* records_used, void* str
 // The buffer's name is only a host-side stand-in in host code, so its device
 // address is looked up with cudaGetSymbolAddress, once per device, with that
 // device current; the first call on each device does this lookup (make that
-// first call before any stream capture).  All calls share the one buffer and
+// first call before any stream capture).  The address is kept for the life
+// of the process, so a device reset while the library is loaded is not
+// supported.  All calls share the one buffer and
 // it keeps the previous call's contents: every call clears the parts that
 // must start at zero, and calls whose executions overlap on the GPU (two
 // streams, or two threads) race on it and must be serialised by the caller.
 // ---------------------------------------------------------------------------
 namespace sad {
 
-constexpr size_t kStaticScratchBytes = 64ull << 20;       // 64 MiB
+constexpr size_t kStaticScratchBytes = SAD_NOALLOC_SCRATCH_BYTES;  // 64 MiB
 constexpr int64_t kStaticMaxPixels = 4194304;             // e.g. 2048 x 2048
 constexpr int32_t kStaticMaxCapacity = 262144;
 constexpr int kMaxDevices = 64;

@@ -277,12 +277,15 @@ size_t sad_densify_workspace_bytes(int32_t capacity, int32_t H, int32_t W) {
   return dp_layout(capacity, H, W).total;
 }
 
-int sad_densify_prune(float* params, float* m, float* v, int32_t capacity, int32_t H, int32_t W,
-                      int32_t K, const float* stats, const float* target, uint32_t* map,
-                      const sad_dp_params* dp, int32_t* n_active_out, void* workspace,
-                      size_t workspace_bytes, void* stream) {
+// The whole densify/prune event on the stream; the active count after it is
+// left in the workspace's state page (*after_out points there) and, if
+// n_active_dev is given, copied to that device int32.  Nothing synchronises.
+static int dp_run(float* params, float* m, float* v, int32_t capacity, int32_t H, int32_t W,
+                  int32_t K, const float* stats, const float* target, uint32_t* map,
+                  const sad_dp_params* dp, int32_t* n_active_dev, void* workspace,
+                  size_t workspace_bytes, void* stream, const uint32_t** after_out) {
   if (int e = check_problem(capacity, H, W, K, map != nullptr)) return e;
-  if (!dp || !n_active_out) return einval("sad_densify_prune: null parameters or output");
+  if (!dp) return einval("sad_densify_prune: null parameters");
   if (capacity > 0 && (!params || !m || !v || !stats || !target))
     return einval("sad_densify_prune: null pointer");
   if (!(dp->densify_pct >= 0.0 && dp->densify_pct <= 1.0 && dp->prune_pct >= 0.0 &&
@@ -295,11 +298,18 @@ int sad_densify_prune(float* params, float* m, float* v, int32_t capacity, int32
     set_error("sad_densify_prune: workspace has %zu bytes, needs %zu", workspace_bytes, L.total);
     return SAD_EWORKSPACE;
   }
+  cudaStream_t st = as_stream(stream);
   if (capacity == 0) {
-    *n_active_out = 0;
+    *after_out = nullptr;
+    if (n_active_dev) {
+      const cudaError_t e = cudaMemsetAsync(n_active_dev, 0, sizeof(int32_t), st);
+      if (e != cudaSuccess) {
+        set_error("sad_densify_prune: %s", cudaGetErrorString(e));
+        return SAD_ECUDA;
+      }
+    }
     return SAD_OK;
   }
-  cudaStream_t st = as_stream(stream);
   char* base = static_cast<char*>(workspace);
   DpState* S = reinterpret_cast<DpState*>(base + L.state);
   uint32_t* keys = reinterpret_cast<uint32_t*>(base + L.keys);
@@ -364,8 +374,33 @@ int sad_densify_prune(float* params, float* m, float* v, int32_t capacity, int32
   if (map) { TraceScope tr_(st, "k_dp_seed_map"); k_dp_seed_map<<<gp, 256, 0, st>>>(claim, P, K, map); }
   { TraceScope tr_(st, "k_dp_count_after"); k_dp_count_after<<<gs, 256, 0, st>>>(params, capacity, S); }
   if (int r = check_launch("sad_densify_prune")) return r;
+  *after_out = &S->n_active_after;
+  if (n_active_dev) {
+    e = cudaMemcpyAsync(n_active_dev, &S->n_active_after, sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) {
+      set_error("sad_densify_prune: %s", cudaGetErrorString(e));
+      return SAD_ECUDA;
+    }
+  }
+  return SAD_OK;
+}
+
+int sad_densify_prune(float* params, float* m, float* v, int32_t capacity, int32_t H, int32_t W,
+                      int32_t K, const float* stats, const float* target, uint32_t* map,
+                      const sad_dp_params* dp, int32_t* n_active_out, void* workspace,
+                      size_t workspace_bytes, void* stream) {
+  if (!n_active_out) return einval("sad_densify_prune: null output");
+  const uint32_t* after_dev = nullptr;
+  if (int r = dp_run(params, m, v, capacity, H, W, K, stats, target, map, dp, nullptr, workspace,
+                     workspace_bytes, stream, &after_dev))
+    return r;
+  if (!after_dev) {
+    *n_active_out = 0;
+    return SAD_OK;
+  }
+  cudaStream_t st = as_stream(stream);
   uint32_t after = 0;
-  e = cudaMemcpyAsync(&after, &S->n_active_after, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaMemcpyAsync(&after, after_dev, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     set_error("sad_densify_prune: %s", cudaGetErrorString(e));
@@ -373,6 +408,18 @@ int sad_densify_prune(float* params, float* m, float* v, int32_t capacity, int32
   }
   *n_active_out = static_cast<int32_t>(after);
   return SAD_OK;
+}
+
+int sad_densify_prune_async(float* params, float* m, float* v, int32_t capacity, int32_t H, int32_t W,
+                            int32_t K, const float* stats, const float* target, uint32_t* map,
+                            const sad_dp_params* dp, int32_t* n_active_dev, void* workspace,
+                            size_t workspace_bytes, void* stream) {
+  if (!n_active_dev) return einval("sad_densify_prune_async: null output");
+  if ((reinterpret_cast<uintptr_t>(n_active_dev) & 3u) != 0)
+    return einval("sad_densify_prune_async: misaligned output");
+  const uint32_t* after_dev = nullptr;
+  return dp_run(params, m, v, capacity, H, W, K, stats, target, map, dp, n_active_dev, workspace,
+                workspace_bytes, stream, &after_dev);
 }
 
 }  // extern "C"

@@ -181,6 +181,62 @@ static int run_update(const void* table, bool h2, int32_t capacity, int32_t H, i
   return check_launch(name);
 }
 
+// ---------------------------------------------------------------------------
+// exact top-K of sampled pixels by brute force over every site: the set the
+// propagation approximates (Sec. 4.3), scored and ordered exactly as a pass
+// does (fp32 score of fixed operation order, keys ordered by logit then id)
+// ---------------------------------------------------------------------------
+constexpr int kExactThreads = 256;
+
+template <int K>
+__global__ void __launch_bounds__(kExactThreads) k_exact_topk(const float4* __restrict__ geo,
+                                                              const float4* __restrict__ met, int cap,
+                                                              int W, const int64_t* __restrict__ pix,
+                                                              uint32_t* __restrict__ out) {
+  __shared__ uint64_t s_best[kExactThreads / 32];
+  __shared__ uint64_t s_win;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int64_t q = pix[blockIdx.x];
+  const float px = static_cast<float>(q % W) + 0.5f, py = static_cast<float>(q / W) + 0.5f;
+  uint64_t v[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = 0ull;
+  for (int i = t; i < cap; i += kExactThreads) {
+    const float4 mt = ldg(&met[i]);
+    if (mt.w == 0.f) continue;
+    const float l = score_exact(px, py, ldg(&geo[i]), mt);
+    if (l != l) continue;  // a NaN logit never enters
+    const uint64_t c = make_key(l, static_cast<uint32_t>(i));
+    if (c > v[K - 1]) list_insert<K>(v, c);
+  }
+  // K rounds: the best head over the block wins and its thread pops it (ids
+  // are distinct, so exactly one thread holds the winning key)
+  for (int r = 0; r < K; ++r) {
+    uint64_t h = v[0];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint64_t y = __shfl_xor_sync(0xffffffffu, h, o);
+      h = y > h ? y : h;
+    }
+    if (lane == 0) s_best[warp] = h;
+    __syncthreads();
+    if (t == 0) {
+      uint64_t b = 0ull;
+      for (int w = 0; w < kExactThreads / 32; ++w) b = s_best[w] > b ? s_best[w] : b;
+      s_win = b;
+      out[static_cast<size_t>(blockIdx.x) * K + r] = b ? key_id(b) : kInvalid;
+    }
+    __syncthreads();
+    const uint64_t win = s_win;
+    if (win != 0ull && v[0] == win) {
+#pragma unroll
+      for (int k = 0; k < K - 1; ++k) v[k] = v[k + 1];
+      v[K - 1] = 0ull;
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace sad
 
 using namespace sad;
@@ -330,6 +386,27 @@ int sad_grid_expand(const uint32_t* map_grid, int32_t H, int32_t W, int32_t s_gr
                                          reinterpret_cast<uint4*>(map_pixels));
   }
   return check_launch("k_grid_expand");
+}
+
+int sad_exact_topk(const float* prep, int32_t capacity, int32_t H, int32_t W, int32_t K,
+                   const int64_t* pixels, int64_t n, uint32_t* ids_out, void* stream) {
+  if (int st = check_problem(capacity, H, W, K, true)) return st;
+  if (n < 0 || n > 0x7fffffff) return einval("sad_exact_topk: n must be in [0, 2^31)");
+  if (n == 0) return SAD_OK;
+  if (!pixels || !ids_out || (!prep && capacity > 0)) return einval("sad_exact_topk: null pointer");
+  if (!aligned16(prep) || (reinterpret_cast<uintptr_t>(pixels) & 7u))
+    return einval("sad_exact_topk: misaligned pointer");
+  const float4* p4 = reinterpret_cast<const float4*>(prep);
+  const float4 *geo = p4, *met = p4 + capacity;
+  cudaStream_t st = as_stream(stream);
+  const unsigned grid = static_cast<unsigned>(n);
+  TraceScope tr_(st, "k_exact_topk");
+  switch (K) {
+    case 4: k_exact_topk<4><<<grid, kExactThreads, 0, st>>>(geo, met, capacity, W, pixels, ids_out); break;
+    case 8: k_exact_topk<8><<<grid, kExactThreads, 0, st>>>(geo, met, capacity, W, pixels, ids_out); break;
+    default: k_exact_topk<16><<<grid, kExactThreads, 0, st>>>(geo, met, capacity, W, pixels, ids_out); break;
+  }
+  return check_launch("k_exact_topk");
 }
 
 }  // extern "C"

@@ -49,6 +49,7 @@ class EncodeConfig:
     warm_half2_jump: int = 0   # > 0: warm-up passes with at least this jump use the half2 table
     keep_grads: bool = False   # fused: also write the step's gradients to Encoder.grads
     tile_w: int = 16           # fused: adjoint tiles 16x16 (16) or 32x8 (32)
+    graph: bool = False        # fused: replay the iteration and the budget events as CUDA graphs
     extra: dict = field(default_factory=dict)
 
 
@@ -129,8 +130,10 @@ class Encoder:
         self.target = target.contiguous()
         self.H, self.W = int(target.shape[0]), int(target.shape[1])
         self.dev = target.device
-        self.stream = stream
         c = self.cfg
+        if c.graph and stream is None:
+            stream = torch.cuda.Stream(device=self.dev)   # graphs are captured on a side stream
+        self.stream = stream
         H, W, K = self.H, self.W, c.K
         self.n0 = min(c.n_sites, H * W)
         self.cap = max(self.n0, int(math.ceil(c.capacity_factor * self.n0)))
@@ -164,7 +167,11 @@ class Encoder:
                                  prune_pct=min(0.95, c.prune_pct * self.pct_scale), alpha=c.alpha)
         self.t_pass = 0
         self.it = 0
-        self.n_active = self.n0
+        self._n_active = self.n0
+        self._n_dev = torch.full((1,), self.n0, dtype=torch.int32, device=self.dev)
+        self._n_dirty = False
+        self._g_step = None
+        self._g_dense = {}
         self.history = []
         if c.tau_diffusion > 0:
             c.fused = False   # the smoothing sits between the gradient and Adam
@@ -285,33 +292,87 @@ class Encoder:
         capi.sad_adam_step(self.params, self.grads, self.m, self.v, self.H, self.W, self.it, self.hp,
                            self.stream)
 
-    def densify(self):
+    @property
+    def n_active(self) -> int:
+        """Active sites now (reads the device count of the last budget event)."""
+        if self._n_dirty:
+            if self.stream is not None:
+                self.stream.synchronize()
+            self._n_active = int(self._n_dev.item())
+            self._n_dirty = False
+        return self._n_active
+
+    def _densify_calls(self, cur_map):
         c = self.cfg
         capi.sad_prepare_sites(self.params, self.H, self.W, self.prep, self.stream)
-        capi.sad_site_stats(self.prep, self.cap, self.H, self.W, c.K, self.maps[0], self.target,
+        capi.sad_site_stats(self.prep, self.cap, self.H, self.W, c.K, cur_map, self.target,
                             self.stats, self.ws, self.stream)
         # on a candidate grid the children are found by the next passes (the
-        # per-pixel map is rebuilt from the grid), so they are not seeded
-        self.n_active = capi.sad_densify_prune(self.params, self.m, self.v, self.H, self.W, c.K,
-                                               self.stats, self.target,
-                                               self.maps[0] if c.s_grid == 1 else None, self.dp,
-                                               self.ws_dp, self.stream)
+        # per-pixel map is rebuilt from the grid), so they are not seeded;
+        # the event runs in stream order (no host round trip)
+        capi.sad_densify_prune_async(self.params, self.m, self.v, self.H, self.W, c.K, self.stats,
+                                     self.target, cur_map if c.s_grid == 1 else None, self.dp,
+                                     self._n_dev, self.ws_dp, self.stream)
         if c.fused:   # the step expects the prepared table of the current sites
             capi.sad_prepare_sites(self.params, self.H, self.W, self.prep, self.stream)
-        return self.n_active
+
+    def densify(self):
+        """One densify-then-prune event (Sec. 4.5), enqueued on the stream.
+        With cfg.graph (fused form) the event is replayed from a CUDA graph of
+        these calls, one graph per map buffer, captured at its second use."""
+        c = self.cfg
+        self._n_dirty = True
+        if not (c.graph and c.fused):
+            self._densify_calls(self.maps[0])
+            return
+        key = self._par
+        g = self._g_dense.get(key)
+        if g is None and self._g_dense.get("warm"):
+            g = self._capture(lambda: self._densify_calls(self.bufs[key]))
+            self._g_dense[key] = g
+        if g is None:
+            self._densify_calls(self.bufs[key])   # the first event also loads its kernels
+            self._g_dense["warm"] = True
+        else:
+            g.replay()
+
+    def _capture(self, calls):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(self.stream):
+            g.capture_begin(capture_error_mode="thread_local")
+            calls()
+            g.capture_end()
+        return g
+
+    def _graph_step(self):
+        """A fused iteration replayed from a CUDA graph (captured after one
+        eager iteration): the per-image state row on the device carries the
+        Adam step, pass index and map parity, so every replay is the next
+        iteration."""
+        c = self.cfg
+        if c.cand_every != 1 or c.cand_passes != 1 or self.it == 0:
+            return self.step()
+        if self._g_step is None:
+            self._g_step = self._capture(lambda: self._call(self.stream))
+        self.it += 1
+        self._g_step.replay()
+        self._par ^= 1
+        self.t_pass += 1
+        self.maps = [self.bufs[self._par], self.bufs[1 - self._par]]
 
     def run(self, iters: int | None = None, log_every: int = 0):
         c = self.cfg
         n = c.iters if iters is None else iters
         if self.t_pass == 0:
             self.init()
+        step = self._graph_step if (c.graph and c.fused) else self.step
         for _ in range(n):
-            self.step()
+            step()
             if (c.densify_every > 0 and c.densify_start <= self.it <= c.densify_end
                     and self.it % c.densify_every == 0):
                 self.densify()
             if log_every and self.it % log_every == 0:
-                self.history.append((self.it, psnr_from_loss(float(self.loss.item())), self.n_active))
+                self.history.append((self.it, psnr_from_loss(self._loss_value()), self.n_active))
         return self
 
     def render(self):
@@ -320,10 +381,15 @@ class Encoder:
         capi.sad_render(self.prep, self.cap, self.H, self.W, self.cfg.K, self.maps[0], rgb, self.stream)
         return rgb
 
+    def _loss_value(self) -> float:
+        if self.stream is not None:
+            self.stream.synchronize()
+        return float(self.loss.item())
+
     def psnr(self) -> float:
         """PSNR of the current sites over the current field (the loss comes
         from the fused training kernel; gradients are discarded)."""
         capi.sad_prepare_sites(self.params, self.H, self.W, self.prep, self.stream)
         capi.sad_train_grads(self.params, self.prep, self.H, self.W, self.cfg.K, self.maps[0],
                              self.target, self.grads, self.loss, self.ws, stream=self.stream)
-        return psnr_from_loss(float(self.loss.item()))
+        return psnr_from_loss(self._loss_value())

@@ -258,8 +258,9 @@ def deactivate_random(params: np.ndarray, frac: float, seed: int) -> np.ndarray:
 
 def knn_map(params: np.ndarray, H: int, W: int, K: int, seed: int,
             truncate_frac: float = 0.0, shuffle: bool = False,
-            include_inactive_frac: float = 0.0) -> np.ndarray:
-    """Spatially coherent random top-K index map (uint32[P, K]).
+            include_inactive_frac: float = 0.0, pixels=None) -> np.ndarray:
+    """Spatially coherent random top-K index map (uint32[P, K]; with
+    ``pixels``, only those pixel indices: uint32[len(pixels), K]).
 
     Each pixel lists the K sites whose positions are nearest to its centre in
     plain Euclidean distance (scipy cKDTree; this is not the method's score).
@@ -271,13 +272,14 @@ def knn_map(params: np.ndarray, H: int, W: int, K: int, seed: int,
     from scipy.spatial import cKDTree
 
     g = rng(seed)
-    P = H * W
+    pix = np.arange(H * W) if pixels is None else np.asarray(pixels, dtype=np.int64)
+    P = len(pix)
     active = np.nonzero(params[PX] >= 0)[0]
     ids = np.full((P, K), INVALID, dtype=np.uint32)
     kk = min(K, len(active))
     if kk > 0:
         tree = cKDTree(np.stack([params[PX, active], params[PY, active]], 1).astype(np.float64))
-        yy, xx = np.divmod(np.arange(P), W)
+        yy, xx = np.divmod(pix, W)
         q = np.stack([xx + 0.5, yy + 0.5], 1)
         _, nn = tree.query(q, k=kk, workers=-1)
         nn = nn.reshape(P, kk)

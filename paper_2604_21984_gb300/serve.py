@@ -69,6 +69,7 @@ class Request:
     # filled in by the server
     done_event: torch.cuda.Event | None = None
     latency: float | None = None
+    cancelled: bool = False
     result: object = None          # encode: float32[11, n] params; decode: float32[n, 3]
     loss: torch.Tensor | None = None
 
@@ -194,6 +195,8 @@ class _Lane:
             ev.record(st)
             done = []
             for b, a in enumerate(self.members):
+                if a.get("cancelled"):
+                    continue
                 a["left"] -= T
                 a["last_lane"], a["last_event"] = self, ev
                 if a["left"] <= 0:
@@ -288,8 +291,12 @@ class Server:
         return torch.zeros(n, dtype=torch.uint8, device=self.dev)
 
     def footprint_bytes(self):
+        """Device bytes held for serving: the pools, the two lane workspaces and
+        the library's fixed scratch buffer of the workspace-free backward
+        (every device that loads the library holds it)."""
         c = self.cfg
-        return pool_bytes(c.site_pool, c.pixel_pool, c.K) + self.fast.ws.numel() + self.bulk.ws.numel()
+        return (pool_bytes(c.site_pool, c.pixel_pool, c.K) + self.fast.ws.numel() + self.bulk.ws.numel()
+                + capi.NOALLOC_SCRATCH_BYTES)
 
     def add_resident(self, params: torch.Tensor, H: int, W: int, passes: int = 16, J: int = 2,
                      seed: int = 11):
@@ -346,6 +353,28 @@ class Server:
             self.decodes.append(req)
         else:
             raise ValueError(req.kind)
+
+    def cancel(self, req: Request) -> bool:
+        """Withdraw a request that has not completed.  A waiting encode or
+        decode is dropped; an admitted encode leaves the pools: its slot and
+        pixel ranges and its state row are handed back and reused only after
+        the device work that last touched them (its lane drops it at the next
+        re-plan).  Returns False if the request is not pending here."""
+        if req in self.waiting:
+            self.waiting.remove(req)
+        elif req in self.decodes:
+            self.decodes.remove(req)
+        else:
+            a = next((a for a in self.active if a["req"] is req), None)
+            if a is None:
+                return False
+            self.active.remove(a)
+            a["cancelled"] = True
+            self._retire(a, a["last_event"])
+        req.cancelled = True
+        req.done_event = None
+        req.result = None
+        return True
 
     def _retire(self, a, ev):
         e = a["entry"]
@@ -618,14 +647,15 @@ def run_stream(server, requests, max_inflight_ticks: int = 2, iters_per_tick: in
     torch.cuda.synchronize(server.dev)
     wall = time.perf_counter() - t0
     for r in requests:
-        r.latency = start.elapsed_time(r.done_event) / 1e3 - r.arrival
+        if not r.cancelled:
+            r.latency = start.elapsed_time(r.done_event) / 1e3 - r.arrival
     return wall
 
 
 def latency_summary(requests):
     out = {}
     for kind in ("encode", "decode"):
-        lat = sorted(r.latency for r in requests if r.kind == kind)
+        lat = sorted(r.latency for r in requests if r.kind == kind and not r.cancelled)
         if not lat:
             continue
         out[kind] = dict(n=len(lat), p50_s=float(np.percentile(lat, 50)),

@@ -65,8 +65,10 @@ def test_reference_arm_line(tmp_path):
     assert r.returncode == 0, r.stderr
     d = json.loads(r.stdout.strip().splitlines()[-1])
     assert d["impl"] == "reference" and d["value"] > 0
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == (os.cpu_count() or 1) and cb["cpu_model"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+    assert d["config"]["H"] == d["config"]["W"] == 2048 and d["config"]["K"] == 16
 
 
 def test_ncu_counters_only_for_the_sources_they_were_taken_on(monkeypatch):

@@ -75,3 +75,26 @@ def test_product_path_has_no_oracle_import():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle|sad_oracle|oracle/", txt, re.M), f
+
+
+def test_batch_above_the_image_limit_is_rejected(L):
+    """A batch descriptor holds at most 64 images (the per-image fixed-point
+    scales and the step's image table are sized for that): 65 images are
+    refused on the host by the workspace query and by every batched call,
+    before any launch."""
+    from paper_2604_21984_gb300 import capi
+    ims = [dict(H=16, W=16, site_offset=4 * i, capacity=4, pixel_offset=256 * i, seed=i, state_index=i)
+           for i in range(65)]
+    tab = capi.batch_table(ims)
+    tp = ctypes.cast(tab, ctypes.c_void_p)
+    assert L.sad_step_workspace_bytes(tp, 65, 16, 16, 260, 65 * 256, 0) == 0
+    assert L.sad_step_workspace_bytes(tp, 64, 16, 16, 260, 65 * 256, 0) > 0
+    p = ctypes.c_void_p(256)          # never dereferenced: the count check fails first
+    st = L.sad_train_step(tp, 65, 16, 4, 16, p, p, p, p, 260, p, p, 65 * 256, p, p, None, p, 128,
+                          None, p, 1 << 20, None)
+    assert st == 1 and b"B <= 64" in L.sad_last_error()
+    st = L.sad_batch_update(tp, 65, 16, 4, p, 260, p, p, 65 * 256, p, 128, None)
+    assert st == 1 and b"B <= 64" in L.sad_last_error()
+    st = L.sad_train_step(tp, 0, 16, 4, 16, p, p, p, p, 260, p, p, 65 * 256, p, p, None, p, 128,
+                          None, p, 1 << 20, None)
+    assert st == 1

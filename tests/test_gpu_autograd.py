@@ -74,3 +74,34 @@ def test_autograd_vs_finite_differences_config3(capi, oracle):
         nrel = np.linalg.norm(got[j] - fds[j]) / max(np.linalg.norm(fds[j]), 1e-300)
         print(f"plane {j:2d}: max err/tol {ratio:.3f}, norm-relative {nrel:.2e}")
         assert ratio <= 1.0 and nrel <= 1e-4, j
+
+
+def test_autograd_overflowing_map_gives_complete_gradients(capi):
+    """A spatially incoherent map needs far more per-tile records than the
+    default workspace holds; the backward must notice, grow the workspace and
+    return the same gradients as a call whose workspace fits everything."""
+    torch = pytest.importorskip("torch")
+    H = W = 128
+    K, n = 16, 20000
+    p = gen.sites_random_spd(H, W, n, seed=31)
+    ids = gen.random_map(H * W, K, n, seed=32, invalid_frac=0.05)
+    g = gen.grad_image(H, W, seed=33)
+    m = capi.map_from_ids(ids)
+    pt = dev(p)
+    prep = capi.empty_prep(n)
+    capi.sad_prepare_sites(pt, H, W, prep)
+    rgb = torch.empty((H, W, 3), dtype=torch.float32, device="cuda")
+    fwd = torch.empty((2, H * W), dtype=torch.float32, device="cuda")
+    capi.sad_render_save(prep, n, H, W, K, m, rgb, fwd)
+    gd = dev(g)
+    small = capi.backward_workspace(H, W, K, n)
+    out = torch.empty((11, n), dtype=torch.float32, device="cuda")
+    capi.sad_render_backward_saved(pt, prep, H, W, K, m, gd, rgb, fwd, out, small)
+    st, used = capi.sad_workspace_status(small)
+    assert st == capi.SAD_EWORKSPACE          # the default size really overflows
+    big = capi.backward_workspace(H, W, K, n, max_records=used)
+    ref = torch.empty_like(out)
+    capi.sad_render_backward_saved(pt, prep, H, W, K, m, gd, rgb, fwd, ref, big)
+    assert capi.sad_workspace_status(big)[0] == 0
+    _, grads = _autograd_grads(capi, p, ids, H, W, g)
+    assert np.array_equal(grads, ref.cpu().numpy().astype(np.float64))

@@ -181,3 +181,30 @@ def test_target_bpp_schedule(capi):
         tgt = budget.target_sites(bpp, H, W)
         print("bpp", bpp, "target", tgt, "scale", round(enc.pct_scale, 3), "active", enc.n_active)
         assert abs(enc.n_active - tgt) <= 0.15 * tgt
+
+
+def test_graph_replayed_encode_with_budget_events_equals_eager(capi):
+    """The encode loop with densify/prune events runs with no host round trip
+    (sad_densify_prune_async) and can be replayed from CUDA graphs: the
+    iteration graph and the budget-event graphs (one per map buffer; events
+    every 75 iterations alternate the buffers) give bit-identical sites,
+    loss and active count to the eager loop."""
+    torch = pytest.importorskip("torch")
+    from paper_2604_21984_gb300.encode import EncodeConfig, Encoder
+    H, W = 96, 128
+    img = dev(gen.image_noise_polygons_lines(H, W, seed=45, n_polygons=8, n_lines=4))
+    out = []
+    for graph in (False, True):
+        cfg = EncodeConfig(n_sites=700, K=16, J=4, iters=400, densify_every=75, densify_start=75,
+                           densify_end=375, seed=9, graph=graph)
+        enc = Encoder(img, cfg)
+        enc.init()
+        enc.run()
+        torch.cuda.synchronize()
+        if graph:
+            assert enc._g_step is not None and {0, 1} <= set(enc._g_dense)   # both buffers replayed
+        out.append((enc.params.clone(), enc.loss.clone(), enc.n_active, enc.it, enc.t_pass))
+    (pa, la, na, ia, ta), (pb, lb, nb, ib, tb) = out
+    assert torch.equal(pa, pb) and torch.equal(la, lb)
+    assert na == nb and na != 700 and ia == ib == 400 and ta == tb
+    assert na == int((pb[0] >= 0).sum().item())

@@ -135,3 +135,74 @@ def test_served_encode_trains_like_the_plain_loop(capi):
     torch.cuda.synchronize()
     assert torch.equal(a.result, b.result)
     assert a.loss.item() == b.loss.item()
+
+
+def test_submit_rejects_what_cannot_be_served(capi):
+    """Admission failures are raised at submit, on the host, before any work
+    is queued: an encode above max_side, an encode that fits max_side but not
+    the pools left beside a resident set, a decode of an unknown resident
+    set, a decode above max_decode_per_tick."""
+    torch = pytest.importorskip("torch")
+    from paper_2604_21984_gb300.serve import Request, Server
+    srv = Server(_small_cfg())
+    with pytest.raises(ValueError, match="max_side"):
+        srv.submit(Request("encode", image=_img(300, 200, 1), iters=5))
+    ok = Request("encode", image=_img(256, 256, 2), iters=5)
+    srv.submit(ok)                                  # fits while the pools are empty
+    assert srv.cancel(ok) and not srv.busy()
+    p = dev(gen.sites_random_spd(400, 500, 12000, seed=3))
+    srv.add_resident(p, 400, 500, passes=4)        # 200000 of the 262144 pool pixels
+    with pytest.raises(ValueError, match="pools left"):
+        srv.submit(Request("encode", image=_img(256, 256, 2), iters=5))
+    xy = torch.zeros((10, 2), dtype=torch.float32)
+    with pytest.raises(ValueError, match="unknown resident"):
+        srv.submit(Request("decode", resident=1, xy=xy))
+    with pytest.raises(ValueError, match="unknown resident"):
+        srv.submit(Request("decode", resident=-1, xy=xy))
+    with pytest.raises(ValueError, match="max_decode_per_tick"):
+        srv.submit(Request("decode", resident=0, xy=torch.zeros(((1 << 16) + 1, 2))))
+    with pytest.raises(ValueError):
+        srv.submit(Request("render"))
+    assert not srv.busy()
+    d = Request("decode", resident=0, xy=xy)
+    srv.submit(d)
+    assert srv.cancel(d) and not srv.busy() and d.cancelled
+
+
+def test_cancel_hands_back_ranges_and_rows(capi):
+    """Withdrawing a waiting and an admitted encode: the others finish with
+    the same sites as when served without them, the cancelled ones never
+    complete, and the allocator's free totals and the free state rows come
+    back to their starting values."""
+    torch = pytest.importorskip("torch")
+    from paper_2604_21984_gb300.serve import Request, Server
+    srv = Server(_small_cfg())
+    free_s, free_p, rows = srv.sites.free_total(), srv.pixels.free_total(), len(srv.free_rows)
+    specs = [((64, 64), 21, 30), ((48, 80), 22, 25), ((56, 40), 23, 20)]
+    reqs = [Request("encode", image=_img(H, W, sd), iters=it, seed=sd) for (H, W), sd, it in specs]
+    for r in reqs:
+        srv.submit(r)
+    srv.train_tick(1)                                # admits all three, one iteration each
+    assert len(srv.active) == 3
+    late = Request("encode", image=_img(32, 32, 24), iters=10, seed=24)
+    srv.submit(late)
+    assert srv.cancel(late) and late not in srv.waiting
+    assert srv.cancel(reqs[1])                       # admitted, with work in flight
+    assert not srv.cancel(reqs[1])                   # already withdrawn
+    while srv.busy():
+        srv.train_tick(4)
+    torch.cuda.synchronize()
+    assert reqs[1].cancelled and reqs[1].result is None and reqs[1].done_event is None
+    assert srv.sites.free_total() == free_s
+    assert srv.pixels.free_total() == free_p
+    assert len(srv.free_rows) == rows
+    # the survivors are unaffected by the withdrawal
+    for k in (0, 2):
+        (H, W), sd, it = specs[k]
+        solo = Server(_small_cfg())
+        r = Request("encode", image=_img(H, W, sd), iters=it, seed=sd)
+        solo.submit(r)
+        while solo.busy():
+            solo.train_tick(4)
+        torch.cuda.synchronize()
+        assert torch.equal(r.result, reqs[k].result), k

@@ -233,3 +233,51 @@ def test_grid_passes_bit_exact(capi, oracle, cell):
         np.testing.assert_array_equal(capi.ids_from_map(d),
                                       oracle.topk_pass_fp32(op, oracle.topk_seed_fp32(op, Hi, Wi, K), Hi, Wi, K,
                                                             oracle.step_code(0, Hi, Wi), J, 17))
+
+
+@pytest.mark.parametrize("K", [4, 8, 16])
+def test_exact_topk_matches_brute_force(capi, oracle, K):
+    """sad_exact_topk (the reference a map's recall is measured against) is
+    the oracle's fp32 score over every active site with the list order of
+    R2, bit for bit; against the fp64 definition (oracle.exact_topk) its sets
+    differ only where two logits are within float32 rounding of each other."""
+    torch = pytest.importorskip("torch")
+    H, W = 90, 70
+    p = gen.sites_random_spd(H, W, 1500, seed=41)
+    p = gen.deactivate_random(p, 0.2, seed=42)
+    cap = p.shape[1]
+    _, prep = prepare(capi, p, H, W)
+    rng = np.random.default_rng(43)
+    pix = np.concatenate([[0, H * W - 1], rng.choice(H * W, 126, replace=False)]).astype(np.int64)
+    got = capi.sad_exact_topk(prep, cap, H, W, K, torch.from_numpy(pix).cuda())
+    got = got.cpu().numpy().view(np.uint32)
+    pf = oracle.prepare_fp32(p, H, W)
+    act = np.nonzero(pf["active"])[0]
+    row, col = np.divmod(pix, W)
+    px = (col.astype(np.float32) + np.float32(0.5))[:, None]
+    py = (row.astype(np.float32) + np.float32(0.5))[:, None]
+    ids = np.broadcast_to(act, (len(pix), len(act)))
+    ell = oracle.score_fp32(pf, ids, px, py)
+    ref = oracle.select_topk(ids, ell.astype(np.float64), ~np.isnan(ell), K)
+    assert np.array_equal(got, ref)
+    ex, exl = oracle.exact_topk(p, H, W, K + 1, pixels=pix)
+    same = [set(a) == set(b[:K]) for a, b in zip(got, ex)]
+    for k in np.nonzero(~np.array(same))[0]:        # only a near-tie at the K-th place may differ
+        gap = abs(exl[k, K - 1] - exl[k, K])
+        assert gap < 1e-5 * max(1.0, abs(exl[k, K - 1])), (k, gap)
+    assert np.mean(same) >= 0.95
+
+
+def test_exact_topk_with_fewer_active_sites_than_K(capi, oracle):
+    torch = pytest.importorskip("torch")
+    H, W, K = 20, 30, 16
+    p = gen.sites_random_spd(H, W, 40, seed=44)
+    p = gen.deactivate_random(p, 0.9, seed=45)
+    n_act = int((p[0] >= 0).sum())
+    assert n_act < K
+    _, prep = prepare(capi, p, H, W)
+    pix = np.arange(0, H * W, 7, dtype=np.int64)
+    got = capi.sad_exact_topk(prep, p.shape[1], H, W, K, torch.from_numpy(pix).cuda()).cpu().numpy().view(np.uint32)
+    ref, _ = oracle.exact_topk(p, H, W, K, pixels=pix)
+    assert np.all(got[:, n_act:] == INV)
+    assert all(set(a[:n_act]) == set(b[:n_act]) for a, b in zip(got, ref))

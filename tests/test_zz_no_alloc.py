@@ -45,3 +45,25 @@ def test_noalloc_rejects_oversize_problem():
     assert L.sad_render_backward_noalloc(p, p, 10, 4096, 2048, 16, p, p, p, None, None) == 1
     assert b"static limit" in L.sad_last_error()
     assert L.sad_render_backward_noalloc(p, p, 300000, 64, 64, 16, p, p, p, None, None) == 1
+
+
+def test_noalloc_reports_record_overflow_within_the_limits():
+    """Spatially incoherent lists (every pixel lists 16 random sites of
+    262144) stay inside the size limits but need far more per-tile records
+    than the fixed buffer holds: the call must say so through status_out."""
+    torch = pytest.importorskip("torch")
+    capi = require_gpu()
+    H = W = 512
+    K, n = 16, 262144
+    p = gen.sites_random_spd(H, W, n, seed=21)
+    ids = gen.random_map(H * W, K, n, seed=22, invalid_frac=0.0)
+    g = dev(gen.grad_image(H, W, seed=23))
+    pt, prep = prepare(capi, p, H, W)
+    m = capi.map_from_ids(ids)
+    got = torch.empty((11, n), dtype=torch.float32, device="cuda")
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    capi.sad_render_backward_noalloc(pt, prep, H, W, K, m, g, got, status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == capi.SAD_EWORKSPACE
+    # the buffer keeps working for a problem that fits
+    test_noalloc_matches_workspace_backward_twice()
