@@ -79,6 +79,10 @@ def parse():
     ap.add_argument("--no-c4", action="store_true", help="skip the batched-vs-plain leg")
     ap.add_argument("--no-c5", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-decode", action="store_true", help="skip the packed-decode leg")
+    ap.add_argument("--no-sad1d", action="store_true", help="skip the 1-D SAD leg")
+    ap.add_argument("--c3-side", type=int, default=2048,
+                    help="side of the headline workload (sites at the same density); smaller sides are "
+                         "for profiler captures only")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--legs-only", default="", help="comma list of legs to run alone (encode,c3,c4,c5)")
     ap.add_argument("--c4-iters", type=int, default=500, help="training iterations of the c4 leg")
@@ -415,6 +419,31 @@ def encode_iteration(capi, dev, args, rank, peak, peak_kind):
         host_loss.copy_(enc.loss, non_blocking=True)
         torch.cuda.synchronize()
         e2e_s += time.perf_counter() - t0
+    # the same iteration replayed from a CUDA graph (the batched form's
+    # launch path): its time against the summed kernel times of the traced
+    # eager steps gives the idle time between the step's launches
+    g_ms = None
+    try:
+        gs = torch.cuda.Stream(device=dev)
+        gs.wait_stream(torch.cuda.current_stream(dev))
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(gs):
+            graph.capture_begin(capture_error_mode="thread_local")
+            enc._call(gs)
+            graph.capture_end()
+            for _ in range(3):
+                graph.replay()
+            gev = [E() for _ in range(args.steps + 1)]
+            gev[0].record(gs)
+            for i in range(args.steps):
+                graph.replay()
+                gev[i + 1].record(gs)
+        torch.cuda.synchronize()
+        g_ms = statistics.median(gev[i].elapsed_time(gev[i + 1]) for i in range(args.steps))
+        del graph
+    except Exception as e:   # reported, the rest of the line stands
+        g_ms = f"{type(e).__name__}: {e}"
+    kernel_sum = sum(v / max(n, 1) for n, v in trace.values())
     kname, klaunch, kms = dominant(trace)
     alg = {"k_step_tile": P * (K * 4 * 2 + 12) + enc.cap * 48}
     roofline = None
@@ -437,6 +466,9 @@ def encode_iteration(capi, dev, args, rank, peak, peak_kind):
            "l2": "flushed (256 MB write) before every timed step",
            "kernels_ms": {k: round(v / max(n, 1), 5) for k, (n, v) in sorted(trace.items())},
            "unfused_step_ms": round(statistics.median(u_ms), 5),
+           "graph_replay_ms_per_step": round(g_ms, 5) if isinstance(g_ms, float) else g_ms,
+           "kernel_sum_ms_per_step": round(kernel_sum, 5),
+           "idle_between_launches_ms": (round(g_ms - kernel_sum, 5) if isinstance(g_ms, float) else None),
            "e2e": {"value": round(P * args.steps / e2e_s / 1e6, 3), "unit": UNIT,
                    "h2d_bytes_per_step": int(host_img.numel() * 4), "d2h_bytes_per_step": 4},
            "roofline": roofline}
@@ -447,6 +479,11 @@ def encode_iteration(capi, dev, args, rank, peak, peak_kind):
 def run_ours(args):
     import torch
     import torch.distributed as dist
+
+    global H_C3, W_C3, N_C3
+    if args.c3_side != 2048:   # a profiler case: the same workload, scaled
+        H_C3 = W_C3 = args.c3_side
+        N_C3 = int(round(262144 * (args.c3_side / 2048.0) ** 2))
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -475,7 +512,7 @@ def run_ours(args):
     if world == 1:
         line["encode_iteration"] = encode_iteration(capi, dev, args, rank, peak, peak_kind)
         torch.cuda.empty_cache()
-        want = [k for k in ("encode", "c3", "c4", "c5", "decode") if not getattr(args, "no_" + k)]
+        want = [k for k in ("encode", "c3", "c4", "c5", "decode", "sad1d") if not getattr(args, "no_" + k)]
         for leg in want:
             try:
                 line[leg] = LEGS[leg](capi, dev, peak, peak_kind, args)
@@ -534,6 +571,19 @@ def encode_leg(capi, dev, peak, peak_kind, args, iters=2000):
     # separate calls on the float32 table
     res["separate_calls"] = run(fused=False)
     res["cand_half2"] = run(cand_half2=True)
+    # PSNR of the fused form and the two f3 variants over three seeds
+    # (training is chaotic in float rounding, so one seed does not separate
+    # them): seed 0 from the runs above, seeds 1 and 2 untimed
+    seeds = {"fused": [res["psnr_db"]], "cand_every_8": [res["cand_every_8"]["psnr_db"]],
+             "s_grid_2": [res["s_grid_2"]["psnr_db"]]}
+    for sd in (1, 2):
+        for name, kw in (("fused", {}), ("cand_every_8", {"cand_every": 8}), ("s_grid_2", {"s_grid": 2})):
+            enc = Encoder(img, EncodeConfig(n_sites=N_C2, K=K_C2, J=J_C2, iters=iters, seed=sd, **kw))
+            enc.run()
+            seeds[name].append(round(enc.psnr(), 3))
+            del enc
+    res["psnr_over_seeds_0_1_2"] = {k: {"per_seed": v, "mean": round(statistics.mean(v), 3)}
+                                    for k, v in seeds.items()}
     return res
 
 
@@ -958,7 +1008,63 @@ def decode_leg(capi, dev, peak, peak_kind, args, n_query=1 << 20, n_sites=1 << 2
             "max_abs_colour_diff_packed_vs_prepared": round(float((r1 - r2).abs().max().item()), 5)}
 
 
-LEGS = {"encode": encode_leg, "c3": c3_leg, "c4": c4_leg, "c5": c5_leg, "decode": decode_leg}
+# SFU throughput of sm_103a: 16 exponentials per clock per SM (4 per SM
+# sub-partition), the bound of the 1-D step
+SFU_PEAK = 152 * 16 * 2.07e9
+
+
+def sad1d_leg(capi, dev, peak, peak_kind, args, B=8192, N=64, L=1024, steps=20, fit_steps=500):
+    """1-D SAD (Sec. "1D Signal Fitting"): the fused training step of a batch
+    of B synthetic signals (smooth sine, step + sine, multi-frequency), L
+    samples and N sites each, at K = N (every site, the paper's 64-site fits)
+    and K = 16; Msamples/s of training, the PSNR after `fit_steps` steps, and
+    the step's bound: every (sample, listed site) pair takes two
+    exponentials (the forward and the adjoint pass), against the SFU rate."""
+    import numpy as np
+    import torch
+    from paper_2604_21984_gb300 import inputs as gen
+    y = torch.from_numpy(gen.signals_1d(B, L, seed=7000)).to(dev)
+    p0 = torch.from_numpy(gen.sites_1d(y.cpu().numpy(), N)).to(dev)
+    hp = capi.sad1d_hparams()
+    E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    out = {"workload": f"{B} signals x {L} samples, {N} sites each (4 parameters), fused render + MSE + "
+                       f"adjoint + Adam per step"}
+    for K in (N, 16):
+        p = p0.clone()
+        m = torch.zeros_like(p)
+        v = torch.zeros_like(p)
+        loss = torch.empty(B, dtype=torch.float32, device=dev)
+        t = 0
+        for _ in range(3):
+            t += 1
+            capi.sad1d_train_step(p, m, v, B, N, L, K, y, loss, hp, t)
+        torch.cuda.synchronize()
+        e0, e1 = E(), E()
+        e0.record()
+        for _ in range(steps):
+            t += 1
+            capi.sad1d_train_step(p, m, v, B, N, L, K, y, loss, hp, t)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        while t < fit_steps:
+            t += 1
+            capi.sad1d_train_step(p, m, v, B, N, L, K, y, loss, hp, t)
+        psnr = 10 * np.log10(1.0 / np.maximum(loss.cpu().numpy(), 1e-12))
+        exps = 2.0 * B * L * min(K, N) / (ms / 1e3)
+        out[f"K{K}"] = {"ms_per_step": round(ms, 4), "msamples_per_s": round(B * L / (ms / 1e3) / 1e6, 1),
+                        "median_psnr_db_after_%d" % fit_steps: round(float(np.median(psnr)), 2),
+                        "roofline": {"bound": "alu", "achieved": round(exps / 1e9, 1),
+                                     "peak": round(SFU_PEAK / 1e9, 1), "unit": "G exp/s",
+                                     "frac": round(exps / SFU_PEAK, 4),
+                                     "peak_kind": "derived: 152 SMs x 16 SFU ops/clk x 2070 MHz"}}
+    out["paper_context"] = ("64 sites x 4 params: 57.2 dB (step), 42.0 dB (multi-frequency) on the "
+                            "paper's own three targets; signals here are synthetic stand-ins")
+    return out
+
+
+LEGS = {"encode": encode_leg, "c3": c3_leg, "c4": c4_leg, "c5": c5_leg, "decode": decode_leg,
+        "sad1d": sad1d_leg}
 
 
 # ----------------------------------------------------------------------------

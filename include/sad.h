@@ -27,9 +27,12 @@
  *    list positions 4j..4j+3, i.e. uint32[K/4][H*W][4].  Sentinel 0xffffffff.
  *    K must be 4, 8 or 16.  Lists are ordered by logit descending, ties by
  *    smaller id (for maps produced by sad_update_topk).
- *  - The prepared site table (the "pack" of App. "Data Layout and Packing") is float32[3][capacity][4]:
+ *  - The prepared site table (the "pack" of App. "Data Layout and Packing") is float32[5][capacity][4]:
  *      plane 0 {x, y, tau*s, r}, plane 1 {G00, G01, G11, active},
- *      plane 2 {cr, cg, cb, 0},  with s = 1/max(H,W) (Sec. 4.1).
+ *      plane 2 {cr, cg, cb, 0},  with s = 1/max(H,W) (Sec. 4.1); planes 3
+ *      and 4 hold the same site folded for the softmax blend (the blend
+ *      record): with G' = (tau s)^2 G, plane 3 {x, y, tau s r, G'00} (tau s r
+ *      = -inf for an inactive site), plane 4 {G'01, G'11, cr, cg}.
  *    Every device pointer must be 16-byte aligned.
  */
 #ifndef SAD_H
@@ -88,7 +91,7 @@ int sad_trace_collect(sad_trace_entry* out, int32_t max_entries, int32_t* n_out)
  *   reduction + degree-7 Taylor polynomial); G00 = e+ ux^2 + e- uy^2,
  *   G01 = (e+ - e-) ux uy, G11 = e+ uy^2 + e- ux^2; tau*s = exp(log_tau) s;
  *   active = (x >= 0).
- * params: float32[11][capacity] (read).  prep: float32[3][capacity][4] (written).
+ * params: float32[11][capacity] (read).  prep: float32[5][capacity][4] (written).
  */
 int sad_prepare_sites(const float* params, int32_t capacity, int32_t H, int32_t W,
                       float* prep, void* stream);
@@ -288,7 +291,7 @@ int sad_train_grads(const float* params, const float* prep, int32_t capacity, in
  * Scratch is one SAD_NOALLOC_SCRATCH_BYTES buffer inside the library
  * (allocated on every device that loads the library, kept until exit).
  * Limits: H*W <= 4194304 and capacity <= 262144, else SAD_EINVAL; within them
- * about 0.9 million per-tile records fit (a 2048 x 2048 render of 262144
+ * about 1.2 million per-tile records fit (a 2048 x 2048 render of 262144
  * random sites at K = 16 makes about 0.83 million; spatially incoherent lists
  * make many more and overflow).  The first call on a device looks up the
  * buffer's device address and keeps it for the life of the process (make that
@@ -591,6 +594,45 @@ int sad_decode_packed(const uint32_t* packed, const float* q_host, int32_t capac
                       float* rgb, void* stream);
 int sad_render_packed(const uint32_t* packed, const float* q_host, int32_t capacity, int32_t H,
                       int32_t W, int32_t K, const uint32_t* map, float* rgb, void* stream);
+
+/*
+ * 1-D SAD (Sec. "1D Signal Fitting"): the soft partition of unity of Sec. 4.2
+ * on a line.  A batch of B independent signals of L samples each (sample k at
+ * x = k + 0.5, s = 1/L), each with its own N sites of four parameters,
+ * float32[4][B*N] planes (p position in samples, c value, log_tau, r radius
+ * in samples; site i of signal b at column b*N + i):
+ *   l_i(x) = tau_i s (r_i - |x - p_i|),   tau = exp(log_tau),
+ * the value at x is the softmax blend of the K sites of the signal with the
+ * largest logit (ties to the smaller index); K >= N blends all N sites (the
+ * paper's 64-site fits).  Limits: 1 <= N <= 1024; K >= N, or K <= 16.
+ *
+ * sad1d_render -- values: float32[B][L] (written).
+ */
+int sad1d_render(const float* params, int32_t B, int32_t N, int32_t L, int32_t K, float* values,
+                 void* stream);
+
+/* Adam of the 1-D sites (Sec. 6.1 conventions; Kingma & Ba 2015). */
+typedef struct sad1d_adam_hparams {
+  float lr[4];          /* per plane p, c, log_tau, r; p and r in normalised units (value * s) */
+  float beta1, beta2, eps;
+  float log_tau_min, log_tau_max; /* clamp of log_tau after the step */
+} sad1d_adam_hparams;
+
+/*
+ * sad1d_train_step -- one fused training iteration of every signal: render,
+ * L_b = mean over samples of (c(x) - y(x))^2 (loss: float32[B], written),
+ * the adjoint with the top-K sets held fixed (dL/dc_i = sum w_i g,
+ * delta_i = w_i g (c_i - cbar) = dL/dl_i, dl/dlog_tau = l, dl/dr = tau s,
+ * dl/dp = tau s sign(x - p), 0 at x = p; g = 2 (c - y) / L), summed per site
+ * in a fixed order (no atomics), then bias-corrected Adam with Adam step t
+ * (1-based) and the clamps p, r in [0, L], log_tau in [log_tau_min,
+ * log_tau_max].  params, m, v: float32[4][B*N] (updated); target:
+ * float32[B][L]; grads_out: float32[4][B*N] or NULL.  One 256-thread block
+ * per signal: the results of a signal do not depend on the rest of the batch.
+ */
+int sad1d_train_step(float* params, float* m, float* v, int32_t B, int32_t N, int32_t L, int32_t K,
+                     const float* target, float* loss, const sad1d_adam_hparams* hp, int32_t t,
+                     float* grads_out, void* stream);
 
 #ifdef __cplusplus
 }

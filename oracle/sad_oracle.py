@@ -37,6 +37,8 @@ Part 5: packed 16-byte evaluation sites (App. "Data Layout and Packing",
 Part 6: tau diffusion (App. "Tau Diffusion").
 Part 7: half2 candidate sites (App. "Data Layout and Packing", Packed
   candidate sites): candidate_halves / candidate_words / candidate_table_fp32.
+Part 8: 1-D SAD (Sec. "1D Signal Fitting"): sad1d_logits / sad1d_topk /
+  sad1d_render / sad1d_backward / sad1d_adam_step / sad1d_train_step.
 """
 from __future__ import annotations
 
@@ -1113,3 +1115,128 @@ def candidate_table_fp32(prep):
         out[f] = h[:, k].copy()
     out["active"] = h[:, 7] != F32(0)
     return out
+
+
+# =============================================================================
+# Part 8: 1-D SAD (Sec. "1D Signal Fitting"), fp64
+# =============================================================================
+# Each site of a 1-D signal has a position p (samples), a value c, a log
+# temperature and a radius r (four parameters).  The 2-D score with the 1-D
+# distance: sample k sits at x = k + 0.5, s = 1/L, d_i(x) = |x - p_i| s -
+# r_i s, l_i(x) = -tau_i d_i(x) (Sec. 4.1-4.2); the value at x is the softmax
+# blend over the K sites of largest logit (ties to the smaller index; K = N
+# blends over every site: the soft partition of unity of the paper's 64-site
+# fits).  Parameters: float[4, N] planes (p, c, log_tau, r).
+
+P1_P, P1_C, P1_LOGTAU, P1_R = range(4)
+SAD1D_PLANES = ("p", "c", "log_tau", "r")
+SAD1D_LR = {"p": 2e-3, "c": 1e-2, "log_tau": 1e-2, "r": 1e-3}
+
+
+def sad1d_samples(L):
+    """Sample centres x_k = k + 0.5 of a signal of L samples."""
+    return np.arange(L, dtype=np.float64) + 0.5
+
+
+def sad1d_logits(params, L, xs=None):
+    """l_i(x) = -tau_i (|x - p_i| s - r_i s), float64[X, N]."""
+    p = np.asarray(params, dtype=np.float64)
+    xs = sad1d_samples(L) if xs is None else np.asarray(xs, dtype=np.float64)
+    s = 1.0 / L
+    tau = np.exp(p[P1_LOGTAU])
+    d = np.abs(xs[:, None] - p[P1_P][None, :]) * s - p[P1_R][None, :] * s
+    return -tau[None, :] * d
+
+
+def sad1d_topk(params, L, K, xs=None):
+    """Indices of the K largest logits per sample (ties to the smaller index):
+    int64[X, min(K, N)]."""
+    ell = sad1d_logits(params, L, xs)
+    X, N = ell.shape
+    kk = min(K, N)
+    idx = np.broadcast_to(np.arange(N), (X, N))
+    sel = select_topk(idx, ell, np.ones(ell.shape, bool), kk)
+    return sel.astype(np.int64)
+
+
+def sad1d_render(params, L, K, xs=None):
+    """Blended value per sample: float64[X]."""
+    p = np.asarray(params, dtype=np.float64)
+    ell = sad1d_logits(p, L, xs)
+    ids = sad1d_topk(p, L, K, xs)
+    l = np.take_along_axis(ell, ids, axis=1)
+    w = np.exp(l - l.max(axis=1, keepdims=True))
+    w /= w.sum(axis=1, keepdims=True)
+    return (w * p[P1_C][ids]).sum(axis=1)
+
+
+def sad1d_backward(params, L, K, g, xs=None):
+    """Adjoint of the 1-D blend for upstream dL/dc(x) = g (float[X]), with the
+    top-K sets held fixed: float64[4, N] gradients.  Per sample and listed
+    site: dL/dc_i = w_i g; delta_i = w_i g (c_i - cbar) = dL/dl_i; dl/dlog_tau
+    = l; dl/dr = tau s; dl/dp = tau s sign(x - p) (0 at x = p, where the
+    distance has its kink)."""
+    p = np.asarray(params, dtype=np.float64)
+    xs = sad1d_samples(L) if xs is None else np.asarray(xs, dtype=np.float64)
+    g = np.asarray(g, dtype=np.float64)
+    ell = sad1d_logits(p, L, xs)
+    ids = sad1d_topk(p, L, K, xs)
+    l = np.take_along_axis(ell, ids, axis=1)
+    w = np.exp(l - l.max(axis=1, keepdims=True))
+    w /= w.sum(axis=1, keepdims=True)
+    ck = p[P1_C][ids]
+    cbar = (w * ck).sum(axis=1, keepdims=True)
+    delta = w * g[:, None] * (ck - cbar)
+    s = 1.0 / L
+    tau = np.exp(p[P1_LOGTAU])[ids]
+    sgn = np.sign(xs[:, None] - p[P1_P][ids])
+    N = p.shape[1]
+    out = np.zeros((4, N))
+    np.add.at(out[P1_C], ids, w * g[:, None])
+    np.add.at(out[P1_LOGTAU], ids, delta * l)
+    np.add.at(out[P1_R], ids, delta * tau * s)
+    np.add.at(out[P1_P], ids, delta * tau * s * sgn)
+    return out
+
+
+def sad1d_loss_and_grad(values, target):
+    """L = mean over samples of (c(x) - y(x))^2 and dL/dc = 2 (c - y) / L."""
+    r = np.asarray(values, dtype=np.float64) - np.asarray(target, dtype=np.float64)
+    return float(np.mean(r * r)), 2.0 * r / len(r)
+
+
+def sad1d_adam_step(params, grads, m, v, t, L, lr=None, beta1=0.9, beta2=0.999, eps=1e-8,
+                    log_tau_range=(2.0, 20.0)):
+    """One bias-corrected Adam step (Kingma & Ba 2015) of the 1-D sites, with
+    the 2-D conventions of Sec. 6.1: p and r optimised in normalised units
+    (value * s: gradient / s, step / s), p clamped to [0, L], r to [0, L],
+    log_tau to [2, 20]; values unclamped.  Returns new (params, m, v), fp64."""
+    lr = dict(SAD1D_LR if lr is None else lr)
+    p = np.array(params, dtype=np.float64)
+    g = np.asarray(grads, dtype=np.float64)
+    m = np.array(m, dtype=np.float64)
+    v = np.array(v, dtype=np.float64)
+    s = 1.0 / L
+    for j, name in enumerate(SAD1D_PLANES):
+        unit = s if j in (P1_P, P1_R) else 1.0
+        gj = g[j] / unit
+        m[j] = beta1 * m[j] + (1 - beta1) * gj
+        v[j] = beta2 * v[j] + (1 - beta2) * gj * gj
+        mhat = m[j] / (1 - beta1 ** t)
+        vhat = v[j] / (1 - beta2 ** t)
+        p[j] = p[j] - lr[name] * mhat / (np.sqrt(vhat) + eps) / unit
+    p[P1_P] = np.clip(p[P1_P], 0.0, float(L))
+    p[P1_R] = np.clip(p[P1_R], 0.0, float(L))
+    p[P1_LOGTAU] = np.clip(p[P1_LOGTAU], *log_tau_range)
+    return p, m, v
+
+
+def sad1d_train_step(params, m, v, t, target, K, lr=None):
+    """One 1-D training iteration: render over the top-K sets, MSE, adjoint,
+    Adam.  Returns (params, m, v, loss, grads), fp64."""
+    L = len(target)
+    vals = sad1d_render(params, L, K)
+    loss, g = sad1d_loss_and_grad(vals, target)
+    grads = sad1d_backward(params, L, K, g)
+    p2, m2, v2 = sad1d_adam_step(params, grads, m, v, t, L, lr)
+    return p2, m2, v2, loss, grads

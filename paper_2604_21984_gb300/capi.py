@@ -27,6 +27,7 @@ INVALID = 0xFFFFFFFF
 STEP_KEEP_LISTS = 1   # batch-image flag (include/sad.h SAD_STEP_KEEP_LISTS)
 PLANE_LOGTAU = 2      # plane of log tau in the site parameter and gradient arrays
 SAD_EWORKSPACE = 3    # status: per-tile records did not fit the workspace
+PREP_PLANES = 5       # float4 planes of the prepared site table (include/sad.h)
 NOALLOC_SCRATCH_BYTES = 64 << 20   # include/sad.h SAD_NOALLOC_SCRATCH_BYTES: held on every device
 
 
@@ -51,6 +52,11 @@ class BatchImage(ctypes.Structure):
     _fields_ = [("H", ctypes.c_int32), ("W", ctypes.c_int32), ("site_offset", ctypes.c_int32),
                 ("capacity", ctypes.c_int32), ("pixel_offset", ctypes.c_int64),
                 ("seed", ctypes.c_uint64), ("state_index", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class Sad1dAdam(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float * 4), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("log_tau_min", ctypes.c_float), ("log_tau_max", ctypes.c_float)]
 
 
 class TraceEntry(ctypes.Structure):
@@ -83,6 +89,12 @@ _SIGS = {
                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int32,
                                        ctypes.c_uint64, ctypes.c_void_p]),
+    "sad1d_render": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "sad1d_train_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.POINTER(Sad1dAdam), ctypes.c_int32,
+                                        ctypes.c_void_p, ctypes.c_void_p]),
     "sad_exact_topk": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                       ctypes.c_void_p]),
@@ -249,7 +261,7 @@ def _ptr(t, dtype, name, numel=None):
 # ----------------------------------------------------------------------------
 
 def empty_prep(cap, device="cuda"):
-    return torch.empty((3, max(cap, 1), 4), dtype=torch.float32, device=device)
+    return torch.empty((PREP_PLANES, max(cap, 1), 4), dtype=torch.float32, device=device)
 
 
 def empty_map(H, W, K, device="cuda"):
@@ -759,3 +771,40 @@ def sad_tau_diffusion(params, H, W, K, map_in, lam, g_logtau, g_out, stream=None
                                    _ptr(g_out, torch.float32, "g_out", cap), _stream(stream)),
            "sad_tau_diffusion")
     return g_out
+
+
+# ----------------------------------------------------------------------------
+# 1-D SAD (Sec. "1D Signal Fitting")
+# ----------------------------------------------------------------------------
+
+SAD1D_LR = (2e-3, 1e-2, 1e-2, 1e-3)   # p, c, log_tau, r
+
+
+def sad1d_hparams(lr=SAD1D_LR, beta1=0.9, beta2=0.999, eps=1e-8, log_tau_range=(2.0, 20.0)):
+    h = Sad1dAdam()
+    for j in range(4):
+        h.lr[j] = lr[j]
+    h.beta1, h.beta2, h.eps = beta1, beta2, eps
+    h.log_tau_min, h.log_tau_max = log_tau_range
+    return h
+
+
+def sad1d_render(params, B, N, L, K, values=None, stream=None):
+    """Values of B signals (params float32[4, B*N] device): float32[B, L]."""
+    if values is None:
+        values = torch.empty((B, L), dtype=torch.float32, device=params.device)
+    _check(lib().sad1d_render(_ptr(params, torch.float32, "params", 4 * B * N), B, N, L, K,
+                              _ptr(values, torch.float32, "values", B * L), _stream(stream)), "sad1d_render")
+    return values
+
+
+def sad1d_train_step(params, m, v, B, N, L, K, target, loss, hp, t, grads_out=None, stream=None):
+    """One fused 1-D training iteration of every signal (Adam step t)."""
+    _check(lib().sad1d_train_step(_ptr(params, torch.float32, "params", 4 * B * N),
+                                  _ptr(m, torch.float32, "m", 4 * B * N),
+                                  _ptr(v, torch.float32, "v", 4 * B * N), B, N, L, K,
+                                  _ptr(target, torch.float32, "target", B * L),
+                                  _ptr(loss, torch.float32, "loss", B), ctypes.byref(hp), t,
+                                  _ptr(grads_out, torch.float32, "grads_out", 4 * B * N),
+                                  _stream(stream)), "sad1d_train_step")
+    return loss

@@ -1,31 +1,32 @@
-// Adjoint of the blend (App. "Gradient Computation and Reduction", Per-pixel gradients) with an atomic-free,
-// deterministic gradient reduction that replaces the per-tile hash table plus
-// global float atomics of Sec. 4.8, Alg. 1 (threadgroup hash reduction).
+// Adjoint of the blend (App. "Gradient Computation and Reduction", Per-pixel
+// gradients) with a deterministic gradient reduction that replaces the
+// per-tile hash table plus global float atomics of Sec. 4.8, Alg. 1
+// (threadgroup hash reduction).
 //
-// Per 16x16 pixel tile (one CTA, one pixel per thread):
-//  1. forward: every pixel recomputes its max-subtracted softmax over its K
-//     listed sites (nothing from the forward pass is stored), forms its
-//     upstream gradient g (given, or 2(c - I)/P for the fused MSE loss) and
-//     parks {m, 1/Z, cbar, g} in shared memory;
+// Per 16x16 pixel tile (one CTA, one pixel per thread; sad_tile.cuh):
+//  1. forward: every pixel forms its max-subtracted softmax over its K
+//     listed sites (recomputed, or from the render's saved max logit, 1/Z
+//     and blend), its upstream gradient g (given, or 2(c - I)/P for the
+//     fused MSE loss), and parks {m, 1/Z, cbar, g} in shared memory;
 //  2. the tile's distinct sites get slots in a shared hash table (the paper's
 //     multiplicative hash, linear probing); each warp records, per slot, the
-//     bitmask of its 32 pixels that list the site (__match_any_sync, no
-//     atomics: a warp owns its mask word);
+//     bitmask of its 32 pixels that list the site;
 //  3. the masks give each slot a stable, pixel-ordered pair list; one warp
 //     walks a slot's list 32 pairs at a time with the site's parameters in
-//     registers (lane i takes pairs i, i+32, ...) and a fixed butterfly sums
-//     the lane partials, giving ten sufficient statistics per (site, tile):
+//     registers (lane i takes pairs i, i+32, ...) and a fixed-order
+//     reduction sums the lane partials, giving ten sufficient statistics per
+//     (site, tile):
 //       sum w g (3),  sum d,  sum d n,  sum d dx/n,  sum d dy/n,
 //       sum d dx^2/n, sum d dx dy/n, sum d dy^2/n,   d = dL/dl = w g.(c_k - cbar)
 //     written as one partial record per (site, tile).  If the table fills,
 //     the remaining sites are handled in further rounds.
-// Then every record's statistics are added into per-site sums in exact
-// 64-bit fixed point (integer atomics, per-statistic scale from the largest
-// record value), which makes each site's total independent of the order of
-// the additions; the eleven parameter gradients follow from the statistics by
-// the chain rule through G(a, b, u) of Sec. 4.1.
+// Then a segmented reduce (sad_reduce.cuh) files the records by site and sums
+// each site's records exactly, with no atomic on any gradient value; the
+// eleven parameter gradients follow from the statistics by the chain rule
+// through G(a, b, u) of Sec. 4.1.
 #include "sad_device.cuh"
 #include "sad_host.h"
+#include "sad_reduce.cuh"
 #include "sad_tile.cuh"
 
 #include <mutex>
@@ -36,13 +37,14 @@ namespace sad {
 // workspace layout
 // ---------------------------------------------------------------------------
 struct WsLayout {
-  size_t hdr, tile_loss, records, acc, total;
+  size_t hdr, tile_loss, cnt, start, bsums, dir, records, total;
   uint32_t max_records, n_tiles;
 };
 
 static inline size_t align256(size_t v) { return (v + 255) & ~static_cast<size_t>(255); }
 
-// records: 48 B per (site, tile); acc: 10 int64 fixed-point sums per site
+// records: 48 B per (site, tile) plus its 4-byte directory entry; per site a
+// record count and a segment start; the scan's block sums
 static WsLayout ws_layout(int H, int W, int K, int cap, int64_t max_records) {
   WsLayout L{};
   const uint64_t tiles_x = (W + kTileSide - 1) / kTileSide;
@@ -53,10 +55,14 @@ static WsLayout ws_layout(int H, int W, int K, int cap, int64_t max_records) {
   if (max_records <= 0 && mr < 128ull * L.n_tiles) mr = 128ull * L.n_tiles;
   if (mr > 0xfffffff0ull) mr = 0xfffffff0ull;
   L.max_records = static_cast<uint32_t>(mr);
+  const size_t c = static_cast<size_t>(cap);
   size_t o = 0;
   L.hdr = o;        o = align256(o + sizeof(WsHeader));
   L.tile_loss = o;  o = align256(o + sizeof(float) * L.n_tiles);
-  L.acc = o;        o = align256(o + sizeof(unsigned long long) * 10 * static_cast<size_t>(cap));
+  L.cnt = o;        o = align256(o + sizeof(uint32_t) * c);
+  L.start = o;      o = align256(o + sizeof(uint32_t) * c);
+  L.bsums = o;      o = align256(o + sizeof(uint32_t) * (seg_blocks(c) + 1));
+  L.dir = o;        o = align256(o + sizeof(uint32_t) * L.max_records);
   L.records = o;    o = align256(o + sizeof(Record) * L.max_records);
   L.total = o;
   return L;
@@ -79,6 +85,7 @@ __global__ void __launch_bounds__(kTileThreads, MODE == kModeStats ? 2 : (SAVED 
   c.y0 = static_cast<int>(blockIdx.x / tiles_x) * kTileSide;
   c.pix_off = 0;
   c.sr = SiteRange{0u, static_cast<uint32_t>(cap)};
+  c.site_cum = 0u;
   c.tile = blockIdx.x;
   c.img = 0;
   c.two_over_P = 2.0f / static_cast<float>(static_cast<double>(H) * W);
@@ -99,27 +106,9 @@ __global__ void __launch_bounds__(kTileThreads, MODE == kModeStats ? 2 : (SAVED 
 #pragma unroll
   for (int k = 0; k < K; ++k) lk[k] = 0.f;
   __shared__ TileShared<K, MODE> sm;
+  io.lists = map;
+  io.lists_P = P;
   tile_body<K, MODE, false, kTileSide, SAVED>(c, io, ids, lk, sm);
-}
-
-// ---------------------------------------------------------------------------
-// per-site sums of the per-tile records in exact fixed point
-//
-// Statistic j of every record of image b is scaled by 2^S, S = 61 - e - 32
-// with max |value| < 2^e over that image's records of statistic j (at most
-// 2^32 records), rounded to an int64 and
-// added with integer atomics: no sum can overflow, integer addition is
-// associative, so each site's total is the same bit pattern whatever the order
-// of the additions (and of the other images in a batch), and its rounding
-// error is below 2^-29 of the image's largest record value of that statistic.
-// ---------------------------------------------------------------------------
-// Exact sum of statistic j of site i of image img back to float.
-__device__ __forceinline__ float fixed_value(const unsigned long long* __restrict__ accq,
-                                             const WsHeader* __restrict__ hdr, size_t c, int j,
-                                             size_t i, uint32_t img, bool& nonzero) {
-  const long long q = static_cast<long long>(accq[j * c + i]);
-  nonzero |= q != 0;
-  return static_cast<float>(static_cast<double>(q) * pow2(-fixed_shift(hdr->pmax[img][j])));
 }
 
 // Chain rule from the ten statistics of a site to its 11 parameter gradients
@@ -155,39 +144,40 @@ __device__ __forceinline__ void grads_from_stats(const float (&acc)[10], float4 
   out[PUY] = nrm2 > 0.f ? gth * rawx / nrm2 : 0.f;
 }
 
-// Per site (single image): the exact sums back to float, then the chain rule.
+// Per site (single image): the exact segment sums, then the chain rule.
 __global__ void k_site_grads(const float* __restrict__ params, const float4* __restrict__ geo,
                              const float4* __restrict__ met, int cap,
-                             const WsHeader* __restrict__ hdr,
-                             const unsigned long long* __restrict__ accq,
+                             const uint32_t* __restrict__ start, const uint32_t* __restrict__ boff,
+                             const uint32_t* __restrict__ dir, const Record* __restrict__ rec,
                              float* __restrict__ grads) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= cap) return;
   const size_t c = static_cast<size_t>(cap);
   float acc[10];
-  bool any = false;
-#pragma unroll
-  for (int j = 0; j < 10; ++j) acc[j] = fixed_value(accq, hdr, c, j, i, 0u, any);
+  const uint32_t n = site_exact_sums<10>(i < cap, static_cast<uint32_t>(i), static_cast<uint32_t>(cap),
+                                         start, boff, dir, rec, acc);  // every lane takes part
+  if (i >= cap) return;
   float out[kNParams];
 #pragma unroll
   for (int j = 0; j < kNParams; ++j) out[j] = 0.f;
-  if (any)
+  if (n)
     grads_from_stats(acc, geo[i], met[i], params[PUX * c + i], params[PUY * c + i],
                      params[PA * c + i], params[PB * c + i], out);
 #pragma unroll
   for (int j = 0; j < kNParams; ++j) grads[j * c + i] = out[j];
 }
 
-// Per site: the exact statistic sums back to float (statistics mode).
-__global__ void k_site_stats(int cap, const WsHeader* __restrict__ hdr,
-                             const unsigned long long* __restrict__ accq,
-                             float* __restrict__ stats) {
+// Per site: the exact segment sums of the statistics (statistics mode).
+__global__ void k_site_stats(int cap, const uint32_t* __restrict__ start,
+                             const uint32_t* __restrict__ boff, const uint32_t* __restrict__ dir,
+                             const Record* __restrict__ rec, float* __restrict__ stats) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= cap) return;
   const size_t c = static_cast<size_t>(cap);
-  bool any = false;
+  float acc[8];
+  site_exact_sums<8>(i < cap, static_cast<uint32_t>(i), static_cast<uint32_t>(cap), start, boff, dir, rec,
+                     acc);  // every lane takes part
+  if (i >= cap) return;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) stats[j * c + i] = fixed_value(accq, hdr, c, j, i, 0u, any);
+  for (int j = 0; j < 8; ++j) stats[j * c + i] = acc[j];
 }
 
 __global__ void k_loss_final(const float* __restrict__ tile_loss, uint32_t n_tiles, float inv_P,
@@ -228,8 +218,10 @@ static int run_backward(const float* params, const float* prep, int cap, int H, 
   }
   WsLayout LL = L1;
   {
-    const uint64_t per = sizeof(Record) + sizeof(uint64_t);
-    uint64_t mr = 1 + (ws_bytes - L1.total) / per;
+    // per record: its 48 bytes and its directory entry; the two regions'
+    // 256-byte alignment can hide up to 512 bytes, so start above and step down
+    const uint64_t per = sizeof(Record) + sizeof(uint32_t);
+    uint64_t mr = 1 + (ws_bytes - L1.total + 512) / per;
     if (mr > 0xfffffff0ull) mr = 0xfffffff0ull;
     for (int it = 0; it < 64 && mr > 1; ++it, --mr) {
       const WsLayout T = ws_layout(H, W, K, cap, static_cast<int64_t>(mr));
@@ -243,11 +235,13 @@ static int run_backward(const float* params, const float* prep, int cap, int H, 
   WsHeader* hdr = reinterpret_cast<WsHeader*>(base + LL.hdr);
   float* tile_loss = reinterpret_cast<float*>(base + LL.tile_loss);
   Record* rec = reinterpret_cast<Record*>(base + LL.records);
-  unsigned long long* accq = reinterpret_cast<unsigned long long*>(base + LL.acc);
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(base + LL.cnt);
+  uint32_t* start = reinterpret_cast<uint32_t*>(base + LL.start);
+  uint32_t* bsums = reinterpret_cast<uint32_t*>(base + LL.bsums);
+  uint32_t* dir = reinterpret_cast<uint32_t*>(base + LL.dir);
 
   cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st);
-  if (e == cudaSuccess && cap > 0)
-    e = cudaMemsetAsync(accq, 0, sizeof(unsigned long long) * 10 * static_cast<size_t>(cap), st);
+  if (e == cudaSuccess && cap > 0) e = cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * static_cast<size_t>(cap), st);
   if (e != cudaSuccess) {
     set_error("%s memset: %s", name, cudaGetErrorString(e));
     return SAD_ECUDA;
@@ -267,6 +261,7 @@ static int run_backward(const float* params, const float* prep, int cap, int H, 
   io.records = rec;
   io.max_records = LL.max_records;
   io.hdr = hdr;
+  io.site_cnt = cnt;
   io.fwd = fwd;
   io.rgb_in = rgb_in;
 #define SAD_TILE_LAUNCH(KK, MM) \
@@ -303,16 +298,15 @@ static int run_backward(const float* params, const float* prep, int cap, int H, 
     if (int r = check_launch("k_loss_final")) return r;
   }
   if (cap == 0) return SAD_OK;
-  const int sgrid = 152 * 8;
+  // the segmented reduce: segment starts, records filed by site, exact sums
+  run_seg_scan(cnt, static_cast<uint32_t>(cap), start, bsums, st);
+  { TraceScope tr_(st, "k_rec_scatter"); k_rec_scatter<<<152 * 8, 256, 0, st>>>(rec, hdr, LL.max_records, start, bsums, cnt, dir); }
+  if (int r = check_launch("k_rec_scatter")) return r;
   if (stats_mode) {
-    { TraceScope tr_(st, "k_seg_accum"); k_seg_accum<8><<<sgrid, 256, 0, st>>>(rec, hdr, LL.max_records, cap, accq); }
-    if (int r = check_launch("k_seg_accum")) return r;
-    { TraceScope tr_(st, "k_site_stats"); k_site_stats<<<(cap + 255) / 256, 256, 0, st>>>(cap, hdr, accq, stats); }
+    { TraceScope tr_(st, "k_site_stats"); k_site_stats<<<(cap + 255) / 256, 256, 0, st>>>(cap, start, bsums, dir, rec, stats); }
     return check_launch("k_site_stats");
   }
-  { TraceScope tr_(st, "k_seg_accum"); k_seg_accum<10><<<sgrid, 256, 0, st>>>(rec, hdr, LL.max_records, cap, accq); }
-  if (int r = check_launch("k_seg_accum")) return r;
-  { TraceScope tr_(st, "k_site_grads"); k_site_grads<<<(cap + 255) / 256, 256, 0, st>>>(params, geo, met, cap, hdr, accq, grads); }
+  { TraceScope tr_(st, "k_site_grads"); k_site_grads<<<(cap + 255) / 256, 256, 0, st>>>(params, geo, met, cap, start, bsums, dir, rec, grads); }
   return check_launch("k_site_grads");
 }
 

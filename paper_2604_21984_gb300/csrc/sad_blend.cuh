@@ -31,15 +31,19 @@ __device__ __forceinline__ void blend_step(float l, bool ok, float4 ck, float& m
   c.z += b * ck.z;
 }
 
+// The blend reads each listed site's blend record (two 16-byte gathers,
+// {x, y, tau s r, G'00} and {G'01, G'11, cr, cg}, plus cb from the colour
+// plane: 36 bytes per (pixel, site)), with l = tau s r - sqrt(dx G' dx).
 // m_out / iz_out (optional): the max logit and 1/Z of the blend (0 if no
 // listed site is valid), the per-pixel state the saved-forward adjoint reads.
 template <int NP>
 __device__ __forceinline__ float3 blend_planes(const uint4* __restrict__ map, size_t P, size_t q,
                                                float px, float py, SiteRange sr,
-                                               const float4* __restrict__ geo,
-                                               const float4* __restrict__ met,
+                                               const float4* __restrict__ ba,
+                                               const float4* __restrict__ bb,
                                                const float4* __restrict__ col,
                                                float* m_out = nullptr, float* iz_out = nullptr) {
+  const float* __restrict__ colf = reinterpret_cast<const float*>(col);
   float m = -INFINITY, z = 0.f;
   float3 c = make_float3(0.f, 0.f, 0.f);
 #pragma unroll
@@ -48,18 +52,22 @@ __device__ __forceinline__ float3 blend_planes(const uint4* __restrict__ map, si
     const uint32_t id4[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
     for (int u0 = 0; u0 < 4; u0 += 2) {
-      float4 g[2], mt[2], ck[2];
+      float4 A[2], B[2];
+      float cb[2];
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const uint32_t id = sr.has(id4[u0 + u]) ? id4[u0 + u] : sr.lo;  // clamped: loads issue early
-        g[u] = ldg(&geo[id]);
-        mt[u] = ldg(&met[id]);
-        ck[u] = ldg(&col[id]);
+        A[u] = ldg(&ba[id]);
+        B[u] = ldg(&bb[id]);
+        cb[u] = ldg(&colf[4 * static_cast<size_t>(id) + 2]);
       }
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
-        const bool ok = sr.has(id4[u0 + u]) && mt[u].w != 0.f;
-        blend_step(score_fast(px, py, g[u], mt[u]).l, ok, ck[u], m, z, c);
+        const bool ok = sr.has(id4[u0 + u]) && A[u].z > -INFINITY;  // an inactive site has -inf
+        const float dx = px - A[u].x, dy = py - A[u].y;
+        const float qq = A[u].w * dx * dx + 2.f * B[u].x * dx * dy + B[u].y * dy * dy;
+        const float l = A[u].z - sqrtf(fmaxf(qq, 0.f));
+        blend_step(l, ok, make_float4(B[u].z, B[u].w, cb[u], 0.f), m, z, c);
       }
     }
   }

@@ -88,10 +88,14 @@ __device__ __forceinline__ bool key_before(float la, uint32_t ia, float lb, uint
 // result is reproducible: u = (ux,uy)/|(ux,uy)| (or (1,0)), e+ = exp(b+a),
 // e- = exp(b-a), G00 = e+ ux^2 + e- uy^2, G01 = (e+ - e-) ux uy,
 // G11 = e+ uy^2 + e- ux^2, tau s = exp(log_tau) s, active = (x >= 0).
+// The blend record (ba, bb) is the same site folded for the softmax blend
+// and its 36 bytes per (pixel, site) gather: with G' = (tau s)^2 G the logit
+// is l = tau s r - sqrt(dx G' dx), so ba = {x, y, tau s r, G'00} (tau s r =
+// -inf for an inactive site) and bb = {G'01, G'11, cr, cg}; cb stays in col.
 __device__ __forceinline__ void prepare_site(float x, float y, float logtau, float r, float cr,
                                              float cg, float cb, float ux, float uy, float a,
                                              float b, float s, float4& geo, float4& met,
-                                             float4& col) {
+                                             float4& col, float4& ba, float4& bb) {
   const float nrm = __fsqrt_rn(__fadd_rn(__fmul_rn(ux, ux), __fmul_rn(uy, uy)));
   float uxn = 1.f, uyn = 0.f;
   if (nrm > 0.f) {
@@ -105,9 +109,13 @@ __device__ __forceinline__ void prepare_site(float x, float y, float logtau, flo
   const float G01 = __fmul_rn(__fsub_rn(ep, em), xy);
   const float G11 = __fadd_rn(__fmul_rn(ep, yy), __fmul_rn(em, xx));
   const float ts = __fmul_rn(exp32_repro(logtau), s);
+  const bool act = x >= 0.f;
   geo = make_float4(x, y, ts, r);
-  met = make_float4(G00, G01, G11, x >= 0.f ? 1.f : 0.f);
+  met = make_float4(G00, G01, G11, act ? 1.f : 0.f);
   col = make_float4(cr, cg, cb, 0.f);
+  const float t2 = ts * ts;
+  ba = make_float4(x, y, act ? ts * r : -INFINITY, t2 * G00);
+  bb = make_float4(t2 * G01, t2 * G11, cr, cg);
 }
 
 template <typename T>

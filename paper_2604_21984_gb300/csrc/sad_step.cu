@@ -11,20 +11,24 @@
 //     lists, writes the new ones), then - on the lists just computed, still in
 //     registers - the fused render + MSE + adjoint of the tile (per-tile
 //     records, deterministic);
-//  2. k_seg_accum: exact fixed-point per-site sums of the records;
-//  3. k_site_step, one thread per site: the chain rule to the 11 gradients,
+//  2. the segmented reduce of the records (sad_reduce.cuh): a scan of the
+//     per-site record counts and k_rec_scatter, which files the records by
+//     site;
+//  3. k_site_step, one thread per site: the exact sum of the site's records,
+//     the chain rule to the 11 gradients,
 //     Adam with the paper's clamps (Sec. 6.1), and the prepared table of the
 //     updated site for the next iteration; its blocks also take the
 //     per-image mean loss (fixed-order sums) and advance each image's state
 //     row.
-// Each image uses its own site range, pixel range, injection seed and
-// fixed-point scale, so an image's result does not depend on the rest of the
-// batch.
+// Each image uses its own site range, pixel range and injection seed, and a
+// site's sum depends on its own records only, so an image's result does not
+// depend on the rest of the batch.
 #include <cmath>
 
 #include "sad_adam.cuh"
 #include "sad_blend.cuh"
 #include "sad_host.h"
+#include "sad_reduce.cuh"
 #include "sad_tile.cuh"
 #include "sad_topk.cuh"
 
@@ -84,6 +88,7 @@ __device__ __forceinline__ TileCtx tile_ctx(const BatchDesc& d, int b, uint32_t 
   c.y0 = static_cast<int>(lt / im.tiles_x) * (kTileThreads / d.tw);
   c.pix_off = im.pix_off;
   c.sr = SiteRange{im.site_lo, im.site_n};
+  c.site_cum = im.site_cum;
   c.tile = tile;
   c.img = static_cast<uint32_t>(b);
   c.two_over_P = im.two_over_P;
@@ -147,7 +152,10 @@ __global__ void __launch_bounds__(kTileThreads, UPDATE_ONLY ? 3 : 4)
   }
   if (!UPDATE_ONLY) {
     __syncthreads();  // every thread's queue is drained before the tables overwrite it
-    tile_body<K, kModeGrad, true, TW>(c, io, ids, lk, sm.t);
+    TileIO tio = io;
+    tio.lists = map_out;  // this thread's own pixel's lists, written just above
+    tio.lists_P = Ptot;
+    tile_body<K, kModeGrad, true, TW>(c, tio, ids, lk, sm.t);
   }
 }
 
@@ -180,7 +188,10 @@ __global__ void __launch_bounds__(kTileThreads, 3)
 #pragma unroll
   for (int k = 0; k < K; ++k) lk[k] = 0.f;
   __shared__ TileShared<K, kModeGrad> sm;
-  tile_body<K, kModeGrad, false, TW>(c, io, ids, lk, sm);
+  TileIO tio = io;
+  tio.lists = map;
+  tio.lists_P = Ptot;
+  tile_body<K, kModeGrad, false, TW>(c, tio, ids, lk, sm);
 }
 
 // After a propagation-only pass: every image's pass index and map parity advance.
@@ -192,17 +203,23 @@ __global__ void k_state_pass(const BatchDesc d, int32_t* __restrict__ state) {
   st[2] ^= 1;
 }
 
+// The filed records of the step (the segmented reduce's output).
+struct SiteSums {
+  const uint32_t* start;  // local segment start per compacted site index
+  const uint32_t* boff;   // offset per block of kSegBlock sites; boff[nb] = records filed
+  const uint32_t* dir;    // record indices, by segment
+  const Record* rec;
+};
+
 // The ten exact statistic sums of site i -> 11 gradients -> Adam -> prepared
 // table for the next iteration.  adam = false only prepares.  One thread per
-// site of the table (slot ranges of the images only), and the accumulators
-// are cleared once read, so the next call finds them zero without a memset
-// over the whole site array.
+// site of the table (slot ranges of the images only; j is the compacted
+// index).
 __device__ __forceinline__ void site_work(const BatchDesc& d, uint32_t j, float* __restrict__ params,
                                           float* __restrict__ m, float* __restrict__ v,
                                           float4* __restrict__ geo, float4* __restrict__ met,
-                                          float4* __restrict__ col, int cap,
-                                          const WsHeader* __restrict__ hdr,
-                                          unsigned long long* __restrict__ accq, const AdamArgs& A,
+                                          float4* __restrict__ col, int cap, const float (&acc)[10],
+                                          bool any, const AdamArgs& A,
                                           const float2* __restrict__ bias,
                                           float* __restrict__ grads_out, bool adam) {
   const int b = image_of_slot(d, j);
@@ -221,18 +238,6 @@ __device__ __forceinline__ void site_work(const BatchDesc& d, uint32_t j, float*
     }
   }
   if (adam) {
-    float acc[10];
-    bool any = false;
-#pragma unroll
-    for (int k = 0; k < 10; ++k) {
-      const long long q = static_cast<long long>(accq[k * c + i]);
-      any |= q != 0;
-      acc[k] = static_cast<float>(static_cast<double>(q) * pow2(-fixed_shift(hdr->pmax[b][k])));
-    }
-    if (any) {
-#pragma unroll
-      for (int k = 0; k < 10; ++k) accq[k * c + i] = 0ull;
-    }
     float g[kNParams];
 #pragma unroll
     for (int k = 0; k < kNParams; ++k) g[k] = 0.f;
@@ -279,7 +284,7 @@ __device__ __forceinline__ void site_work(const BatchDesc& d, uint32_t j, float*
     }
   }
   prepare_site(p[PX], p[PY], p[PLOGTAU], p[PR], p[PCR], p[PCG], p[PCB], p[PUX], p[PUY], p[PA],
-               p[PB], im.s, geo[i], met[i], col[i]);
+               p[PB], im.s, geo[i], met[i], col[i], col[c + i], col[2 * c + i]);
 }
 
 // The step's finish for image b: its mean loss from the tile losses (fixed
@@ -315,20 +320,24 @@ __device__ __forceinline__ void finish_image(const BatchDesc& d, int b, const fl
 __global__ void k_site_step(const BatchDesc d, float* __restrict__ params, float* __restrict__ m,
                             float* __restrict__ v, float4* __restrict__ geo,
                             float4* __restrict__ met, float4* __restrict__ col, int cap,
-                            const WsHeader* __restrict__ hdr,
-                            unsigned long long* __restrict__ accq, AdamArgs A,
+                            const SiteSums S, AdamArgs A,
                             const float2* __restrict__ bias, float* __restrict__ grads_out,
                             bool adam, const float* __restrict__ tile_loss, float* __restrict__ loss,
                             int32_t* __restrict__ state) {
   __shared__ float s_w[8];
   const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < d.n_sites) site_work(d, j, params, m, v, geo, met, col, cap, hdr, accq, A, bias, grads_out, adam);
+  // the site's exact record sums: every lane of the warp takes part (a site
+  // with many records is summed by the whole warp)
+  float acc[10];
+  bool any = false;
+  if (adam) any = site_exact_sums<10>(j < d.n_sites, j, d.n_sites, S.start, S.boff, S.dir, S.rec, acc) != 0u;
+  if (j < d.n_sites) site_work(d, j, params, m, v, geo, met, col, cap, acc, any, A, bias, grads_out, adam);
   if (tile_loss != nullptr)
     for (int b = blockIdx.x; b < d.B; b += gridDim.x) finish_image(d, b, tile_loss, loss, state, s_w);
 }
 
-__global__ void __launch_bounds__(256) k_decode_batch(const BatchDesc d, const float4* __restrict__ geo,
-                                                      const float4* __restrict__ met,
+__global__ void __launch_bounds__(256) k_decode_batch(const BatchDesc d, const float4* __restrict__ ba,
+                                                      const float4* __restrict__ bb,
                                                       const float4* __restrict__ col,
                                                       const uint4* __restrict__ map, size_t Ptot,
                                                       int K, const float2* __restrict__ xy,
@@ -348,9 +357,9 @@ __global__ void __launch_bounds__(256) k_decode_batch(const BatchDesc d, const f
     const size_t q = im.pix_off + static_cast<size_t>(cy) * im.W + cx;
     const SiteRange sr{im.site_lo, im.site_n};
     switch (K) {
-      case 4: c = blend_planes<1>(map, Ptot, q, p.x, p.y, sr, geo, met, col); break;
-      case 8: c = blend_planes<2>(map, Ptot, q, p.x, p.y, sr, geo, met, col); break;
-      default: c = blend_planes<4>(map, Ptot, q, p.x, p.y, sr, geo, met, col); break;
+      case 4: c = blend_planes<1>(map, Ptot, q, p.x, p.y, sr, ba, bb, col); break;
+      case 8: c = blend_planes<2>(map, Ptot, q, p.x, p.y, sr, ba, bb, col); break;
+      default: c = blend_planes<4>(map, Ptot, q, p.x, p.y, sr, ba, bb, col); break;
     }
   }
   rgb[3 * i] = c.x;
@@ -395,7 +404,7 @@ __global__ void k_insert_pixels(const uint4* __restrict__ src_map, const float* 
 }
 
 struct StepLayout {
-  size_t hdr, tile_loss, acc, bias, records, total;
+  size_t hdr, cnt, tile_loss, bias, start, bsums, dir, records, total;
   uint32_t max_records;
 };
 
@@ -408,13 +417,17 @@ static StepLayout step_layout(uint32_t n_tiles, uint64_t total_pixels, int K, in
   if (max_records <= 0 && mr < 128ull * n_tiles) mr = 128ull * n_tiles;
   if (mr > 0xfffffff0ull) mr = 0xfffffff0ull;
   L.max_records = static_cast<uint32_t>(mr);
-  // the accumulators keep their offset whatever the table (they must stay
-  // zero between calls)
+  // the per-site record counts keep their offset whatever the table (they
+  // must stay zero between calls: the scatter counts them back down)
+  const size_t c = static_cast<size_t>(total_cap);
   size_t o = 0;
   L.hdr = o;       o = al256(o + sizeof(WsHeader));
-  L.acc = o;       o = al256(o + sizeof(unsigned long long) * 10 * static_cast<size_t>(total_cap));
+  L.cnt = o;       o = al256(o + sizeof(uint32_t) * c);
   L.tile_loss = o; o = al256(o + sizeof(float) * n_tiles);
   L.bias = o;      o = al256(o + sizeof(float2) * kMaxImages);
+  L.start = o;     o = al256(o + sizeof(uint32_t) * c);
+  L.bsums = o;     o = al256(o + sizeof(uint32_t) * (seg_blocks(c) + 1));
+  L.dir = o;       o = al256(o + sizeof(uint32_t) * L.max_records);
   L.records = o;   o = al256(o + sizeof(Record) * L.max_records);
   L.total = o;
   return L;
@@ -503,7 +516,7 @@ int sad_prepare_batch(const sad_batch_image* images, int32_t B, const float* par
   AdamArgs A{};
   { TraceScope tr_(as_stream(stream), "k_site_step"); k_site_step<<<(d.n_sites + 255) / 256, 256, 0, as_stream(stream)>>>(
       d, const_cast<float*>(params), nullptr, nullptr, p4, p4 + total_capacity,
-      p4 + 2 * static_cast<size_t>(total_capacity), total_capacity, nullptr, nullptr, A, nullptr,
+      p4 + 2 * static_cast<size_t>(total_capacity), total_capacity, SiteSums{}, A, nullptr,
       nullptr, false, nullptr, nullptr, nullptr); }
   return check_launch("sad_prepare_batch");
 }
@@ -541,8 +554,10 @@ int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t 
   }
   StepLayout L = L1;
   {
-    const uint64_t per = sizeof(Record);
-    uint64_t mr = 1 + (workspace_bytes - L1.total) / per;
+    // per record: its 48 bytes and its directory entry; the two regions'
+    // 256-byte alignment can hide up to 512 bytes, so start above and step down
+    const uint64_t per = sizeof(Record) + sizeof(uint32_t);
+    uint64_t mr = 1 + (workspace_bytes - L1.total + 512) / per;
     if (mr > 0xfffffff0ull) mr = 0xfffffff0ull;
     for (int it = 0; it < 64 && mr > 1; ++it, --mr) {
       const StepLayout T = step_layout(d.n_tiles, static_cast<uint64_t>(total_pixels), K,
@@ -557,7 +572,10 @@ int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t 
   char* base = static_cast<char*>(workspace);
   WsHeader* hdr = reinterpret_cast<WsHeader*>(base + L.hdr);
   float* tile_loss = reinterpret_cast<float*>(base + L.tile_loss);
-  unsigned long long* accq = reinterpret_cast<unsigned long long*>(base + L.acc);
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(base + L.cnt);
+  uint32_t* start = reinterpret_cast<uint32_t*>(base + L.start);
+  uint32_t* bsums = reinterpret_cast<uint32_t*>(base + L.bsums);
+  uint32_t* dir = reinterpret_cast<uint32_t*>(base + L.dir);
   Record* rec = reinterpret_cast<Record*>(base + L.records);
   const cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st);
   if (e != cudaSuccess) {
@@ -576,6 +594,7 @@ int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t 
   io.records = rec;
   io.max_records = L.max_records;
   io.hdr = hdr;
+  io.site_cnt = cnt;
   float2* bias = reinterpret_cast<float2*>(base + L.bias);
   io.bias = bias;
   io.beta1 = hp->beta1;
@@ -616,8 +635,12 @@ int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t 
 #undef SAD_KEEP
   }
   if (int r = check_launch("k_step_tile / k_keep_tile")) return r;
-  { TraceScope tr_(st, "k_seg_accum"); k_seg_accum<10><<<152 * 8, 256, 0, st>>>(rec, hdr, L.max_records, total_capacity, accq); }
-  if (int r = check_launch("k_seg_accum")) return r;
+  // the segmented reduce: segment starts of the batch's sites (compacted
+  // index), records filed by site
+  run_seg_scan(cnt, d.n_sites, start, bsums, st);
+  { TraceScope tr_(st, "k_rec_scatter"); k_rec_scatter<<<152 * 8, 256, 0, st>>>(rec, hdr, L.max_records, start, bsums, cnt, dir); }
+  if (int r = check_launch("k_rec_scatter")) return r;
+  const SiteSums S{start, bsums, dir, rec};
   const AdamArgs A = adam_args(hp);
   {
     // the site step also finishes the step (per-image loss, state rows)
@@ -625,7 +648,7 @@ int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t 
     TraceScope tr_(st, "k_site_step");
     k_site_step<<<grid, 256, 0, st>>>(d, params, m, v, p4, p4 + total_capacity,
                                       p4 + 2 * static_cast<size_t>(total_capacity), total_capacity,
-                                      hdr, accq, A, bias, grads_out, true, tile_loss, loss, image_state);
+                                      S, A, bias, grads_out, true, tile_loss, loss, image_state);
   }
   return check_launch("k_site_step");
 }
@@ -712,7 +735,8 @@ int sad_decode_batch(const sad_batch_image* images, int32_t B, int32_t K, const 
     return einval("sad_decode_batch: misaligned pointer");
   const float4* p4 = reinterpret_cast<const float4*>(prep);
   { TraceScope tr_(as_stream(stream), "k_decode_batch"); k_decode_batch<<<static_cast<unsigned>((n + 255) / 256), 256, 0, as_stream(stream)>>>(
-      d, p4, p4 + total_capacity, p4 + 2 * static_cast<size_t>(total_capacity),
+      d, p4 + 3 * static_cast<size_t>(total_capacity), p4 + 4 * static_cast<size_t>(total_capacity),
+      p4 + 2 * static_cast<size_t>(total_capacity),
       reinterpret_cast<const uint4*>(map), static_cast<size_t>(total_pixels), K,
       reinterpret_cast<const float2*>(xy), query_image, n, rgb); }
   return check_launch("k_decode_batch");

@@ -10,13 +10,15 @@
 //     the render's max logit, 1/Z and blend.  It then forms its upstream
 //     gradient g (given, or 2(c - I)/P for the fused MSE loss);
 //  2. the tile's distinct sites get slots in a shared hash table (the paper's
-//     multiplicative hash, linear probing), one probe per group of lanes that
-//     list the same id at the same rank; each warp ORs its lanes into its own
-//     word of a per-slot pixel mask (order independent);
+//     multiplicative hash, linear probing), every lane probing for each of
+//     its entries; each lane ORs its bit into its warp's word of a per-slot
+//     pixel mask (order independent);
 //  3. the masks give each slot a stable, pixel-ordered pair list; one warp
 //     walks a slot's list 32 pairs at a time with the site's parameters in
 //     registers and a fixed-order recursive-halving reduction sums the lane
-//     partials into ten statistics per (site, tile), written as one record.
+//     partials into ten statistics per (site, tile), written as one record,
+//     and counts the record for its site (the per-site sums are the
+//     segmented reduce of sad_reduce.cuh).
 //     If the table fills, the remaining sites are handled in further rounds.
 #pragma once
 
@@ -36,7 +38,7 @@ constexpr int kModeStats = 1;
 
 struct alignas(16) Record {
   uint32_t site;  // global site id
-  uint32_t img;   // image index (selects the fixed-point scale)
+  uint32_t cj;    // compacted site index of the launch (its segment of the reduction)
   float acc[10];
 };
 static_assert(sizeof(Record) == 48, "record layout");
@@ -47,9 +49,8 @@ struct WsHeader {
   uint32_t cursor;    // records written
   uint32_t overflow;  // records that did not fit
   uint32_t pad[62];
-  uint32_t pmax[kMaxImages][16];  // per image and statistic: bits of the largest |value|
 };
-static_assert(sizeof(WsHeader) == 256 + 4 * 16 * kMaxImages, "header layout");
+static_assert(sizeof(WsHeader) == 256, "header layout");
 
 // ---------------------------------------------------------------------------
 // block-wide exclusive scan of a 64-bit value over 256 threads (fixed order)
@@ -125,6 +126,7 @@ struct TileCtx {
   int x0, y0;        // tile origin inside the image
   size_t pix_off;    // first pixel of the image in the packed per-pixel arrays
   SiteRange sr;      // the image's site ids
+  uint32_t site_cum; // compacted index of the image's first site (sites of the images before it)
   uint32_t tile;     // global tile index (slot of the tile loss)
   uint32_t img;      // image index (< kMaxImages)
   float two_over_P;  // 2 / (H W): gradient of the mean loss
@@ -139,10 +141,16 @@ struct TileIO {
   Record* records;
   uint32_t max_records;
   WsHeader* hdr;
+  uint32_t* site_cnt;  // records per compacted site index (incremented per stored record)
   float2* bias = nullptr;  // training step: per image {1 - beta1^t, 1 - beta2^t} for the site step
   float beta1 = 0.f, beta2 = 0.f;
   const float* fwd = nullptr;     // saved forward: float32[2][P] {max logit, 1/Z} per pixel
   const float* rgb_in = nullptr;  // saved forward: the blend c per pixel, float32[P][3]
+  // the tile's lists in global memory (K/4 uint4 planes of lists_P entries,
+  // indexed by the packed pixel index), re-read by the slot rounds instead of
+  // keeping the ids in registers through the tile body
+  const uint4* lists = nullptr;
+  size_t lists_P = 0;
 };
 
 // Adjoint (MODE = kModeGrad) or budget statistics (kModeStats) of one tile
@@ -165,6 +173,7 @@ struct TileShared {
   uint32_t cnt[kSlots];
   uint32_t off[kSlots];
   uint32_t rix[kSlots];
+  uint8_t slot8[K][kTileThreads];  // this round's slot of each listed entry
   uint8_t list[kTileThreads * K];
   // per pixel.  gradient mode: {m, 1/Z, g.cbar, gx}, {gy, gz, -, -};
   // statistics mode: {m, 1/Z, cbar.x, cbar.y}, {cbar.z, I}, {c' of the
@@ -176,7 +185,6 @@ struct TileShared {
   uint64_t scan[kW];
   float red[kW];
   uint32_t base;
-  uint32_t pmax[10];
 };
 
 template <int K, int MODE, bool HAVE_L = false, int TW = kTileSide, bool SAVED = false>
@@ -208,7 +216,6 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
   auto& s_scan = sm.scan;
   auto& s_red = sm.red;
   auto& s_base = sm.base;
-  auto& s_pmax = sm.pmax;
 
   const int t = threadIdx.x;
   const int lane = t & 31, warp = t >> 5;
@@ -222,7 +229,6 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
   const size_t q = inimg ? c.pix_off + static_cast<size_t>(y) * W + x : 0;
   const SiteRange sr = c.sr;
   const float px = x + 0.5f, py = y + 0.5f;
-  if (t < 10) s_pmax[t] = 0u;
 
   // ---- 1. per-pixel forward (entries outside the image's sites are invalid)
 #pragma unroll
@@ -411,36 +417,47 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
 
   // ---- 2..3. rounds: slot assignment, stable pair lists, warp per slot ---
   uint32_t pending = vm;
-  uint32_t slot[K];
+  uint32_t got = 0u;      // entries that got a slot this round (slots in sm.slot8)
   const uint32_t lt_mask = (1u << lane) - 1u;
   for (;;) {
+    // this round's ids from the lists in memory (the same entries as ids[],
+    // validated the same way; ids[] is dead after the forward)
+    uint32_t idr[K];
+#pragma unroll
+    for (int j = 0; j < K / 4; ++j) {
+      uint4 w = make_uint4(kInvalid, kInvalid, kInvalid, kInvalid);
+      if (inimg) w = ldg(&io.lists[j * io.lists_P + q]);
+      idr[4 * j] = w.x;
+      idr[4 * j + 1] = w.y;
+      idr[4 * j + 2] = w.z;
+      idr[4 * j + 3] = w.w;
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) idr[k] = sr.has(idr[k]) ? idr[k] : kInvalid;
     for (int i = t; i < kSlots; i += kTileThreads) {
       s_keys[i] = kInvalid;
 #pragma unroll
       for (int w = 0; w < kWarps; ++w) s_mask[w][i] = 0u;
     }
     __syncthreads();
-    // Lanes holding the same id at list position k form a group (neighbouring
-    // pixels mostly list the same sites at the same ranks): its lowest lane
-    // probes the table once and ORs the whole group's bits into the warp's
-    // own mask word, so no two lanes of one instruction hit the same shared
-    // address.  OR is order independent, so the masks (and the pair lists
-    // built from them) are deterministic.
+    // Every lane probes the table for each of its pending entries and ORs
+    // its own bit into its warp's mask word of the slot (lanes of one warp
+    // that list the same site at the same rank hit the same word; the shared
+    // atomics serialise them, which costs less than grouping the lanes
+    // first).  OR is order independent, so the masks (and the pair lists
+    // built from them) are deterministic.  Slot numbers are kept as bytes.
+    got = 0u;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const bool want = (pending >> k & 1u) != 0u;
-      const uint32_t idk = want ? ids[k] : kInvalid;
-      const unsigned grp = __match_any_sync(0xffffffffu, idk);
-      const int leader = __ffs(grp) - 1;
-      uint32_t sl = kNone;
-      if (want && lane == leader) {
-        sl = probe_slot(idk, s_keys);
-        if (sl != kNone) atomicOr(&s_mask[warp][sl], grp);
+      if ((pending >> k & 1u) != 0u) {
+        const uint32_t sl = probe_slot(idr[k], s_keys);
+        if (sl != kNone) {
+          atomicOr(&s_mask[warp][sl], 1u << lane);
+          pending &= ~(1u << k);
+          got |= 1u << k;
+          sm.slot8[k][t] = static_cast<uint8_t>(sl);
+        }
       }
-      sl = __shfl_sync(0xffffffffu, sl, leader);
-      if (!want) sl = kNone;
-      if (sl != kNone) pending &= ~(1u << k);
-      slot[k] = sl;
     }
     __syncthreads();
     uint64_t packed = 0;
@@ -464,8 +481,8 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const uint32_t sl = slot[k];
-      if (sl != kNone) {
+      if ((got >> k & 1u) != 0u) {
+        const uint32_t sl = sm.slot8[k][t];
         const uint32_t pos = s_off[sl] + s_wpre[warp][sl] + __popc(s_mask[warp][sl] & lt_mask);
         s_list[pos] = static_cast<uint8_t>(t);
       }
@@ -556,13 +573,14 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
         if (ridx < max_records) {
           float* dst = reinterpret_cast<float*>(&records[ridx]);
           if (lane == 0) {
+            const uint32_t cj = c.site_cum + (id - sr.lo);
             dst[0] = __uint_as_float(id);
-            dst[1] = __uint_as_float(c.img);
+            dst[1] = __uint_as_float(cj);
+            atomicAdd(&io.site_cnt[cj], 1u);  // an integer count, not a value
           }
           if ((lane & 1) == 0 && stat < 10) {
             const float v = isfinite(tot) ? tot : 0.f;  // non-finite contributions are dropped
             dst[2 + stat] = v;
-            if (v != 0.f) atomicMax(&s_pmax[stat], __float_as_uint(fabsf(v)));
           }
         } else if (lane == 0) {
           hdr->overflow = 1u;
@@ -570,47 +588,6 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
       }
     }
     if (!__syncthreads_or(pending != 0u)) break;
-  }
-  if (t < 10 && s_pmax[t]) atomicMax(&hdr->pmax[c.img][t], s_pmax[t]);
-}
-
-// ---------------------------------------------------------------------------
-// exact fixed-point per-site sums of per-tile records: statistic j of every
-// record of image b is scaled by 2^S, S = 61 - e - 32 with max |value| < 2^e
-// over that image's records of statistic j (fewer than 2^32 records), rounded
-// to an int64 and added with integer atomics, so each site's total is the
-// same bit pattern whatever the order of the additions (and whatever else is
-// in the batch); its rounding error is below 2^-29 of that maximum.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ int fixed_shift(uint32_t pmax_bits) {
-  if (pmax_bits == 0u) return 0;
-  int e;
-  frexpf(__uint_as_float(pmax_bits), &e);  // pmax < 2^e; fewer than 2^32 records
-  return 61 - e - 32;
-}
-
-__device__ __forceinline__ double pow2(int s) {  // exact 2^s for |s| < 1000
-  return __longlong_as_double(static_cast<long long>(1023 + s) << 52);
-}
-
-template <int NV>
-static __global__ void k_seg_accum(const Record* __restrict__ rec, const WsHeader* __restrict__ hdr,
-                            uint32_t max_records, int cap, unsigned long long* __restrict__ acc) {
-  const uint32_t n = min(hdr->cursor, max_records);
-  const size_t c = static_cast<size_t>(cap);
-  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-    const float4* src = reinterpret_cast<const float4*>(&rec[r]);
-    const float4 r0 = src[0], r1 = src[1], r2 = src[2];
-    const uint32_t site = __float_as_uint(r0.x);
-    const uint32_t img = __float_as_uint(r0.y);
-    const float v[10] = {r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x, r2.y, r2.z, r2.w};
-#pragma unroll
-    for (int j = 0; j < NV; ++j) {
-      if (v[j] != 0.f) {
-        const long long q = __double2ll_rn(static_cast<double>(v[j]) * pow2(fixed_shift(hdr->pmax[img][j])));
-        atomicAdd(&acc[j * c + site], static_cast<unsigned long long>(q));
-      }
-    }
   }
 }
 

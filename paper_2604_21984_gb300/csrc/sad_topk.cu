@@ -11,14 +11,15 @@ namespace sad {
 // ---------------------------------------------------------------------------
 __global__ void k_prepare(const float* __restrict__ params, int cap, float s,
                           float4* __restrict__ geo, float4* __restrict__ met,
-                          float4* __restrict__ col) {
+                          float4* __restrict__ col, float4* __restrict__ ba,
+                          float4* __restrict__ bb) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= cap) return;
   const size_t c = static_cast<size_t>(cap);
   prepare_site(params[PX * c + i], params[PY * c + i], params[PLOGTAU * c + i], params[PR * c + i],
                params[PCR * c + i], params[PCG * c + i], params[PCB * c + i], params[PUX * c + i],
                params[PUY * c + i], params[PA * c + i], params[PB * c + i], s, geo[i], met[i],
-               col[i]);
+               col[i], ba[i], bb[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -254,7 +255,9 @@ int sad_prepare_sites(const float* params, int32_t capacity, int32_t H, int32_t 
   const int bs = 256;
   { TraceScope tr_(as_stream(stream), "k_prepare"); k_prepare<<<(capacity + bs - 1) / bs, bs, 0, as_stream(stream)>>>(params, capacity, s, p4,
                                                                      p4 + capacity,
-                                                                     p4 + 2 * (size_t)capacity); }
+                                                                     p4 + 2 * (size_t)capacity,
+                                                                     p4 + 3 * (size_t)capacity,
+                                                                     p4 + 4 * (size_t)capacity); }
   return check_launch("k_prepare");
 }
 

@@ -53,6 +53,11 @@ class EncodeConfig:
     extra: dict = field(default_factory=dict)
 
 
+def _nullctx():
+    import contextlib
+    return contextlib.nullcontext()
+
+
 def jump_code(t: int, H: int, W: int) -> int:
     """Step parameter of pass t: jump s_t = max(1, B / 2^(min(t, log2 B - 1) + 1))
     in the high 16 bits, t in the low 16 bits (Sec. 4.3; App. step encoding)."""
@@ -220,9 +225,16 @@ class Encoder:
         self.maps.reverse()
         self.t_pass += 1
 
+    def _follow_current_stream(self):
+        """Order the encoder's own stream after the work torch has queued on
+        the current stream (the zero-filled arrays, the state row)."""
+        if self.stream is not None:
+            self.stream.wait_stream(torch.cuda.current_stream(self.dev))
+
     def init(self):
         """Gradient-weighted sites and the JFA warm-up of the field."""
         c = self.cfg
+        self._follow_current_stream()
         if c.s_grid > 1:
             H, W = self.H, self.W
             s = 1.0 / max(H, W)
@@ -241,7 +253,8 @@ class Encoder:
         if c.fused:
             # Adam step 1 next; pass indices continue after the warm-up's; the
             # current map is bufs[0] (state parity 0)
-            self.state.copy_(torch.tensor([[1, self.t_pass, 0, 0]], dtype=torch.int32))
+            with torch.cuda.stream(self.stream) if self.stream is not None else _nullctx():
+                self.state.copy_(torch.tensor([[1, self.t_pass, 0, 0]], dtype=torch.int32))
             self.bufs = (self.maps[0], self.maps[1])
             self._par = 0
             self._call = capi.TrainStepCall(self.table, c.K, c.J, self.params, self.m, self.v, self.prep,
@@ -334,7 +347,8 @@ class Encoder:
             self._densify_calls(self.bufs[key])   # the first event also loads its kernels
             self._g_dense["warm"] = True
         else:
-            g.replay()
+            with torch.cuda.stream(self.stream):   # a graph replays on the current stream
+                g.replay()
 
     def _capture(self, calls):
         g = torch.cuda.CUDAGraph()
@@ -355,7 +369,8 @@ class Encoder:
         if self._g_step is None:
             self._g_step = self._capture(lambda: self._call(self.stream))
         self.it += 1
-        self._g_step.replay()
+        with torch.cuda.stream(self.stream):   # a graph replays on the current stream
+            self._g_step.replay()
         self._par ^= 1
         self.t_pass += 1
         self.maps = [self.bufs[self._par], self.bufs[1 - self._par]]
@@ -378,7 +393,10 @@ class Encoder:
     def render(self):
         capi.sad_prepare_sites(self.params, self.H, self.W, self.prep, self.stream)
         rgb = torch.empty((self.H, self.W, 3), dtype=torch.float32, device=self.dev)
+        self._follow_current_stream()
         capi.sad_render(self.prep, self.cap, self.H, self.W, self.cfg.K, self.maps[0], rgb, self.stream)
+        if self.stream is not None:
+            torch.cuda.current_stream(self.dev).wait_stream(self.stream)
         return rgb
 
     def _loss_value(self) -> float:

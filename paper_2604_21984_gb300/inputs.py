@@ -394,3 +394,44 @@ def resident_sets(seed: int, n: int, sites=(16384, 1 << 20), sites_per_pixel: fl
         side = max(1, int(round(math.sqrt(N / sites_per_pixel))))
         out.append((side, side, N, int(g.integers(1 << 31))))
     return out
+
+
+# ----------------------------------------------------------------------------
+# 1-D signals (Sec. "1D Signal Fitting")
+# ----------------------------------------------------------------------------
+
+def signals_1d(B: int, L: int, seed: int) -> np.ndarray:
+    """B synthetic 1-D targets of L samples, float32[B, L]: the three target
+    families of the paper's 1-D experiment, chosen per signal with seeded
+    random parameters -- a smooth sine, a step plus a sine, and a
+    multi-frequency periodic signal (three sines, frequencies 1..12 periods
+    per signal).  Samples at t = (k + 0.5) / L."""
+    g = rng(seed)
+    t = (np.arange(L) + 0.5) / L
+    kind = g.integers(0, 3, B)
+    f = g.uniform(1.0, 4.0, (B, 1))
+    ph = g.uniform(0.0, 2 * math.pi, (B, 3))
+    amp = g.uniform(0.2, 0.5, (B, 1))
+    smooth = 0.5 + amp * np.sin(2 * math.pi * f * t[None, :] + ph[:, :1])
+    edge = g.uniform(0.25, 0.75, (B, 1))
+    lo, hi = g.uniform(0.1, 0.4, (B, 1)), g.uniform(0.6, 0.9, (B, 1))
+    step = np.where(t[None, :] < edge, lo, hi) + 0.1 * np.sin(2 * math.pi * 3 * f * t[None, :] + ph[:, 1:2])
+    fr = g.uniform(1.0, 12.0, (B, 3))
+    w = g.uniform(0.05, 0.25, (B, 3))
+    multi = 0.5 + sum(w[:, j:j + 1] * np.sin(2 * math.pi * fr[:, j:j + 1] * t[None, :] + ph[:, j:j + 1])
+                      for j in range(3))
+    out = np.where((kind == 0)[:, None], smooth, np.where((kind == 1)[:, None], step, multi))
+    return out.astype(np.float32)
+
+
+def sites_1d(targets: np.ndarray, N: int) -> np.ndarray:
+    """Initial 1-D sites for float[B, L] targets, float32[4, B*N] planes (p, c,
+    log_tau, r): N sites per signal at the centres of N equal cells, each
+    taking the target's value at its sample, tau with tau s (L/N) = 4, r = 0."""
+    B, L = targets.shape
+    p = np.zeros((4, B, N), dtype=np.float64)
+    pos = (np.arange(N) + 0.5) * L / N
+    p[0] = pos[None, :]
+    p[1] = targets[:, np.minimum(pos.astype(np.int64), L - 1)]
+    p[2] = math.log(4.0 * N)
+    return p.reshape(4, B * N).astype(np.float32)

@@ -258,7 +258,7 @@ class Server:
         Pmax = c.max_side * c.max_side
         nmax = encode_sites(c.max_side, c.max_side, c.sites_per_pixel)
         self._st_params = torch.empty(capi.N_PARAMS * nmax, **f32)
-        self._st_prep = torch.empty(12 * nmax, **f32)
+        self._st_prep = torch.empty(4 * capi.PREP_PLANES * nmax, **f32)
         self._st_maps = [torch.empty(K * Pmax, dtype=torch.int32, device=self.dev) for _ in range(2)]
         # decode staging
         self._dq_xy = torch.empty((c.max_decode_per_tick, 2), **f32)
@@ -430,7 +430,7 @@ class Server:
         H, W, n = entry["H"], entry["W"], entry["capacity"]
         P = H * W
         params = self._st_params[:capi.N_PARAMS * n].view(capi.N_PARAMS, n)
-        prep = self._st_prep[:12 * n]
+        prep = self._st_prep[:4 * capi.PREP_PLANES * n]
         ma = self._st_maps[0][:c.K * P].view(c.K // 4, P, 4)
         mb = self._st_maps[1][:c.K * P].view(c.K // 4, P, 4)
         target = req.image.contiguous()

@@ -14,7 +14,7 @@ HEADER = os.path.join(ROOT, "include", "sad.h")
 def _declared():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(sad_[a-z_0-9]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(sad(?:1d)?_[a-z_0-9]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -34,7 +34,7 @@ def test_every_declared_symbol_is_exported(L):
 
 
 def test_status_strings_and_version(L):
-    assert L.sad_abi_version() == 5
+    assert L.sad_abi_version() == 6
     assert L.sad_status_string(0) == b"ok"
     assert L.sad_status_string(1) == b"invalid argument"
     assert L.sad_status_string(99) == b"unknown status"
