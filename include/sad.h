@@ -469,7 +469,7 @@ typedef struct sad_batch_image {
 
 /* Workspace bytes of sad_train_step (0 = invalid table); same record rule as
  * sad_backward_workspace_bytes with P = total_pixels.  The workspace must be
- * ZEROED once when allocated: its per-site accumulators (at a fixed offset
+ * ZEROED once when allocated: its per-site record counts (at a fixed offset
  * that depends on total_capacity only) are cleared by each call after use,
  * so one workspace serves any sequence of tables over the same arrays.  A
  * call that returned an error may leave them dirty: zero the workspace again. */

@@ -145,16 +145,17 @@ __device__ __forceinline__ void grads_from_stats(const float (&acc)[10], float4 
 }
 
 // Per site (single image): the exact segment sums, then the chain rule.
-__global__ void k_site_grads(const float* __restrict__ params, const float4* __restrict__ geo,
+__global__ void __launch_bounds__(kSumThreads) k_site_grads(const float* __restrict__ params, const float4* __restrict__ geo,
                              const float4* __restrict__ met, int cap,
                              const uint32_t* __restrict__ start, const uint32_t* __restrict__ boff,
                              const uint32_t* __restrict__ dir, const Record* __restrict__ rec,
-                             float* __restrict__ grads) {
+                             const WsHeader* __restrict__ hdr, int L, float* __restrict__ grads) {
+  __shared__ WarpSums<10> s_ws[kSumThreads / 32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const size_t c = static_cast<size_t>(cap);
   float acc[10];
-  const uint32_t n = site_exact_sums<10>(i < cap, static_cast<uint32_t>(i), static_cast<uint32_t>(cap),
-                                         start, boff, dir, rec, acc);  // every lane takes part
+  const uint32_t n = warp_site_sums<10>(i < cap, static_cast<uint32_t>(i), static_cast<uint32_t>(cap), start, boff,
+                                        dir, rec, hdr->pmax[0], L, s_ws[threadIdx.x >> 5], acc);  // every lane takes part
   if (i >= cap) return;
   float out[kNParams];
 #pragma unroll
@@ -167,14 +168,16 @@ __global__ void k_site_grads(const float* __restrict__ params, const float4* __r
 }
 
 // Per site: the exact segment sums of the statistics (statistics mode).
-__global__ void k_site_stats(int cap, const uint32_t* __restrict__ start,
+__global__ void __launch_bounds__(kSumThreads) k_site_stats(int cap, const uint32_t* __restrict__ start,
                              const uint32_t* __restrict__ boff, const uint32_t* __restrict__ dir,
-                             const Record* __restrict__ rec, float* __restrict__ stats) {
+                             const Record* __restrict__ rec, const WsHeader* __restrict__ hdr, int L,
+                             float* __restrict__ stats) {
+  __shared__ WarpSums<8> s_ws[kSumThreads / 32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const size_t c = static_cast<size_t>(cap);
   float acc[8];
-  site_exact_sums<8>(i < cap, static_cast<uint32_t>(i), static_cast<uint32_t>(cap), start, boff, dir, rec,
-                     acc);  // every lane takes part
+  warp_site_sums<8>(i < cap, static_cast<uint32_t>(i), static_cast<uint32_t>(cap), start, boff, dir, rec,
+                    hdr->pmax[0], L, s_ws[threadIdx.x >> 5], acc);  // every lane takes part
   if (i >= cap) return;
 #pragma unroll
   for (int j = 0; j < 8; ++j) stats[j * c + i] = acc[j];
@@ -299,14 +302,15 @@ static int run_backward(const float* params, const float* prep, int cap, int H, 
   }
   if (cap == 0) return SAD_OK;
   // the segmented reduce: segment starts, records filed by site, exact sums
-  run_seg_scan(cnt, static_cast<uint32_t>(cap), start, bsums, st);
-  { TraceScope tr_(st, "k_rec_scatter"); k_rec_scatter<<<152 * 8, 256, 0, st>>>(rec, hdr, LL.max_records, start, bsums, cnt, dir); }
+  run_seg_scan(cnt, static_cast<uint32_t>(cap), start, bsums, hdr, st);
+  const int L = count_bits(LL.n_tiles);
+  { TraceScope tr_(st, "k_rec_scatter"); k_rec_scatter<<<152 * 8, 256, 0, st>>>(rec, hdr, LL.max_records, start, bsums, dir); }
   if (int r = check_launch("k_rec_scatter")) return r;
   if (stats_mode) {
-    { TraceScope tr_(st, "k_site_stats"); k_site_stats<<<(cap + 255) / 256, 256, 0, st>>>(cap, start, bsums, dir, rec, stats); }
+    { TraceScope tr_(st, "k_site_stats"); k_site_stats<<<(cap + kSumThreads - 1) / kSumThreads, kSumThreads, 0, st>>>(cap, start, bsums, dir, rec, hdr, L, stats); }
     return check_launch("k_site_stats");
   }
-  { TraceScope tr_(st, "k_site_grads"); k_site_grads<<<(cap + 255) / 256, 256, 0, st>>>(params, geo, met, cap, start, bsums, dir, rec, grads); }
+  { TraceScope tr_(st, "k_site_grads"); k_site_grads<<<(cap + kSumThreads - 1) / kSumThreads, kSumThreads, 0, st>>>(params, geo, met, cap, start, bsums, dir, rec, hdr, L, grads); }
   return check_launch("k_site_grads");
 }
 

@@ -1,7 +1,7 @@
 // Fused, batched training step (the paper's GPU-resident iteration, Sec. 5;
 // Sec. 6.3 epoch = one pass over all pixels) over up to kMaxImages images.
 //
-// One iteration is three kernels and one small memset, all on one stream.  Each
+// One iteration is five kernels and one small memset, all on one stream.  Each
 // image's counters (Adam step, pass index, which map buffer is current) live
 // in a device state row that the step itself advances, so a fixed set of
 // images always makes the same call, which is captured once in a CUDA graph
@@ -11,11 +11,12 @@
 //     lists, writes the new ones), then - on the lists just computed, still in
 //     registers - the fused render + MSE + adjoint of the tile (per-tile
 //     records, deterministic);
-//  2. the segmented reduce of the records (sad_reduce.cuh): a scan of the
+//  2. the segmented reduce of the records (sad_reduce.cuh): k_seg_scan of the
 //     per-site record counts and k_rec_scatter, which files the records by
 //     site;
-//  3. k_site_step, one thread per site: the exact sum of the site's records,
-//     the chain rule to the 11 gradients,
+//  3. k_site_step, one thread per site: the exact sum of the site's records
+//     (its warp shares out the records of its 32 sites), the chain rule to
+//     the 11 gradients,
 //     Adam with the paper's clamps (Sec. 6.1), and the prepared table of the
 //     updated site for the next iteration; its blocks also take the
 //     per-image mean loss (fixed-order sums) and advance each image's state
@@ -209,6 +210,7 @@ struct SiteSums {
   const uint32_t* boff;   // offset per block of kSegBlock sites; boff[nb] = records filed
   const uint32_t* dir;    // record indices, by segment
   const Record* rec;
+  const WsHeader* hdr;    // per image the scale of the sums
 };
 
 // The ten exact statistic sums of site i -> 11 gradients -> Adam -> prepared
@@ -295,14 +297,14 @@ __device__ __forceinline__ void finish_image(const BatchDesc& d, int b, const fl
   const BatchImg& im = d.img[b];
   const uint32_t n = (b + 1 < d.B ? d.img[b + 1].tile_off : d.n_tiles) - im.tile_off;
   float v = 0.f;
-  for (uint32_t i = threadIdx.x; i < n; i += 256) v += tile_loss[im.tile_off + i];
+  for (uint32_t i = threadIdx.x; i < n; i += kSumThreads) v += tile_loss[im.tile_off + i];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
     float sum = 0.f;
-    for (int w = 0; w < 8; ++w) sum += s_w[w];
+    for (int w = 0; w < kSumThreads / 32; ++w) sum += s_w[w];
     if (loss) loss[b] = sum / static_cast<float>(static_cast<double>(im.H) * im.W);
     int32_t* st = state + kStateWords * im.state;  // the image's step is done
     st[0] += 1;
@@ -316,21 +318,30 @@ __device__ __forceinline__ void finish_image(const BatchDesc& d, int b, const fl
 
 // Per site: gradient -> Adam -> prepared table; with tile_loss, the blocks
 // also do the step's per-image finish (no site step reads a state row, so
-// advancing them here is safe).  256 threads per block.
-__global__ void k_site_step(const BatchDesc d, float* __restrict__ params, float* __restrict__ m,
+// advancing them here is safe).  kSumThreads threads per block.
+__global__ void __launch_bounds__(kSumThreads, 4) k_site_step(const BatchDesc d, float* __restrict__ params, float* __restrict__ m,
                             float* __restrict__ v, float4* __restrict__ geo,
                             float4* __restrict__ met, float4* __restrict__ col, int cap,
                             const SiteSums S, AdamArgs A,
                             const float2* __restrict__ bias, float* __restrict__ grads_out,
                             bool adam, const float* __restrict__ tile_loss, float* __restrict__ loss,
                             int32_t* __restrict__ state) {
-  __shared__ float s_w[8];
+  __shared__ float s_w[kSumThreads / 32];
+  __shared__ WarpSums<10> s_ws[kSumThreads / 32];
   const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-  // the site's exact record sums: every lane of the warp takes part (a site
-  // with many records is summed by the whole warp)
+  // the site's exact record sums: every lane of the warp takes part (the
+  // warp's records are shared out evenly over its lanes)
   float acc[10];
   bool any = false;
-  if (adam) any = site_exact_sums<10>(j < d.n_sites, j, d.n_sites, S.start, S.boff, S.dir, S.rec, acc) != 0u;
+  if (adam) {
+    // the image's scale: its largest record values and its own tile count
+    // (not the batch's), so that its sums do not depend on the batch
+    const int b = j < d.n_sites ? image_of_slot(d, j) : 0;
+    const uint32_t nt = (b + 1 < d.B ? d.img[b + 1].tile_off : d.n_tiles) - d.img[b].tile_off;
+    const int L = 32 - __clz(nt > 0u ? nt : 1u);  // 2^L > nt
+    any = warp_site_sums<10, 2>(j < d.n_sites, j, d.n_sites, S.start, S.boff, S.dir, S.rec, S.hdr->pmax[b], L,
+                             s_ws[threadIdx.x >> 5], acc) != 0u;
+  }
   if (j < d.n_sites) site_work(d, j, params, m, v, geo, met, col, cap, acc, any, A, bias, grads_out, adam);
   if (tile_loss != nullptr)
     for (int b = blockIdx.x; b < d.B; b += gridDim.x) finish_image(d, b, tile_loss, loss, state, s_w);
@@ -418,7 +429,7 @@ static StepLayout step_layout(uint32_t n_tiles, uint64_t total_pixels, int K, in
   if (mr > 0xfffffff0ull) mr = 0xfffffff0ull;
   L.max_records = static_cast<uint32_t>(mr);
   // the per-site record counts keep their offset whatever the table (they
-  // must stay zero between calls: the scatter counts them back down)
+  // must stay zero between calls: the segment scan clears them)
   const size_t c = static_cast<size_t>(total_cap);
   size_t o = 0;
   L.hdr = o;       o = al256(o + sizeof(WsHeader));
@@ -514,7 +525,7 @@ int sad_prepare_batch(const sad_batch_image* images, int32_t B, const float* par
   if (!params || !prep || !aligned16(prep)) return einval("sad_prepare_batch: bad pointer");
   float4* p4 = reinterpret_cast<float4*>(prep);
   AdamArgs A{};
-  { TraceScope tr_(as_stream(stream), "k_site_step"); k_site_step<<<(d.n_sites + 255) / 256, 256, 0, as_stream(stream)>>>(
+  { TraceScope tr_(as_stream(stream), "k_site_step"); k_site_step<<<(d.n_sites + kSumThreads - 1) / kSumThreads, kSumThreads, 0, as_stream(stream)>>>(
       d, const_cast<float*>(params), nullptr, nullptr, p4, p4 + total_capacity,
       p4 + 2 * static_cast<size_t>(total_capacity), total_capacity, SiteSums{}, A, nullptr,
       nullptr, false, nullptr, nullptr, nullptr); }
@@ -637,16 +648,16 @@ int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t 
   if (int r = check_launch("k_step_tile / k_keep_tile")) return r;
   // the segmented reduce: segment starts of the batch's sites (compacted
   // index), records filed by site
-  run_seg_scan(cnt, d.n_sites, start, bsums, st);
-  { TraceScope tr_(st, "k_rec_scatter"); k_rec_scatter<<<152 * 8, 256, 0, st>>>(rec, hdr, L.max_records, start, bsums, cnt, dir); }
+  run_seg_scan(cnt, d.n_sites, start, bsums, hdr, st);
+  { TraceScope tr_(st, "k_rec_scatter"); k_rec_scatter<<<152 * 8, 256, 0, st>>>(rec, hdr, L.max_records, start, bsums, dir); }
   if (int r = check_launch("k_rec_scatter")) return r;
-  const SiteSums S{start, bsums, dir, rec};
+  const SiteSums S{start, bsums, dir, rec, hdr};
   const AdamArgs A = adam_args(hp);
   {
     // the site step also finishes the step (per-image loss, state rows)
-    const unsigned grid = d.n_sites > 0 ? (d.n_sites + 255) / 256 : 1;
+    const unsigned grid = d.n_sites > 0 ? (d.n_sites + kSumThreads - 1) / kSumThreads : 1;
     TraceScope tr_(st, "k_site_step");
-    k_site_step<<<grid, 256, 0, st>>>(d, params, m, v, p4, p4 + total_capacity,
+    k_site_step<<<grid, kSumThreads, 0, st>>>(d, params, m, v, p4, p4 + total_capacity,
                                       p4 + 2 * static_cast<size_t>(total_capacity), total_capacity,
                                       S, A, bias, grads_out, true, tile_loss, loss, image_state);
   }

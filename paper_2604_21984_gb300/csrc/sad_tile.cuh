@@ -37,7 +37,7 @@ constexpr int kModeGrad = 0;
 constexpr int kModeStats = 1;
 
 struct alignas(16) Record {
-  uint32_t site;  // global site id
+  uint32_t rank;  // place among its site's records (from the site's record count)
   uint32_t cj;    // compacted site index of the launch (its segment of the reduction)
   float acc[10];
 };
@@ -48,9 +48,11 @@ constexpr int kMaxImages = 64;
 struct WsHeader {
   uint32_t cursor;    // records written
   uint32_t overflow;  // records that did not fit
-  uint32_t pad[62];
+  uint32_t done;      // blocks of the segment scan that have finished
+  uint32_t pad[61];
+  uint32_t pmax[kMaxImages][16];  // per image and statistic: bits of the largest |record value|
 };
-static_assert(sizeof(WsHeader) == 256, "header layout");
+static_assert(sizeof(WsHeader) == 256 + 4 * 16 * kMaxImages, "header layout");
 
 // ---------------------------------------------------------------------------
 // block-wide exclusive scan of a 64-bit value over 256 threads (fixed order)
@@ -185,6 +187,7 @@ struct TileShared {
   uint64_t scan[kW];
   float red[kW];
   uint32_t base;
+  uint32_t pmax[10];  // the tile's largest |record value| per statistic (float bits)
 };
 
 template <int K, int MODE, bool HAVE_L = false, int TW = kTileSide, bool SAVED = false>
@@ -216,6 +219,7 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
   auto& s_scan = sm.scan;
   auto& s_red = sm.red;
   auto& s_base = sm.base;
+  auto& s_pmax = sm.pmax;
 
   const int t = threadIdx.x;
   const int lane = t & 31, warp = t >> 5;
@@ -229,6 +233,7 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
   const size_t q = inimg ? c.pix_off + static_cast<size_t>(y) * W + x : 0;
   const SiteRange sr = c.sr;
   const float px = x + 0.5f, py = y + 0.5f;
+  if (t < 10) s_pmax[t] = 0u;
 
   // ---- 1. per-pixel forward (entries outside the image's sites are invalid)
 #pragma unroll
@@ -417,6 +422,7 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
 
   // ---- 2..3. rounds: slot assignment, stable pair lists, warp per slot ---
   uint32_t pending = vm;
+  uint32_t pm = 0u;  // lanes 2i: the largest |value| of statistic i in this warp's records (float bits)
   uint32_t got = 0u;      // entries that got a slot this round (slots in sm.slot8)
   const uint32_t lt_mask = (1u << lane) - 1u;
   for (;;) {
@@ -479,6 +485,15 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
     }
     if (t == 0) s_base = atomicAdd(&hdr->cursor, static_cast<uint32_t>(total >> 32));
     __syncthreads();
+    // thread t files slot t's record: its index, its site's compacted index
+    // and its place among the site's records (the count's old value), taken
+    // here so that the atomic's round trip overlaps the list build
+    uint32_t r_idx = kNone, r_cj = 0u, r_rank = 0u;
+    if (t < kSlots && s_keys[t] != kInvalid) {
+      r_idx = s_base + s_rix[t];
+      r_cj = c.site_cum + (s_keys[t] - sr.lo);
+      if (r_idx < max_records) r_rank = atomicAdd(&io.site_cnt[r_cj], 1u);  // a count, not a value
+    }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       if ((got >> k & 1u) != 0u) {
@@ -487,6 +502,7 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
         s_list[pos] = static_cast<uint8_t>(t);
       }
     }
+    if (r_idx < max_records) *reinterpret_cast<uint2*>(&records[r_idx]) = make_uint2(r_rank, r_cj);
     __syncthreads();
     // one warp per slot: lanes walk the slot's pixel-ordered pairs, then a
     // fixed-order reduction sums the 32 lane partials.  Warps take balanced
@@ -506,6 +522,7 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
         const uint32_t cnt = s_cnt[sl];
         const uint32_t id = s_keys[sl];
         const uint32_t off = s_off[sl];
+        const uint32_t ridx = s_base + s_rix[sl];
         const float4 gs = ldg(&geo[id]), ms = ldg(&met[id]), cs = ldg(&col[id]);
         float acc[10];
 #pragma unroll
@@ -568,19 +585,12 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
         // sum the 10 lane partials over the warp by recursive halving (fixed
         // order): afterwards lanes 2i and 2i+1 hold the total of statistic i
         const float tot = warp_sum10_halving(acc, lane);
-        const uint32_t ridx = s_base + s_rix[sl];
         const int stat = lane >> 1;
         if (ridx < max_records) {
-          float* dst = reinterpret_cast<float*>(&records[ridx]);
-          if (lane == 0) {
-            const uint32_t cj = c.site_cum + (id - sr.lo);
-            dst[0] = __uint_as_float(id);
-            dst[1] = __uint_as_float(cj);
-            atomicAdd(&io.site_cnt[cj], 1u);  // an integer count, not a value
-          }
           if ((lane & 1) == 0 && stat < 10) {
             const float v = isfinite(tot) ? tot : 0.f;  // non-finite contributions are dropped
-            dst[2 + stat] = v;
+            records[ridx].acc[stat] = v;
+            pm = max(pm, __float_as_uint(fabsf(v)));
           }
         } else if (lane == 0) {
           hdr->overflow = 1u;
@@ -589,6 +599,11 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
     }
     if (!__syncthreads_or(pending != 0u)) break;
   }
+  // the image's scale of the per-site sums: the largest |record value| of
+  // each statistic (the max is order independent)
+  if (pm != 0u) atomicMax(&s_pmax[lane >> 1], pm);  // a bound, not a value
+  __syncthreads();
+  if (t < 10 && s_pmax[t]) atomicMax(&hdr->pmax[c.img][t], s_pmax[t]);
 }
 
 }  // namespace sad

@@ -33,8 +33,8 @@ def test_trace_counts_launches(capi):
     finally:
         capi.sad_trace_enable(prev)
     assert tr["k_step_tile"][0] == 3
-    # the segmented reduce: two scan launches and the scatter per step
-    assert tr["k_seg_scan_local"][0] == 3 and tr["k_seg_scan_blocks"][0] == 3
+    # the segmented reduce: one scan launch and the scatter per step
+    assert tr["k_seg_scan"][0] == 3
     assert tr["k_rec_scatter"][0] == 3
     assert tr["k_site_step"][0] == 3
     assert "k_step_finish" not in tr        # the site step finishes the step
