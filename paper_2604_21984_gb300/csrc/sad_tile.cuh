@@ -175,6 +175,7 @@ struct TileShared {
   uint32_t cnt[kSlots];
   uint32_t off[kSlots];
   uint32_t rix[kSlots];
+  uint8_t order[kSlots];           // this round's slots with a record, by record index
   uint8_t slot8[K][kTileThreads];  // this round's slot of each listed entry
   uint8_t list[kTileThreads * K];
   // per pixel.  gradient mode: {m, 1/Z, g.cbar, gx}, {gy, gz, -, -};
@@ -187,6 +188,7 @@ struct TileShared {
   uint64_t scan[kW];
   float red[kW];
   uint32_t base;
+  uint32_t next;      // the walk's next record index (slots are taken in turn by the warps)
   uint32_t pmax[10];  // the tile's largest |record value| per statistic (float bits)
 };
 
@@ -446,23 +448,30 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
       for (int w = 0; w < kWarps; ++w) s_mask[w][i] = 0u;
     }
     __syncthreads();
-    // Every lane probes the table for each of its pending entries and ORs
-    // its own bit into its warp's mask word of the slot (lanes of one warp
-    // that list the same site at the same rank hit the same word; the shared
-    // atomics serialise them, which costs less than grouping the lanes
-    // first).  OR is order independent, so the masks (and the pair lists
+    // Every lane probes the table for each of its pending entries.  Lanes
+    // next to each other that got the same slot form a run; the run's first
+    // lane ORs the run's bits into its warp's mask word of the slot (one
+    // shared atomic per run instead of one per lane: lanes of a warp that
+    // list the same site at the same rank would otherwise serialise on one
+    // word).  OR is order independent, so the masks (and the pair lists
     // built from them) are deterministic.  Slot numbers are kept as bytes.
     got = 0u;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      if ((pending >> k & 1u) != 0u) {
-        const uint32_t sl = probe_slot(idr[k], s_keys);
-        if (sl != kNone) {
-          atomicOr(&s_mask[warp][sl], 1u << lane);
-          pending &= ~(1u << k);
-          got |= 1u << k;
-          sm.slot8[k][t] = static_cast<uint8_t>(sl);
-        }
+      uint32_t sl = kNone;
+      if ((pending >> k & 1u) != 0u) sl = probe_slot(idr[k], s_keys);
+      const uint32_t left = __shfl_up_sync(0xffffffffu, sl, 1);
+      const bool lead = sl != kNone && (lane == 0 || left != sl);
+      const unsigned breaks = __ballot_sync(0xffffffffu, lead || sl == kNone);
+      if (lead) {
+        const unsigned above = breaks & ~((2u << lane) - 1u);  // run breaks after this lane
+        const unsigned upto = above ? (above & (0u - above)) - 1u : 0xffffffffu;
+        atomicOr(&s_mask[warp][sl], upto & ~((1u << lane) - 1u));
+      }
+      if (sl != kNone) {
+        pending &= ~(1u << k);
+        got |= 1u << k;
+        sm.slot8[k][t] = static_cast<uint8_t>(sl);
       }
     }
     __syncthreads();
@@ -482,8 +491,12 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
       s_cnt[t] = static_cast<uint32_t>(packed & 0xffffffffu);
       s_off[t] = static_cast<uint32_t>(ex & 0xffffffffu);
       s_rix[t] = static_cast<uint32_t>(ex >> 32);
+      if (packed != 0u) sm.order[ex >> 32] = static_cast<uint8_t>(t);
     }
-    if (t == 0) s_base = atomicAdd(&hdr->cursor, static_cast<uint32_t>(total >> 32));
+    if (t == 0) {
+      s_base = atomicAdd(&hdr->cursor, static_cast<uint32_t>(total >> 32));
+      sm.next = 0u;
+    }
     __syncthreads();
     // thread t files slot t's record: its index, its site's compacted index
     // and its place among the site's records (the count's old value), taken
@@ -505,20 +518,17 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
     if (r_idx < max_records) *reinterpret_cast<uint2*>(&records[r_idx]) = make_uint2(r_rank, r_cj);
     __syncthreads();
     // one warp per slot: lanes walk the slot's pixel-ordered pairs, then a
-    // fixed-order reduction sums the 32 lane partials.  Warps take balanced
-    // slot ranges: a slot's work is its pairs plus one reduction (counted as
-    // 32 pairs), and warp w takes the slots whose work prefix falls in
-    // [w T / 8, (w + 1) T / 8) of the tile's total T.
-    const uint32_t tw = static_cast<uint32_t>(total & 0xffffffffu) + 32u * static_cast<uint32_t>(total >> 32);
-    const uint32_t wlo = static_cast<uint32_t>((static_cast<uint64_t>(tw) * warp) / kWarps);
-    const uint32_t whi = static_cast<uint32_t>((static_cast<uint64_t>(tw) * (warp + 1)) / kWarps);
-    for (int g = 0; g < kSlots / 32; ++g) {
-      const int mine = g * 32 + lane;
-      const uint32_t wpre = s_off[mine] + 32u * s_rix[mine];
-      unsigned todo = __ballot_sync(0xffffffffu, s_cnt[mine] != 0u && wpre >= wlo && wpre < whi);
-      while (todo) {
-        const int sl = g * 32 + __ffs(todo) - 1;
-        todo &= todo - 1;
+    // fixed-order reduction sums the 32 lane partials.  The warps take the
+    // slots in turn from a shared counter (a slot's record is the same
+    // whichever warp computes it).
+    const uint32_t n_rec = static_cast<uint32_t>(total >> 32);
+    for (;;) {
+      uint32_t j = 0u;
+      if (lane == 0) j = atomicAdd(&sm.next, 1u);
+      j = __shfl_sync(0xffffffffu, j, 0);
+      if (j >= n_rec) break;
+      {
+        const int sl = sm.order[j];
         const uint32_t cnt = s_cnt[sl];
         const uint32_t id = s_keys[sl];
         const uint32_t off = s_off[sl];
