@@ -119,6 +119,26 @@ __device__ __forceinline__ float warp_sum10_halving(const float (&in)[10], int l
   return a[0] + __shfl_xor_sync(0xffffffffu, a[0], 1);
 }
 
+// The same over each half-warp (16 lanes, offsets 8, 4, 2, 1; the halves sum
+// their own values): returns, on lane l, the total of value l % 16 of its
+// half (values 10..15 are padding).
+__device__ __forceinline__ float half_sum10_halving(const float (&in)[10], int lane) {
+  float a[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) a[j] = j < 10 ? in[j] : 0.f;
+#pragma unroll
+  for (int h = 8; h >= 1; h >>= 1) {
+    const bool up = (lane & h) != 0;
+#pragma unroll
+    for (int j = 0; j < h; ++j) {
+      const float keep = up ? a[h + j] : a[j];
+      const float give = up ? a[j] : a[h + j];
+      a[j] = keep + __shfl_xor_sync(0xffffffffu, give, h);
+    }
+  }
+  return a[0];
+}
+
 // ---------------------------------------------------------------------------
 // per-tile kernel
 // ---------------------------------------------------------------------------
@@ -175,14 +195,16 @@ struct TileShared {
   uint32_t cnt[kSlots];
   uint32_t off[kSlots];
   uint32_t rix[kSlots];
-  uint8_t order[kSlots];           // this round's slots with a record, by record index
+  uint8_t order[kSlots];           // this round's slots with a record, largest pair counts first
+  uint32_t hist[16];               // slots per 16-wide pair-count bucket (largest first)
+  uint32_t hoff[16];               // their exclusive prefix
   uint8_t slot8[K][kTileThreads];  // this round's slot of each listed entry
   uint8_t list[kTileThreads * K];
-  // per pixel.  gradient mode: {m, 1/Z, g.cbar, gx}, {gy, gz, -, -};
+  // per pixel.  gradient mode: {m, 1/Z, g.cbar, gx}, {gy, gz, px, py};
   // statistics mode: {m, 1/Z, cbar.x, cbar.y}, {cbar.z, I}, {c' of the
   // dominant site (blend without it), dominant id}
   float4 pa[kTileThreads];
-  float2 pg[MODE == kModeStats ? 1 : kTileThreads];
+  float4 pg[MODE == kModeStats ? 1 : kTileThreads];
   float4 pb[MODE == kModeStats ? kTileThreads : 1];
   float4 pc[MODE == kModeStats ? kTileThreads : 1];
   uint64_t scan[kW];
@@ -407,7 +429,7 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
     s_pc[t] = make_float4(c2.x, c2.y, c2.z, __uint_as_float(did));
   } else {
     s_pa[t] = make_float4(m, iz, g.x * cb.x + g.y * cb.y + g.z * cb.z, g.x);
-    s_pg[t] = make_float2(g.y, g.z);
+    s_pg[t] = make_float4(g.y, g.z, px, py);
   }
   if (tile_loss) {  // deterministic tile sum of the per-pixel squared error
     float v = lpx;
@@ -424,7 +446,7 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
 
   // ---- 2..3. rounds: slot assignment, stable pair lists, warp per slot ---
   uint32_t pending = vm;
-  uint32_t pm = 0u;  // lanes 2i: the largest |value| of statistic i in this warp's records (float bits)
+  uint32_t pm = 0u;  // lanes i and 16 + i: the largest |value| of statistic i in this warp's records (float bits)
   uint32_t got = 0u;      // entries that got a slot this round (slots in sm.slot8)
   const uint32_t lt_mask = (1u << lane) - 1u;
   for (;;) {
@@ -442,6 +464,7 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) idr[k] = sr.has(idr[k]) ? idr[k] : kInvalid;
+    if (t < 16) sm.hist[t] = 0u;
     for (int i = t; i < kSlots; i += kTileThreads) {
       s_keys[i] = kInvalid;
 #pragma unroll
@@ -476,6 +499,7 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
     }
     __syncthreads();
     uint64_t packed = 0;
+    uint32_t b_id = 0u, b_pos = 0u;  // the slot's pair-count bucket and its place there
     if (t < kSlots && s_keys[t] != kInvalid) {
       uint32_t c = 0;
 #pragma unroll
@@ -484,6 +508,8 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
         c += __popc(s_mask[w][t]);
       }
       packed = static_cast<uint64_t>(c) | (1ull << 32);
+      b_id = 15u - min(15u, (c - 1u) >> 4);
+      b_pos = atomicAdd(&sm.hist[b_id], 1u);  // a place in the walk order, not a value
     }
     uint64_t total;
     const uint64_t ex = block_excl_scan256(packed, s_scan, total);
@@ -491,7 +517,16 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
       s_cnt[t] = static_cast<uint32_t>(packed & 0xffffffffu);
       s_off[t] = static_cast<uint32_t>(ex & 0xffffffffu);
       s_rix[t] = static_cast<uint32_t>(ex >> 32);
-      if (packed != 0u) sm.order[ex >> 32] = static_cast<uint8_t>(t);
+    }
+    if (t < 32) {  // bucket offsets (the histogram is complete: the scan synchronised)
+      const uint32_t h = t < 16 ? sm.hist[t] : 0u;
+      uint32_t x = h;
+#pragma unroll
+      for (int o = 1; o < 16; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (t < 16) sm.hoff[t] = x - h;
     }
     if (t == 0) {
       s_base = atomicAdd(&hdr->cursor, static_cast<uint32_t>(total >> 32));
@@ -516,20 +551,25 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
       }
     }
     if (r_idx < max_records) *reinterpret_cast<uint2*>(&records[r_idx]) = make_uint2(r_rank, r_cj);
+    if (packed != 0u) sm.order[sm.hoff[b_id] + b_pos] = static_cast<uint8_t>(t);
     __syncthreads();
-    // one warp per slot: lanes walk the slot's pixel-ordered pairs, then a
-    // fixed-order reduction sums the 32 lane partials.  The warps take the
-    // slots in turn from a shared counter (a slot's record is the same
-    // whichever warp computes it).
+    // Two slots at a time, one per half-warp: the 16 lanes walk the slot's
+    // pixel-ordered pairs, then a fixed-order reduction sums their partials.
+    // The warps take pairs of slots in turn from a shared counter, in the
+    // order of the slots' pair counts (16-wide buckets, largest first), so
+    // the two halves walk similar counts; a slot's record is the same
+    // whichever half-warp computes it.
     const uint32_t n_rec = static_cast<uint32_t>(total >> 32);
+    const int half = lane >> 4, hl = lane & 15;
     for (;;) {
       uint32_t j = 0u;
-      if (lane == 0) j = atomicAdd(&sm.next, 1u);
+      if (lane == 0) j = atomicAdd(&sm.next, 2u);
       j = __shfl_sync(0xffffffffu, j, 0);
       if (j >= n_rec) break;
       {
-        const int sl = sm.order[j];
-        const uint32_t cnt = s_cnt[sl];
+        const bool live = j + half < n_rec;  // the odd last slot leaves a half idle
+        const int sl = sm.order[live ? j + half : j];
+        const uint32_t cnt = live ? s_cnt[sl] : 0u;
         const uint32_t id = s_keys[sl];
         const uint32_t off = s_off[sl];
         const uint32_t ridx = s_base + s_rix[sl];
@@ -537,20 +577,20 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
         float acc[10];
 #pragma unroll
         for (int j = 0; j < 10; ++j) acc[j] = 0.f;
-        for (uint32_t i = lane; i < cnt; i += 32) {
-          const uint32_t p = s_list[off + i];
-          const float4 A = s_pa[p];
-          const float dx = (x0 + static_cast<int>(p & (TW - 1)) + 0.5f) - gs.x;
-          const float dy = (y0 + static_cast<int>(p >> kLog2TW) + 0.5f) - gs.y;
-          const float qq = ms.x * dx * dx + 2.f * ms.y * dx * dy + ms.z * dy * dy;
-          // gradient mode: n and 1/n from one reciprocal square root (the
-          // adjoint's tolerance allows its few-ulp error; no division)
-          const float qc = fmaxf(qq, 0.f);
-          const float rq = rsqrtf(qc);
-          const float n = MODE == kModeStats ? sqrtf(qc) : (qc > 0.f ? qc * rq : 0.f);
-          // (ms.w = 0 only for a listed inactive site in the saved-forward mode)
-        const float w = __expf(gs.z * (gs.w - n) - A.x) * A.y * (SAVED ? ms.w : 1.f);
-          if (MODE == kModeStats) {
+        // (ms.w = 0 only for a listed inactive site in the saved-forward
+        // mode: its weights are zero, so its pairs are skipped)
+        const uint32_t n_pairs = (SAVED && ms.w == 0.f) ? 0u : cnt;
+        const uint32_t n_most = max(n_pairs, __shfl_xor_sync(0xffffffffu, n_pairs, 16));
+        if (MODE == kModeStats) {
+          for (uint32_t i = hl; i < n_most; i += 16) {
+            if (i >= n_pairs) continue;
+            const uint32_t p = s_list[off + i];
+            const float4 A = s_pa[p];
+            const float dx = (x0 + static_cast<int>(p & (TW - 1)) + 0.5f) - gs.x;
+            const float dy = (y0 + static_cast<int>(p >> kLog2TW) + 0.5f) - gs.y;
+            const float qq = ms.x * dx * dx + 2.f * ms.y * dx * dy + ms.z * dy * dy;
+            const float n = sqrtf(fmaxf(qq, 0.f));
+            const float w = __expf(gs.z * (gs.w - n) - A.x) * A.y;
             // A = {m, 1/Z, cbar.x, cbar.y}, B = {cbar.z, I}
             const float4 B = s_pb[p];
             const float ex = A.z - B.y, ey = A.w - B.z, ez = B.x - B.w;
@@ -573,37 +613,52 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
             }
             const float fx = cp.x - B.y, fy = cp.y - B.z, fz = cp.z - B.w;
             acc[7] += fx * fx + fy * fy + fz * fz - e;
-          } else {
-            // A = {m, 1/Z, g.cbar, gx}, B = {gy, gz}
-            const float2 B = s_pg[p];
+          }
+        } else {
+          const float g01 = 2.f * ms.y;
+          for (uint32_t i = hl; i < n_most; i += 16) {
+            if (i >= n_pairs) continue;
+            const uint32_t p = s_list[off + i];
+            // A = {m, 1/Z, g.cbar, gx}, B = {gy, gz, px, py}
+            const float4 A = s_pa[p];
+            const float4 B = s_pg[p];
+            const float dx = B.z - gs.x, dy = B.w - gs.y;
+            const float qq = (ms.x * dx + g01 * dy) * dx + ms.z * dy * dy;
+            // n and 1/n from one reciprocal square root (the adjoint's
+            // tolerance allows its few-ulp error; no division); 1/n is taken
+            // as 0 at the site itself, where the position terms vanish
+            const float qc = fmaxf(qq, 0.f);
+            const float rq = qc > 0.f ? rsqrtf(qc) : 0.f;
+            const float n = qc * rq;
+            const float w = __expf(gs.z * (gs.w - n) - A.x) * A.y;
             const float d = w * (A.w * cs.x + B.x * cs.y + B.y * cs.z - A.z);
             acc[0] += w * A.w;
             acc[1] += w * B.x;
             acc[2] += w * B.y;
             acc[3] += d;
             acc[4] += d * n;
-            if (n > 0.f) {
-              const float a = d * rq;
-              acc[5] += a * dx;
-              acc[6] += a * dy;
-              acc[7] += a * dx * dx;
-              acc[8] += a * dx * dy;
-              acc[9] += a * dy * dy;
-            }
+            const float a = d * rq;
+            const float ax = a * dx, ay = a * dy;
+            acc[5] += ax;
+            acc[6] += ay;
+            acc[7] += ax * dx;
+            acc[8] += ax * dy;
+            acc[9] += ay * dy;
           }
         }
-        // sum the 10 lane partials over the warp by recursive halving (fixed
-        // order): afterwards lanes 2i and 2i+1 hold the total of statistic i
-        const float tot = warp_sum10_halving(acc, lane);
-        const int stat = lane >> 1;
-        if (ridx < max_records) {
-          if ((lane & 1) == 0 && stat < 10) {
-            const float v = isfinite(tot) ? tot : 0.f;  // non-finite contributions are dropped
-            records[ridx].acc[stat] = v;
-            pm = max(pm, __float_as_uint(fabsf(v)));
+        // sum the 10 lane partials over each half by recursive halving (fixed
+        // order): afterwards lane i of a half holds the total of statistic i
+        const float tot = half_sum10_halving(acc, lane);
+        if (live) {
+          if (ridx < max_records) {
+            if (hl < 10) {
+              const float v = isfinite(tot) ? tot : 0.f;  // non-finite contributions are dropped
+              records[ridx].acc[hl] = v;
+              pm = max(pm, __float_as_uint(fabsf(v)));
+            }
+          } else if (hl == 0) {
+            hdr->overflow = 1u;
           }
-        } else if (lane == 0) {
-          hdr->overflow = 1u;
         }
       }
     }
@@ -611,7 +666,7 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
   }
   // the image's scale of the per-site sums: the largest |record value| of
   // each statistic (the max is order independent)
-  if (pm != 0u) atomicMax(&s_pmax[lane >> 1], pm);  // a bound, not a value
+  if (pm != 0u) atomicMax(&s_pmax[lane & 15], pm);  // a bound, not a value
   __syncthreads();
   if (t < 10 && s_pmax[t]) atomicMax(&hdr->pmax[c.img][t], s_pmax[t]);
 }
