@@ -119,6 +119,16 @@ __device__ __forceinline__ float warp_sum10_halving(const float (&in)[10], int l
   return a[0] + __shfl_xor_sync(0xffffffffu, a[0], 1);
 }
 
+constexpr float kLog2e = 1.4426950408889634f;
+
+// 2^x by the hardware's approximate base-2 exponential (the instruction the
+// fast exponential uses; subnormal results flush to zero)
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // The same over each half-warp (16 lanes, offsets 8, 4, 2, 1; the halves sum
 // their own values): returns, on lane l, the total of value l % 16 of its
 // half (values 10..15 are padding).
@@ -200,7 +210,8 @@ struct TileShared {
   uint32_t hoff[16];               // their exclusive prefix
   uint8_t slot8[K][kTileThreads];  // this round's slot of each listed entry
   uint8_t list[kTileThreads * K];
-  // per pixel.  gradient mode: {m, 1/Z, g.cbar, gx}, {gy, gz, px, py};
+  // per pixel.  gradient mode: {m log2 e - log2(1/Z), 1/Z, g.cbar, gx},
+  // {gy, gz, px, py};
   // statistics mode: {m, 1/Z, cbar.x, cbar.y}, {cbar.z, I}, {c' of the
   // dominant site (blend without it), dominant id}
   float4 pa[kTileThreads];
@@ -428,7 +439,10 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
     s_pb[t] = make_float4(cb.z, I.x, I.y, I.z);
     s_pc[t] = make_float4(c2.x, c2.y, c2.z, __uint_as_float(did));
   } else {
-    s_pa[t] = make_float4(m, iz, g.x * cb.x + g.y * cb.y + g.z * cb.z, g.x);
+    // the pair weight is exp2(tau s log2 e (r - n) - M2) with M2 = m log2 e -
+    // log2(1/Z): the max logit and the normaliser folded into one offset
+    const float m2 = vm ? m * kLog2e - __log2f(iz) : 0.f;
+    s_pa[t] = make_float4(m2, iz, g.x * cb.x + g.y * cb.y + g.z * cb.z, g.x);
     s_pg[t] = make_float4(g.y, g.z, px, py);
   }
   if (tile_loss) {  // deterministic tile sum of the per-pixel squared error
@@ -580,10 +594,8 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
         // (ms.w = 0 only for a listed inactive site in the saved-forward
         // mode: its weights are zero, so its pairs are skipped)
         const uint32_t n_pairs = (SAVED && ms.w == 0.f) ? 0u : cnt;
-        const uint32_t n_most = max(n_pairs, __shfl_xor_sync(0xffffffffu, n_pairs, 16));
         if (MODE == kModeStats) {
-          for (uint32_t i = hl; i < n_most; i += 16) {
-            if (i >= n_pairs) continue;
+          for (uint32_t i = hl; i < n_pairs; i += 16) {
             const uint32_t p = s_list[off + i];
             const float4 A = s_pa[p];
             const float dx = (x0 + static_cast<int>(p & (TW - 1)) + 0.5f) - gs.x;
@@ -616,10 +628,10 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
           }
         } else {
           const float g01 = 2.f * ms.y;
-          for (uint32_t i = hl; i < n_most; i += 16) {
-            if (i >= n_pairs) continue;
+          const float tsl = gs.z * kLog2e;
+          for (uint32_t i = hl; i < n_pairs; i += 16) {
             const uint32_t p = s_list[off + i];
-            // A = {m, 1/Z, g.cbar, gx}, B = {gy, gz, px, py}
+            // A = {M2, 1/Z, g.cbar, gx}, B = {gy, gz, px, py}
             const float4 A = s_pa[p];
             const float4 B = s_pg[p];
             const float dx = B.z - gs.x, dy = B.w - gs.y;
@@ -630,7 +642,7 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
             const float qc = fmaxf(qq, 0.f);
             const float rq = qc > 0.f ? rsqrtf(qc) : 0.f;
             const float n = qc * rq;
-            const float w = __expf(gs.z * (gs.w - n) - A.x) * A.y;
+            const float w = ex2_approx(fmaf(tsl, gs.w - n, -A.x));
             const float d = w * (A.w * cs.x + B.x * cs.y + B.y * cs.z - A.z);
             acc[0] += w * A.w;
             acc[1] += w * B.x;
