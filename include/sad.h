@@ -27,12 +27,14 @@
  *    list positions 4j..4j+3, i.e. uint32[K/4][H*W][4].  Sentinel 0xffffffff.
  *    K must be 4, 8 or 16.  Lists are ordered by logit descending, ties by
  *    smaller id (for maps produced by sad_update_topk).
- *  - The prepared site table (the "pack" of App. "Data Layout and Packing") is float32[5][capacity][4]:
+ *  - The prepared site table (the "pack" of App. "Data Layout and Packing") is float32[6][capacity][4]:
  *      plane 0 {x, y, tau*s, r}, plane 1 {G00, G01, G11, active},
  *      plane 2 {cr, cg, cb, 0},  with s = 1/max(H,W) (Sec. 4.1); planes 3
  *      and 4 hold the same site folded for the softmax blend (the blend
  *      record): with G' = (tau s)^2 G, plane 3 {x, y, tau s r, G'00} (tau s r
- *      = -inf for an inactive site), plane 4 {G'01, G'11, cr, cg}.
+ *      = -inf for an inactive site), plane 4 {G'01, G'11, cr, cg}; plane 5
+ *      holds cb densely, one float per site (float32[capacity] at the start
+ *      of the plane; the rest of the plane is unused).
  *    Every device pointer must be 16-byte aligned.
  */
 #ifndef SAD_H
@@ -91,7 +93,7 @@ int sad_trace_collect(sad_trace_entry* out, int32_t max_entries, int32_t* n_out)
  *   reduction + degree-7 Taylor polynomial); G00 = e+ ux^2 + e- uy^2,
  *   G01 = (e+ - e-) ux uy, G11 = e+ uy^2 + e- ux^2; tau*s = exp(log_tau) s;
  *   active = (x >= 0).
- * params: float32[11][capacity] (read).  prep: float32[5][capacity][4] (written).
+ * params: float32[11][capacity] (read).  prep: float32[6][capacity][4] (written).
  */
 int sad_prepare_sites(const float* params, int32_t capacity, int32_t H, int32_t W,
                       float* prep, void* stream);

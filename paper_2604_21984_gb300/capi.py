@@ -27,7 +27,7 @@ INVALID = 0xFFFFFFFF
 STEP_KEEP_LISTS = 1   # batch-image flag (include/sad.h SAD_STEP_KEEP_LISTS)
 PLANE_LOGTAU = 2      # plane of log tau in the site parameter and gradient arrays
 SAD_EWORKSPACE = 3    # status: per-tile records did not fit the workspace
-PREP_PLANES = 5       # float4 planes of the prepared site table (include/sad.h)
+PREP_PLANES = 6       # float4 planes of the prepared site table (include/sad.h)
 NOALLOC_SCRATCH_BYTES = 64 << 20   # include/sad.h SAD_NOALLOC_SCRATCH_BYTES: held on every device
 
 

@@ -32,8 +32,8 @@ __device__ __forceinline__ void blend_step(float l, bool ok, float4 ck, float& m
 }
 
 // The blend reads each listed site's blend record (two 16-byte gathers,
-// {x, y, tau s r, G'00} and {G'01, G'11, cr, cg}, plus cb from the colour
-// plane: 36 bytes per (pixel, site)), with l = tau s r - sqrt(dx G' dx).
+// {x, y, tau s r, G'00} and {G'01, G'11, cr, cg}, plus cb from the dense
+// blue plane: 36 bytes per (pixel, site)), with l = tau s r - sqrt(dx G' dx).
 // m_out / iz_out (optional): the max logit and 1/Z of the blend (0 if no
 // listed site is valid), the per-pixel state the saved-forward adjoint reads.
 template <int NP>
@@ -41,9 +41,8 @@ __device__ __forceinline__ float3 blend_planes(const uint4* __restrict__ map, si
                                                float px, float py, SiteRange sr,
                                                const float4* __restrict__ ba,
                                                const float4* __restrict__ bb,
-                                               const float4* __restrict__ col,
+                                               const float* __restrict__ cbd,
                                                float* m_out = nullptr, float* iz_out = nullptr) {
-  const float* __restrict__ colf = reinterpret_cast<const float*>(col);
   float m = -INFINITY, z = 0.f;
   float3 c = make_float3(0.f, 0.f, 0.f);
 #pragma unroll
@@ -59,7 +58,7 @@ __device__ __forceinline__ float3 blend_planes(const uint4* __restrict__ map, si
         const uint32_t id = sr.has(id4[u0 + u]) ? id4[u0 + u] : sr.lo;  // clamped: loads issue early
         A[u] = ldg(&ba[id]);
         B[u] = ldg(&bb[id]);
-        cb[u] = ldg(&colf[4 * static_cast<size_t>(id) + 2]);
+        cb[u] = ldg(&cbd[id]);
       }
 #pragma unroll
       for (int u = 0; u < 2; ++u) {

@@ -91,11 +91,14 @@ __device__ __forceinline__ bool key_before(float la, uint32_t ia, float lb, uint
 // The blend record (ba, bb) is the same site folded for the softmax blend
 // and its 36 bytes per (pixel, site) gather: with G' = (tau s)^2 G the logit
 // is l = tau s r - sqrt(dx G' dx), so ba = {x, y, tau s r, G'00} (tau s r =
-// -inf for an inactive site) and bb = {G'01, G'11, cr, cg}; cb stays in col.
+// -inf for an inactive site) and bb = {G'01, G'11, cr, cg}; cb goes to a
+// dense plane (cbd: one float per site), whose 4-byte gathers spread over
+// all 32 shared-memory banks of the L1 (cb inside the 16-byte colour record
+// falls on 8 of them).
 __device__ __forceinline__ void prepare_site(float x, float y, float logtau, float r, float cr,
                                              float cg, float cb, float ux, float uy, float a,
                                              float b, float s, float4& geo, float4& met,
-                                             float4& col, float4& ba, float4& bb) {
+                                             float4& col, float4& ba, float4& bb, float& cbd) {
   const float nrm = __fsqrt_rn(__fadd_rn(__fmul_rn(ux, ux), __fmul_rn(uy, uy)));
   float uxn = 1.f, uyn = 0.f;
   if (nrm > 0.f) {
@@ -116,6 +119,7 @@ __device__ __forceinline__ void prepare_site(float x, float y, float logtau, flo
   const float t2 = ts * ts;
   ba = make_float4(x, y, act ? ts * r : -INFINITY, t2 * G00);
   bb = make_float4(t2 * G01, t2 * G11, cr, cg);
+  cbd = cb;
 }
 
 template <typename T>

@@ -21,8 +21,9 @@ __global__ void __launch_bounds__(256, 5) k_render(const float4* __restrict__ ge
   float m, iz;
   const float3 c = blend_planes<K / 4>(map, P, q, x + 0.5f, y + 0.5f,
                                       SiteRange{0u, static_cast<uint32_t>(cap)}, geo + 3 * static_cast<size_t>(cap),
-                                      geo + 4 * static_cast<size_t>(cap), col, SAVE ? &m : nullptr,
-                                      SAVE ? &iz : nullptr);
+                                      geo + 4 * static_cast<size_t>(cap),
+                                      reinterpret_cast<const float*>(geo + 5 * static_cast<size_t>(cap)),
+                                      SAVE ? &m : nullptr, SAVE ? &iz : nullptr);
   rgb[3 * q] = c.x;
   rgb[3 * q + 1] = c.y;
   rgb[3 * q + 2] = c.z;
@@ -49,7 +50,8 @@ __global__ void __launch_bounds__(256, 5) k_decode(const float4* __restrict__ ge
   const size_t P = static_cast<size_t>(H) * W;
   const float3 c = blend_planes<K / 4>(map, P, static_cast<size_t>(cy) * W + cx, p.x, p.y,
                                        SiteRange{0u, static_cast<uint32_t>(cap)}, geo + 3 * static_cast<size_t>(cap),
-                                       geo + 4 * static_cast<size_t>(cap), col);
+                                       geo + 4 * static_cast<size_t>(cap),
+                                       reinterpret_cast<const float*>(geo + 5 * static_cast<size_t>(cap)));
   rgb[3 * i] = c.x;
   rgb[3 * i + 1] = c.y;
   rgb[3 * i + 2] = c.z;

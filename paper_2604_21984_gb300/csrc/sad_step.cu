@@ -286,7 +286,8 @@ __device__ __forceinline__ void site_work(const BatchDesc& d, uint32_t j, float*
     }
   }
   prepare_site(p[PX], p[PY], p[PLOGTAU], p[PR], p[PCR], p[PCG], p[PCB], p[PUX], p[PUY], p[PA],
-               p[PB], im.s, geo[i], met[i], col[i], col[c + i], col[2 * c + i]);
+               p[PB], im.s, geo[i], met[i], col[i], col[c + i], col[2 * c + i],
+               reinterpret_cast<float*>(col + 3 * c)[i]);
 }
 
 // The step's finish for image b: its mean loss from the tile losses (fixed
@@ -349,7 +350,7 @@ __global__ void __launch_bounds__(kSumThreads, 4) k_site_step(const BatchDesc d,
 
 __global__ void __launch_bounds__(256) k_decode_batch(const BatchDesc d, const float4* __restrict__ ba,
                                                       const float4* __restrict__ bb,
-                                                      const float4* __restrict__ col,
+                                                      const float* __restrict__ cbd,
                                                       const uint4* __restrict__ map, size_t Ptot,
                                                       int K, const float2* __restrict__ xy,
                                                       const int32_t* __restrict__ qimg, int64_t n,
@@ -368,9 +369,9 @@ __global__ void __launch_bounds__(256) k_decode_batch(const BatchDesc d, const f
     const size_t q = im.pix_off + static_cast<size_t>(cy) * im.W + cx;
     const SiteRange sr{im.site_lo, im.site_n};
     switch (K) {
-      case 4: c = blend_planes<1>(map, Ptot, q, p.x, p.y, sr, ba, bb, col); break;
-      case 8: c = blend_planes<2>(map, Ptot, q, p.x, p.y, sr, ba, bb, col); break;
-      default: c = blend_planes<4>(map, Ptot, q, p.x, p.y, sr, ba, bb, col); break;
+      case 4: c = blend_planes<1>(map, Ptot, q, p.x, p.y, sr, ba, bb, cbd); break;
+      case 8: c = blend_planes<2>(map, Ptot, q, p.x, p.y, sr, ba, bb, cbd); break;
+      default: c = blend_planes<4>(map, Ptot, q, p.x, p.y, sr, ba, bb, cbd); break;
     }
   }
   rgb[3 * i] = c.x;
@@ -747,7 +748,7 @@ int sad_decode_batch(const sad_batch_image* images, int32_t B, int32_t K, const 
   const float4* p4 = reinterpret_cast<const float4*>(prep);
   { TraceScope tr_(as_stream(stream), "k_decode_batch"); k_decode_batch<<<static_cast<unsigned>((n + 255) / 256), 256, 0, as_stream(stream)>>>(
       d, p4 + 3 * static_cast<size_t>(total_capacity), p4 + 4 * static_cast<size_t>(total_capacity),
-      p4 + 2 * static_cast<size_t>(total_capacity),
+      reinterpret_cast<const float*>(p4 + 5 * static_cast<size_t>(total_capacity)),
       reinterpret_cast<const uint4*>(map), static_cast<size_t>(total_pixels), K,
       reinterpret_cast<const float2*>(xy), query_image, n, rgb); }
   return check_launch("k_decode_batch");

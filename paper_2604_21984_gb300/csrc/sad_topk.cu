@@ -12,14 +12,14 @@ namespace sad {
 __global__ void k_prepare(const float* __restrict__ params, int cap, float s,
                           float4* __restrict__ geo, float4* __restrict__ met,
                           float4* __restrict__ col, float4* __restrict__ ba,
-                          float4* __restrict__ bb) {
+                          float4* __restrict__ bb, float* __restrict__ cbd) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= cap) return;
   const size_t c = static_cast<size_t>(cap);
   prepare_site(params[PX * c + i], params[PY * c + i], params[PLOGTAU * c + i], params[PR * c + i],
                params[PCR * c + i], params[PCG * c + i], params[PCB * c + i], params[PUX * c + i],
                params[PUY * c + i], params[PA * c + i], params[PB * c + i], s, geo[i], met[i],
-               col[i], ba[i], bb[i]);
+               col[i], ba[i], bb[i], cbd[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -257,7 +257,8 @@ int sad_prepare_sites(const float* params, int32_t capacity, int32_t H, int32_t 
                                                                      p4 + capacity,
                                                                      p4 + 2 * (size_t)capacity,
                                                                      p4 + 3 * (size_t)capacity,
-                                                                     p4 + 4 * (size_t)capacity); }
+                                                                     p4 + 4 * (size_t)capacity,
+                                                                     reinterpret_cast<float*>(p4 + 5 * (size_t)capacity)); }
   return check_launch("k_prepare");
 }
 

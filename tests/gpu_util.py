@@ -38,6 +38,14 @@ def prep_to_oracle_dict(prep_t, cap):
             "cr": a[2, :, 0], "cg": a[2, :, 1], "cb": a[2, :, 2]}
 
 
+def prep_blend_copies(prep_t, cap):
+    """The verbatim copies in the blend record and the dense blue plane:
+    {x, y, cr, cg, cb} from planes 3, 4 and 5."""
+    a = prep_t.cpu().numpy()
+    return {"x": a[3, :cap, 0], "y": a[3, :cap, 1], "cr": a[4, :cap, 2], "cg": a[4, :cap, 3],
+            "cb": a[5].reshape(-1)[:cap]}
+
+
 def assert_grads_close(got, ref, rel=1e-4, floor_frac=1e-4, planes=range(11), names=None):
     """Norm-relative per parameter plane, with an absolute floor of
     floor_frac * max|ref| of that plane."""

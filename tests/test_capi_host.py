@@ -34,7 +34,7 @@ def test_every_declared_symbol_is_exported(L):
 
 
 def test_status_strings_and_version(L):
-    assert L.sad_abi_version() == 6
+    assert L.sad_abi_version() == 7
     assert L.sad_status_string(0) == b"ok"
     assert L.sad_status_string(1) == b"invalid argument"
     assert L.sad_status_string(99) == b"unknown status"

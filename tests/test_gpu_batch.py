@@ -57,7 +57,8 @@ def test_fused_step_matches_unfused_sequence(capi, oracle):
     # the prepared table was refreshed for the new parameters
     prep2 = capi.empty_prep(n)
     capi.sad_prepare_sites(tr.params, H, W, prep2)
-    assert torch.equal(prep2, tr.prep)
+    assert torch.equal(prep2[:5], tr.prep[:5])                       # the float4 planes
+    assert torch.equal(prep2[5].reshape(-1)[:n], tr.prep[5].reshape(-1)[:n])   # the dense blue plane
 
 
 def test_batch_results_do_not_depend_on_the_batch(capi):

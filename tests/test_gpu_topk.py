@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from paper_2604_21984_gb300 import inputs as gen
-from tests.gpu_util import dev, prep_to_oracle_dict, prepare, require_gpu
+from tests.gpu_util import dev, prep_blend_copies, prep_to_oracle_dict, prepare, require_gpu
 
 pytestmark = pytest.mark.gpu
 INV = 0xFFFFFFFF
@@ -33,6 +33,9 @@ def test_prepare_bit_exact(capi, oracle, kind):
     for k in ("x", "y", "ts", "r", "G00", "G01", "G11", "active", "cr", "cg", "cb"):
         assert np.array_equal(got[k].view(np.uint32) if got[k].dtype == np.float32 else got[k],
                               ref[k].view(np.uint32) if ref[k].dtype == np.float32 else ref[k]), k
+    copies = prep_blend_copies(prep, p.shape[1])      # blend record + dense blue plane
+    for k, v in copies.items():
+        assert np.array_equal(v.view(np.uint32), ref[k].view(np.uint32)), k
 
 
 @pytest.mark.parametrize("K", [4, 8, 16])
