@@ -190,6 +190,14 @@ __device__ __forceinline__ void pixel_update(uint64_t (&v)[K], bool inimg, int c
   // cache.
   int qn = 0;
   auto drain = [&]() {
+    // Score the queue in groups of NG; only ids whose key beats the list's
+    // last key at the start of the drain are kept (compacted to the front
+    // of the queue: a kept id never overwrites an unread one).  Few are
+    // kept (about 0.2 insertions per pixel and pass once the field has
+    // settled), so the insertion network below runs for those alone
+    // instead of for every scored candidate of every lane in the warp.
+    const uint64_t thr = v[K - 1];
+    int nw = 0;
 #pragma unroll 1
     for (int i = 0; i < qn; i += NG) {
       uint32_t id[NG];
@@ -205,11 +213,19 @@ __device__ __forceinline__ void pixel_update(uint64_t (&v)[K], bool inimg, int c
           const float l = score_exact(px, py, g[u], m[u]);
           if (l == l) c = make_key(l, id[u]);
         }
-        // an id queued twice (offered by two neighbours) finds itself in
-        // the list the second time; only candidates that beat the list's
-        // last key pay for that test
-        if (c > v[K - 1] && !list_has<K>(v, id[u])) list_insert<K>(v, c);
+        if (c > thr) s_q[nw++][tid] = id[u];
       }
+    }
+    // Insert the kept ids, re-scored: an id queued twice (offered by two
+    // neighbours) finds itself in the list the second time, and a key that
+    // an earlier insertion pushed below the list's last one is dropped.
+#pragma unroll 1
+    for (int i = 0; i < nw; ++i) {
+      const uint32_t id = s_q[i][tid];
+      float4 g, m;
+      sites.load(id, g, m);
+      const uint64_t c = make_key(score_exact(px, py, g, m), id);
+      if (c > v[K - 1] && !list_has<K>(v, id)) list_insert<K>(v, c);
     }
     qn = 0;
   };
