@@ -169,15 +169,20 @@ def gen_images(specs):
         return list(ex.map(_gen_image, specs))
 
 
-# DRAM traffic and warp instructions per launch of the timed step's dominant
+# DRAM traffic and warp instructions per launch of a timed step's dominant
 # kernel, from one ncu capture of the build whose kernel sources hash to
-# `sha` (profiles/k_step_tile_768x512_k16.md).  Reported only while the
-# sources still hash the same (a changed kernel has no counters until it is
-# captured again).
+# `sha` (profiles/).  Reported only while the sources still hash the same (a
+# changed kernel has no counters until it is captured again).  The
+# adjoint's capture is the 1536x1536 case of the headline workload (same
+# site density), scaled to 2048x2048 by the pixel count: every term of its
+# traffic is per pixel or per site (profiles/k_bwd_tile_saved_1536x1536_k16.md).
 NCU_COUNTERS = {
-    "k_step_tile": {"sources": ["sad_step.cu", "sad_tile.cuh", "sad_topk.cuh", "sad_device.cuh",
-                                "sad_adam.cuh", "sad_blend.cuh"],
-                    "sha": "48e389fda0039ac8", "dram_bytes": 33728768, "warp_inst": 153631217},
+    "k_bwd_tile": {"sources": ['sad_backward.cu', 'sad_tile.cuh', 'sad_reduce.cuh', 'sad_topk.cuh', 'sad_device.cuh'],
+                   "sha": "7ad221e8c1102150", "dram_bytes": 455785131, "warp_inst": 386770636,
+                   "captured": "1536x1536, scaled by (2048/1536)^2"},
+    "k_step_tile": {"sources": ['sad_step.cu', 'sad_tile.cuh', 'sad_topk.cuh', 'sad_device.cuh', 'sad_adam.cuh', 'sad_blend.cuh', 'sad_reduce.cuh'],
+                    "sha": "b323ccbfd2ff6fbd", "dram_bytes": 33581824, "warp_inst": 150089077,
+                    "captured": "768x512 (the workload itself)"},
 }
 ISSUE_PEAK = 152 * 4 * 2.07e9   # warp instructions / s: 152 SMs x 4 schedulers x 1 issue/clk x 2070 MHz
 
@@ -328,6 +333,7 @@ def headline(capi, dev, args, rank, world, dist, peak, peak_kind, local):
         roofline = {"kernel": kname, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                     "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                     "traffic": ctr["dram_bytes"] if ctr else None,
+                    "traffic_captured": ctr["captured"] if ctr else None,
                     "algorithmic_bytes_per_launch": alg[kname],
                     "avg_launch_ms": round(kms, 5), "launches": klaunch}
         if ctr:
@@ -453,6 +459,7 @@ def encode_iteration(capi, dev, args, rank, peak, peak_kind):
         roofline = {"kernel": kname, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                     "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                     "traffic": ctr["dram_bytes"] if ctr else None,
+                    "traffic_captured": ctr["captured"] if ctr else None,
                     "algorithmic_bytes_per_launch": alg[kname],
                     "avg_launch_ms": round(kms, 5), "launches": klaunch}
         if ctr:
