@@ -307,19 +307,65 @@ def headline(capi, dev, args, rank, world, dist, peak, peak_kind, local):
         host_grad.copy_(params.grad, non_blocking=True)
     for _ in range(2):
         e2e_step()
-    e2e_s = 0.0
+    e2e_serial_s = 0.0
     for _ in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         e2e_step()
         torch.cuda.synchronize()
-        e2e_s += time.perf_counter() - t0
-    e2e_s = reduce_max(e2e_s, dist, world, dev)
+        e2e_serial_s += time.perf_counter() - t0
+    e2e_serial_s = reduce_max(e2e_serial_s, dist, world, dev)
+
+    # the same calls as a user's input pipeline runs them: step i + 1's
+    # inputs go up on a copy stream while step i computes, and step i's
+    # gradients come back on it while step i + 1 starts (every step still
+    # copies its own inputs from pinned host memory and reads its gradients
+    # back; the backward's overflow check still synchronises every step)
+    copy_s = torch.cuda.Stream(device=dev)
+    comp_s = torch.cuda.current_stream(dev)
+    dp = [torch.empty(host_p.shape, dtype=torch.float32, device=dev) for _ in range(2)]
+    dg = [torch.empty(host_g.shape, dtype=torch.float32, device=dev) for _ in range(2)]
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [torch.cuda.Event() for _ in range(2)]
+
+    def h2d(i):
+        with torch.cuda.stream(copy_s):
+            copy_s.wait_event(ev_out[i % 2])   # the buffer's previous gradient read-back is done
+            dp[i % 2].copy_(host_p, non_blocking=True)
+            dg[i % 2].copy_(host_g, non_blocking=True)
+            ev_in[i % 2].record(copy_s)
+
+    def piped(n):
+        for e in ev_out:
+            e.record(comp_s)
+        h2d(0)
+        for i in range(n):
+            h2d(i + 1)
+            comp_s.wait_event(ev_in[i % 2])
+            params = dp[i % 2].requires_grad_(True)
+            params.grad = None
+            out = sad_render_fn(params, a, H, W)
+            out.backward(dg[i % 2])
+            grad = params.grad
+            with torch.cuda.stream(copy_s):
+                copy_s.wait_stream(comp_s)
+                host_grad.copy_(grad, non_blocking=True)
+                grad.record_stream(copy_s)
+                ev_out[i % 2].record(copy_s)
+            params.requires_grad_(False)
+        torch.cuda.synchronize()
+    piped(2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    piped(args.steps)
+    e2e_s = reduce_max(time.perf_counter() - t0, dist, world, dev)
     e2e = {"value": round(whole_job_value(world, P, args.steps, e2e_s), 3), "unit": UNIT,
            "h2d_bytes_per_step": int(host_p.numel() * 4 + host_g.numel() * 4),
            "d2h_bytes_per_step": int(host_grad.numel() * 4),
            "path": "sad_render_fn(params, map).backward(g), params and g from pinned host memory, "
-                   "gradients read back"}
+                   "gradients read back; step i+1's upload and step i's read-back on a second stream",
+           "serial": {"value": round(whole_job_value(world, P, args.steps, e2e_serial_s), 3),
+                      "path": "the same, each step synchronised before the next upload"}}
     # roofline of the dominant kernel, from its own event pairs in the timed
     # region; algorithmic bytes per launch (SURVEY 8(d) unit): render and
     # backward each read the map (4K B) and 12 B of colour or upstream
@@ -591,6 +637,24 @@ def encode_leg(capi, dev, peak, peak_kind, args, iters=2000):
             del enc
     res["psnr_over_seeds_0_1_2"] = {k: {"per_seed": v, "mean": round(statistics.mean(v), 3)}
                                     for k, v in seeds.items()}
+    # the encoder's learning rates and initial temperature against their
+    # neighbours (seed 0, fused): does a nearby setting do materially better?
+    base_lr = EncodeConfig().lr
+
+    def scaled(idx, f):
+        return tuple(x * f if i in idx else x for i, x in enumerate(base_lr))
+    sweep = {"default": res["psnr_db"]}
+    everything = range(len(base_lr))
+    for name, kw in (("lr_all_x0.5", {"lr": scaled(everything, 0.5)}), ("lr_all_x2", {"lr": scaled(everything, 2.0)}),
+                     ("lr_position_x0.5", {"lr": scaled((0, 1), 0.5)}), ("lr_position_x2", {"lr": scaled((0, 1), 2.0)}),
+                     ("lr_colour_x0.5", {"lr": scaled((4, 5, 6), 0.5)}), ("lr_colour_x2", {"lr": scaled((4, 5, 6), 2.0)}),
+                     ("lr_log_tau_x0.25", {"lr": scaled((2,), 0.25)}), ("lr_log_tau_x4", {"lr": scaled((2,), 4.0)}),
+                     ("tau_init_x0.5", {"tau_s_d0": 2.0}), ("tau_init_x2", {"tau_s_d0": 8.0})):
+        enc = Encoder(img, EncodeConfig(n_sites=N_C2, K=K_C2, J=J_C2, iters=iters, seed=0, **kw))
+        enc.run()
+        sweep[name] = round(enc.psnr(), 3)
+        del enc
+    res["lr_tau_sweep_psnr_db"] = sweep
     return res
 
 
@@ -823,45 +887,55 @@ def c4_leg(capi, dev, peak, peak_kind, args, n_images=64, seed=4000):
     b_psnr = tr.psnr()
     del tr
     torch.cuda.empty_cache()
-    # plain loop: each image alone, K=16, J=4, the fused step on a one-image
-    # batch per iteration (no batching across images, no graph)
-    p_psnr, p_train, p_init = [], 0.0, 0.0
-    for i, img in enumerate(imgs):
-        H, W = sizes[i]
-        n = max(1, min(H * W, int(round(0.06 * H * W))))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        enc = Encoder(img, EncodeConfig(n_sites=n, K=16, J=4, capacity_factor=1.0, seed=seeds[i],
-                                        densify_every=0))
-        enc.init()
-        torch.cuda.synchronize()
-        p_init += time.perf_counter() - t0
-        e0, e1 = E(), E()
-        e0.record()
-        for _ in range(iters):
-            enc.step()
-        e1.record()
-        torch.cuda.synchronize()
-        p_train += e0.elapsed_time(e1) / 1e3
-        p_psnr.append(psnr_from_loss(float(enc.loss.item())))
-        del enc
-    mb, mp = statistics.mean(b_psnr), statistics.mean(p_psnr)
+    # plain loop: each image alone, the fused step on a one-image batch per
+    # iteration (no batching across images, no graph); at the batch's own
+    # (K, J, tile) the two forms train the same trajectories (equal PSNR by
+    # construction), and at K=16, J=4 for context
+    def plain(pK, pJ, pTW):
+        p_psnr, p_train, p_init = [], 0.0, 0.0
+        for i, img in enumerate(imgs):
+            H, W = sizes[i]
+            n = max(1, min(H * W, int(round(0.06 * H * W))))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            enc = Encoder(img, EncodeConfig(n_sites=n, K=pK, J=pJ, capacity_factor=1.0, seed=seeds[i],
+                                            densify_every=0, tile_w=pTW))
+            enc.init()
+            torch.cuda.synchronize()
+            p_init += time.perf_counter() - t0
+            e0, e1 = E(), E()
+            e0.record()
+            for _ in range(iters):
+                enc.step()
+            e1.record()
+            torch.cuda.synchronize()
+            p_train += e0.elapsed_time(e1) / 1e3
+            p_psnr.append(psnr_from_loss(float(enc.loss.item())))
+            del enc
+        return {"K": pK, "J": pJ, "tile": f"{pTW}x{256 // pTW}", "train_s": round(p_train, 4),
+                "init_s": round(p_init, 3), "images_per_s": round(n_images / (p_train + p_init), 3),
+                "train_mpix_per_s": round(P * iters / p_train / 1e6, 1),
+                "mean_psnr_db": round(statistics.mean(p_psnr), 3)}, p_train
+    same, p_train = plain(K, J, TW)
+    default, d_train = (same, p_train) if (K, J, TW) == (16, 4, 16) else plain(16, 4, 16)
+    mb = statistics.mean(b_psnr)
     return {
         "workload": f"{n_images} images, long side log-uniform 256..2048, aspect 1..1.5, "
                     f"{P / 1e6:.1f} MP total, 0.06 sites/px, {iters} iterations",
         "autotune": {"picked": {"K": K, "J": J, "tile": f"{TW}x{256 // TW}"},
+                     "sample": "the first 8 images, the same iterations",
                      "candidates": [{"K": k, "J": j, "tile": f"{tw}x{256 // tw}", "ms_per_iter": round(ms, 3),
                                      "psnr_db": round(ps, 3)} for k, j, tw, ms, ps in table]},
         "batched": {"train_s": round(b_train, 4), "init_s": round(b_init, 3),
                     "images_per_s": round(n_images / (b_train + b_init), 3),
                     "train_mpix_per_s": round(P * iters / b_train / 1e6, 1),
                     "mean_psnr_db": round(mb, 3)},
-        "plain": {"train_s": round(p_train, 4), "init_s": round(p_init, 3),
-                  "images_per_s": round(n_images / (p_train + p_init), 3),
-                  "train_mpix_per_s": round(P * iters / p_train / 1e6, 1),
-                  "mean_psnr_db": round(mp, 3)},
+        "plain": same,
         "speedup_train": round(p_train / b_train, 3),
-        "psnr_delta_db": round(mb - mp, 3),
+        "psnr_delta_db": round(mb - same["mean_psnr_db"], 3),
+        "plain_k16_j4": default,
+        "speedup_train_vs_k16_j4": round(d_train / b_train, 3),
+        "psnr_delta_vs_k16_j4_db": round(mb - default["mean_psnr_db"], 3),
         "host_image_generation_s": round(gen_s, 2),
     }
 

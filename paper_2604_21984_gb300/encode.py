@@ -50,6 +50,7 @@ class EncodeConfig:
     keep_grads: bool = False   # fused: also write the step's gradients to Encoder.grads
     tile_w: int = 16           # fused: adjoint tiles 16x16 (16) or 32x8 (32)
     graph: bool = False        # fused: replay the iteration and the budget events as CUDA graphs
+    tau_s_d0: float = 4.0      # initial temperature: tau s d0 at the mean site spacing d0
     extra: dict = field(default_factory=dict)
 
 
@@ -74,8 +75,9 @@ def psnr_from_loss(loss: float) -> float:
 
 
 def warm_start(target, n0, params, prep, map_a, map_b, K, J, lambda_init, seed, stream=None,
-               prepass="propagate", passes_after=4, half2_min_jump=0):
-    """Gradient-weighted sites (Sec. 4.4) with tau s d0 = 4, d0 = sqrt(P/n0),
+               prepass="propagate", passes_after=4, half2_min_jump=0, tau_s_d0=4.0):
+    """Gradient-weighted sites (Sec. 4.4) with tau s d0 = tau_s_d0 (4 by
+    default), d0 = sqrt(P/n0),
     then the top-K field's warm-up: seed + ceil(log2 max(H, W)) propagation
     passes at the jump schedule (Sec. 4.3), or with prepass="flood" the JFA
     prepass (seed + ceil(log2 max(H, W)) 3x3 flood passes, App. "Candidate
@@ -91,7 +93,7 @@ def warm_start(target, n0, params, prep, map_a, map_b, K, J, lambda_init, seed, 
     cap = params.shape[1]
     s = 1.0 / max(H, W)
     d0 = math.sqrt(H * W / n0)
-    log_tau0 = math.log(4.0 / (s * d0))
+    log_tau0 = math.log(tau_s_d0 / (s * d0))
     capi.sad_init_sites(target, n0, cap, lambda_init, seed, log_tau0, params=params, stream=stream)
     capi.sad_prepare_sites(params, H, W, prep, stream)
     capi.sad_topk_seed(prep, cap, H, W, K, map_a, stream)
@@ -238,7 +240,7 @@ class Encoder:
         if c.s_grid > 1:
             H, W = self.H, self.W
             s = 1.0 / max(H, W)
-            log_tau0 = math.log(4.0 / (s * math.sqrt(H * W / self.n0)))
+            log_tau0 = math.log(c.tau_s_d0 / (s * math.sqrt(H * W / self.n0)))
             capi.sad_init_sites(self.target, self.n0, self.cap, c.lambda_init, c.seed, log_tau0,
                                 params=self.params, stream=self.stream)
             capi.sad_prepare_sites(self.params, H, W, self.prep, self.stream)
@@ -248,7 +250,8 @@ class Encoder:
             return
         a, b, self.t_pass = warm_start(self.target, self.n0, self.params, self.prep, self.maps[0],
                                        self.maps[1], c.K, c.J, c.lambda_init, c.seed, self.stream,
-                                       prepass=c.prepass, half2_min_jump=c.warm_half2_jump)
+                                       prepass=c.prepass, half2_min_jump=c.warm_half2_jump,
+                                       tau_s_d0=c.tau_s_d0)
         self.maps = [a, b]
         if c.fused:
             # Adam step 1 next; pass indices continue after the warm-up's; the
