@@ -639,17 +639,23 @@ def encode_leg(capi, dev, peak, peak_kind, args, iters=2000):
                                     for k, v in seeds.items()}
     # the encoder's learning rates and initial temperature against their
     # neighbours (seed 0, fused): does a nearby setting do materially better?
+    # And the configuration's literal rates (1e-3 positions, 5e-3 colours
+    # read in normalised units) for the record.
     base_lr = EncodeConfig().lr
 
     def scaled(idx, f):
         return tuple(x * f if i in idx else x for i, x in enumerate(base_lr))
-    sweep = {"default": res["psnr_db"]}
+    sweep = {"default": res["psnr_db"], "default_lr": list(base_lr)}
     everything = range(len(base_lr))
     for name, kw in (("lr_all_x0.5", {"lr": scaled(everything, 0.5)}), ("lr_all_x2", {"lr": scaled(everything, 2.0)}),
                      ("lr_position_x0.5", {"lr": scaled((0, 1), 0.5)}), ("lr_position_x2", {"lr": scaled((0, 1), 2.0)}),
+                     ("lr_radius_x0.5", {"lr": scaled((3,), 0.5)}), ("lr_radius_x2", {"lr": scaled((3,), 2.0)}),
                      ("lr_colour_x0.5", {"lr": scaled((4, 5, 6), 0.5)}), ("lr_colour_x2", {"lr": scaled((4, 5, 6), 2.0)}),
-                     ("lr_log_tau_x0.25", {"lr": scaled((2,), 0.25)}), ("lr_log_tau_x4", {"lr": scaled((2,), 4.0)}),
-                     ("tau_init_x0.5", {"tau_s_d0": 2.0}), ("tau_init_x2", {"tau_s_d0": 8.0})):
+                     ("lr_log_tau_x0.5", {"lr": scaled((2,), 0.5)}), ("lr_log_tau_x2", {"lr": scaled((2,), 2.0)}),
+                     ("lr_direction_aniso_x0.5", {"lr": scaled((7, 8, 9), 0.5)}),
+                     ("lr_direction_aniso_x2", {"lr": scaled((7, 8, 9), 2.0)}),
+                     ("tau_init_x0.5", {"tau_s_d0": 2.0}), ("tau_init_x2", {"tau_s_d0": 8.0}),
+                     ("config_literal_lr", {"lr": capi.LR_CONFIG2_LITERAL})):
         enc = Encoder(img, EncodeConfig(n_sites=N_C2, K=K_C2, J=J_C2, iters=iters, seed=0, **kw))
         enc.run()
         sweep[name] = round(enc.psnr(), 3)

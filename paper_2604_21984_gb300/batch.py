@@ -35,7 +35,7 @@ class BatchConfig:
     sites_per_pixel: float = 0.06
     lambda_init: float = 0.3
     seed: int = 0
-    lr: tuple = (1e-3, 1e-3, 1e-2, 1e-3, 5e-3, 5e-3, 5e-3, 1e-2, 1e-2, 1e-2, 0.0)
+    lr: tuple = capi.LR_DEFAULT
     graph: bool = True
     cand_every: int = 1   # f_cand: candidate refresh every this many iterations
     tile_w: int = 16      # adjoint tiles: 16 (16x16) or 32 (32x8)

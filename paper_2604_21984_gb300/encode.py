@@ -37,7 +37,7 @@ class EncodeConfig:
     prune_pct: float = 0.033
     alpha: float = 0.7
     seed: int = 0
-    lr: tuple = (1e-3, 1e-3, 1e-2, 1e-3, 5e-3, 5e-3, 5e-3, 1e-2, 1e-2, 1e-2, 0.0)
+    lr: tuple = capi.LR_DEFAULT
     fused: bool = True   # one sad_train_step per iteration (else the separate calls)
     cand_every: int = 1  # f_cand: refresh the candidate lists every this many iterations
     cand_passes: int = 1  # n_cand: propagation passes per refresh

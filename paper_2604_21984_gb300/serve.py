@@ -52,7 +52,7 @@ class ServeConfig:
     # plain loop; the reverse order gives a 4x lower p50 but a higher p99)
     fast_priority: int = 0
     bulk_priority: int = -1
-    lr: tuple = (1e-3, 1e-3, 1e-2, 1e-3, 5e-3, 5e-3, 5e-3, 1e-2, 1e-2, 1e-2, 0.0)
+    lr: tuple = capi.LR_DEFAULT
 
 
 @dataclass
