@@ -367,7 +367,7 @@ def headline(capi, dev, args, rank, world, dist, peak, peak_kind, local):
            "serial": {"value": round(whole_job_value(world, P, args.steps, e2e_serial_s), 3),
                       "path": "the same, each step synchronised before the next upload"}}
     # roofline of the dominant kernel, from its own event pairs in the timed
-    # region; algorithmic bytes per launch (SURVEY 8(d) unit): render and
+    # region; algorithmic bytes per launch (per pixel and per site): render and
     # backward each read the map (4K B) and 12 B of colour or upstream
     # gradient per pixel and the 48-byte prepared record of every site
     kname, klaunch, kms = dominant(trace)

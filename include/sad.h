@@ -293,7 +293,7 @@ int sad_train_grads(const float* params, const float* prep, int32_t capacity, in
  * Scratch is one SAD_NOALLOC_SCRATCH_BYTES buffer inside the library
  * (allocated on every device that loads the library, kept until exit).
  * Limits: H*W <= 4194304 and capacity <= 262144, else SAD_EINVAL; within them
- * about 1.2 million per-tile records fit (a 2048 x 2048 render of 262144
+ * about 1.0 million per-tile records fit (a 2048 x 2048 render of 262144
  * random sites at K = 16 makes about 0.83 million; spatially incoherent lists
  * make many more and overflow).  The first call on a device looks up the
  * buffer's device address and keeps it for the life of the process (make that

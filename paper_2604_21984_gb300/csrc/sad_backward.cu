@@ -37,7 +37,7 @@ namespace sad {
 // workspace layout
 // ---------------------------------------------------------------------------
 struct WsLayout {
-  size_t hdr, tile_loss, cnt, start, bsums, dir, records, total;
+  size_t hdr, tile_loss, cnt, start, bsums, dir, place, records, total;
   uint32_t max_records, n_tiles;
 };
 
@@ -63,6 +63,7 @@ static WsLayout ws_layout(int H, int W, int K, int cap, int64_t max_records) {
   L.start = o;      o = align256(o + sizeof(uint32_t) * c);
   L.bsums = o;      o = align256(o + sizeof(uint32_t) * (seg_blocks(c) + 1));
   L.dir = o;        o = align256(o + sizeof(uint32_t) * L.max_records);
+  L.place = o;      o = align256(o + sizeof(uint2) * L.max_records);
   L.records = o;    o = align256(o + sizeof(Record) * L.max_records);
   L.total = o;
   return L;
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(kSumThreads) k_site_grads(const float* __restr
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const size_t c = static_cast<size_t>(cap);
   float acc[10];
-  const uint32_t n = warp_site_sums<10>(i < cap, static_cast<uint32_t>(i), static_cast<uint32_t>(cap), start, boff,
+  const uint32_t n = warp_site_sums<10, 2>(i < cap, static_cast<uint32_t>(i), static_cast<uint32_t>(cap), start, boff,
                                         dir, rec, hdr->pmax[0], L, s_ws[threadIdx.x >> 5], acc);  // every lane takes part
   if (i >= cap) return;
   float out[kNParams];
@@ -223,7 +224,7 @@ static int run_backward(const float* params, const float* prep, int cap, int H, 
   {
     // per record: its 48 bytes and its directory entry; the two regions'
     // 256-byte alignment can hide up to 512 bytes, so start above and step down
-    const uint64_t per = sizeof(Record) + sizeof(uint32_t);
+    const uint64_t per = sizeof(Record) + sizeof(uint32_t) + sizeof(uint2);
     uint64_t mr = 1 + (ws_bytes - L1.total + 512) / per;
     if (mr > 0xfffffff0ull) mr = 0xfffffff0ull;
     for (int it = 0; it < 64 && mr > 1; ++it, --mr) {
@@ -238,6 +239,7 @@ static int run_backward(const float* params, const float* prep, int cap, int H, 
   WsHeader* hdr = reinterpret_cast<WsHeader*>(base + LL.hdr);
   float* tile_loss = reinterpret_cast<float*>(base + LL.tile_loss);
   Record* rec = reinterpret_cast<Record*>(base + LL.records);
+  uint2* place = reinterpret_cast<uint2*>(base + LL.place);
   uint32_t* cnt = reinterpret_cast<uint32_t*>(base + LL.cnt);
   uint32_t* start = reinterpret_cast<uint32_t*>(base + LL.start);
   uint32_t* bsums = reinterpret_cast<uint32_t*>(base + LL.bsums);
@@ -262,6 +264,7 @@ static int run_backward(const float* params, const float* prep, int cap, int H, 
   io.rgb_out = rgb_out;
   io.tile_loss = tl;
   io.records = rec;
+  io.place = place;
   io.max_records = LL.max_records;
   io.hdr = hdr;
   io.site_cnt = cnt;
@@ -304,7 +307,7 @@ static int run_backward(const float* params, const float* prep, int cap, int H, 
   // the segmented reduce: segment starts, records filed by site, exact sums
   run_seg_scan(cnt, static_cast<uint32_t>(cap), start, bsums, hdr, st);
   const int L = count_bits(LL.n_tiles);
-  { TraceScope tr_(st, "k_rec_scatter"); k_rec_scatter<<<152 * 8, 256, 0, st>>>(rec, hdr, LL.max_records, start, bsums, dir); }
+  { TraceScope tr_(st, "k_rec_scatter"); k_rec_scatter<<<152 * 8, 256, 0, st>>>(place, hdr, LL.max_records, start, bsums, dir); }
   if (int r = check_launch("k_rec_scatter")) return r;
   if (stats_mode) {
     { TraceScope tr_(st, "k_site_stats"); k_site_stats<<<(cap + kSumThreads - 1) / kSumThreads, kSumThreads, 0, st>>>(cap, start, bsums, dir, rec, hdr, L, stats); }

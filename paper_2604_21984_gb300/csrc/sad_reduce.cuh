@@ -204,9 +204,10 @@ __device__ __forceinline__ uint32_t seg_start(const uint32_t* __restrict__ start
   return start_local[j] + boff[j / kSegBlock];
 }
 
-// Files record r at its place in its site's segment of the directory.  Each
-// thread takes four records a pass (all loads issued before the stores).
-static __global__ void k_rec_scatter(const Record* __restrict__ rec, const WsHeader* __restrict__ hdr,
+// Files record r at its place in its site's segment of the directory (place:
+// the records' {place, site} pairs, contiguous).  Each thread takes four
+// records a pass (all loads issued before the stores).
+static __global__ void k_rec_scatter(const uint2* __restrict__ place, const WsHeader* __restrict__ hdr,
                                      uint32_t max_records, const uint32_t* __restrict__ start_local,
                                      const uint32_t* __restrict__ boff, uint32_t* __restrict__ dir) {
   const uint64_t n = min(hdr->cursor, max_records);
@@ -216,7 +217,7 @@ static __global__ void k_rec_scatter(const Record* __restrict__ rec, const WsHea
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const uint64_t r = r0 + u * stride;
-      rc[u] = r < n ? ldg(reinterpret_cast<const uint2*>(rec + r)) : make_uint2(0u, 0u);  // {rank, cj}
+      rc[u] = r < n ? ldg(place + r) : make_uint2(0u, 0u);  // {rank, cj}
     }
     uint32_t at[4];
 #pragma unroll

@@ -416,7 +416,7 @@ __global__ void k_insert_pixels(const uint4* __restrict__ src_map, const float* 
 }
 
 struct StepLayout {
-  size_t hdr, cnt, tile_loss, bias, start, bsums, dir, records, total;
+  size_t hdr, cnt, tile_loss, bias, start, bsums, dir, place, records, total;
   uint32_t max_records;
 };
 
@@ -440,6 +440,7 @@ static StepLayout step_layout(uint32_t n_tiles, uint64_t total_pixels, int K, in
   L.start = o;     o = al256(o + sizeof(uint32_t) * c);
   L.bsums = o;     o = al256(o + sizeof(uint32_t) * (seg_blocks(c) + 1));
   L.dir = o;       o = al256(o + sizeof(uint32_t) * L.max_records);
+  L.place = o;     o = al256(o + sizeof(uint2) * L.max_records);
   L.records = o;   o = al256(o + sizeof(Record) * L.max_records);
   L.total = o;
   return L;
@@ -568,7 +569,7 @@ int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t 
   {
     // per record: its 48 bytes and its directory entry; the two regions'
     // 256-byte alignment can hide up to 512 bytes, so start above and step down
-    const uint64_t per = sizeof(Record) + sizeof(uint32_t);
+    const uint64_t per = sizeof(Record) + sizeof(uint32_t) + sizeof(uint2);
     uint64_t mr = 1 + (workspace_bytes - L1.total + 512) / per;
     if (mr > 0xfffffff0ull) mr = 0xfffffff0ull;
     for (int it = 0; it < 64 && mr > 1; ++it, --mr) {
@@ -589,6 +590,7 @@ int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t 
   uint32_t* bsums = reinterpret_cast<uint32_t*>(base + L.bsums);
   uint32_t* dir = reinterpret_cast<uint32_t*>(base + L.dir);
   Record* rec = reinterpret_cast<Record*>(base + L.records);
+  uint2* place = reinterpret_cast<uint2*>(base + L.place);
   const cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st);
   if (e != cudaSuccess) {
     set_error("sad_train_step memset: %s", cudaGetErrorString(e));
@@ -604,6 +606,7 @@ int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t 
   io.rgb_out = nullptr;
   io.tile_loss = tile_loss;
   io.records = rec;
+  io.place = place;
   io.max_records = L.max_records;
   io.hdr = hdr;
   io.site_cnt = cnt;
@@ -650,7 +653,7 @@ int sad_train_step(const sad_batch_image* images, int32_t B, int32_t K, int32_t 
   // the segmented reduce: segment starts of the batch's sites (compacted
   // index), records filed by site
   run_seg_scan(cnt, d.n_sites, start, bsums, hdr, st);
-  { TraceScope tr_(st, "k_rec_scatter"); k_rec_scatter<<<152 * 8, 256, 0, st>>>(rec, hdr, L.max_records, start, bsums, dir); }
+  { TraceScope tr_(st, "k_rec_scatter"); k_rec_scatter<<<152 * 8, 256, 0, st>>>(place, hdr, L.max_records, start, bsums, dir); }
   if (int r = check_launch("k_rec_scatter")) return r;
   const SiteSums S{start, bsums, dir, rec, hdr};
   const AdamArgs A = adam_args(hp);

@@ -171,6 +171,7 @@ struct TileIO {
   float* rgb_out;                 // optional render
   float* tile_loss;               // optional per-tile squared-error sums
   Record* records;
+  uint2* place;  // per record {place among its site's records, compacted site index}, for the scatter
   uint32_t max_records;
   WsHeader* hdr;
   uint32_t* site_cnt;  // records per compacted site index (incremented per stored record)
@@ -564,7 +565,11 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
         s_list[pos] = static_cast<uint8_t>(t);
       }
     }
-    if (r_idx < max_records) *reinterpret_cast<uint2*>(&records[r_idx]) = make_uint2(r_rank, r_cj);
+    if (r_idx < max_records) {
+      const uint2 rc = make_uint2(r_rank, r_cj);
+      *reinterpret_cast<uint2*>(&records[r_idx]) = rc;
+      io.place[r_idx] = rc;  // the scatter reads these 8 bytes contiguously
+    }
     if (packed != 0u) sm.order[sm.hoff[b_id] + b_pos] = static_cast<uint8_t>(t);
     __syncthreads();
     // Two slots at a time, one per half-warp: the 16 lanes walk the slot's
