@@ -129,6 +129,26 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+// The same over each quarter-warp (8 lanes, offsets 4, 2, 1; the quarters
+// sum their own values): returns, on lane l, the totals of values 2 (l % 8)
+// and 2 (l % 8) + 1 of its quarter (values 10..15 are padding).
+__device__ __forceinline__ float2 quarter_sum10_halving(const float (&in)[10], int lane) {
+  float a[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) a[j] = j < 10 ? in[j] : 0.f;
+#pragma unroll
+  for (int h = 8, o = 4; o >= 1; h >>= 1, o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < h; ++j) {
+      const float keep = up ? a[h + j] : a[j];
+      const float give = up ? a[j] : a[h + j];
+      a[j] = keep + __shfl_xor_sync(0xffffffffu, give, o);
+    }
+  }
+  return make_float2(a[0], a[1]);
+}
+
 // The same over each half-warp (16 lanes, offsets 8, 4, 2, 1; the halves sum
 // their own values): returns, on lane l, the total of value l % 16 of its
 // half (values 10..15 are padding).
@@ -207,8 +227,8 @@ struct TileShared {
   uint32_t off[kSlots];
   uint32_t rix[kSlots];
   uint8_t order[kSlots];           // this round's slots with a record, largest pair counts first
-  uint32_t hist[16];               // slots per 16-wide pair-count bucket (largest first)
-  uint32_t hoff[16];               // their exclusive prefix
+  uint32_t hist[32];               // slots per 8-wide pair-count bucket (largest first)
+  uint32_t hoff[32];               // their exclusive prefix
   uint8_t slot8[K][kTileThreads];  // this round's slot of each listed entry
   uint8_t list[kTileThreads * K];
   // per pixel.  gradient mode: {m log2 e - log2(1/Z), 1/Z, g.cbar, gx},
@@ -461,7 +481,9 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
 
   // ---- 2..3. rounds: slot assignment, stable pair lists, warp per slot ---
   uint32_t pending = vm;
-  uint32_t pm = 0u;  // lanes i and 16 + i: the largest |value| of statistic i in this warp's records (float bits)
+  // lanes i, 8 + i, 16 + i, 24 + i (i < 5): the largest |value| of statistics
+  // 2i (pm) and 2i + 1 (pm1) in this warp's records (float bits)
+  uint32_t pm = 0u, pm1 = 0u;
   uint32_t got = 0u;      // entries that got a slot this round (slots in sm.slot8)
   const uint32_t lt_mask = (1u << lane) - 1u;
   for (;;) {
@@ -479,7 +501,7 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) idr[k] = sr.has(idr[k]) ? idr[k] : kInvalid;
-    if (t < 16) sm.hist[t] = 0u;
+    if (t < 32) sm.hist[t] = 0u;
     for (int i = t; i < kSlots; i += kTileThreads) {
       s_keys[i] = kInvalid;
 #pragma unroll
@@ -523,7 +545,7 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
         c += __popc(s_mask[w][t]);
       }
       packed = static_cast<uint64_t>(c) | (1ull << 32);
-      b_id = 15u - min(15u, (c - 1u) >> 4);
+      b_id = 31u - min(31u, (c - 1u) >> 3);
       b_pos = atomicAdd(&sm.hist[b_id], 1u);  // a place in the walk order, not a value
     }
     uint64_t total;
@@ -534,14 +556,14 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
       s_rix[t] = static_cast<uint32_t>(ex >> 32);
     }
     if (t < 32) {  // bucket offsets (the histogram is complete: the scan synchronised)
-      const uint32_t h = t < 16 ? sm.hist[t] : 0u;
+      const uint32_t h = sm.hist[t];
       uint32_t x = h;
 #pragma unroll
-      for (int o = 1; o < 16; o <<= 1) {
+      for (int o = 1; o < 32; o <<= 1) {
         const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
       }
-      if (t < 16) sm.hoff[t] = x - h;
+      sm.hoff[t] = x - h;
     }
     if (t == 0) {
       s_base = atomicAdd(&hdr->cursor, static_cast<uint32_t>(total >> 32));
@@ -572,22 +594,22 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
     }
     if (packed != 0u) sm.order[sm.hoff[b_id] + b_pos] = static_cast<uint8_t>(t);
     __syncthreads();
-    // Two slots at a time, one per half-warp: the 16 lanes walk the slot's
+    // Four slots at a time, one per quarter-warp: the 8 lanes walk the slot's
     // pixel-ordered pairs, then a fixed-order reduction sums their partials.
-    // The warps take pairs of slots in turn from a shared counter, in the
-    // order of the slots' pair counts (16-wide buckets, largest first), so
-    // the two halves walk similar counts; a slot's record is the same
-    // whichever half-warp computes it.
+    // The warps take groups of four slots in turn from a shared counter, in
+    // the order of the slots' pair counts (8-wide buckets, largest first),
+    // so the quarters of a warp walk similar counts; a slot's record is the
+    // same whichever quarter-warp computes it.
     const uint32_t n_rec = static_cast<uint32_t>(total >> 32);
-    const int half = lane >> 4, hl = lane & 15;
+    const int quarter = lane >> 3, ql = lane & 7;
     for (;;) {
       uint32_t j = 0u;
-      if (lane == 0) j = atomicAdd(&sm.next, 2u);
+      if (lane == 0) j = atomicAdd(&sm.next, 4u);
       j = __shfl_sync(0xffffffffu, j, 0);
       if (j >= n_rec) break;
       {
-        const bool live = j + half < n_rec;  // the odd last slot leaves a half idle
-        const int sl = sm.order[live ? j + half : j];
+        const bool live = j + quarter < n_rec;  // the last group may leave quarters idle
+        const int sl = sm.order[live ? j + quarter : j];
         const uint32_t cnt = live ? s_cnt[sl] : 0u;
         const uint32_t id = s_keys[sl];
         const uint32_t off = s_off[sl];
@@ -600,7 +622,7 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
         // mode: its weights are zero, so its pairs are skipped)
         const uint32_t n_pairs = (SAVED && ms.w == 0.f) ? 0u : cnt;
         if (MODE == kModeStats) {
-          for (uint32_t i = hl; i < n_pairs; i += 16) {
+          for (uint32_t i = ql; i < n_pairs; i += 8) {
             const uint32_t p = s_list[off + i];
             const float4 A = s_pa[p];
             const float dx = (x0 + static_cast<int>(p & (TW - 1)) + 0.5f) - gs.x;
@@ -634,7 +656,7 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
         } else {
           const float g01 = 2.f * ms.y;
           const float tsl = gs.z * kLog2e;
-          for (uint32_t i = hl; i < n_pairs; i += 16) {
+          for (uint32_t i = ql; i < n_pairs; i += 8) {
             const uint32_t p = s_list[off + i];
             // A = {M2, 1/Z, g.cbar, gx}, B = {gy, gz, px, py}
             const float4 A = s_pa[p];
@@ -663,17 +685,20 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
             acc[9] += ay * dy;
           }
         }
-        // sum the 10 lane partials over each half by recursive halving (fixed
-        // order): afterwards lane i of a half holds the total of statistic i
-        const float tot = half_sum10_halving(acc, lane);
+        // sum the 10 lane partials over each quarter by recursive halving
+        // (fixed order): afterwards lane i of a quarter holds the totals of
+        // statistics 2i and 2i + 1
+        const float2 tot = quarter_sum10_halving(acc, lane);
         if (live) {
           if (ridx < max_records) {
-            if (hl < 10) {
-              const float v = isfinite(tot) ? tot : 0.f;  // non-finite contributions are dropped
-              records[ridx].acc[hl] = v;
-              pm = max(pm, __float_as_uint(fabsf(v)));
+            if (ql < 5) {
+              const float v0 = isfinite(tot.x) ? tot.x : 0.f;  // non-finite contributions are dropped
+              const float v1 = isfinite(tot.y) ? tot.y : 0.f;
+              *reinterpret_cast<float2*>(&records[ridx].acc[2 * ql]) = make_float2(v0, v1);
+              pm = max(pm, __float_as_uint(fabsf(v0)));
+              pm1 = max(pm1, __float_as_uint(fabsf(v1)));
             }
-          } else if (hl == 0) {
+          } else if (ql == 0) {
             hdr->overflow = 1u;
           }
         }
@@ -683,7 +708,8 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
   }
   // the image's scale of the per-site sums: the largest |record value| of
   // each statistic (the max is order independent)
-  if (pm != 0u) atomicMax(&s_pmax[lane & 15], pm);  // a bound, not a value
+  if (pm != 0u) atomicMax(&s_pmax[2 * (lane & 7)], pm);  // a bound, not a value
+  if (pm1 != 0u) atomicMax(&s_pmax[2 * (lane & 7) + 1], pm1);
   __syncthreads();
   if (t < 10 && s_pmax[t]) atomicMax(&hdr->pmax[c.img][t], s_pmax[t]);
 }
