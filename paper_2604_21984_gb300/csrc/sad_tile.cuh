@@ -229,7 +229,6 @@ struct TileShared {
   uint8_t order[kSlots];           // this round's slots with a record, largest pair counts first
   uint32_t hist[32];               // slots per 8-wide pair-count bucket (largest first)
   uint32_t hoff[32];               // their exclusive prefix
-  uint8_t slot8[K][kTileThreads];  // this round's slot of each listed entry
   uint8_t list[kTileThreads * K];
   // per pixel.  gradient mode: {m log2 e - log2(1/Z), 1/Z, g.cbar, gx},
   // {gy, gz, px, py};
@@ -484,7 +483,7 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
   // lanes i, 8 + i, 16 + i, 24 + i (i < 5): the largest |value| of statistics
   // 2i (pm) and 2i + 1 (pm1) in this warp's records (float bits)
   uint32_t pm = 0u, pm1 = 0u;
-  uint32_t got = 0u;      // entries that got a slot this round (slots in sm.slot8)
+  uint32_t got = 0u;      // entries that got a slot this round (their slots replace the ids in idr[])
   const uint32_t lt_mask = (1u << lane) - 1u;
   for (;;) {
     // this round's ids from the lists in memory (the same entries as ids[],
@@ -531,7 +530,7 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
       if (sl != kNone) {
         pending &= ~(1u << k);
         got |= 1u << k;
-        sm.slot8[k][t] = static_cast<uint8_t>(sl);
+        idr[k] = sl;  // the id is not needed again this round
       }
     }
     __syncthreads();
@@ -582,7 +581,7 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       if ((got >> k & 1u) != 0u) {
-        const uint32_t sl = sm.slot8[k][t];
+        const uint32_t sl = idr[k];
         const uint32_t pos = s_off[sl] + s_wpre[warp][sl] + __popc(s_mask[warp][sl] & lt_mask);
         s_list[pos] = static_cast<uint8_t>(t);
       }
