@@ -55,30 +55,31 @@ struct WsHeader {
 static_assert(sizeof(WsHeader) == 256 + 4 * 16 * kMaxImages, "header layout");
 
 // ---------------------------------------------------------------------------
-// block-wide exclusive scan of a 64-bit value over 256 threads (fixed order)
+// block-wide exclusive scan of the packed slot counts over 256 threads (fixed order)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint64_t block_excl_scan256(uint64_t v, uint64_t* warp_tot,
-                                                       uint64_t& total) {
+// 32-bit form for the slot scan: each value packs a pair count (at most 256
+// per slot, 4096 per tile) in its low 16 bits and a record count (at most
+// 256) in its high 16 bits, so the sums never carry across.  warp_tot must
+// not be written again before a barrier that follows the call.
+__device__ __forceinline__ uint32_t block_excl_scan256_u32(uint32_t v, uint32_t* warp_tot,
+                                                           uint32_t& total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint64_t x = v;
+  uint32_t x = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
     if (lane >= o) x += y;
   }
   if (lane == 31) warp_tot[warp] = x;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    uint64_t run = 0;
-    for (int w = 0; w < kTileThreads / 32; ++w) {
-      run += warp_tot[w];
-      warp_tot[w] = run;
-    }
+  uint32_t pre = 0u, run = 0u;
+#pragma unroll
+  for (int w = 0; w < kTileThreads / 32; ++w) {  // every thread adds the eight warp totals itself
+    const uint32_t tw = warp_tot[w];
+    pre += w < warp ? tw : 0u;
+    run += tw;
   }
-  __syncthreads();
-  const uint64_t pre = warp ? warp_tot[warp - 1] : 0ull;
-  total = warp_tot[kTileThreads / 32 - 1];
-  __syncthreads();
+  total = run;
   return pre + x - v;
 }
 
@@ -238,7 +239,7 @@ struct TileShared {
   float4 pg[MODE == kModeStats ? 1 : kTileThreads];
   float4 pb[MODE == kModeStats ? kTileThreads : 1];
   float4 pc[MODE == kModeStats ? kTileThreads : 1];
-  uint64_t scan[kW];
+  uint32_t scan[kW];
   float red[kW];
   uint32_t base;
   uint32_t next;      // the walk's next record index (slots are taken in turn by the warps)
@@ -534,7 +535,7 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
       }
     }
     __syncthreads();
-    uint64_t packed = 0;
+    uint32_t packed = 0;
     uint32_t b_id = 0u, b_pos = 0u;  // the slot's pair-count bucket and its place there
     if (t < kSlots && s_keys[t] != kInvalid) {
       uint32_t c = 0;
@@ -543,16 +544,16 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
         s_wpre[w][t] = static_cast<uint16_t>(c);
         c += __popc(s_mask[w][t]);
       }
-      packed = static_cast<uint64_t>(c) | (1ull << 32);
+      packed = c | (1u << 16);
       b_id = 31u - min(31u, (c - 1u) >> 3);
       b_pos = atomicAdd(&sm.hist[b_id], 1u);  // a place in the walk order, not a value
     }
-    uint64_t total;
-    const uint64_t ex = block_excl_scan256(packed, s_scan, total);
+    uint32_t total;
+    const uint32_t ex = block_excl_scan256_u32(packed, s_scan, total);
     if (t < kSlots) {
-      s_cnt[t] = static_cast<uint32_t>(packed & 0xffffffffu);
-      s_off[t] = static_cast<uint32_t>(ex & 0xffffffffu);
-      s_rix[t] = static_cast<uint32_t>(ex >> 32);
+      s_cnt[t] = packed & 0xffffu;
+      s_off[t] = ex & 0xffffu;
+      s_rix[t] = ex >> 16;
     }
     if (t < 32) {  // bucket offsets (the histogram is complete: the scan synchronised)
       const uint32_t h = sm.hist[t];
@@ -565,7 +566,7 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
       sm.hoff[t] = x - h;
     }
     if (t == 0) {
-      s_base = atomicAdd(&hdr->cursor, static_cast<uint32_t>(total >> 32));
+      s_base = atomicAdd(&hdr->cursor, total >> 16);
       sm.next = 0u;
     }
     __syncthreads();
@@ -599,7 +600,7 @@ __device__ __forceinline__ void tile_body(const TileCtx& c, const TileIO& io, ui
     // the order of the slots' pair counts (8-wide buckets, largest first),
     // so the quarters of a warp walk similar counts; a slot's record is the
     // same whichever quarter-warp computes it.
-    const uint32_t n_rec = static_cast<uint32_t>(total >> 32);
+    const uint32_t n_rec = total >> 16;
     const int quarter = lane >> 3, ql = lane & 7;
     for (;;) {
       uint32_t j = 0u;
