@@ -523,7 +523,7 @@ def sad_densify_prune_async(params, m, v, H, W, K, stats, target, map_inout, dp,
 # sweep on the 768x512 encode workload (2000 iterations, 2 images x 3 runs);
 # LR_CONFIG2_LITERAL is 1e-3 for positions and 5e-3 for colours read in
 # normalised units, with the other planes at 1e-2 / 1e-3.
-LR_DEFAULT = (1.25e-4, 1.25e-4, 1e-2, 6.25e-5, 1.25e-3, 1.25e-3, 1.25e-3, 7.5e-3, 7.5e-3, 7.5e-3, 0.0)
+LR_DEFAULT = (6.25e-5, 6.25e-5, 1e-2, 6.25e-5, 1.25e-3, 1.25e-3, 1.25e-3, 1.5e-2, 1.5e-2, 1.5e-2, 0.0)
 LR_CONFIG2_LITERAL = (1e-3, 1e-3, 1e-2, 1e-3, 5e-3, 5e-3, 5e-3, 1e-2, 1e-2, 1e-2, 0.0)
 
 
