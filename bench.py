@@ -325,7 +325,8 @@ def headline(capi, dev, args, rank, world, dist, peak, peak_kind, local):
     # inputs go up on a copy stream while step i computes, and step i's
     # gradients come back on it while step i + 1 starts (every step still
     # copies its own inputs from pinned host memory and reads its gradients
-    # back; the backward's overflow check still synchronises every step)
+    # back; the backward's workspace holds the worst case, so no step
+    # synchronises the host)
     copy_s = torch.cuda.Stream(device=dev)
     comp_s = torch.cuda.current_stream(dev)
     dp = [torch.empty(host_p.shape, dtype=torch.float32, device=dev) for _ in range(2)]

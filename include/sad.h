@@ -243,14 +243,27 @@ size_t sad_backward_workspace_bytes(int32_t H, int32_t W, int32_t K, int32_t cap
                                     int64_t max_records);
 
 /*
+ * The most per-tile partial records that sad_render_backward /
+ * sad_render_backward_saved / sad_train_grads can produce for ANY top-K map
+ * of an H x W, list size K, `capacity`-site problem: one record per 16x16
+ * tile and distinct site listed in it, so n_tiles * min(256 K, capacity)
+ * with n_tiles = ceil(H/16) ceil(W/16).  A workspace of
+ * sad_backward_workspace_bytes(H, W, K, capacity, this bound) never
+ * overflows, so its caller needs no sad_workspace_status read (a bound
+ * above 2^32 - 16 cannot be held by one workspace).  Returns -1 for an
+ * invalid problem (H or W <= 0, capacity < 0, K not 4, 8 or 16).
+ */
+int64_t sad_backward_max_records(int32_t H, int32_t W, int32_t K, int32_t capacity);
+
+/*
  * sad_render_backward -- adjoint of sad_render into every site parameter
  * (App. "Gradient Computation and Reduction", Per-pixel gradients), with the top-K map a frozen index set.
  * Per pixel the softmax is recomputed (nothing from the forward is stored);
  * per 16x16 tile the contributions are reduced per site in a fixed order
  * (per-tile partials, no float atomics; replaces the tile hash + global float
- * atomics of Sec. 4.8), then each site's partials are summed in exact 64-bit
- * fixed point (integer atomics: order independent).  Bitwise reproducible
- * run to run.
+ * atomics of Sec. 4.8), then a segmented reduce sums each site's partials in
+ * exact 64-bit fixed point (no atomics on the values: integer sums, order
+ * independent).  Bitwise reproducible run to run.
  * grad_rgb: float32[H][W][3] = dL/dc.  grads: float32[11][capacity], fully
  * written (zero for sites no pixel lists).  params/prep must describe the
  * same sites.  If more partial records are produced than the workspace holds,

@@ -8,11 +8,16 @@ softmax); the backward recomputes every (pixel, site) weight from its logit
 inside the CUDA adjoint instead of storing the N x K weights.  All work runs
 in libsad.so through the C-ABI binding.
 
-The adjoint writes one partial record per (site, tile) into a workspace sized
-for H*W*K/8 records, ten times what a propagated top-K map of random sites
-needs; a spatially incoherent map can need more.  ``CHECK_OVERFLOW`` (on by
-default) reads the workspace's record count after every backward (a stream
-synchronisation): on an overflow the workspace grows to the count reported
+The adjoint writes one partial record per (site, tile) into a workspace.
+When the workspace for the problem's worst case (every 16x16 tile listing
+min(256 K, N) distinct sites, ``capi.sad_backward_max_records``) takes at most
+``WORST_CASE_BYTES`` and half of the device's free memory, that is the one
+allocated: no map can overflow it, so the backward reads no status and never
+synchronises the stream.  Otherwise the workspace holds H*W*K/8 records, ten
+times what a propagated top-K map of random sites needs, and a spatially
+incoherent map can need more: ``CHECK_OVERFLOW`` (on by default) then reads
+the workspace's record count after every backward (a stream
+synchronisation); on an overflow the workspace grows to the count reported
 and the backward runs again, so the gradients are always complete.  A caller
 that knows its maps fit may turn the check off.
 """
@@ -24,21 +29,31 @@ from . import capi
 
 
 CHECK_OVERFLOW = True
+WORST_CASE_BYTES = 8 << 30
 
 
 class _Workspaces:
-    """Per-(device, problem) cache of the backward workspace."""
+    """Per-(device, problem) cache of the backward workspace: (workspace,
+    whether it holds the worst case)."""
 
     def __init__(self):
         self._ws = {}
 
     def get(self, device, H, W, K, cap, min_records=0):
         key = (str(device), H, W, K, cap)
-        ws, n = self._ws.get(key, (None, 0))
+        ws, n, exact = self._ws.get(key, (None, 0, False))
         if ws is None or n < min_records:
-            ws = capi.backward_workspace(H, W, K, cap, max_records=min_records, device=device)
-            self._ws = {key: (ws, min_records)}   # keep only the latest problem
-        return ws
+            worst = capi.sad_backward_max_records(H, W, K, cap)
+            nbytes = capi.lib().sad_backward_workspace_bytes(H, W, K, cap, worst)
+            free = torch.cuda.mem_get_info(device)[0]
+            if min_records == 0 and worst < 0xFFFFFFF0 and nbytes <= min(WORST_CASE_BYTES, free // 2):
+                ws = capi.backward_workspace(H, W, K, cap, max_records=worst, device=device)
+                n, exact = worst, True
+            else:
+                ws = capi.backward_workspace(H, W, K, cap, max_records=min_records, device=device)
+                n, exact = min_records, False
+            self._ws = {key: (ws, n, exact)}   # keep only the latest problem
+        return ws, exact
 
 
 _WS = _Workspaces()
@@ -68,14 +83,14 @@ class SADRender(torch.autograd.Function):
         cap = params.shape[1]
         grads = torch.empty_like(params)
         g = grad_rgb.contiguous().to(torch.float32)
-        ws = _WS.get(params.device, H, W, K, cap)
+        ws, exact = _WS.get(params.device, H, W, K, cap)
         capi.sad_render_backward_saved(params, prep, H, W, K, topk_map, g, rgb, fwd, grads, ws)
-        if CHECK_OVERFLOW:
+        if CHECK_OVERFLOW and not exact:
             st, used = capi.sad_workspace_status(ws)
             if st == capi.SAD_EWORKSPACE:
                 # the record count is a property of the map alone: a workspace
                 # of that many records holds them all on the second run
-                ws = _WS.get(params.device, H, W, K, cap, min_records=used)
+                ws, _ = _WS.get(params.device, H, W, K, cap, min_records=used)
                 capi.sad_render_backward_saved(params, prep, H, W, K, topk_map, g, rgb, fwd, grads, ws)
                 st, used = capi.sad_workspace_status(ws)
             if st != 0:

@@ -135,6 +135,8 @@ _SIGS = {
     "sad_backward_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32,
                                                        ctypes.c_int32, ctypes.c_int32,
                                                        ctypes.c_int64]),
+    "sad_backward_max_records": (ctypes.c_int64, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                   ctypes.c_int32]),
     "sad_render_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -287,6 +289,13 @@ def backward_workspace(H, W, K, cap, max_records=0, device="cuda"):
     if n == 0:
         raise ValueError("invalid problem for sad_backward_workspace_bytes")
     return torch.empty(n, dtype=torch.uint8, device=device)
+
+
+def sad_backward_max_records(H, W, K, cap):
+    n = lib().sad_backward_max_records(H, W, K, cap)
+    if n < 0:
+        raise ValueError("invalid problem for sad_backward_max_records")
+    return int(n)
 
 
 # ----------------------------------------------------------------------------

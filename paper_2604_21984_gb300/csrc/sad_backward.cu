@@ -329,6 +329,13 @@ size_t sad_backward_workspace_bytes(int32_t H, int32_t W, int32_t K, int32_t cap
   return ws_layout(H, W, K, capacity, max_records).total;
 }
 
+int64_t sad_backward_max_records(int32_t H, int32_t W, int32_t K, int32_t capacity) {
+  if (H <= 0 || W <= 0 || capacity < 0 || (K != 4 && K != 8 && K != 16)) return -1;
+  const int64_t n_tiles = static_cast<int64_t>((H + kTileSide - 1) / kTileSide) * ((W + kTileSide - 1) / kTileSide);
+  const int64_t per_tile = static_cast<int64_t>(kTileThreads) * K;  // each pixel lists K entries
+  return n_tiles * (per_tile < capacity ? per_tile : static_cast<int64_t>(capacity));
+}
+
 int sad_render_backward(const float* params, const float* prep, int32_t capacity, int32_t H,
                         int32_t W, int32_t K, const uint32_t* map, const float* grad_rgb,
                         float* grads, void* workspace, size_t workspace_bytes, void* stream) {

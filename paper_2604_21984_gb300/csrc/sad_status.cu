@@ -32,6 +32,6 @@ const char* sad_status_string(int status) {
 
 const char* sad_last_error(void) { return sad::g_last_error.c_str(); }
 
-int sad_abi_version(void) { return 7; }
+int sad_abi_version(void) { return 8; }
 
 }  // extern "C"

@@ -34,7 +34,7 @@ def test_every_declared_symbol_is_exported(L):
 
 
 def test_status_strings_and_version(L):
-    assert L.sad_abi_version() == 7
+    assert L.sad_abi_version() == 8
     assert L.sad_status_string(0) == b"ok"
     assert L.sad_status_string(1) == b"invalid argument"
     assert L.sad_status_string(99) == b"unknown status"
@@ -48,6 +48,16 @@ def test_workspace_size_query(L):
     assert L.sad_backward_workspace_bytes(0, 64, 8, 256, 0) == 0       # empty image
     more = L.sad_backward_workspace_bytes(64, 64, 8, 256, 10 ** 6)
     assert more > small
+
+
+def test_backward_record_bound(L):
+    # 4 x 4 tiles of 16 x 16; a tile's 256 pixels list at most 256 K distinct sites
+    assert L.sad_backward_max_records(64, 64, 8, 256) == 16 * 256            # capped by the sites
+    assert L.sad_backward_max_records(64, 64, 8, 10 ** 6) == 16 * 256 * 8    # capped by the lists
+    assert L.sad_backward_max_records(65, 48, 4, 10 ** 6) == 5 * 3 * 256 * 4  # ragged edge tiles count whole
+    assert L.sad_backward_max_records(64, 64, 8, 0) == 0
+    assert L.sad_backward_max_records(64, 64, 5, 256) == -1
+    assert L.sad_backward_max_records(0, 64, 8, 256) == -1
 
 
 def test_bad_arguments_rejected_on_host(L):

@@ -76,11 +76,17 @@ def test_autograd_vs_finite_differences_config3(capi, oracle):
         assert ratio <= 1.0 and nrel <= 1e-4, j
 
 
-def test_autograd_overflowing_map_gives_complete_gradients(capi):
+@pytest.mark.parametrize("worst_case_bytes", [8 << 30, 0])
+def test_autograd_overflowing_map_gives_complete_gradients(capi, monkeypatch, worst_case_bytes):
     """A spatially incoherent map needs far more per-tile records than the
-    default workspace holds; the backward must notice, grow the workspace and
-    return the same gradients as a call whose workspace fits everything."""
+    default workspace holds.  With the worst-case workspace allowed, autograd
+    allocates that one (no status read); with it forbidden, the backward must
+    notice the overflow, grow the workspace and run again.  Either way the
+    gradients equal those of a call whose workspace fits everything."""
     torch = pytest.importorskip("torch")
+    from paper_2604_21984_gb300 import autograd
+    monkeypatch.setattr(autograd, "WORST_CASE_BYTES", worst_case_bytes)
+    monkeypatch.setattr(autograd, "_WS", autograd._Workspaces())
     H = W = 128
     K, n = 16, 20000
     p = gen.sites_random_spd(H, W, n, seed=31)
@@ -105,3 +111,6 @@ def test_autograd_overflowing_map_gives_complete_gradients(capi):
     assert capi.sad_workspace_status(big)[0] == 0
     _, grads = _autograd_grads(capi, p, ids, H, W, g)
     assert np.array_equal(grads, ref.cpu().numpy().astype(np.float64))
+    (_, n, exact), = autograd._WS._ws.values()
+    assert exact == (worst_case_bytes > 0)
+    assert n == (capi.sad_backward_max_records(H, W, K, p.shape[1]) if exact else used)
