@@ -10,8 +10,9 @@
 // empty entry is key 0, below every real candidate.
 //
 // Per pixel (one thread):
-//  A. score the pixel's own list (independent gathers) and sort it with a
-//     bitonic network; drop duplicate ids (only possible in a damaged input);
+//  A. score the pixel's own list (independent gathers) and sort it
+//     (odd-even transposition passes until one swaps nothing); drop
+//     duplicate ids (only possible in a damaged input);
 //  B. filter each neighbour list and the J injected ids against the list
 //     and queue the novel ids in shared memory (per-thread column);
 //  C. the thread scores its queue and inserts the winners, after each
@@ -42,24 +43,35 @@ __device__ __forceinline__ float key_logit(uint64_t k) {
   return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
 }
 
+// Sorts keys descending by odd-even transposition: each pass compares the
+// even pairs (0,1), (2,3), ... then the odd pairs (1,2), (3,4), ..., and the
+// passes stop once one swaps nothing (then every adjacent pair is in order).
+// A pixel's own list arrives sorted by its previous logits, so one pass
+// (K - 1 compare-exchanges) confirms an unchanged order and a few fix a
+// slightly changed one; K passes sort any input.  Keys are distinct (they
+// hold the id), so the order is the same whatever the sorting network.
 template <int K>
-__device__ __forceinline__ void bitonic_sort_desc(uint64_t (&v)[K]) {
+__device__ __forceinline__ void sort_desc(uint64_t (&v)[K]) {
+#pragma unroll 1
+  for (int pass = 0; pass < K; ++pass) {
+    bool sw = false;
 #pragma unroll
-  for (int k = 2; k <= K; k <<= 1) {
-#pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-#pragma unroll
-      for (int i = 0; i < K; ++i) {
-        const int l = i ^ j;
-        if (l > i) {
-          const bool desc = (i & k) == 0;
-          const uint64_t a = v[i], b = v[l];
-          const bool sw = desc ? (a < b) : (a > b);
-          v[i] = sw ? b : a;
-          v[l] = sw ? a : b;
-        }
-      }
+    for (int i = 0; i + 1 < K; i += 2) {
+      const uint64_t a = v[i], b = v[i + 1];
+      const bool s = a < b;
+      v[i] = s ? b : a;
+      v[i + 1] = s ? a : b;
+      sw |= s;
     }
+#pragma unroll
+    for (int i = 1; i + 1 < K; i += 2) {
+      const uint64_t a = v[i], b = v[i + 1];
+      const bool s = a < b;
+      v[i] = s ? b : a;
+      v[i + 1] = s ? a : b;
+      sw |= s;
+    }
+    if (!sw) break;
   }
 }
 
@@ -167,7 +179,7 @@ __device__ __forceinline__ void pixel_update(uint64_t (&v)[K], bool inimg, int c
     v[4 * j + 2] = cand_key(w.z, sr, px, py, sites);
     v[4 * j + 3] = cand_key(w.w, sr, px, py, sites);
   }
-  bitonic_sort_desc<K>(v);
+  sort_desc<K>(v);
   bool dup = false;
 #pragma unroll
   for (int k = 1; k < K; ++k) dup |= v[k] != 0ull && v[k] == v[k - 1];
@@ -175,7 +187,7 @@ __device__ __forceinline__ void pixel_update(uint64_t (&v)[K], bool inimg, int c
 #pragma unroll
     for (int k = K - 1; k > 0; --k)
       if (v[k] != 0ull && v[k] == v[k - 1]) v[k] = 0ull;
-    bitonic_sort_desc<K>(v);
+    sort_desc<K>(v);
   }
 
   // B + C. Novel ids (valid, not in the list) go to the thread's queue
