@@ -45,7 +45,7 @@ __global__ void k_seed(const float4* __restrict__ geo, const float4* __restrict_
 constexpr int kUpdThreads = 256;
 
 template <int K, class Sites>
-__global__ void __launch_bounds__(kUpdThreads, 3) k_topk_update(Sites sites, int cap, int H, int W,
+__global__ void __launch_bounds__(kUpdThreads, 4) k_topk_update(Sites sites, int cap, int H, int W,
                                                              const uint4* __restrict__ map_in,
                                                              uint4* __restrict__ map_out,
                                                              uint32_t code, int J, uint64_t seed,

@@ -154,7 +154,11 @@ __device__ __forceinline__ uint64_t cand_key(uint32_t id, SiteRange sr, float px
 // at plane index pix_off.  q_local = row*W + col (injection counter).  Threads
 // outside the image pass inimg = false and get an empty list; the queue
 // column `tid` of s_q must be private to the thread.
-template <int K, int NT, int NG = 4, class Sites>
+// STORE_ALL: every offer writes its id at the queue's end and only a novel
+// id advances the count (no branch per offer; the unused slot is
+// overwritten by the next offer).  Faster inside the fused step's tile
+// kernel, slower in the stand-alone pass (measured), the same result.
+template <int K, int NT, int NG = 4, bool STORE_ALL = false, class Sites>
 __device__ __forceinline__ void pixel_update(uint64_t (&v)[K], bool inimg, int col, int row, int H,
                                              int W, SiteRange sr, const Sites& sites,
                                              const uint4* __restrict__ map_in, size_t P,
@@ -242,8 +246,16 @@ __device__ __forceinline__ void pixel_update(uint64_t (&v)[K], bool inimg, int c
     qn = 0;
   };
   auto offer = [&](uint32_t id) {
-    if (!sr.has(id) || list_has<K>(v, id)) return;
-    s_q[qn++][tid] = id;
+    if (STORE_ALL) {
+      // qn <= kQueue - 1 here: a stage starts with room for all its offers
+      const bool in_range = sr.has(id);
+      const bool listed = list_has<K>(v, id);
+      s_q[qn][tid] = id;
+      qn += (in_range && !listed) ? 1 : 0;
+    } else {
+      if (!sr.has(id) || list_has<K>(v, id)) return;
+      s_q[qn++][tid] = id;
+    }
   };
   // One drain call site (the drain body is large; more copies cost
   // instruction-cache misses): stages 0..3 offer the four neighbours'
