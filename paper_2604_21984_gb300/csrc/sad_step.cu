@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kTileThreads, UPDATE_ONLY ? 3 : 4)
   // the propagation's candidate queue and the tile body's tables are never
   // live together: one shared region
   __shared__ union Smem {
-    uint32_t q[kQueue][kTileThreads];
+    uint32_t q[kQueueStep][kTileThreads];
     TileShared<K, kModeGrad> t;
   } sm;
   auto& s_q = sm.q;
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kTileThreads, UPDATE_ONLY ? 3 : 4)
   const bool inimg = x < c.W && y < c.H;
   const uint32_t code = (1u << 16) | (static_cast<uint32_t>(st[1]) & 0xffffu);
   uint64_t v[K];
-  pixel_update<K, kTileThreads, 2, !UPDATE_ONLY>(v, inimg, x, y, c.H, c.W, c.sr, F32Sites{io.geo, io.met}, map_in, Ptot,
+  pixel_update<K, kTileThreads, 2, !UPDATE_ONLY, kQueueStep>(v, inimg, x, y, c.H, c.W, c.sr, F32Sites{io.geo, io.met}, map_in, Ptot,
                                 im.pix_off, code, J, im.seed, s_q, t);
   uint32_t ids[K];
   float lk[K];

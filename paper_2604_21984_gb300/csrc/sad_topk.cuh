@@ -27,7 +27,11 @@
 
 namespace sad {
 
-constexpr int kQueue = 24;  // per-thread queue of novel candidate ids
+// per-thread queues of novel candidate ids: the stand-alone pass's, and the
+// fused step's (longer: with room for two neighbours' offers the step
+// drains once, at the end, in most pixels)
+constexpr int kQueue = 24;
+constexpr int kQueueStep = 32;
 
 __device__ __forceinline__ uint64_t make_key(float l, uint32_t id) {
   uint32_t u = __float_as_uint(__fadd_rn(l, 0.0f));
@@ -153,12 +157,12 @@ __device__ __forceinline__ uint64_t cand_key(uint32_t id, SiteRange sr, float px
 // map_in: K/4 planes of uint4 with plane stride P; the image's pixels start
 // at plane index pix_off.  q_local = row*W + col (injection counter).  Threads
 // outside the image pass inimg = false and get an empty list; the queue
-// column `tid` of s_q must be private to the thread.
+// column `tid` of s_q (QL rows) must be private to the thread.
 // STORE_ALL: every offer writes its id at the queue's end and only a novel
 // id advances the count (no branch per offer; the unused slot is
 // overwritten by the next offer).  Faster inside the fused step's tile
 // kernel, slower in the stand-alone pass (measured), the same result.
-template <int K, int NT, int NG = 4, bool STORE_ALL = false, class Sites>
+template <int K, int NT, int NG = 4, bool STORE_ALL = false, int QL = kQueue, class Sites>
 __device__ __forceinline__ void pixel_update(uint64_t (&v)[K], bool inimg, int col, int row, int H,
                                              int W, SiteRange sr, const Sites& sites,
                                              const uint4* __restrict__ map_in, size_t P,
@@ -247,7 +251,7 @@ __device__ __forceinline__ void pixel_update(uint64_t (&v)[K], bool inimg, int c
   };
   auto offer = [&](uint32_t id) {
     if (STORE_ALL) {
-      // qn <= kQueue - 1 here: a stage starts with room for all its offers
+      // qn <= QL - 1 here: a stage starts with room for all its offers
       const bool in_range = sr.has(id);
       const bool listed = list_has<K>(v, id);
       s_q[qn][tid] = id;
@@ -262,7 +266,7 @@ __device__ __forceinline__ void pixel_update(uint64_t (&v)[K], bool inimg, int c
   // lists, stage 4 the injected ids.  After a stage the queue is drained
   // unless it has room for the next one: K ids before a neighbour, J
   // (at most 16, checked by every entry point) before the injections.
-  static_assert(kQueue >= K && kQueue >= 16, "queue must hold a neighbour list or the injections");
+  static_assert(QL >= K && QL >= 16, "queue must hold a neighbour list or the injections");
   const int s = static_cast<int>(code >> 16);
   const uint64_t base = (static_cast<uint64_t>(code) << 32);
 #pragma unroll 1
@@ -291,7 +295,7 @@ __device__ __forceinline__ void pixel_update(uint64_t (&v)[K], bool inimg, int c
         offer(sr.lo + static_cast<uint32_t>(((h >> 32) * static_cast<uint64_t>(sr.n)) >> 32));
       }
     }
-    if (d == 4 || qn > kQueue - (d == 3 ? (J > K ? J : K) : K)) drain();
+    if (d == 4 || qn > QL - (d == 3 ? (J > K ? J : K) : K)) drain();
   }
 }
 
