@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_topk_update(Sites sites, int
   const size_t P = static_cast<size_t>(H) * W;
   const size_t q = static_cast<size_t>(row) * W + col;
   uint64_t v[K];
-  pixel_update<K, kUpdThreads>(v, true, col, row, H, W, SiteRange{0u, static_cast<uint32_t>(cap)},
+  pixel_update<K, kUpdThreads, 2>(v, true, col, row, H, W, SiteRange{0u, static_cast<uint32_t>(cap)},
                                sites, map_in, P, 0, code, J, seed, s_q, tid, cell);
 #pragma unroll
   for (int j = 0; j < K / 4; ++j)
