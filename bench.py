@@ -178,10 +178,10 @@ def gen_images(specs):
 # traffic is per pixel or per site (profiles/k_bwd_tile_saved_1536x1536_k16.md).
 NCU_COUNTERS = {
     "k_bwd_tile": {"sources": ['sad_backward.cu', 'sad_tile.cuh', 'sad_reduce.cuh', 'sad_topk.cuh', 'sad_device.cuh'],
-                   "sha": "ce1c5026949cbff0", "dram_bytes": 459583488, "warp_inst": 354813316,
+                   "sha": "3308b5fe9bc0b788", "dram_bytes": 459431481, "warp_inst": 354853513,
                    "captured": "1536x1536, scaled by (2048/1536)^2"},
     "k_step_tile": {"sources": ['sad_step.cu', 'sad_tile.cuh', 'sad_topk.cuh', 'sad_device.cuh', 'sad_adam.cuh', 'sad_blend.cuh', 'sad_reduce.cuh'],
-                    "sha": "cc63fb34af74d84c", "dram_bytes": 34487808, "warp_inst": 128697751,
+                    "sha": "0480d8670eec6fa6", "dram_bytes": 34931200, "warp_inst": 114684082,
                     "captured": "768x512 (the workload itself)"},
 }
 ISSUE_PEAK = 152 * 4 * 2.07e9   # warp instructions / s: 152 SMs x 4 schedulers x 1 issue/clk x 2070 MHz
