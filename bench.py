@@ -178,25 +178,35 @@ def gen_images(specs):
 # traffic is per pixel or per site (profiles/k_bwd_tile_saved_1536x1536_k16.md).
 NCU_COUNTERS = {
     "k_bwd_tile": {"sources": ['sad_backward.cu', 'sad_tile.cuh', 'sad_reduce.cuh', 'sad_topk.cuh', 'sad_device.cuh'],
-                   "sha": "3308b5fe9bc0b788", "dram_bytes": 459431481, "warp_inst": 354853513,
+                   "sha": "1f11e1444225d702", "dram_bytes": 459431481, "warp_inst": 354853513,
                    "captured": "1536x1536, scaled by (2048/1536)^2"},
     "k_step_tile": {"sources": ['sad_step.cu', 'sad_tile.cuh', 'sad_topk.cuh', 'sad_device.cuh', 'sad_adam.cuh', 'sad_blend.cuh', 'sad_reduce.cuh'],
-                    "sha": "0480d8670eec6fa6", "dram_bytes": 34931200, "warp_inst": 114684082,
+                    "sha": "ef2ec2baa1c5f3fc", "dram_bytes": 34931200, "warp_inst": 114684082,
                     "captured": "768x512 (the workload itself)"},
 }
 ISSUE_PEAK = 152 * 4 * 2.07e9   # warp instructions / s: 152 SMs x 4 schedulers x 1 issue/clk x 2070 MHz
 
 
-def ncu_counters(kernel):
+def source_code_hash(files):
+    """Hash of the kernels' source code without its comments and blank
+    space, so that stored counters follow the code, not the comments."""
     import hashlib
+    import re
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2604_21984_gb300", "csrc", f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
+    return h.hexdigest()[:16]
+
+
+def ncu_counters(kernel):
     c = NCU_COUNTERS.get(kernel)
     if c is None:
         return None
-    h = hashlib.sha256()
-    for f in c["sources"]:
-        with open(os.path.join(ROOT, "paper_2604_21984_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return c if h.hexdigest()[:16] == c["sha"] else None
+    return c if source_code_hash(c["sources"]) == c["sha"] else None
 
 
 def reduce_max(x, dist, world, device):

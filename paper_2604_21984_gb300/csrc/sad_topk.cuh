@@ -52,8 +52,9 @@ __device__ __forceinline__ float key_logit(uint64_t k) {
 // passes stop once one swaps nothing (then every adjacent pair is in order).
 // A pixel's own list arrives sorted by its previous logits, so one pass
 // (K - 1 compare-exchanges) confirms an unchanged order and a few fix a
-// slightly changed one; K passes sort any input.  Keys are distinct (they
-// hold the id), so the order is the same whatever the sorting network.
+// slightly changed one; K passes sort any input.  Keys that compare equal
+// are equal values (the empty key, or a repeated id in a damaged list), so
+// the result is the same whatever the sorting network.
 template <int K>
 __device__ __forceinline__ void sort_desc(uint64_t (&v)[K]) {
 #pragma unroll 1
