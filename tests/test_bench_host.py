@@ -71,21 +71,28 @@ def test_reference_arm_line(tmp_path):
     assert d["config"]["H"] == d["config"]["W"] == 2048 and d["config"]["K"] == 16
 
 
-def test_ncu_counters_only_for_the_sources_they_were_taken_on(monkeypatch):
+def test_ncu_counters_only_for_the_sources_they_were_taken_on(monkeypatch, tmp_path):
     """The roofline's `traffic` comes from a stored ncu capture; it is
-    reported only while the kernel's sources hash to the capture's value,
-    and dropped (null) as soon as any of them changes."""
-    import hashlib
+    reported only while the kernel's code (comments and blank space aside)
+    hashes to the capture's value, and dropped (null) as soon as the code
+    changes."""
     sys.path.insert(0, ROOT)
     import bench
     entry = bench.NCU_COUNTERS["k_step_tile"]
-    h = hashlib.sha256()
-    for f in entry["sources"]:
-        with open(os.path.join(ROOT, "paper_2604_21984_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    current = dict(entry, sha=h.hexdigest()[:16])
+    current = dict(entry, sha=bench.source_code_hash(entry["sources"]))
     monkeypatch.setitem(bench.NCU_COUNTERS, "k_step_tile", current)
     assert bench.ncu_counters("k_step_tile") == current
     monkeypatch.setitem(bench.NCU_COUNTERS, "k_step_tile", dict(entry, sha="0" * 16))
     assert bench.ncu_counters("k_step_tile") is None
     assert bench.ncu_counters("no_such_kernel") is None
+    # a comment or blank-space edit keeps the hash, a code edit changes it
+    d = tmp_path / "paper_2604_21984_gb300" / "csrc"
+    d.mkdir(parents=True)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    f = d / "k.cu"
+    f.write_text("int f(int a) {\n  return a + 1;  // one more\n}\n")
+    h0 = bench.source_code_hash(["k.cu"])
+    f.write_text("/* the successor */\nint f(int a) {\n\n    return a + 1;  // the next integer\n}\n")
+    assert bench.source_code_hash(["k.cu"]) == h0
+    f.write_text("int f(int a) {\n  return a + 2;  // one more\n}\n")
+    assert bench.source_code_hash(["k.cu"]) != h0
