@@ -179,10 +179,10 @@ def gen_images(specs):
 NCU_COUNTERS = {
     "k_bwd_tile": {"sources": ['sad_backward.cu', 'sad_tile.cuh', 'sad_reduce.cuh', 'sad_topk.cuh', 'sad_device.cuh'],
                    "sha": "1f11e1444225d702", "dram_bytes": 459431481, "warp_inst": 354853513,
-                   "captured": "1536x1536, scaled by (2048/1536)^2"},
+                   "captured": "1536x1536, scaled by (2048/1536)^2", "size": [2048, 2048]},
     "k_step_tile": {"sources": ['sad_step.cu', 'sad_tile.cuh', 'sad_topk.cuh', 'sad_device.cuh', 'sad_adam.cuh', 'sad_blend.cuh', 'sad_reduce.cuh'],
                     "sha": "ef2ec2baa1c5f3fc", "dram_bytes": 34931200, "warp_inst": 114684082,
-                    "captured": "768x512 (the workload itself)"},
+                    "captured": "768x512 (the workload itself)", "size": [512, 768]},
 }
 ISSUE_PEAK = 152 * 4 * 2.07e9   # warp instructions / s: 152 SMs x 4 schedulers x 1 issue/clk x 2070 MHz
 
@@ -202,9 +202,12 @@ def source_code_hash(files):
     return h.hexdigest()[:16]
 
 
-def ncu_counters(kernel):
+def ncu_counters(kernel, H, W):
+    """The stored counters of `kernel` for an H x W launch: only for the
+    size they were taken (or scaled) to, and only while the code is the
+    captured build's."""
     c = NCU_COUNTERS.get(kernel)
-    if c is None:
+    if c is None or c["size"] != [H, W]:
         return None
     return c if source_code_hash(c["sources"]) == c["sha"] else None
 
@@ -391,7 +394,7 @@ def headline(capi, dev, args, rank, world, dist, peak, peak_kind, local):
     roofline = None
     if kname in alg:
         achieved = alg[kname] / (kms / 1e3) / 1e9
-        ctr = ncu_counters(kname)
+        ctr = ncu_counters(kname, H, W)
         roofline = {"kernel": kname, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                     "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                     "traffic": ctr["dram_bytes"] if ctr else None,
@@ -524,7 +527,7 @@ def encode_iteration(capi, dev, args, rank, peak, peak_kind):
     roofline = None
     if kname in alg:
         achieved = alg[kname] / (kms / 1e3) / 1e9
-        ctr = ncu_counters(kname)
+        ctr = ncu_counters(kname, H, W)
         roofline = {"kernel": kname, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                     "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                     "traffic": ctr["dram_bytes"] if ctr else None,
@@ -556,10 +559,12 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    global H_C3, W_C3, N_C3
+    global H_C3, W_C3, N_C3, WORKLOAD
     if args.c3_side != 2048:   # a profiler case: the same workload, scaled
         H_C3 = W_C3 = args.c3_side
         N_C3 = int(round(262144 * (args.c3_side / 2048.0) ** 2))
+        WORKLOAD = (WORKLOAD.replace("2048x2048", f"{H_C3}x{W_C3}").replace("262144 sites", f"{N_C3} sites")
+                    + " (scaled down from 2048x2048 for a profiler capture)")
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -73,18 +73,20 @@ def test_reference_arm_line(tmp_path):
 
 def test_ncu_counters_only_for_the_sources_they_were_taken_on(monkeypatch, tmp_path):
     """The roofline's `traffic` comes from a stored ncu capture; it is
-    reported only while the kernel's code (comments and blank space aside)
-    hashes to the capture's value, and dropped (null) as soon as the code
-    changes."""
+    reported only for the launch size it was taken (or scaled) to, and only
+    while the kernel's code (comments and blank space aside) hashes to the
+    capture's value: dropped (null) as soon as the code changes."""
     sys.path.insert(0, ROOT)
     import bench
     entry = bench.NCU_COUNTERS["k_step_tile"]
     current = dict(entry, sha=bench.source_code_hash(entry["sources"]))
     monkeypatch.setitem(bench.NCU_COUNTERS, "k_step_tile", current)
-    assert bench.ncu_counters("k_step_tile") == current
+    H, W = entry["size"]
+    assert bench.ncu_counters("k_step_tile", H, W) == current
+    assert bench.ncu_counters("k_step_tile", H // 2, W) is None   # another launch size
     monkeypatch.setitem(bench.NCU_COUNTERS, "k_step_tile", dict(entry, sha="0" * 16))
-    assert bench.ncu_counters("k_step_tile") is None
-    assert bench.ncu_counters("no_such_kernel") is None
+    assert bench.ncu_counters("k_step_tile", H, W) is None
+    assert bench.ncu_counters("no_such_kernel", H, W) is None
     # a comment or blank-space edit keeps the hash, a code edit changes it
     d = tmp_path / "paper_2604_21984_gb300" / "csrc"
     d.mkdir(parents=True)
