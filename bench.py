@@ -178,10 +178,10 @@ def gen_images(specs):
 # traffic is per pixel or per site (profiles/k_bwd_tile_saved_1536x1536_k16.md).
 NCU_COUNTERS = {
     "k_bwd_tile": {"sources": ['sad_backward.cu', 'sad_tile.cuh', 'sad_reduce.cuh', 'sad_topk.cuh', 'sad_device.cuh'],
-                   "sha": "1f11e1444225d702", "dram_bytes": 459431481, "warp_inst": 354853513,
+                   "sha": "f363d50ae2ad06d1", "dram_bytes": 459043726, "warp_inst": 354819156,
                    "captured": "1536x1536, scaled by (2048/1536)^2", "size": [2048, 2048]},
     "k_step_tile": {"sources": ['sad_step.cu', 'sad_tile.cuh', 'sad_topk.cuh', 'sad_device.cuh', 'sad_adam.cuh', 'sad_blend.cuh', 'sad_reduce.cuh'],
-                    "sha": "ef2ec2baa1c5f3fc", "dram_bytes": 34931200, "warp_inst": 114684082,
+                    "sha": "e77352c2bd1fd65d", "dram_bytes": 34656256, "warp_inst": 114674775,
                     "captured": "768x512 (the workload itself)", "size": [512, 768]},
 }
 ISSUE_PEAK = 152 * 4 * 2.07e9   # warp instructions / s: 152 SMs x 4 schedulers x 1 issue/clk x 2070 MHz

@@ -333,6 +333,9 @@ __device__ __forceinline__ uint32_t warp_site_sums(bool have, uint32_t j, uint32
   for (int o = 1; o < 32; o <<= 1) {
     const uint32_t ko = __shfl_up_sync(kFull, key, o);
     const bool take = lane >= o && ko == key;
+    // no run reaches o lanes back: no later offset adds anything either
+    // (equal keys are adjacent), so the scan is complete
+    if (!__any_sync(kFull, take)) break;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       const long long t = __shfl_up_sync(kFull, run[k], o);
